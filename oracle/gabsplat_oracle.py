@@ -1,0 +1,435 @@
+"""FP64 CPU oracle of the 3D Gabor splatting rasterizer -- TEST INFRASTRUCTURE ONLY.
+
+This module exists to check the CUDA path.  Only the tests, the package smoke check and the
+CPU-baseline leg of the benchmark may import it; the product path never does, and it shares
+no code with the CUDA kernels (the only common module is the seeded input generator).
+
+What it computes (paper: "3DGabSplat", arXiv 2508.05343), per camera:
+
+1. project():   the 3D Gabor primitive of Sec. 3.2 (Eq. 5: a Gaussian envelope times the
+   weighted filter bank (1 - sum w_i) + sum w_i cos(2 pi f_i . (x - mu))) is mapped to ray space
+   with the EWA local affine map JW (Sec. 3.1, Eq. 2; supplement A.1).  The envelope becomes the
+   top-left 2x2 of J W Sigma W^T J^T (Sec. 3.1), each frequency becomes f_proj = ((JW)^-1)^T f
+   (Eq. 7), and z-integration turns it into f2D = f_proj_xy - (S_02, S_12)/S_22 * f_proj_z with S the
+   inverse of the ray-space covariance (Eq. 8-9; supplement A.2).  Colour is the SH expansion at
+   the viewing direction.  Everything here is float64 and differentiable with torch.autograd.
+2. bin_spec():  the tile binning.  Which 16x16 tiles a primitive touches and the depth used for
+   ordering are integer/bit decisions, so they are defined by a written float32 procedure (the
+   binning specification, op order fixed, no fused multiply-add) which the GPU follows
+   independently.  Pairs are ordered by (tile, float32 depth bits, primitive index) - the
+   "sorted by depth" step of Sec. 3.1 and the tile-based rasterizer of Sec. 3.3.3.
+3. render():    per pixel, front-to-back alpha compositing (Eq. 10) of the 2D Gabor primitives
+   (Eq. 9 text: G2D(x) [(1 - sum w) + sum w cos(2 pi f2D . (x - mu2D))]) with the conventions
+   of the tile rasterizer the paper adopts: alpha = min(alpha_max, o * Gabor2D), pairs with
+   alpha < alpha_min are skipped, compositing stops before the pair whose transmittance
+   T (1 - alpha) would fall below T_min, and the background is added with the final T.
+4. render_backward(): the exact adjoint of 1-3 by reverse-mode autodiff in float64, with the
+   skip/stop decisions held fixed and zero gradient through the clamps.
+
+Readings of points the paper leaves open (frame of f, S in ray space, dropped z-integration
+constants, 3DGS conventions) are listed in the design notes; they are fixed here as:
+S is the inverse of the undilated ray-space covariance; J's third row is (0, 0, 1); the
+z-integration constants C1, C2 are dropped as in Eq. 9; the envelope is unnormalised (Eq. 1);
+frequencies are world-frame cycles per unit; pixel centres sit at (i + 0.5, j + 0.5).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+F64 = torch.float64
+TILE = 16
+
+
+def default_config(eps2d=0.3, bg=(0.0, 0.0, 0.0)):
+    """Rasterizer constants (float32 values, so both sides compare against identical thresholds)."""
+    f = lambda v: float(np.float32(v))
+    return dict(eps2d=f(eps2d), alpha_max=f(0.99), alpha_min=f(1.0 / 255.0), T_min=f(1e-4),
+                bg=tuple(f(b) for b in bg))
+
+
+# ----------------------------------------------------------------------------------------------
+# Primitive geometry (Sec. 3.1: Sigma = R S S^T R^T)
+# ----------------------------------------------------------------------------------------------
+def rotation_from_quaternion(q: torch.Tensor) -> torch.Tensor:
+    """Rotation matrix of the normalised quaternion (w, x, y, z); q: [n,4] -> [n,3,3]."""
+    q = q / torch.linalg.norm(q, dim=-1, keepdim=True)
+    w, x, y, z = q.unbind(-1)
+    rows = [
+        torch.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+        torch.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+        torch.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1),
+    ]
+    return torch.stack(rows, -2)
+
+
+def covariance_3d(scales: torch.Tensor, quats: torch.Tensor) -> torch.Tensor:
+    """Sigma = R S S^T R^T with S = diag(scales) (Sec. 3.1)."""
+    R = rotation_from_quaternion(quats)
+    M = R * scales[:, None, :]
+    return M @ M.transpose(-1, -2)
+
+
+# ----------------------------------------------------------------------------------------------
+# Real spherical harmonics up to degree 3 (view-dependent colour c_k of Sec. 3.1)
+# Index l*l + l + m, m = -l..l; the standard orthonormal real basis on the unit sphere.
+# ----------------------------------------------------------------------------------------------
+def sh_basis(d: torch.Tensor, degree: int) -> torch.Tensor:
+    """d: [n,3] unit directions -> [n,(degree+1)^2] real SH values."""
+    x, y, z = d.unbind(-1)
+    pi = math.pi
+    out = [torch.full_like(x, 0.5 * math.sqrt(1.0 / pi))]
+    if degree >= 1:
+        c1 = math.sqrt(3.0 / (4.0 * pi))
+        out += [c1 * y, c1 * z, c1 * x]
+    if degree >= 2:
+        out += [0.5 * math.sqrt(15.0 / pi) * x * y,
+                0.5 * math.sqrt(15.0 / pi) * y * z,
+                0.25 * math.sqrt(5.0 / pi) * (3.0 * z * z - 1.0),
+                0.5 * math.sqrt(15.0 / pi) * x * z,
+                0.25 * math.sqrt(15.0 / pi) * (x * x - y * y)]
+    if degree >= 3:
+        out += [0.25 * math.sqrt(35.0 / (2.0 * pi)) * y * (3.0 * x * x - y * y),
+                0.5 * math.sqrt(105.0 / pi) * x * y * z,
+                0.25 * math.sqrt(21.0 / (2.0 * pi)) * y * (5.0 * z * z - 1.0),
+                0.25 * math.sqrt(7.0 / pi) * z * (5.0 * z * z - 3.0),
+                0.25 * math.sqrt(21.0 / (2.0 * pi)) * x * (5.0 * z * z - 1.0),
+                0.25 * math.sqrt(105.0 / pi) * z * (x * x - y * y),
+                0.25 * math.sqrt(35.0 / (2.0 * pi)) * x * (x * x - 3.0 * y * y)]
+    return torch.stack(out, -1)
+
+
+# ----------------------------------------------------------------------------------------------
+# Projection and splatting (Sec. 3.1, Sec. 3.3.1-3.3.2, supplement A)
+# ----------------------------------------------------------------------------------------------
+def camera_tensors(cam):
+    W = torch.tensor(np.asarray(cam["R"], np.float64).reshape(3, 3), dtype=F64)
+    tc = torch.tensor(np.asarray(cam["t"], np.float64).reshape(3), dtype=F64)
+    return W, tc
+
+
+def jacobian(t: torch.Tensor, cam, third_row: str = "z") -> torch.Tensor:
+    """Local affine Jacobian J of the perspective map at camera-space mean t ([n,3] -> [n,3,3]).
+
+    Rows 0 and 1 are the derivative of (fx x/z, fy y/z) with the 3DGS field-of-view guard (x/z and
+    y/z clamped to 1.3 tan(fov/2)).  The paper needs a square J for (JW)^-1 (Eq. 7) but never gives
+    the third row; "z" uses (0, 0, 1), "ewa" the EWA row t/|t|.  The splatted frequency does not
+    depend on this choice (it only reparametrises the integrated coordinate).
+    """
+    fx, fy = cam["fx"], cam["fy"]
+    limx = 1.3 * (0.5 * cam["width"] / fx)
+    limy = 1.3 * (0.5 * cam["height"] / fy)
+    tx, ty, tz = t.unbind(-1)
+    ux = torch.clamp(tx / tz, -limx, limx)
+    uy = torch.clamp(ty / tz, -limy, limy)
+    zero = torch.zeros_like(tz)
+    r0 = torch.stack([fx / tz, zero, -fx * ux / tz], -1)
+    r1 = torch.stack([zero, fy / tz, -fy * uy / tz], -1)
+    if third_row == "z":
+        r2 = torch.stack([zero, zero, torch.ones_like(tz)], -1)
+    else:
+        r2 = t / torch.linalg.norm(t, dim=-1, keepdim=True)
+    return torch.stack([r0, r1, r2], -2)
+
+
+def splat_frequency(f_proj: torch.Tensor, sigma_ray: torch.Tensor) -> torch.Tensor:
+    """Eq. 8: f2D = f_proj_xy - (S_02, S_12) / S_22 * f_proj_z with S = inverse(ray-space covariance).
+
+    f_proj: [n,K,3]; sigma_ray: [n,3,3] -> [n,K,2].
+    """
+    S = torch.linalg.inv(sigma_ray)
+    ratio = S[:, 0:2, 2] / S[:, 2:3, 2]                       # [n,2]
+    return f_proj[..., 0:2] - ratio[:, None, :] * f_proj[..., 2:3]
+
+
+def project(prims: dict, cam, cfg, third_row: str = "z") -> dict:
+    """Per-primitive 2D Gabor parameters in float64 (differentiable in every attribute)."""
+    W, tc = camera_tensors(cam)
+    means, scales, quats = prims["means"], prims["scales"], prims["quats"]
+    t = means @ W.T + tc                                        # camera-space mean
+    J = jacobian(t, cam, third_row)
+    M = J @ W                                                   # the local affine map JW
+    sigma = covariance_3d(scales, quats)
+    sigma_ray = M @ sigma @ M.transpose(-1, -2)                 # Sigma' = J W Sigma W^T J^T (Eq. 2)
+    eye2 = torch.eye(2, dtype=F64)
+    cov2d = sigma_ray[:, 0:2, 0:2] + cfg["eps2d"] * eye2        # top-left 2x2 (+ dilation)
+    conic_m = torch.linalg.inv(cov2d)
+    conic = torch.stack([conic_m[:, 0, 0], conic_m[:, 0, 1], conic_m[:, 1, 1]], -1)
+    mu2d = torch.stack([cam["fx"] * t[:, 0] / t[:, 2] + cam["cx"], cam["fy"] * t[:, 1] / t[:, 2] + cam["cy"]], -1)
+    K = prims["weights"].shape[1]
+    if K > 0:
+        f_proj = torch.einsum("nji,nkj->nki", torch.linalg.inv(M), prims["freqs"])   # ((JW)^-1)^T f  (Eq. 7)
+        f2d = splat_frequency(f_proj, sigma_ray)
+    else:
+        f2d = torch.zeros(means.shape[0], 0, 2, dtype=F64)
+    campos = -(W.T @ tc)
+    v = means - campos
+    dirs = v / torch.linalg.norm(v, dim=-1, keepdim=True)
+    deg = int(round(math.sqrt(prims["sh"].shape[1]))) - 1
+    basis = sh_basis(dirs, deg)                                 # [n, (d+1)^2]
+    rgb = torch.clamp_min(torch.einsum("nc,ncj->nj", basis, prims["sh"]) + 0.5, 0.0)
+    return dict(mu2d=mu2d, conic=conic, opacity=prims["opacity"], rgb=rgb, f2d=f2d,
+                weights=prims["weights"], depth=t[:, 2], cov2d=cov2d)
+
+
+# ----------------------------------------------------------------------------------------------
+# Binning specification (float32, fixed op order; integer results must match the GPU bit for bit)
+# ----------------------------------------------------------------------------------------------
+def bin_spec(prims_np: dict, cam, cfg) -> dict:
+    """Tile binning per the written float32 specification.
+
+    Every float32 operation below is a single IEEE round-to-nearest operation in the stated order
+    (numpy never fuses multiply-add).  Determinant, eigenvalue and radius are float64 functions of
+    the float32 covariance entries.  Returns per-primitive depth/mean/covariance/radius/rect,
+    the emitted (key, value) pairs in emission order, the stably sorted pairs and tile ranges.
+    """
+    f32 = np.float32
+    mu = np.asarray(prims_np["means"], f32)
+    sc = np.asarray(prims_np["scales"], f32)
+    q = np.asarray(prims_np["quats"], f32)
+    n = mu.shape[0]
+    Wm = np.asarray(cam["R"], f32).reshape(3, 3)
+    tc = np.asarray(cam["t"], f32).reshape(3)
+    fx, fy, cx, cy = f32(cam["fx"]), f32(cam["fy"]), f32(cam["cx"]), f32(cam["cy"])
+    width, height = int(cam["width"]), int(cam["height"])
+    znear, zfar, eps = f32(cam["znear"]), f32(cam["zfar"]), f32(cfg["eps2d"])
+    tiles_x, tiles_y = (width + TILE - 1) // TILE, (height + TILE - 1) // TILE
+
+    # camera-space mean: t_i = ((W_i0 m0 + W_i1 m1) + W_i2 m2) + tc_i
+    t = [((Wm[i, 0] * mu[:, 0] + Wm[i, 1] * mu[:, 1]) + Wm[i, 2] * mu[:, 2]) + tc[i] for i in range(3)]
+    tx, ty, tz = t
+    mux = (fx * tx) / tz + cx
+    muy = (fy * ty) / tz + cy
+    # normalised quaternion and rotation
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    nrm = np.sqrt(((w * w + x * x) + y * y) + z * z)
+    w, x, y, z = w / nrm, x / nrm, y / nrm, z / nrm
+    one, two = f32(1.0), f32(2.0)
+    R = [[one - two * (y * y + z * z), two * (x * y - w * z), two * (x * z + w * y)],
+         [two * (x * y + w * z), one - two * (x * x + z * z), two * (y * z - w * x)],
+         [two * (x * z - w * y), two * (y * z + w * x), one - two * (x * x + y * y)]]
+    M = [[R[i][j] * sc[:, j] for j in range(3)] for i in range(3)]
+    Sig = [[None] * 3 for _ in range(3)]
+    for i in range(3):
+        for j in range(i, 3):
+            Sig[i][j] = (M[i][0] * M[j][0] + M[i][1] * M[j][1]) + M[i][2] * M[j][2]
+            Sig[j][i] = Sig[i][j]
+    # J rows 0-1 (field-of-view guarded) and T = J[0:2] W
+    limx = f32(1.3) * ((f32(0.5) * f32(width)) / fx)
+    limy = f32(1.3) * ((f32(0.5) * f32(height)) / fy)
+    ux = np.minimum(np.maximum(tx / tz, -limx), limx)
+    uy = np.minimum(np.maximum(ty / tz, -limy), limy)
+    J00, J02 = fx / tz, -((fx * ux) / tz)
+    J11, J12 = fy / tz, -((fy * uy) / tz)
+    T = [[J00 * Wm[0, j] + J02 * Wm[2, j] for j in range(3)],
+         [J11 * Wm[1, j] + J12 * Wm[2, j] for j in range(3)]]
+    U = [[(T[a][0] * Sig[0][j] + T[a][1] * Sig[1][j]) + T[a][2] * Sig[2][j] for j in range(3)] for a in range(2)]
+    A00 = (U[0][0] * T[0][0] + U[0][1] * T[0][1]) + U[0][2] * T[0][2]
+    A01 = (U[0][0] * T[1][0] + U[0][1] * T[1][1]) + U[0][2] * T[1][2]
+    A11 = (U[1][0] * T[1][0] + U[1][1] * T[1][1]) + U[1][2] * T[1][2]
+    ca, cb, cc = A00 + eps, A01, A11 + eps
+    # float64 determinant / largest eigenvalue / 3-sigma radius
+    da, db, dc = ca.astype(np.float64), cb.astype(np.float64), cc.astype(np.float64)
+    det = da * dc - db * db
+    mid = 0.5 * (da + dc)
+    lam = mid + np.sqrt(np.maximum(0.0, mid * mid - det))
+    with np.errstate(invalid="ignore"):
+        rad = np.ceil(3.0 * np.sqrt(np.maximum(lam, 0.0)))
+    finite = np.isfinite(mux) & np.isfinite(muy) & np.isfinite(det) & np.isfinite(rad)
+    valid = (tz > znear) & (tz <= zfar) & (det > 0.0) & finite
+    mx, my = mux.astype(np.float64), muy.astype(np.float64)
+    with np.errstate(invalid="ignore"):
+        x0 = np.floor((mx - rad) / TILE); x1 = np.floor((mx + rad) / TILE)
+        y0 = np.floor((my - rad) / TILE); y1 = np.floor((my + rad) / TILE)
+    valid &= (x1 >= 0) & (x0 <= tiles_x - 1) & (y1 >= 0) & (y0 <= tiles_y - 1)
+    x0 = np.where(valid, np.clip(x0, 0, tiles_x - 1), 0).astype(np.int64)
+    x1 = np.where(valid, np.clip(x1, 0, tiles_x - 1), -1).astype(np.int64)
+    y0 = np.where(valid, np.clip(y0, 0, tiles_y - 1), 0).astype(np.int64)
+    y1 = np.where(valid, np.clip(y1, 0, tiles_y - 1), -1).astype(np.int64)
+    touched = np.where(valid, (x1 - x0 + 1) * (y1 - y0 + 1), 0).astype(np.int64)
+    offsets = np.concatenate([[0], np.cumsum(touched)[:-1]]) if n else np.zeros(0, np.int64)
+    P = int(touched.sum())
+    depth_bits = tz.astype(f32).view(np.uint32).astype(np.uint64)
+    keys = np.empty(P, np.uint64)
+    vals = np.empty(P, np.uint32)
+    idx = np.nonzero(touched)[0]
+    pos = 0
+    for k in idx:                      # emission order: primitive ascending, tiles row-major
+        ty_r = np.arange(y0[k], y1[k] + 1)
+        tx_r = np.arange(x0[k], x1[k] + 1)
+        tid = (ty_r[:, None] * tiles_x + tx_r[None, :]).reshape(-1).astype(np.uint64)
+        m = tid.size
+        keys[pos:pos + m] = (tid << np.uint64(32)) | depth_bits[k]
+        vals[pos:pos + m] = k
+        pos += m
+    order = np.argsort(keys, kind="stable")
+    skeys, svals = keys[order], vals[order]
+    ntiles = tiles_x * tiles_y
+    tile_of = (skeys >> np.uint64(32)).astype(np.int64)
+    starts = np.searchsorted(tile_of, np.arange(ntiles), side="left")
+    ends = np.searchsorted(tile_of, np.arange(ntiles), side="right")
+    ranges = np.stack([starts, ends], -1).astype(np.uint32)
+    return dict(depth=tz, mu2d=np.stack([mux, muy], -1), cov2d=np.stack([ca, cb, cc], -1), radius=rad,
+                valid=valid, rect=np.stack([x0, x1, y0, y1], -1), touched=touched, offsets=offsets, P=P,
+                keys=keys, vals=vals, sorted_keys=skeys, sorted_vals=svals, ranges=ranges,
+                tiles_x=tiles_x, tiles_y=tiles_y)
+
+
+# ----------------------------------------------------------------------------------------------
+# Compositing (Eq. 10 with the 2D Gabor primitive of Eq. 9)
+# ----------------------------------------------------------------------------------------------
+AMBIG_ALPHA = 1e-5     # |alpha - threshold| below this: float32 and float64 may branch differently
+AMBIG_T = 1e-8         # |T (1 - alpha) - T_min| below this: likewise
+
+
+def gabor_alpha(px, py, rec, cfg):
+    """alpha_raw = o * G2D(x) * [(1 - sum w) + sum w cos(2 pi f2D . (x - mu2D))] for pixels x pairs."""
+    dx = px[:, None] - rec["mu2d"][None, :, 0]
+    dy = py[:, None] - rec["mu2d"][None, :, 1]
+    a, b, c = rec["conic"][:, 0], rec["conic"][:, 1], rec["conic"][:, 2]
+    G = torch.exp(-0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy)
+    w = rec["weights"]
+    if w.shape[1] > 0:
+        phase = 2.0 * math.pi * (dx[..., None] * rec["f2d"][None, :, :, 0] + dy[..., None] * rec["f2d"][None, :, :, 1])
+        bank = (1.0 - w.sum(-1))[None, :] + (w[None] * torch.cos(phase)).sum(-1)
+    else:
+        bank = torch.ones_like(G)
+    return rec["opacity"][None, :] * G * bank
+
+
+def composite(px, py, rec, cfg):
+    """Front-to-back compositing of L depth-ordered pairs at P pixels (Eq. 10).
+
+    Returns colour [P,3], final transmittance [P], the 1-based list position of the last
+    composited pair [P] (0 if none) and ambiguity flags for forward / backward comparisons.
+    """
+    L = rec["mu2d"].shape[0]
+    alpha_raw = gabor_alpha(px, py, rec, cfg)
+    alpha = torch.clamp_max(alpha_raw, cfg["alpha_max"])
+    with torch.no_grad():
+        keep = alpha >= cfg["alpha_min"]
+    a_eff = torch.where(keep, alpha, torch.zeros_like(alpha))
+    T_after = torch.cumprod(1.0 - a_eff, dim=1)
+    idx = torch.arange(L)
+    with torch.no_grad():
+        stop = keep & (T_after < cfg["T_min"])
+        s = torch.where(stop.any(1), stop.int().argmax(1), torch.full((px.shape[0],), L, dtype=torch.long))
+        include = keep & (idx[None, :] < s[:, None])
+        evaluated = idx[None, :] <= s[:, None]
+        last = torch.where(include, idx[None, :] + 1, torch.zeros_like(idx)[None, :]).amax(1)
+        near_min = (alpha - cfg["alpha_min"]).abs() < AMBIG_ALPHA
+        near_T = keep & ((T_after - cfg["T_min"]).abs() < AMBIG_T)
+        near_max = (alpha_raw - cfg["alpha_max"]).abs() < AMBIG_ALPHA
+        amb_f = ((near_min | near_T) & evaluated).any(1)
+        amb_b = amb_f | (near_max & evaluated).any(1)
+    ones = torch.ones(px.shape[0], 1, dtype=F64)
+    T_before = torch.cat([ones, T_after[:, :-1]], 1)
+    weight = torch.where(include, a_eff * T_before, torch.zeros_like(a_eff))
+    C = weight @ rec["rgb"]
+    T_ext = torch.cat([T_before, T_after[:, -1:]], 1) if L > 0 else ones
+    T_final = torch.gather(T_ext, 1, s[:, None])[:, 0]
+    return C, T_final, last, amb_f, amb_b
+
+
+def _tile_pixels(tx, ty, width, height):
+    xs = torch.arange(tx * TILE, min((tx + 1) * TILE, width), dtype=F64)
+    ys = torch.arange(ty * TILE, min((ty + 1) * TILE, height), dtype=F64)
+    gy, gx = torch.meshgrid(ys, xs, indexing="ij")
+    return gx.reshape(-1) + 0.5, gy.reshape(-1) + 0.5, gx.reshape(-1).long(), gy.reshape(-1).long()
+
+
+REC_KEYS = ("mu2d", "conic", "opacity", "rgb", "f2d", "weights")
+
+
+def _to_f64(prims, requires_grad=False):
+    out = {}
+    for k in ("means", "scales", "quats", "opacity", "sh", "freqs", "weights"):
+        out[k] = torch.tensor(np.asarray(prims[k], np.float64), dtype=F64, requires_grad=requires_grad)
+    return out
+
+
+def _render_tiles(proj, spec, cam, cfg, dL_dC=None, tiles=None, max_elems=1 << 22):
+    """Composite every tile (or the listed tile ids); optionally back-propagate dL/dC per tile."""
+    width, height = cam["width"], cam["height"]
+    tiles_x = spec["tiles_x"]
+    bg = torch.tensor(cfg["bg"], dtype=F64)
+    img = torch.zeros(3, height, width, dtype=F64)
+    Tf = torch.ones(height, width, dtype=F64)
+    last = torch.zeros(height, width, dtype=torch.long)
+    amb_f = torch.zeros(height, width, dtype=torch.bool)
+    amb_b = torch.zeros(height, width, dtype=torch.bool)
+    K = proj["weights"].shape[1]
+    tile_list = range(spec["tiles_x"] * spec["tiles_y"]) if tiles is None else tiles
+    for tid in tile_list:
+        s0, s1 = int(spec["ranges"][tid, 0]), int(spec["ranges"][tid, 1])
+        gxp, gyp, gxi, gyi = _tile_pixels(tid % tiles_x, tid // tiles_x, width, height)
+        if s1 == s0:
+            img[:, gyi, gxi] = bg[:, None]
+            continue
+        ids = torch.from_numpy(spec["sorted_vals"][s0:s1].astype(np.int64))
+        rec = {k: proj[k].index_select(0, ids) for k in REC_KEYS}
+        L = s1 - s0
+        chunk = max(1, max_elems // (L * max(K, 1)))
+        for c0 in range(0, gxp.shape[0], chunk):
+            sl = slice(c0, c0 + chunk)
+            C, T, lst, af, ab = composite(gxp[sl], gyp[sl], rec, cfg)
+            out = C + T[:, None] * bg[None, :]
+            if dL_dC is not None:
+                g = dL_dC[:, gyi[sl], gxi[sl]].T
+                (out * g).sum().backward()
+            img[:, gyi[sl], gxi[sl]] = out.detach().T
+            Tf[gyi[sl], gxi[sl]] = T.detach()
+            last[gyi[sl], gxi[sl]] = lst
+            amb_f[gyi[sl], gxi[sl]] = af
+            amb_b[gyi[sl], gxi[sl]] = ab
+    return dict(image=img, T=Tf, n_contrib=last, ambiguous=amb_f, ambiguous_bwd=amb_b)
+
+
+def render(prims: dict, cam, cfg, tiles=None, third_row="z") -> dict:
+    """Forward render in float64.  prims: numpy arrays (means, scales, quats, opacity, sh, freqs, weights)."""
+    spec = bin_spec(prims, cam, cfg)
+    with torch.no_grad():
+        proj = project(_to_f64(prims), cam, cfg, third_row)
+    out = _render_tiles(proj, spec, cam, cfg, tiles=tiles)
+    out["spec"] = spec
+    out["proj"] = {k: v.detach() for k, v in proj.items()}
+    return out
+
+
+def render_backward(prims: dict, cam, cfg, dL_dC) -> dict:
+    """Gradients of sum(dL_dC * image) w.r.t. every primitive attribute (float64, exact adjoint).
+
+    Also returns the per-primitive 2D gradients (w.r.t. mu2d, conic (a, b, c), opacity, rgb, f2d,
+    weights as used by the compositing step) under the key "grad2d".
+    """
+    spec = bin_spec(prims, cam, cfg)
+    leaves = _to_f64(prims, requires_grad=True)
+    proj = project(leaves, cam, cfg)
+    rec = {k: proj[k].detach().clone().requires_grad_(True) for k in REC_KEYS}
+    g = torch.as_tensor(np.asarray(dL_dC, np.float64), dtype=F64)
+    out = _render_tiles(rec, spec, cam, cfg, dL_dC=g)
+    g2d = {k: (rec[k].grad if rec[k].grad is not None else torch.zeros_like(rec[k])) for k in REC_KEYS}
+    outs = [proj[k] for k in REC_KEYS if proj[k].requires_grad]
+    gouts = [g2d[k] for k in REC_KEYS if proj[k].requires_grad]
+    torch.autograd.backward(outs, gouts)
+    grads = {k: (v.grad if v.grad is not None else torch.zeros_like(v)).numpy() for k, v in leaves.items()}
+    grads["grad2d"] = {k: v.numpy() for k, v in g2d.items()}
+    grads["image"] = out["image"].numpy()
+    grads["ambiguous_bwd"] = out["ambiguous_bwd"].numpy()
+    return grads
+
+
+# ----------------------------------------------------------------------------------------------
+# Photometric loss (Sec. 3.4.1, the L1 part; L2 for the gradient-check configuration)
+# ----------------------------------------------------------------------------------------------
+def loss_and_grad(image, target, kind="l1"):
+    """Mean L1 or mean squared error over all pixels and channels, and dL/dimage."""
+    image = np.asarray(image, np.float64)
+    target = np.asarray(target, np.float64)
+    diff = image - target
+    N = diff.size
+    if kind == "l1":
+        return float(np.abs(diff).sum() / N), np.sign(diff) / N
+    return float((diff * diff).sum() / N), 2.0 * diff / N

@@ -1,0 +1,422 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each test checks the oracle against mathematics the paper fixes or against a library routine:
+closed forms, numerical quadrature of the z-integral (supplement A.2), the stated special cases
+(Sec. 3.2.2), brute-force sequential compositing, finite differences, scipy's spherical
+harmonics and rotations.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import gabsplat_oracle as O
+from paper_2508_05343_b300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def tiny_scene(seed, n=24, K=2, sh_degree=1, box=0.6, log_scale=(-2.0, 0.3)):
+    spec = scenes.SceneSpec(n=n, K=K, sh_degree=sh_degree, layout="uniform", box=box, log_scale=log_scale)
+    return scenes.make_scene(spec, seed)
+
+
+def tiny_camera(w=40, h=36, dist=3.0, az=20.0, el=10.0):
+    return scenes.orbit_camera(w, h, az, el, dist)
+
+
+def t64(a, rg=False):
+    return torch.tensor(np.asarray(a, np.float64), requires_grad=rg)
+
+
+# ------------------------------------------------------------------------------------------
+# Library pins: spherical harmonics, rotations
+# ------------------------------------------------------------------------------------------
+def test_sh_basis_matches_scipy():
+    from scipy.special import sph_harm_y
+    rng = np.random.default_rng(0)
+    d = rng.standard_normal((64, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    theta = np.arccos(np.clip(d[:, 2], -1, 1))
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    ours = O.sh_basis(t64(d), 3).numpy()
+    for l in range(4):
+        for m in range(-l, l + 1):
+            if m > 0:
+                ref = math.sqrt(2) * (-1) ** m * sph_harm_y(l, m, theta, phi).real
+            elif m < 0:
+                ref = math.sqrt(2) * (-1) ** m * sph_harm_y(l, -m, theta, phi).imag
+            else:
+                ref = sph_harm_y(l, 0, theta, phi).real
+            np.testing.assert_allclose(ours[:, l * l + l + m], ref, atol=1e-13, err_msg=f"l={l} m={m}")
+
+
+def test_rotation_matches_scipy():
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(1)
+    q = rng.standard_normal((32, 4)) * rng.uniform(0.2, 3.0, (32, 1))      # any norm > 0
+    ours = O.rotation_from_quaternion(t64(q)).numpy()
+    ref = Rotation.from_quat(q[:, [1, 2, 3, 0]]).as_matrix()               # scipy is scalar-last
+    np.testing.assert_allclose(ours, ref, atol=1e-13)
+
+
+def test_covariance_is_rotated_scale():
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(2)
+    q = rng.standard_normal((16, 4))
+    s = np.exp(rng.normal(-1, 0.5, (16, 3)))
+    ours = O.covariance_3d(t64(s), t64(q)).numpy()
+    R = Rotation.from_quat(q[:, [1, 2, 3, 0]]).as_matrix()
+    ref = np.einsum("nij,nj,nkj->nik", R, s * s, R)
+    np.testing.assert_allclose(ours, ref, atol=1e-14)
+
+
+# ------------------------------------------------------------------------------------------
+# Projection pins (Sec. 3.1, Eq. 2; Sec. 3.3.1, Eq. 7)
+# ------------------------------------------------------------------------------------------
+def test_jacobian_is_derivative_of_pinhole_projection():
+    cam = tiny_camera(64, 48)
+    W, tc = O.camera_tensors(cam)
+    rng = np.random.default_rng(3)
+    mu = rng.uniform(-0.5, 0.5, (10, 3))
+    t = t64(mu) @ W.T + tc
+    JW = (O.jacobian(t, cam) @ W).numpy()
+
+    def pi(x):
+        c = W.numpy() @ x + tc.numpy()
+        return np.array([cam["fx"] * c[0] / c[2] + cam["cx"], cam["fy"] * c[1] / c[2] + cam["cy"]])
+
+    for k in range(mu.shape[0]):
+        num = np.zeros((2, 3))
+        for j in range(3):
+            e = np.zeros(3); e[j] = 1e-6
+            num[:, j] = (pi(mu[k] + e) - pi(mu[k] - e)) / 2e-6
+        np.testing.assert_allclose(JW[k, :2], num, rtol=1e-7, atol=1e-6)
+
+
+def test_mean_projection_is_pinhole():
+    cam = tiny_camera()
+    prims = tiny_scene(4)
+    proj = O.project(O._to_f64(prims), cam, O.default_config())
+    c = prims["means"].astype(np.float64) @ np.asarray(cam["R"], np.float64).T + np.asarray(cam["t"], np.float64)
+    ref = np.stack([cam["fx"] * c[:, 0] / c[:, 2] + cam["cx"], cam["fy"] * c[:, 1] / c[:, 2] + cam["cy"]], -1)
+    np.testing.assert_allclose(proj["mu2d"].detach().numpy(), ref, rtol=1e-13)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_z_integration_by_quadrature(seed):
+    """Supplement A.2: integrating exp(-x^T S x / 2) cos(2 pi f.x) over z gives
+    C1 C2 G2D(x, y) cos(2 pi f2D.(x, y)) with G2D built from the top-left 2x2 of S^-1, f2D from Eq. 8,
+    C1 = sqrt(2 pi / S22) and C2 = exp(-2 pi^2 f_z^2 / S22).  Pins the reading of S (ray space)."""
+    from scipy.integrate import quad
+    rng = np.random.default_rng(100 + seed)
+    A = rng.standard_normal((3, 3))
+    sigma = A @ A.T + 0.3 * np.eye(3)
+    f = rng.normal(0, 0.4, 3)
+    f2d = O.splat_frequency(t64(f[None, None, :]), t64(sigma[None])).numpy()[0, 0]
+    S = np.linalg.inv(sigma)
+    cov2 = sigma[:2, :2]
+    C1 = math.sqrt(2 * math.pi / S[2, 2])
+    C2 = math.exp(-2 * math.pi ** 2 * f[2] ** 2 / S[2, 2])
+    for _ in range(6):
+        x, y = rng.normal(0, 1.0, 2)
+        integrand = lambda z: math.exp(-0.5 * np.array([x, y, z]) @ S @ np.array([x, y, z])) * \
+            math.cos(2 * math.pi * (f[0] * x + f[1] * y + f[2] * z))
+        val, _ = quad(integrand, -np.inf, np.inf, epsabs=1e-14, epsrel=1e-12, limit=400)
+        xy = np.array([x, y])
+        ref = C1 * C2 * math.exp(-0.5 * xy @ np.linalg.inv(cov2) @ xy) * math.cos(2 * math.pi * f2d @ xy)
+        assert abs(val - ref) < 1e-10 * max(1.0, abs(ref)), (val, ref)
+
+
+def test_f2d_independent_of_jacobian_third_row():
+    cam = tiny_camera(64, 64, az=35.0, el=-15.0)
+    prims = tiny_scene(5, K=3)
+    cfg = O.default_config()
+    pz = O.project(O._to_f64(prims), cam, cfg, third_row="z")
+    pe = O.project(O._to_f64(prims), cam, cfg, third_row="ewa")
+    np.testing.assert_allclose(pz["f2d"].detach().numpy(), pe["f2d"].detach().numpy(), rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(pz["conic"].detach().numpy(), pe["conic"].detach().numpy(), rtol=1e-12)
+
+
+def test_f2d_conditional_mean_form():
+    """-S_xz/S_zz equals A^-1 b (A, b = blocks of the ray-space covariance): a second formula for Eq. 8."""
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        X = rng.standard_normal((3, 3))
+        sig = X @ X.T + 0.1 * np.eye(3)
+        fp = rng.standard_normal(3)
+        ours = O.splat_frequency(t64(fp[None, None]), t64(sig[None])).numpy()[0, 0]
+        r = np.linalg.solve(sig[:2, :2], sig[:2, 2])
+        np.testing.assert_allclose(ours, fp[:2] + r * fp[2], rtol=1e-10, atol=1e-12)
+
+
+def test_frequency_projection_camera_aligned():
+    """Axis-aligned primitive on the optical axis, f along camera x: f2D = (f tz / fx, 0) cycles/pixel."""
+    cam = scenes.make_camera(64, 64, 60.0, eye=(0, 0, -4.0))
+    prims = dict(means=np.array([[0, 0, 1.0]], np.float32), scales=np.array([[0.1, 0.2, 0.3]], np.float32),
+                 quats=np.array([[1, 0, 0, 0]], np.float32), opacity=np.array([0.8], np.float32),
+                 sh=np.zeros((1, 1, 3), np.float32), freqs=np.array([[[2.5, 0, 0]]], np.float32),
+                 weights=np.array([[0.5]], np.float32))
+    p = O.project(O._to_f64(prims), cam, O.default_config())
+    tz = 5.0
+    np.testing.assert_allclose(p["f2d"].detach().numpy()[0, 0], [2.5 * tz / cam["fx"], 0.0], atol=1e-14)
+
+
+# ------------------------------------------------------------------------------------------
+# Rendering pins (Eq. 9-10)
+# ------------------------------------------------------------------------------------------
+def test_single_primitive_closed_form():
+    """One axis-aligned primitive on the optical axis: the image is rgb*alpha + bg*(1-alpha) with alpha
+    from the analytic 2D footprint sigma_x = fx s_x / tz, f2D = f tz / fx (no matrices involved)."""
+    Wd, Hd = 96, 80
+    cam = scenes.make_camera(Wd, Hd, 60.0, eye=(0, 0, -4.0))
+    cfg = O.default_config(eps2d=0.3, bg=(0.1, 0.2, 0.3))
+    sx, sy, tz, fw, w, o = 0.07, 0.11, 4.0, 3.0, 0.45, 0.9
+    sh = np.array([[[0.3, -0.2, 0.1]]], np.float32)
+    prims = dict(means=np.array([[0, 0, 0.0]], np.float32), scales=np.array([[sx, sy, 0.05]], np.float32),
+                 quats=np.array([[1, 0, 0, 0]], np.float32), opacity=np.array([o], np.float32), sh=sh,
+                 freqs=np.array([[[fw, 0, 0]]], np.float32), weights=np.array([[w]], np.float32))
+    out = O.render(prims, cam, cfg)
+    fx = cam["fx"]
+    vx = (fx * np.float64(np.float32(sx)) / tz) ** 2 + cfg["eps2d"]
+    vy = (fx * np.float64(np.float32(sy)) / tz) ** 2 + cfg["eps2d"]
+    f2 = np.float64(np.float32(fw)) * tz / fx
+    rgb = np.maximum(0, 0.5 / math.sqrt(math.pi) * sh[0, 0].astype(np.float64) + 0.5)
+    r = math.ceil(3 * math.sqrt(max(vx, vy)))
+    xs = np.arange(Wd) + 0.5
+    ys = np.arange(Hd) + 0.5
+    dx = xs[None, :] - Wd / 2
+    dy = ys[:, None] - Hd / 2
+    alpha = np.float64(np.float32(o)) * np.exp(-0.5 * (dx ** 2 / vx + dy ** 2 / vy)) * \
+        ((1 - np.float64(np.float32(w))) + np.float64(np.float32(w)) * np.cos(2 * math.pi * f2 * dx))
+    alpha = np.minimum(alpha, cfg["alpha_max"])
+    alpha = np.where(alpha >= cfg["alpha_min"], alpha, 0.0)
+    tx0, tx1 = math.floor((Wd / 2 - r) / 16), math.floor((Wd / 2 + r) / 16)
+    ty0, ty1 = math.floor((Hd / 2 - r) / 16), math.floor((Hd / 2 + r) / 16)
+    tile_x = (np.arange(Wd) // 16)[None, :]
+    tile_y = (np.arange(Hd) // 16)[:, None]
+    inside = (tile_x >= tx0) & (tile_x <= tx1) & (tile_y >= ty0) & (tile_y <= ty1)
+    alpha = np.where(inside, alpha, 0.0)
+    bg = np.array(cfg["bg"])
+    ref = rgb[:, None, None] * alpha[None] + bg[:, None, None] * (1 - alpha[None])
+    np.testing.assert_allclose(out["image"].numpy(), ref, atol=1e-12)
+    np.testing.assert_allclose(out["T"].numpy(), 1 - alpha, atol=1e-12)
+
+
+def _special_cases():
+    with open(os.path.join(GOLDEN, "special_cases.json")) as fh:
+        return json.load(fh)
+
+
+def test_gaussian_special_case_reduction():
+    """Sec. 3.2.2: f = 0 or w = 0 is 3DGS; K = 0 is the plain Gaussian splatter.  All three agree."""
+    sc = _special_cases()["gaussian_special_case"]
+    cam = tiny_camera(48, 40)
+    cfg = O.default_config()
+    base = tiny_scene(7, n=30, K=3)
+    a = dict(base, weights=np.full_like(base["weights"], sc["w"]))
+    b = dict(base, freqs=np.full_like(base["freqs"], sc["f"]))
+    c = dict(base, freqs=np.zeros((30, 0, 3), np.float32), weights=np.zeros((30, 0), np.float32))
+    ia, ib, ic = (O.render(p, cam, cfg)["image"].numpy() for p in (a, b, c))
+    np.testing.assert_allclose(ia, ic, atol=1e-13)
+    np.testing.assert_allclose(ib, ic, atol=1e-13)
+    assert np.abs(O.render(base, cam, cfg)["image"].numpy() - ic).max() > 1e-3   # Gabor terms matter
+
+
+def test_initialisation_values_avoid_degenerate_gradients():
+    """Sec. 3.4.1: at f = 0 the Gabor terms have zero gradient; at the stated initial values they do not."""
+    sc = _special_cases()
+    cam = tiny_camera(32, 32)
+    cfg = O.default_config()
+    base = tiny_scene(8, n=10, K=2, log_scale=(-1.5, 0.2))
+    rng = np.random.default_rng(8)
+    g = rng.standard_normal((3, 32, 32))
+    deg = dict(base, freqs=np.zeros_like(base["freqs"]), weights=np.full_like(base["weights"], 0.3))
+    gd = O.render_backward(deg, cam, cfg, g)
+    assert np.abs(gd["freqs"]).max() == 0.0 and np.abs(gd["weights"]).max() < 1e-15
+    ini = sc["initialisation"]
+    init = dict(base, freqs=np.full_like(base["freqs"], ini["f"]), weights=np.full_like(base["weights"], ini["w"]))
+    gi = O.render_backward(init, cam, cfg, g)
+    assert np.abs(gi["freqs"]).max() > 0 and np.abs(gi["weights"]).max() > 0
+
+
+def test_constant_colour_weights_telescope():
+    """With every primitive white and a black background, C = 1 - T_final exactly (sum of weights)."""
+    cam = scenes.orbit_camera(64, 48, 0.0, 0.0, 4.0)
+    cfg = O.default_config()
+    prims = scenes.config_scene(0)
+    c0 = 0.5 / math.sqrt(math.pi)
+    prims = dict(prims, sh=np.full_like(prims["sh"], 0.5 / c0))
+    out = O.render(prims, cam, cfg)
+    img, T = out["image"].numpy(), out["T"].numpy()
+    for ch in range(3):
+        np.testing.assert_allclose(img[ch], 1 - T, atol=1e-12)
+    assert (T >= cfg["T_min"]).all() and (T <= 1).all() and (img >= 0).all()
+
+
+def test_transmittance_monotone_and_bounded():
+    cam = scenes.config_cameras(0)[0]
+    cfg = O.default_config()
+    prims = scenes.config_scene(0)
+    out = O.render(prims, cam, cfg)
+    spec, proj = out["spec"], out["proj"]
+    for tid in range(spec["tiles_x"] * spec["tiles_y"]):
+        s0, s1 = spec["ranges"][tid]
+        if s1 == s0:
+            continue
+        ids = torch.from_numpy(spec["sorted_vals"][s0:s1].astype(np.int64))
+        rec = {k: proj[k].index_select(0, ids) for k in O.REC_KEYS}
+        gx, gy, _, _ = O._tile_pixels(tid % spec["tiles_x"], tid // spec["tiles_x"], 128, 128)
+        alpha = torch.clamp_max(O.gabor_alpha(gx, gy, rec, cfg), cfg["alpha_max"])
+        assert (alpha <= cfg["alpha_max"]).all()
+    T = out["T"].numpy()
+    assert (T >= cfg["T_min"]).all() and (T <= 1.0).all()
+    assert (out["image"].numpy() >= 0).all()
+
+
+def _brute_force(prims, cam, cfg):
+    """Sequential per-pixel compositing with scalar math, independent of the tile vectorisation:
+    gather every primitive whose 3-sigma square overlaps the pixel's tile, order by (float32 depth
+    bits, index) with Python's sort, and walk front to back."""
+    spec = O.bin_spec(prims, cam, cfg)
+    proj = O.project(O._to_f64(prims), cam, cfg)
+    P = {k: v.detach().numpy() for k, v in proj.items()}
+    Wd, Hd = cam["width"], cam["height"]
+    img = np.zeros((3, Hd, Wd)); Tf = np.zeros((Hd, Wd)); last = np.zeros((Hd, Wd), np.int64)
+    dbits = spec["depth"].astype(np.float32).view(np.uint32)
+    n = prims["means"].shape[0]
+    for py in range(Hd):
+        for px in range(Wd):
+            tx, ty = px // 16, py // 16
+            plist = []
+            for k in range(n):
+                if not spec["valid"][k]:
+                    continue
+                mx, my = float(spec["mu2d"][k, 0]), float(spec["mu2d"][k, 1])
+                r = float(spec["radius"][k])
+                if 16 * tx <= mx + r and 16 * tx + 16 > mx - r and 16 * ty <= my + r and 16 * ty + 16 > my - r:
+                    plist.append(k)
+            plist.sort(key=lambda k: (int(dbits[k]), k))
+            T, C, lst = 1.0, np.zeros(3), 0
+            for pos, k in enumerate(plist):
+                dx, dy = px + 0.5 - P["mu2d"][k, 0], py + 0.5 - P["mu2d"][k, 1]
+                a, b, c = P["conic"][k]
+                G = math.exp(-0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy)
+                bank = 1.0
+                for i in range(P["weights"].shape[1]):
+                    wi = P["weights"][k, i]
+                    bank += wi * (math.cos(2 * math.pi * (P["f2d"][k, i, 0] * dx + P["f2d"][k, i, 1] * dy)) - 1.0)
+                alpha = min(cfg["alpha_max"], P["opacity"][k] * G * bank)
+                if alpha < cfg["alpha_min"]:
+                    continue
+                if T * (1 - alpha) < cfg["T_min"]:
+                    break
+                C += P["rgb"][k] * alpha * T
+                T *= (1 - alpha)
+                lst = pos + 1
+            img[:, py, px] = C + T * np.array(cfg["bg"])
+            Tf[py, px] = T
+            last[py, px] = lst
+    return img, Tf, last
+
+
+@pytest.mark.parametrize("seed,n,K", [(11, 40, 2), (12, 24, 0), (13, 32, 4)])
+def test_brute_force_matches_tiled_oracle(seed, n, K):
+    cam = tiny_camera(40, 36, dist=2.5)                       # ragged tiles: 40x36 is not a multiple of 16
+    cfg = O.default_config(bg=(0.2, 0.0, 0.5))
+    prims = tiny_scene(seed, n=n, K=K, log_scale=(-2.2, 0.4))
+    prims["opacity"] = np.clip(prims["opacity"] * 1.4, 0, 0.999).astype(np.float32)   # exercise the stop rule
+    out = O.render(prims, cam, cfg)
+    img, T, last = _brute_force(prims, cam, cfg)
+    np.testing.assert_allclose(out["image"].numpy(), img, atol=1e-12)
+    np.testing.assert_allclose(out["T"].numpy(), T, atol=1e-12)
+    np.testing.assert_array_equal(out["n_contrib"].numpy(), last)
+
+
+def test_binning_rects_and_sorted_keys_brute_force():
+    cam = tiny_camera(72, 56, dist=2.0)
+    cfg = O.default_config()
+    prims = tiny_scene(14, n=60, K=1, log_scale=(-2.0, 0.6))
+    spec = O.bin_spec(prims, cam, cfg)
+    tx_n, ty_n = spec["tiles_x"], spec["tiles_y"]
+    pairs = []
+    for k in range(60):
+        if not spec["valid"][k]:
+            continue
+        mx, my, r = float(spec["mu2d"][k, 0]), float(spec["mu2d"][k, 1]), float(spec["radius"][k])
+        for ty in range(ty_n):
+            for tx in range(tx_n):
+                if 16 * tx <= mx + r and 16 * tx + 16 > mx - r and 16 * ty <= my + r and 16 * ty + 16 > my - r:
+                    pairs.append(((ty * tx_n + tx) << 32 | int(np.float32(spec["depth"][k]).view(np.uint32)), k))
+    assert len(pairs) == spec["P"] and spec["P"] > 0
+    ref = sorted(enumerate(pairs), key=lambda e: (e[1][0], e[0]))
+    np.testing.assert_array_equal(spec["sorted_keys"], np.array([p[1][0] for p in ref], np.uint64))
+    np.testing.assert_array_equal(spec["sorted_vals"], np.array([p[1][1] for p in ref], np.uint32))
+    for tid in range(tx_n * ty_n):
+        cnt = sum(1 for p in pairs if p[0] >> 32 == tid)
+        assert spec["ranges"][tid, 1] - spec["ranges"][tid, 0] == cnt
+
+
+def test_binning_float32_close_to_float64():
+    cam = scenes.config_cameras(0)[0]
+    cfg = O.default_config()
+    prims = scenes.config_scene(0)
+    spec = O.bin_spec(prims, cam, cfg)
+    proj = O.project(O._to_f64(prims), cam, cfg)
+    v = spec["valid"]
+    np.testing.assert_allclose(spec["mu2d"][v], proj["mu2d"].detach().numpy()[v], rtol=1e-5)
+    c64 = proj["cov2d"].detach().numpy()[v]
+    np.testing.assert_allclose(spec["cov2d"][v][:, 0], c64[:, 0, 0], rtol=1e-4)
+    np.testing.assert_allclose(spec["cov2d"][v][:, 2], c64[:, 1, 1], rtol=1e-4)
+
+
+# ------------------------------------------------------------------------------------------
+# Gradients: analytic (reverse mode) vs central finite differences
+# ------------------------------------------------------------------------------------------
+def _scalar_loss(prims, cam, cfg, g):
+    return float((O.render(prims, cam, cfg)["image"].numpy() * g).sum())
+
+
+@pytest.mark.parametrize("seed,K,deg", [(21, 2, 1), (22, 1, 3)])
+def test_gradients_match_finite_differences(seed, K, deg):
+    cam = tiny_camera(32, 32, dist=2.2, az=30.0, el=-20.0)
+    cfg = O.default_config(bg=(0.3, 0.1, 0.2))
+    prims = tiny_scene(seed, n=6, K=K, sh_degree=deg, box=0.35, log_scale=(-1.8, 0.3))
+    prims = {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in prims.items()}
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((3, 32, 32))
+    an = O.render_backward(prims, cam, cfg, g)
+    bad, total = 0, 0
+    for key in ("means", "scales", "quats", "opacity", "sh", "freqs", "weights"):
+        arr = prims[key]
+        flat = arr.reshape(-1)
+        num = np.zeros_like(flat)
+        for i in range(flat.size):
+            h = 1e-6 * max(1.0, abs(flat[i]))
+            p = dict(prims); q = flat.copy(); q[i] += h; p[key] = q.reshape(arr.shape)
+            lp = _scalar_loss(p, cam, cfg, g)
+            q[i] -= 2 * h; p[key] = q.reshape(arr.shape)
+            lm = _scalar_loss(p, cam, cfg, g)
+            num[i] = (lp - lm) / (2 * h)
+        a = an[key].reshape(-1)
+        err = np.abs(a - num) / np.maximum(1e-4, np.abs(num))
+        total += flat.size
+        bad += int((err > 1e-5).sum())
+        rel = np.linalg.norm(a - num) / max(np.linalg.norm(num), 1e-12)
+        assert rel < 1e-6, (key, rel)
+    assert bad <= max(1, total // 200), (bad, total)
+
+
+def test_loss_gradients():
+    rng = np.random.default_rng(5)
+    img, tgt = rng.uniform(0, 1, (3, 8, 8)), rng.uniform(0, 1, (3, 8, 8))
+    for kind in ("l1", "l2"):
+        L, g = O.loss_and_grad(img, tgt, kind)
+        i, j, k = 1, 3, 5
+        h = 1e-7
+        im2 = img.copy(); im2[i, j, k] += h
+        L2, _ = O.loss_and_grad(im2, tgt, kind)
+        assert abs((L2 - L) / h - g[i, j, k]) < 1e-6
