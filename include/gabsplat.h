@@ -1,0 +1,223 @@
+/*
+ * gabsplat.h -- C ABI of the B300 (sm_103a) 3D Gabor splatting rasterizer.
+ *
+ * Method: "3DGabSplat: 3D Gabor Splatting for Frequency-adaptive Radiance Field Rendering"
+ * (arXiv 2508.05343).  A primitive k has mean mu_k, covariance Sigma_k = R_k S_k S_k^T R_k^T,
+ * opacity o_k, SH colour coefficients c_k and F = K Gabor components (f_{k,i}, w_{k,i})
+ * (Sec. 3.1, Sec. 3.2.1 Eq. 5).  Rendering projects the envelope with the EWA map
+ * J W Sigma W^T J^T (Sec. 3.1, Eq. 2), each frequency with ((JW)^-1)^T f (Sec. 3.3.1, Eq. 7) and
+ * z-integrates it to f2D (Sec. 3.3.2, Eq. 8), bins the splats into 16x16 tiles sorted by depth
+ * and alpha-composites them front to back (Sec. 3.3.3, Eq. 10).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All pointers named "device" are CUDA device pointers; the library never allocates or frees
+ *    device memory and never synchronises, except gabsplat_device_status, which copies the
+ *    workspace header to the host and synchronises the given stream.  The caller owns every
+ *    buffer, including the workspace.  Every call is asynchronous on `stream` (a cudaStream_t;
+ *    NULL = the legacy default stream).
+ *  - Host-detectable errors (null pointer, n < 0, K > GS_MAX_K, bad image size, workspace too
+ *    small) return immediately without launching anything.  Errors found on the device (pair
+ *    capacity exceeded, a bounded spin that timed out, non-finite projected values) are written
+ *    to a status word inside the workspace; every later stage of the same frame then does
+ *    nothing, and gabsplat_device_status() reports the error.
+ *  - Inputs are activated values: positive scales, opacity and weights in [0, 1).  Quaternions
+ *    (w, x, y, z) may have any non-zero norm; they are normalised on the device and gradients
+ *    flow through the normalisation.
+ *  - Images are planar float32: rgb [3][height][width], transmittance [height][width].
+ *    Pixel (i, j) samples the point (i + 0.5, j + 0.5).
+ */
+#ifndef GABSPLAT_H
+#define GABSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_TILE 16          /* tile edge in pixels (fixed) */
+#define GS_MAX_K 8          /* largest number of Gabor components per primitive */
+#define GS_MAX_SH_DEGREE 3  /* largest spherical-harmonics degree */
+#define GS_MAX_VIEWS 16     /* largest number of views in one batched frame */
+
+typedef struct CUstream_st* gs_stream; /* identical to cudaStream_t */
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1, /* host-side argument check failed */
+  GS_ERR_CAPACITY = 2,    /* more (tile, primitive) pairs than the workspace holds */
+  GS_ERR_TIMEOUT = 3,     /* a bounded device-side wait gave up */
+  GS_ERR_CUDA = 4,        /* a CUDA launch or copy failed */
+  GS_ERR_NONFINITE = 5,   /* a projected mean or covariance was not finite */
+  GS_ERR_WORKSPACE = 6    /* workspace pointer/size does not match the frame description */
+} gs_status;
+
+typedef enum { GS_F32 = 0, GS_BF16 = 1 } gs_dtype;
+typedef enum { GS_LOSS_L1 = 0, GS_LOSS_L2 = 1 } gs_loss_kind;
+
+/* Primitive attributes (Sec. 3.1 and Sec. 3.2.1), all device pointers, row-major.
+ *   means   [n][3] float32          world-space mu_k
+ *   scales  [n][3] float32 (> 0)    diagonal of S_k
+ *   quats   [n][4] float32          rotation R_k as quaternion (w, x, y, z), any norm > 0,
+ *                                   16-byte aligned
+ *   opacity [n]    float32 in [0,1)
+ *   sh      [n][(sh_degree+1)^2][3] float32 or bf16 (storage)   SH colour coefficients c_k
+ *   freqs   [n][K][3]   float32 or bf16    world-frame frequencies f_{k,i}, cycles per unit
+ *   weights [n][K]      float32 or bf16    Gabor weights w_{k,i} in [0, 1)
+ * freqs/weights may be NULL when K == 0.  storage applies to sh, freqs and weights together;
+ * BF16 values are widened to float32 on load and all arithmetic is float32/float64. */
+typedef struct {
+  int n, K, sh_degree, storage;
+  const float* means;
+  const float* scales;
+  const float* quats;
+  const float* opacity;
+  const void* sh;
+  const void* freqs;
+  const void* weights;
+} gs_prims;
+
+/* Pinhole camera.  R (row-major 3x3) and t map world to camera space (x right, y down,
+ * z forward): x_cam = R x_world + t.  Image coordinates: u = fx x/z + cx, v = fy y/z + cy.
+ * Primitives with camera depth z <= znear or z > zfar are culled. */
+typedef struct {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int width, height;
+  float znear, zfar;
+} gs_camera;
+
+/* Rasterizer constants of the tile rasterizer the paper adopts (Sec. 3.3.3):
+ * eps2d is added to the diagonal of the 2D covariance, alpha = min(alpha_max, o Gabor2D(x)),
+ * pairs with alpha < alpha_min are skipped, compositing stops before the pair whose
+ * T (1 - alpha) would drop below T_min, and bg is added with the final transmittance.
+ * Defaults: 0.3, 0.99, 1/255, 1e-4, (0,0,0).  flags must be 0. */
+typedef struct {
+  float eps2d, alpha_max, alpha_min, T_min;
+  float bg[3];
+  unsigned flags;
+} gs_config;
+
+/* Sizes of one frame and the caller-owned device workspace that holds its state between the
+ * calls (projected records, key/value pairs, tile ranges, per-pixel transmittance and last
+ * contributor).  One frame = one view of one scene.  The same frame description and
+ * workspace must be passed to every stage of that frame; the stages of two frames that share
+ * a workspace must not overlap on the device. */
+typedef struct {
+  int n, K, sh_degree, width, height;
+  int reserved;
+  unsigned long long pair_capacity; /* most (tile, primitive) pairs the workspace can hold */
+  void* ws;                         /* device pointer, 256-byte aligned */
+  size_t ws_bytes;
+} gs_frame;
+
+/* Gradients (float32, device, same shapes as gs_prims; overwritten, not accumulated).
+ * means2d [n][2] receives dL/d(projected mean) for density-control statistics; any pointer
+ * may be NULL to skip that output. */
+typedef struct {
+  float* means;
+  float* scales;
+  float* quats;
+  float* opacity;
+  float* sh;
+  float* freqs;
+  float* weights;
+  float* means2d;
+} gs_prim_grads;
+
+/* Device pointers into a workspace, for inspection and tests (valid after the stage that
+ * writes them).  records: [n][record_floats] projected 2D primitives laid out as
+ *   {mu_x, mu_y, conic_a, conic_b, conic_c, opacity, 1 - sum w, depth, r, g, b, 0,
+ *    f2D_0x, f2D_0y, ..., f2D_(K-1)y, w_0 .. w_(K-1), 0 padding to a multiple of 4}
+ * where the 2D Gaussian is exp(-(a dx^2 + c dy^2)/2 - b dx dy).
+ * touched/offsets [n] uint32; keys [pairs] uint64 = tile << 32 | float bits of depth;
+ * values [pairs] uint32 primitive index; ranges [tiles][2] uint32 [start, end);
+ * T_final [H][W] float32; n_contrib [H][W] uint32 (1-based position in the tile's list of
+ * the last composited pair); grad2d [n][grad2d_floats] float32
+ *   {d mu_x, d mu_y, d a, d b, d c, d opacity, d r, d g, d b, d f2D (2K), d w (K), 0 pad}. */
+typedef struct {
+  float* records;
+  unsigned* touched;
+  unsigned* offsets;
+  unsigned long long* keys_sorted;
+  unsigned* values_sorted;
+  unsigned long long* keys_unsorted;
+  unsigned* values_unsorted;
+  unsigned* ranges;
+  float* T_final;
+  unsigned* n_contrib;
+  float* grad2d;
+  int record_floats;
+  int grad2d_floats;
+  int tiles_x, tiles_y;
+} gs_ws_views;
+
+/* Bytes of device workspace a frame needs.  Returns 0 if the sizes are invalid. */
+size_t gabsplat_workspace_size(int n, int K, int sh_degree, int width, int height,
+                               unsigned long long pair_capacity);
+
+/* Zero-fills the workspace (asynchronously on `stream`).  Required once after the workspace is
+ * allocated (or allocate it zero-filled): the single-pass scans tag their look-back words with a
+ * per-frame epoch, and a zeroed word is never mistaken for a published one. */
+gs_status gabsplat_workspace_init(const gs_frame* frame, gs_stream stream);
+
+/* Stage 1, per-primitive projection (Sec. 3.1 Eq. 2, Sec. 3.3.1 Eq. 7, Sec. 3.3.2 Eq. 8):
+ * culls, projects mean and covariance (float64 determinant and conic), evaluates SH colour
+ * at the viewing direction, splats the K frequencies to f2D, and writes one 2D record and
+ * the number of touched tiles per primitive into the workspace.  The config given here applies
+ * to the whole frame (render and backward). */
+gs_status gabsplat_preprocess(const gs_frame* frame, const gs_prims* prims, const gs_camera* cam,
+                              const gs_config* cfg, gs_stream stream);
+
+/* Stage 2, tile binning and depth sort (Sec. 3.1, "sorted by depth"; Sec. 3.3.3): exclusive
+ * scan of the touched-tile counts, emission of one (tile << 32 | depth bits, primitive) pair per
+ * touched tile, a stable least-significant-digit radix sort of the pairs, and per-tile
+ * [start, end) ranges.  The pair count stays on the device.  GS_ERR_CAPACITY (device status)
+ * if it exceeds frame->pair_capacity; gabsplat_device_status() then reports the needed count.
+ * (The scan and the emission run inside the preprocess launch; this call sorts and ranges.) */
+gs_status gabsplat_bin_sort(const gs_frame* frame, gs_stream stream);
+
+/* Stage 3, front-to-back alpha compositing of the 2D Gabor primitives (Sec. 3.3.2 Eq. 9 and
+ * Sec. 3.3.3 Eq. 10) with the constants of the gs_config given to gabsplat_preprocess.
+ * out_rgb [3][H][W] (device, required) and out_T [H][W] (device, may be NULL).  Keeps the final
+ * transmittance and the last contributor per pixel in the workspace for the backward pass. */
+gs_status gabsplat_render_fwd(const gs_frame* frame, float* out_rgb, float* out_T, gs_stream stream);
+
+/* Stage 4, reverse-order backward pass of the differentiable rasterizer (Sec. 3.3.3, trained by
+ * the photometric loss of Sec. 3.4.1).  Given dL/d(rgb) [3][H][W] (device), walks each pixel's
+ * pairs back to front from its last contributor, recomputing transmittance by division instead of
+ * storing per-pair state, accumulates per-primitive 2D gradients, and chains them to every
+ * attribute in gs_prim_grads.  Uses the primitives and camera given to gabsplat_preprocess for
+ * this frame (their buffers must still hold the same values). */
+gs_status gabsplat_render_bwd(const gs_frame* frame, const float* dL_drgb, const gs_prim_grads* grads,
+                              gs_stream stream);
+
+/* Photometric loss of Sec. 3.4.1 (its L1 part; L2 for gradient checks): mean over `count` values
+ * of |image - target| or (image - target)^2.  Writes the loss (float64, device, 1 value) and
+ * dL/d(image) (device, `count` floats).  scratch: device buffer of at least
+ * gabsplat_loss_scratch_bytes(count) bytes. */
+size_t gabsplat_loss_scratch_bytes(long long count);
+gs_status gabsplat_loss(const float* image, const float* target, long long count, int kind, double* loss_out,
+                        float* dL_dimage, void* scratch, gs_stream stream);
+
+/* Synchronises `stream`, then reads the workspace status word.  *status = device-side
+ * gs_status of the last frame, *pairs = number of (tile, primitive) pairs it produced (the
+ * required capacity when *status == GS_ERR_CAPACITY).  Either output pointer may be NULL. */
+gs_status gabsplat_device_status(const gs_frame* frame, int* status, unsigned long long* pairs, gs_stream stream);
+
+/* Device pointers into the workspace of `frame` (no device access). */
+gs_status gabsplat_workspace_views(const gs_frame* frame, gs_ws_views* out);
+
+/* Human-readable name of a status code (static string). */
+const char* gabsplat_status_string(gs_status s);
+
+/* Library version string. */
+const char* gabsplat_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GABSPLAT_H */

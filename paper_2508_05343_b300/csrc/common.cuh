@@ -1,0 +1,186 @@
+// Internal declarations shared by the rasterizer's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "gabsplat.h"
+
+namespace gs {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+constexpr int TILE = GS_TILE;
+constexpr int BLOCK = 256;            // threads per CTA for every tile / chunk kernel
+constexpr int CHUNK = BLOCK;          // primitives per preprocess chunk (one per thread)
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // keys per onesweep partition
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr int MAX_PASSES = 8;
+
+// Number of floats of a projected 2D record and of a per-primitive 2D gradient row.
+__host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
+__host__ __device__ constexpr int rec_floats(int K) { return 12 + round4(3 * K); }
+__host__ __device__ constexpr int g2d_floats(int K) { return round4(9 + 3 * K); }
+
+// ------------------------------------------------------------------------------------------
+// Frame description on the device: up to GS_MAX_VIEWS views, each one camera over one scene.
+// A single-view frame is the special case nviews == 1.
+// ------------------------------------------------------------------------------------------
+struct ViewDesc {
+  const float* means;
+  const float* scales;
+  const float* quats;
+  const float* opacity;
+  const void* sh;
+  const void* freqs;
+  const void* weights;
+  float* out_rgb;
+  float* out_T;
+  const float* dL_drgb;
+  int n, sh_degree;
+  float R[9], t[3];
+  float fx, fy, cx, cy, znear, zfar;
+  float campos[3];
+  int width, height, tiles_x, tiles_y;
+  u32 prim_base;   // first record index of this view
+  u32 tile_base;   // first global tile id of this view
+  u64 pix_base;    // first per-pixel state index of this view
+};
+
+struct FrameTable {
+  int nviews, K, storage, sh_degree;
+  u32 total_prims, total_tiles;
+  u64 total_pixels;
+  float eps2d, alpha_max, alpha_min, T_min;
+  float bg[3];
+  int npasses;
+  ViewDesc v[GS_MAX_VIEWS];
+};
+
+// Device-side header at the start of every workspace.
+struct WsHeader {
+  int status;               // gs_status of the current frame (0 = ok)
+  u32 epoch;                // bumped by the setup kernel once per frame; tags look-back words
+  u64 pairs;                // (tile, primitive) pairs emitted by the frame (may exceed capacity)
+  u32 chunk_counter;        // preprocess chunk allocator
+  u32 tile_counter_fwd;     // render_fwd tile allocator
+  u32 tile_counter_bwd;     // render_bwd tile allocator
+  u32 nonfinite;            // primitives culled because a projected value was not finite
+  u32 sort_counter[MAX_PASSES];
+  u32 timeout_site;         // which bounded wait gave up (diagnostics)
+  u32 pad[15];
+};
+
+// Offsets of every region of a workspace (host-computed; all 256-byte aligned).
+struct WsLayout {
+  size_t header, table, records, touched, offsets, scan_status, keys0, keys1, vals0, vals1, hist,
+      sort_status, ranges, T_final, n_contrib, grad2d, total;
+  u32 n_prims, n_tiles, n_chunks, n_parts;
+  u64 n_pixels, capacity;
+  int K, rec_f, g2d_f;
+};
+
+// Device pointers into a workspace, passed by value to kernels.
+struct WsPtrs {
+  WsHeader* hdr;
+  const FrameTable* tbl;
+  float* records;
+  u32* touched;
+  u32* offsets;
+  u64* scan_status;
+  u64* keys0;
+  u64* keys1;
+  u32* vals0;
+  u32* vals1;
+  u32* hist;          // [MAX_PASSES][RADIX]
+  u64* sort_status;   // [n_parts][RADIX]
+  uint2* ranges;      // [n_tiles]
+  float* T_final;     // [n_pixels]
+  u32* n_contrib;     // [n_pixels]
+  float* grad2d;      // [n_prims][g2d_f]
+  u64 capacity;
+  u32 n_chunks, n_parts;
+};
+
+WsLayout make_layout(u32 n_prims, int K, u32 n_tiles, u64 n_pixels, u64 capacity);
+WsPtrs make_ptrs(const WsLayout& L, void* ws);
+
+// ------------------------------------------------------------------------------------------
+// Decoupled look-back words: [63:62] flag, [61:40] tag, [39:0] value.
+// ------------------------------------------------------------------------------------------
+constexpr u64 LB_FLAG_AGG = 1ull;
+constexpr u64 LB_FLAG_PREFIX = 2ull;
+__device__ __forceinline__ u64 lb_pack(u64 flag, u32 tag, u64 value) {
+  return (flag << 62) | ((u64)(tag & 0x3FFFFFu) << 40) | (value & 0xFFFFFFFFFFull);
+}
+__device__ __forceinline__ u32 lb_flag(u64 w) { return (u32)(w >> 62); }
+__device__ __forceinline__ u32 lb_tag(u64 w) { return (u32)(w >> 40) & 0x3FFFFFu; }
+__device__ __forceinline__ u64 lb_value(u64 w) { return w & 0xFFFFFFFFFFull; }
+
+__device__ __forceinline__ u64 ld_relaxed(const u64* p) {
+  u64 v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(u64* p, u64 v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ u64 global_timer_ns() {
+  u64 t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Every spin-wait gives up after this long (or this many polls) and sets GS_ERR_TIMEOUT.
+constexpr u64 SPIN_LIMIT_NS = 1000000000ull;   // 1 s
+constexpr u32 SPIN_LIMIT_POLLS = 1u << 24;
+
+__device__ __forceinline__ void set_status(WsHeader* hdr, int s) { atomicCAS(&hdr->status, 0, s); }
+__device__ __forceinline__ int read_status(const WsHeader* hdr) {
+  return *((volatile const int*)&hdr->status);
+}
+
+// Which view does a global primitive / tile index belong to (nviews <= 16, linear scan).
+__device__ __forceinline__ int view_of_prim(const FrameTable* t, u32 gi) {
+  int v = 0;
+  const int nv = t->nviews;
+  while (v + 1 < nv && gi >= t->v[v + 1].prim_base) ++v;
+  return v;
+}
+__device__ __forceinline__ int view_of_tile(const FrameTable* t, u32 tile) {
+  int v = 0;
+  const int nv = t->nviews;
+  while (v + 1 < nv && tile >= t->v[v + 1].tile_base) ++v;
+  return v;
+}
+
+template <int STORAGE>
+__device__ __forceinline__ float load_attr(const void* p, size_t i) {
+  if (STORAGE == GS_BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[i]);
+  return __ldg(reinterpret_cast<const float*>(p) + i);
+}
+
+// ------------------------------------------------------------------------------------------
+// Launch helpers (defined in the kernel translation units).
+// ------------------------------------------------------------------------------------------
+struct Launch {
+  int sm_count;
+  cudaStream_t stream;
+};
+int device_sm_count();
+
+cudaError_t launch_setup(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
+cudaError_t launch_preprocess(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
+cudaError_t launch_bin_sort(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
+cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L);
+cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL_drgb, const Launch& L);
+cudaError_t launch_preprocess_bwd(const FrameTable& tbl, const WsPtrs& p, const gs_prim_grads& g, const Launch& L);
+cudaError_t launch_loss(const float* img, const float* tgt, long long count, int kind, double* loss_out, float* dL,
+                        double* partials, int nblocks, cudaStream_t s);
+
+}  // namespace gs

@@ -1,0 +1,736 @@
+// Per-primitive stages: frame setup, projection + touched-tile scan + key emission (forward),
+// and the chain rule from 2D record gradients to primitive attributes (backward).
+//
+// Projection follows the paper: envelope Sigma' = J W Sigma W^T J^T with the 2D covariance its
+// top-left 2x2 (Sec. 3.1, Eq. 2); frequency f_proj = ((JW)^-1)^T f (Sec. 3.3.1, Eq. 7) and the
+// z-integrated 2D frequency f2D = f_proj_xy - (S_02, S_12)/S_22 f_proj_z (Sec. 3.3.2, Eq. 8),
+// evaluated here through the equivalent block form f_proj_xy + A^-1 b f_proj_z where A and b are
+// the xy block and xz/yz column of the ray-space covariance (-S_xz/S_zz = A^-1 b).  With J's third
+// row (0, 0, 1), ((JW)^-1)^T = J^-T W has the closed form used below.
+#include "common.cuh"
+
+namespace gs {
+
+// Correctly rounded single operations: the binning quantities (camera depth, projected mean,
+// 2D covariance) follow a written float32 procedure with a fixed operation order and no
+// fused multiply-add, so tile lists and sort keys are reproducible bit for bit.
+#define FM __fmul_rn
+#define FA __fadd_rn
+#define FS __fsub_rn
+#define FDV __fdiv_rn
+
+__global__ void k_setup(FrameTable tbl, WsPtrs p) {
+  const u32* src = reinterpret_cast<const u32*>(&tbl);
+  u32* dst = reinterpret_cast<u32*>(const_cast<FrameTable*>(p.tbl));
+  for (int i = threadIdx.x; i < (int)(sizeof(FrameTable) / 4); i += blockDim.x) dst[i] = src[i];
+  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) p.hist[i] = 0;
+  if (threadIdx.x == 0) {
+    WsHeader* h = p.hdr;
+    h->status = 0;
+    h->epoch = h->epoch + 1;
+    h->pairs = 0;
+    h->chunk_counter = 0;
+    h->tile_counter_fwd = 0;
+    h->tile_counter_bwd = 0;
+    h->nonfinite = 0;
+    h->timeout_site = 0;
+    for (int i = 0; i < MAX_PASSES; ++i) h->sort_counter[i] = 0;
+  }
+}
+
+// Real spherical harmonics up to degree 3 at unit direction (x, y, z); index l*l + l + m.
+__device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, float* Y) {
+  Y[0] = 0.28209479177387814f;  // 1/(2 sqrt(pi))
+  if (deg < 1) return;
+  const float c1 = 0.48860251190291992f;  // sqrt(3/(4 pi))
+  Y[1] = c1 * y;
+  Y[2] = c1 * z;
+  Y[3] = c1 * x;
+  if (deg < 2) return;
+  const float k2a = 1.0925484305920792f;   // sqrt(15/pi)/2
+  const float k20 = 0.31539156525252005f;  // sqrt(5/pi)/4
+  const float k22 = 0.54627421529603959f;  // sqrt(15/pi)/4
+  Y[4] = k2a * x * y;
+  Y[5] = k2a * y * z;
+  Y[6] = k20 * (3.f * z * z - 1.f);
+  Y[7] = k2a * x * z;
+  Y[8] = k22 * (x * x - y * y);
+  if (deg < 3) return;
+  const float k33 = 0.59004358992664352f;   // sqrt(35/(2 pi))/4
+  const float k32 = 2.8906114426405538f;    // sqrt(105/pi)/2
+  const float k31 = 0.45704579946446572f;   // sqrt(21/(2 pi))/4
+  const float k30 = 0.37317633259011540f;   // sqrt(7/pi)/4
+  const float k32b = 1.4453057213202769f;   // sqrt(105/pi)/4
+  Y[9] = k33 * y * (3.f * x * x - y * y);
+  Y[10] = k32 * x * y * z;
+  Y[11] = k31 * y * (5.f * z * z - 1.f);
+  Y[12] = k30 * z * (5.f * z * z - 3.f);
+  Y[13] = k31 * x * (5.f * z * z - 1.f);
+  Y[14] = k32b * z * (x * x - y * y);
+  Y[15] = k33 * x * (x * x - 3.f * y * y);
+}
+
+// Gradient of sum_j Y_j(d) * w_j w.r.t. the direction d (polynomial extension off the sphere;
+// its tangential part, the only part used, equals that of the spherical function).
+__device__ __forceinline__ void sh_grad(int deg, float x, float y, float z, const float* w, float& gx, float& gy,
+                                        float& gz) {
+  gx = gy = gz = 0.f;
+  if (deg < 1) return;
+  const float c1 = 0.48860251190291992f;
+  gy += c1 * w[1];
+  gz += c1 * w[2];
+  gx += c1 * w[3];
+  if (deg < 2) return;
+  const float k2a = 1.0925484305920792f, k20 = 0.31539156525252005f, k22 = 0.54627421529603959f;
+  gx += k2a * y * w[4];
+  gy += k2a * x * w[4];
+  gy += k2a * z * w[5];
+  gz += k2a * y * w[5];
+  gz += 6.f * k20 * z * w[6];
+  gx += k2a * z * w[7];
+  gz += k2a * x * w[7];
+  gx += 2.f * k22 * x * w[8];
+  gy -= 2.f * k22 * y * w[8];
+  if (deg < 3) return;
+  const float k33 = 0.59004358992664352f, k32 = 2.8906114426405538f, k31 = 0.45704579946446572f,
+              k30 = 0.37317633259011540f, k32b = 1.4453057213202769f;
+  gx += 6.f * k33 * x * y * w[9];
+  gy += 3.f * k33 * (x * x - y * y) * w[9];
+  gx += k32 * y * z * w[10];
+  gy += k32 * x * z * w[10];
+  gz += k32 * x * y * w[10];
+  gy += k31 * (5.f * z * z - 1.f) * w[11];
+  gz += 10.f * k31 * y * z * w[11];
+  gz += k30 * (15.f * z * z - 3.f) * w[12];
+  gx += k31 * (5.f * z * z - 1.f) * w[13];
+  gz += 10.f * k31 * x * z * w[13];
+  gx += 2.f * k32b * x * z * w[14];
+  gy -= 2.f * k32b * y * z * w[14];
+  gz += k32b * (x * x - y * y) * w[14];
+  gx += 3.f * k33 * (x * x - y * y) * w[15];
+  gy -= 6.f * k33 * x * y * w[15];
+}
+
+// Binning quantities of one primitive per the float32 specification.
+struct BinSpec {
+  float tx, ty, tz, mux, muy;
+  float Sig[6];         // Sigma: 00 01 02 11 12 22
+  float T0[3], T1[3];   // rows of J[0:2] W
+  float ux, uy;         // clamped x/z, y/z
+  float A00, A01, A11;  // undilated 2D covariance
+  double det;           // float64 determinant of the dilated 2D covariance
+  bool valid, finite;
+  int x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ void bin_spec(const ViewDesc& V, float eps2d, float mx, float my, float mz, float s0,
+                                         float s1, float s2, float4 q, BinSpec& b) {
+  const float* W = V.R;
+  b.tx = FA(FA(FA(FM(W[0], mx), FM(W[1], my)), FM(W[2], mz)), V.t[0]);
+  b.ty = FA(FA(FA(FM(W[3], mx), FM(W[4], my)), FM(W[5], mz)), V.t[1]);
+  b.tz = FA(FA(FA(FM(W[6], mx), FM(W[7], my)), FM(W[8], mz)), V.t[2]);
+  const float tx = b.tx, ty = b.ty, tz = b.tz;
+  b.mux = FA(FDV(FM(V.fx, tx), tz), V.cx);
+  b.muy = FA(FDV(FM(V.fy, ty), tz), V.cy);
+  float w = q.x, x = q.y, y = q.z, z = q.w;
+  const float nrm = __fsqrt_rn(FA(FA(FA(FM(w, w), FM(x, x)), FM(y, y)), FM(z, z)));
+  w = FDV(w, nrm);
+  x = FDV(x, nrm);
+  y = FDV(y, nrm);
+  z = FDV(z, nrm);
+  float R[9];
+  R[0] = FS(1.f, FM(2.f, FA(FM(y, y), FM(z, z))));
+  R[1] = FM(2.f, FS(FM(x, y), FM(w, z)));
+  R[2] = FM(2.f, FA(FM(x, z), FM(w, y)));
+  R[3] = FM(2.f, FA(FM(x, y), FM(w, z)));
+  R[4] = FS(1.f, FM(2.f, FA(FM(x, x), FM(z, z))));
+  R[5] = FM(2.f, FS(FM(y, z), FM(w, x)));
+  R[6] = FM(2.f, FS(FM(x, z), FM(w, y)));
+  R[7] = FM(2.f, FA(FM(y, z), FM(w, x)));
+  R[8] = FS(1.f, FM(2.f, FA(FM(x, x), FM(y, y))));
+  float M[9];
+  const float s[3] = {s0, s1, s2};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[3 * i + j] = FM(R[3 * i + j], s[j]);
+  float S[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      S[i][j] = FA(FA(FM(M[3 * i + 0], M[3 * j + 0]), FM(M[3 * i + 1], M[3 * j + 1])), FM(M[3 * i + 2], M[3 * j + 2]));
+      S[j][i] = S[i][j];
+    }
+  b.Sig[0] = S[0][0]; b.Sig[1] = S[0][1]; b.Sig[2] = S[0][2];
+  b.Sig[3] = S[1][1]; b.Sig[4] = S[1][2]; b.Sig[5] = S[2][2];
+  const float limx = FM(1.3f, FDV(FM(0.5f, (float)V.width), V.fx));
+  const float limy = FM(1.3f, FDV(FM(0.5f, (float)V.height), V.fy));
+  const float ux = fminf(fmaxf(FDV(tx, tz), -limx), limx);
+  const float uy = fminf(fmaxf(FDV(ty, tz), -limy), limy);
+  b.ux = ux;
+  b.uy = uy;
+  const float J00 = FDV(V.fx, tz), J02 = -FDV(FM(V.fx, ux), tz);
+  const float J11 = FDV(V.fy, tz), J12 = -FDV(FM(V.fy, uy), tz);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    b.T0[j] = FA(FM(J00, W[j]), FM(J02, W[6 + j]));
+    b.T1[j] = FA(FM(J11, W[3 + j]), FM(J12, W[6 + j]));
+  }
+  float U0[3], U1[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    U0[j] = FA(FA(FM(b.T0[0], S[0][j]), FM(b.T0[1], S[1][j])), FM(b.T0[2], S[2][j]));
+    U1[j] = FA(FA(FM(b.T1[0], S[0][j]), FM(b.T1[1], S[1][j])), FM(b.T1[2], S[2][j]));
+  }
+  b.A00 = FA(FA(FM(U0[0], b.T0[0]), FM(U0[1], b.T0[1])), FM(U0[2], b.T0[2]));
+  b.A01 = FA(FA(FM(U0[0], b.T1[0]), FM(U0[1], b.T1[1])), FM(U0[2], b.T1[2]));
+  b.A11 = FA(FA(FM(U1[0], b.T1[0]), FM(U1[1], b.T1[1])), FM(U1[2], b.T1[2]));
+  const float ca = FA(b.A00, eps2d), cb = b.A01, cc = FA(b.A11, eps2d);
+  const double da = ca, db = cb, dc = cc;
+  const double det = __dsub_rn(__dmul_rn(da, dc), __dmul_rn(db, db));
+  const double mid = __dmul_rn(0.5, __dadd_rn(da, dc));
+  const double lam = __dadd_rn(mid, __dsqrt_rn(fmax(0.0, __dsub_rn(__dmul_rn(mid, mid), det))));
+  const double rad = ceil(__dmul_rn(3.0, __dsqrt_rn(fmax(lam, 0.0))));
+  b.det = det;
+  b.finite = isfinite(b.mux) && isfinite(b.muy) && isfinite(det) && isfinite(rad);
+  bool valid = (tz > V.znear) && (tz <= V.zfar) && (det > 0.0) && b.finite;
+  const double mxd = b.mux, myd = b.muy;
+  // division by the tile size 16 is exact, so it is written as a multiplication by 1/16
+  const double fx0 = floor(__dmul_rn(__dsub_rn(mxd, rad), 0.0625));
+  const double fx1 = floor(__dmul_rn(__dadd_rn(mxd, rad), 0.0625));
+  const double fy0 = floor(__dmul_rn(__dsub_rn(myd, rad), 0.0625));
+  const double fy1 = floor(__dmul_rn(__dadd_rn(myd, rad), 0.0625));
+  valid = valid && (fx1 >= 0.0) && (fx0 <= (double)(V.tiles_x - 1)) && (fy1 >= 0.0) &&
+          (fy0 <= (double)(V.tiles_y - 1));
+  b.valid = valid;
+  if (valid) {
+    b.x0 = (int)fmax(fx0, 0.0);
+    b.x1 = (int)fmin(fx1, (double)(V.tiles_x - 1));
+    b.y0 = (int)fmax(fy0, 0.0);
+    b.y1 = (int)fmin(fy1, (double)(V.tiles_y - 1));
+  } else {
+    b.x0 = 0; b.x1 = -1; b.y0 = 0; b.y1 = -1;
+  }
+}
+
+// Project one primitive: binning + the 2D Gabor record.  Returns the touched-tile count.
+template <int K, int STORAGE>
+__device__ __forceinline__ u32 project_one(const FrameTable* tbl, u32 gi, const WsPtrs& p, int& x0, int& y0, int& wx,
+                                           u32& dbits, u32& tile_base, int& tiles_x, bool& nonfinite) {
+  const int v = view_of_prim(tbl, gi);
+  const ViewDesc& V = tbl->v[v];
+  const u32 k = gi - V.prim_base;
+  const float mx = __ldg(V.means + 3 * (size_t)k), my = __ldg(V.means + 3 * (size_t)k + 1),
+              mz = __ldg(V.means + 3 * (size_t)k + 2);
+  const float s0 = __ldg(V.scales + 3 * (size_t)k), s1 = __ldg(V.scales + 3 * (size_t)k + 1),
+              s2 = __ldg(V.scales + 3 * (size_t)k + 2);
+  const float4 q = __ldg(reinterpret_cast<const float4*>(V.quats) + k);
+  BinSpec b;
+  bin_spec(V, tbl->eps2d, mx, my, mz, s0, s1, s2, q, b);
+  tile_base = V.tile_base;
+  tiles_x = V.tiles_x;
+  nonfinite = (b.tz > V.znear) && (b.tz <= V.zfar) && !b.finite;
+  if (!b.valid) {
+    x0 = 0; y0 = 0; wx = 1; dbits = 0;
+    return 0;
+  }
+  x0 = b.x0;
+  y0 = b.y0;
+  wx = b.x1 - b.x0 + 1;
+  dbits = __float_as_uint(b.tz);
+  const u32 cnt = (u32)wx * (u32)(b.y1 - b.y0 + 1);
+
+  // ---- 2D record: conic from the float64 determinant, colour, splatted frequencies ----
+  const double inv_det = 1.0 / b.det;
+  const double da = (double)FA(b.A00, tbl->eps2d), db = (double)b.A01, dc = (double)FA(b.A11, tbl->eps2d);
+  const float ca = (float)(dc * inv_det), cb = (float)(-db * inv_det), cc = (float)(da * inv_det);
+  const float op = __ldg(V.opacity + k);
+
+  // colour: SH at the viewing direction, shifted by 0.5 and clamped at 0
+  float dxv = mx - V.campos[0], dyv = my - V.campos[1], dzv = mz - V.campos[2];
+  const float inv_len = rsqrtf(dxv * dxv + dyv * dyv + dzv * dzv);
+  dxv *= inv_len; dyv *= inv_len; dzv *= inv_len;
+  float Y[16];
+  const int deg = V.sh_degree;
+  sh_eval(deg, dxv, dyv, dzv, Y);
+  const int nsh = (deg + 1) * (deg + 1);
+  float rgb[3] = {0.5f, 0.5f, 0.5f};
+  const size_t shb = (size_t)k * nsh * 3;
+  for (int j = 0; j < nsh; ++j) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rgb[c] += Y[j] * load_attr<STORAGE>(V.sh, shb + 3 * j + c);
+  }
+  float rec[rec_floats(K)];
+  rec[0] = b.mux; rec[1] = b.muy; rec[2] = ca; rec[3] = cb;
+  rec[4] = cc; rec[5] = op; rec[7] = b.tz;
+  rec[8] = fmaxf(rgb[0], 0.f); rec[9] = fmaxf(rgb[1], 0.f); rec[10] = fmaxf(rgb[2], 0.f); rec[11] = 0.f;
+  float wsum = 0.f;
+  if (K > 0) {
+    // A^-1 b with A the undilated 2D block and b the xz / yz column of the ray-space covariance
+    const float* W = V.R;
+    const float Sw0 = b.Sig[0] * W[6] + b.Sig[1] * W[7] + b.Sig[2] * W[8];
+    const float Sw1 = b.Sig[1] * W[6] + b.Sig[3] * W[7] + b.Sig[4] * W[8];
+    const float Sw2 = b.Sig[2] * W[6] + b.Sig[4] * W[7] + b.Sig[5] * W[8];
+    const float bv0 = b.T0[0] * Sw0 + b.T0[1] * Sw1 + b.T0[2] * Sw2;
+    const float bv1 = b.T1[0] * Sw0 + b.T1[1] * Sw1 + b.T1[2] * Sw2;
+    const double detA = (double)b.A00 * (double)b.A11 - (double)b.A01 * (double)b.A01;
+    float r0 = 0.f, r1 = 0.f;
+    if (detA > 0.0) {
+      const double n0 = (double)b.A11 * (double)bv0 - (double)b.A01 * (double)bv1;
+      const double n1 = (double)b.A00 * (double)bv1 - (double)b.A01 * (double)bv0;
+      const float idet = (float)(1.0 / detA);
+      r0 = (float)n0 * idet;
+      r1 = (float)n1 * idet;
+    }
+    const float tzfx = b.tz / V.fx, tzfy = b.tz / V.fy;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const size_t fb = ((size_t)k * K + i) * 3;
+      const float f0 = load_attr<STORAGE>(V.freqs, fb), f1 = load_attr<STORAGE>(V.freqs, fb + 1),
+                  f2 = load_attr<STORAGE>(V.freqs, fb + 2);
+      const float g0 = W[0] * f0 + W[1] * f1 + W[2] * f2;
+      const float g1 = W[3] * f0 + W[4] * f1 + W[5] * f2;
+      const float g2 = W[6] * f0 + W[7] * f1 + W[8] * f2;
+      const float fpx = g0 * tzfx, fpy = g1 * tzfy, fpz = g2 + b.ux * g0 + b.uy * g1;
+      rec[12 + 2 * i] = fpx + r0 * fpz;
+      rec[12 + 2 * i + 1] = fpy + r1 * fpz;
+      const float wi = load_attr<STORAGE>(V.weights, (size_t)k * K + i);
+      rec[12 + 2 * K + i] = wi;
+      wsum += wi;
+    }
+#pragma unroll
+    for (int i = 12 + 3 * K; i < rec_floats(K); ++i) rec[i] = 0.f;
+  }
+  rec[6] = 1.f - wsum;
+  float4* dst = reinterpret_cast<float4*>(p.records + (size_t)gi * rec_floats(K));
+#pragma unroll
+  for (int i = 0; i < rec_floats(K) / 4; ++i) dst[i] = make_float4(rec[4 * i], rec[4 * i + 1], rec[4 * i + 2], rec[4 * i + 3]);
+  return cnt;
+}
+
+// Preprocess + single-pass (decoupled look-back) exclusive scan of touched-tile counts + key emission.
+// Persistent CTAs take 256-primitive chunks in increasing order from an atomic counter, so every chunk
+// a CTA waits on is held by a CTA that is already running.
+template <int K, int STORAGE>
+__global__ void __launch_bounds__(BLOCK) k_preprocess(WsPtrs p) {
+  __shared__ u32 s_chunk;
+  __shared__ u32 s_warp[BLOCK / 32];
+  __shared__ u64 s_excl;
+  const FrameTable* tbl = p.tbl;
+  WsHeader* hdr = p.hdr;
+  if (read_status(hdr) != 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const u32 total = tbl->total_prims;
+  const u32 tag = hdr->epoch;
+  for (u32 i = blockIdx.x * BLOCK + tid; i < tbl->total_tiles; i += gridDim.x * BLOCK) p.ranges[i] = make_uint2(0u, 0u);
+  for (;;) {
+    if (tid == 0) s_chunk = atomicAdd(&hdr->chunk_counter, 1u);
+    __syncthreads();
+    const u32 chunk = s_chunk;
+    if ((u64)chunk * CHUNK >= total) break;
+    const u32 gi = chunk * CHUNK + tid;
+    int x0 = 0, y0 = 0, wx = 1, tiles_x = 1;
+    u32 dbits = 0, tile_base = 0, cnt = 0;
+    bool nonfinite = false;
+    if (gi < total) cnt = project_one<K, STORAGE>(tbl, gi, p, x0, y0, wx, dbits, tile_base, tiles_x, nonfinite);
+    if (__syncthreads_or(nonfinite)) {
+      if (tid == 0) { atomicAdd(&hdr->nonfinite, 1u); set_status(hdr, GS_ERR_NONFINITE); }
+    }
+    // block scan of cnt
+    u32 incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const u32 wv = lane < BLOCK / 32 ? s_warp[lane] : 0u;
+      u32 wi = wv;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += t;
+      }
+      const u32 agg = __shfl_sync(0xffffffffu, wi, 31);
+      if (lane < BLOCK / 32) s_warp[lane] = wi - wv;
+      if (lane == 0) {
+        u64* st = p.scan_status + chunk;
+        u64 excl = 0;
+        if (chunk == 0) {
+          st_relaxed(st, lb_pack(LB_FLAG_PREFIX, tag, agg));
+        } else {
+          st_relaxed(st, lb_pack(LB_FLAG_AGG, tag, agg));
+          u32 pidx = chunk - 1;
+          u32 polls = 0;
+          const u64 t0 = global_timer_ns();
+          for (;;) {
+            const u64 w = ld_relaxed(p.scan_status + pidx);
+            if (lb_flag(w) != 0 && lb_tag(w) == (tag & 0x3FFFFFu)) {
+              excl += lb_value(w);
+              if (lb_flag(w) == LB_FLAG_PREFIX) break;
+              --pidx;  // chunk 0 always publishes a prefix, so pidx never underflows
+              continue;
+            }
+            if (++polls > SPIN_LIMIT_POLLS || ((polls & 1023u) == 0 && global_timer_ns() - t0 > SPIN_LIMIT_NS)) {
+              hdr->timeout_site = 1;
+              set_status(hdr, GS_ERR_TIMEOUT);
+              break;
+            }
+            __nanosleep(32);
+          }
+          st_relaxed(st, lb_pack(LB_FLAG_PREFIX, tag, excl + agg));
+        }
+        s_excl = excl;
+        if ((u64)(chunk + 1) * CHUNK >= total) {  // last chunk: publish the pair count
+          const u64 P = excl + agg;
+          hdr->pairs = P;
+          if (P > p.capacity) set_status(hdr, GS_ERR_CAPACITY);
+        }
+      }
+    }
+    __syncthreads();
+    const u64 off = s_excl + s_warp[warp] + (incl - cnt);
+    if (gi < total) {
+      p.touched[gi] = cnt;
+      p.offsets[gi] = (u32)off;
+    }
+    // warp-cooperative emission: the warp's pairs are contiguous, so lane j of each round writes
+    // pair (round * 32 + j) -> coalesced 8-byte key and 4-byte value stores
+    const u64 warp_off = __shfl_sync(0xffffffffu, off, 0);
+    const u32 my_excl = (u32)(off - warp_off);
+    const u32 warp_total = __shfl_sync(0xffffffffu, my_excl + cnt, 31);
+    for (u32 base = 0; base < warp_total; base += 32) {
+      const u32 j = base + lane;
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int cand = lo + step;
+        const u32 e = __shfl_sync(0xffffffffu, my_excl, cand);
+        if (e <= j) lo = cand;
+      }
+      const u32 o_excl = __shfl_sync(0xffffffffu, my_excl, lo);
+      const int ox0 = __shfl_sync(0xffffffffu, x0, lo);
+      const int oy0 = __shfl_sync(0xffffffffu, y0, lo);
+      const int owx = __shfl_sync(0xffffffffu, wx, lo);
+      const u32 odb = __shfl_sync(0xffffffffu, dbits, lo);
+      const u32 ogi = __shfl_sync(0xffffffffu, gi, lo);
+      const u32 otb = __shfl_sync(0xffffffffu, tile_base, lo);
+      const int otx = __shfl_sync(0xffffffffu, tiles_x, lo);
+      if (j < warp_total) {
+        const u32 local = j - o_excl;
+        const u32 ry = local / (u32)owx;
+        const u32 rx = local - ry * (u32)owx;
+        const u32 tile = otb + (u32)(oy0 + (int)ry) * (u32)otx + (u32)(ox0 + (int)rx);
+        const u64 pos = warp_off + j;
+        if (pos < p.capacity) {
+          p.keys0[pos] = ((u64)tile << 32) | odb;
+          p.vals0[pos] = ogi;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Backward: 2D record gradients -> primitive attribute gradients (exact chain rule of the
+// forward above; clamps pass zero gradient).
+// ------------------------------------------------------------------------------------------
+template <int K, int STORAGE>
+__global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grads G) {
+  const FrameTable* tbl = p.tbl;
+  if (read_status(p.hdr) != 0) return;
+  const ViewDesc& V = tbl->v[0];
+  const int n = V.n;
+  const int deg = V.sh_degree;
+  const int nsh = (deg + 1) * (deg + 1);
+  for (int k = blockIdx.x * BLOCK + threadIdx.x; k < n; k += gridDim.x * BLOCK) {
+    const u32 gi = V.prim_base + k;
+    const bool active = p.touched[gi] != 0;
+    float g2[g2d_floats(K)];
+    if (active) {
+      const float4* src = reinterpret_cast<const float4*>(p.grad2d + (size_t)gi * g2d_floats(K));
+#pragma unroll
+      for (int i = 0; i < g2d_floats(K) / 4; ++i) {
+        const float4 t = src[i];
+        g2[4 * i] = t.x; g2[4 * i + 1] = t.y; g2[4 * i + 2] = t.z; g2[4 * i + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < g2d_floats(K); ++i) g2[i] = 0.f;
+    }
+    float gmean[3] = {0.f, 0.f, 0.f}, gscale[3] = {0.f, 0.f, 0.f}, gquat[4] = {0.f, 0.f, 0.f, 0.f};
+    if (G.opacity) G.opacity[k] = g2[5];
+    if (G.means2d) { G.means2d[2 * (size_t)k] = g2[0]; G.means2d[2 * (size_t)k + 1] = g2[1]; }
+    if (K > 0 && G.weights) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) G.weights[(size_t)k * K + i] = g2[9 + 2 * K + i];
+    }
+    if (!active) {
+      if (G.means) for (int i = 0; i < 3; ++i) G.means[3 * (size_t)k + i] = 0.f;
+      if (G.scales) for (int i = 0; i < 3; ++i) G.scales[3 * (size_t)k + i] = 0.f;
+      if (G.quats) for (int i = 0; i < 4; ++i) G.quats[4 * (size_t)k + i] = 0.f;
+      if (G.sh) for (int i = 0; i < nsh * 3; ++i) G.sh[(size_t)k * nsh * 3 + i] = 0.f;
+      if (K > 0 && G.freqs) for (int i = 0; i < 3 * K; ++i) G.freqs[(size_t)k * 3 * K + i] = 0.f;
+      continue;
+    }
+    const float mx = __ldg(V.means + 3 * (size_t)k), my = __ldg(V.means + 3 * (size_t)k + 1),
+                mz = __ldg(V.means + 3 * (size_t)k + 2);
+    const float s[3] = {__ldg(V.scales + 3 * (size_t)k), __ldg(V.scales + 3 * (size_t)k + 1),
+                        __ldg(V.scales + 3 * (size_t)k + 2)};
+    const float4 q4 = __ldg(reinterpret_cast<const float4*>(V.quats) + k);
+    const float* W = V.R;
+    const float eps = tbl->eps2d;
+    // ---- recompute forward intermediates ----
+    const float tx = W[0] * mx + W[1] * my + W[2] * mz + V.t[0];
+    const float ty = W[3] * mx + W[4] * my + W[5] * mz + V.t[1];
+    const float tz = W[6] * mx + W[7] * my + W[8] * mz + V.t[2];
+    const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float qw = q4.x / qn, qx = q4.y / qn, qy = q4.z / qn, qz = q4.w / qn;
+    float R[9];
+    R[0] = 1.f - 2.f * (qy * qy + qz * qz); R[1] = 2.f * (qx * qy - qw * qz); R[2] = 2.f * (qx * qz + qw * qy);
+    R[3] = 2.f * (qx * qy + qw * qz); R[4] = 1.f - 2.f * (qx * qx + qz * qz); R[5] = 2.f * (qy * qz - qw * qx);
+    R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    float M[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i + j] * s[j];
+    float Sg[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Sg[3 * i + j] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
+    const float limx = 1.3f * (0.5f * (float)V.width / V.fx), limy = 1.3f * (0.5f * (float)V.height / V.fy);
+    const float rux = tx / tz, ruy = ty / tz;
+    const bool clx = (rux < -limx) || (rux > limx), cly = (ruy < -limy) || (ruy > limy);
+    const float ux = fminf(fmaxf(rux, -limx), limx), uy = fminf(fmaxf(ruy, -limy), limy);
+    const float J00 = V.fx / tz, J02 = -V.fx * ux / tz, J11 = V.fy / tz, J12 = -V.fy * uy / tz;
+    float T0[3], T1[3], w3[3];
+    for (int j = 0; j < 3; ++j) {
+      T0[j] = J00 * W[j] + J02 * W[6 + j];
+      T1[j] = J11 * W[3 + j] + J12 * W[6 + j];
+      w3[j] = W[6 + j];
+    }
+    float U0[3], U1[3], Sw[3];   // U_a = Sigma T_a (Sigma symmetric), Sw = Sigma w3
+    for (int i = 0; i < 3; ++i) {
+      U0[i] = Sg[3 * i] * T0[0] + Sg[3 * i + 1] * T0[1] + Sg[3 * i + 2] * T0[2];
+      U1[i] = Sg[3 * i] * T1[0] + Sg[3 * i + 1] * T1[1] + Sg[3 * i + 2] * T1[2];
+      Sw[i] = Sg[3 * i] * w3[0] + Sg[3 * i + 1] * w3[1] + Sg[3 * i + 2] * w3[2];
+    }
+    const float A00 = U0[0] * T0[0] + U0[1] * T0[1] + U0[2] * T0[2];
+    const float A01 = U0[0] * T1[0] + U0[1] * T1[1] + U0[2] * T1[2];
+    const float A11 = U1[0] * T1[0] + U1[1] * T1[1] + U1[2] * T1[2];
+    const float bv0 = T0[0] * Sw[0] + T0[1] * Sw[1] + T0[2] * Sw[2];
+    const float bv1 = T1[0] * Sw[0] + T1[1] * Sw[1] + T1[2] * Sw[2];
+    // dilated 2D covariance inverse (conic), float64 determinant
+    const double ea = (double)(A00 + eps), eb = (double)A01, ec = (double)(A11 + eps);
+    const double idet = 1.0 / (ea * ec - eb * eb);
+    const float Qa = (float)(ec * idet), Qb = (float)(-eb * idet), Qc = (float)(ea * idet);
+    // ---- conic -> 2D covariance: dSigma2D = -Q G Q with G = [[ga, gb/2], [gb/2, gc]] ----
+    const float ga = g2[2], gbh = 0.5f * g2[3], gc = g2[4];
+    const float QG00 = Qa * ga + Qb * gbh, QG01 = Qa * gbh + Qb * gc;
+    const float QG10 = Qb * ga + Qc * gbh, QG11 = Qb * gbh + Qc * gc;
+    float gA00 = -(QG00 * Qa + QG01 * Qb);
+    float gA11 = -(QG10 * Qb + QG11 * Qc);
+    float gA01 = -2.f * (QG00 * Qb + QG01 * Qc);   // the off-diagonal entry appears twice
+    float gtx = 0.f, gty = 0.f, gtz = 0.f, gux = 0.f, guy = 0.f;
+    float gb0 = 0.f, gb1 = 0.f;
+    if (K > 0) {
+      const double detA = (double)A00 * (double)A11 - (double)A01 * (double)A01;
+      float iA00 = 0.f, iA01 = 0.f, iA11 = 0.f, r0 = 0.f, r1 = 0.f;
+      if (detA > 0.0) {
+        const float id = (float)(1.0 / detA);
+        iA00 = A11 * id; iA01 = -A01 * id; iA11 = A00 * id;
+        r0 = (float)((double)A11 * bv0 - (double)A01 * bv1) * id;
+        r1 = (float)((double)A00 * bv1 - (double)A01 * bv0) * id;
+      }
+      float gr0 = 0.f, gr1 = 0.f;
+      const float tzfx = tz / V.fx, tzfy = tz / V.fy;
+      for (int i = 0; i < K; ++i) {
+        const size_t fb = ((size_t)k * K + i) * 3;
+        const float f0 = load_attr<STORAGE>(V.freqs, fb), f1 = load_attr<STORAGE>(V.freqs, fb + 1),
+                    f2 = load_attr<STORAGE>(V.freqs, fb + 2);
+        const float g0 = W[0] * f0 + W[1] * f1 + W[2] * f2;
+        const float g1 = W[3] * f0 + W[4] * f1 + W[5] * f2;
+        const float gg2 = W[6] * f0 + W[7] * f1 + W[8] * f2;
+        const float fpz = gg2 + ux * g0 + uy * g1;
+        const float gfx = g2[9 + 2 * i], gfy = g2[9 + 2 * i + 1];
+        const float gpz = r0 * gfx + r1 * gfy;
+        gr0 += fpz * gfx;
+        gr1 += fpz * gfy;
+        const float gg0 = gfx * tzfx + gpz * ux;
+        const float gg1 = gfy * tzfy + gpz * uy;
+        const float ggz = gpz;
+        gtz += gfx * g0 / V.fx + gfy * g1 / V.fy;
+        gux += gpz * g0;
+        guy += gpz * g1;
+        if (G.freqs) {
+          G.freqs[fb] = W[0] * gg0 + W[3] * gg1 + W[6] * ggz;
+          G.freqs[fb + 1] = W[1] * gg0 + W[4] * gg1 + W[7] * ggz;
+          G.freqs[fb + 2] = W[2] * gg0 + W[5] * gg1 + W[8] * ggz;
+        }
+      }
+      // r = A^-1 b: gb = A^-1 gr, gA = -gb r^T (A symmetric, off-diagonal counted twice)
+      const float u0 = iA00 * gr0 + iA01 * gr1, u1 = iA01 * gr0 + iA11 * gr1;
+      gb0 = u0; gb1 = u1;
+      gA00 -= u0 * r0;
+      gA11 -= u1 * r1;
+      gA01 -= u0 * r1 + u1 * r0;
+    }
+    // ---- A = T Sigma T^T, b = T Sigma w3 ----
+    float gS[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        gS[3 * i + j] = gA00 * T0[i] * T0[j] + gA01 * T0[i] * T1[j] + gA11 * T1[i] * T1[j] +
+                        (gb0 * T0[i] + gb1 * T1[i]) * w3[j];
+    float gT0[3], gT1[3];
+    for (int j = 0; j < 3; ++j) {
+      gT0[j] = 2.f * gA00 * U0[j] + gA01 * U1[j] + gb0 * Sw[j];
+      gT1[j] = 2.f * gA11 * U1[j] + gA01 * U0[j] + gb1 * Sw[j];
+    }
+    // ---- T = J[0:2] W ----
+    const float gJ00 = gT0[0] * W[0] + gT0[1] * W[1] + gT0[2] * W[2];
+    const float gJ02 = gT0[0] * W[6] + gT0[1] * W[7] + gT0[2] * W[8];
+    const float gJ11 = gT1[0] * W[3] + gT1[1] * W[4] + gT1[2] * W[5];
+    const float gJ12 = gT1[0] * W[6] + gT1[1] * W[7] + gT1[2] * W[8];
+    const float itz = 1.f / tz, itz2 = itz * itz;
+    gtz += -V.fx * itz2 * gJ00 + V.fx * ux * itz2 * gJ02 - V.fy * itz2 * gJ11 + V.fy * uy * itz2 * gJ12;
+    gux += -V.fx * itz * gJ02;
+    guy += -V.fy * itz * gJ12;
+    if (!clx) { gtx += gux * itz; gtz -= gux * tx * itz2; }
+    if (!cly) { gty += guy * itz; gtz -= guy * ty * itz2; }
+    // ---- projected mean ----
+    gtx += g2[0] * V.fx * itz;
+    gtz -= g2[0] * V.fx * tx * itz2;
+    gty += g2[1] * V.fy * itz;
+    gtz -= g2[1] * V.fy * ty * itz2;
+    gmean[0] = W[0] * gtx + W[3] * gty + W[6] * gtz;
+    gmean[1] = W[1] * gtx + W[4] * gty + W[7] * gtz;
+    gmean[2] = W[2] * gtx + W[5] * gty + W[8] * gtz;
+    // ---- Sigma = M M^T, M = R diag(s) ----
+    float gM[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        float acc = 0.f;
+        for (int l = 0; l < 3; ++l) acc += (gS[3 * i + l] + gS[3 * l + i]) * M[3 * l + j];
+        gM[3 * i + j] = acc;
+      }
+    float gR[9];
+    for (int j = 0; j < 3; ++j) {
+      gscale[j] = gM[j] * R[j] + gM[3 + j] * R[3 + j] + gM[6 + j] * R[6 + j];
+      for (int i = 0; i < 3; ++i) gR[3 * i + j] = gM[3 * i + j] * s[j];
+    }
+    const float gqw = 2.f * (-qz * gR[1] + qy * gR[2] + qz * gR[3] - qx * gR[5] - qy * gR[6] + qx * gR[7]);
+    const float gqx = 2.f * (qy * gR[1] + qz * gR[2] + qy * gR[3] - 2.f * qx * gR[4] - qw * gR[5] + qz * gR[6] +
+                             qw * gR[7] - 2.f * qx * gR[8]);
+    const float gqy = 2.f * (-2.f * qy * gR[0] + qx * gR[1] + qw * gR[2] + qx * gR[3] + qz * gR[5] - qw * gR[6] +
+                             qz * gR[7] - 2.f * qy * gR[8]);
+    const float gqz = 2.f * (-2.f * qz * gR[0] - qw * gR[1] + qx * gR[2] + qw * gR[3] - 2.f * qz * gR[4] + qy * gR[5] +
+                             qx * gR[6] + qy * gR[7]);
+    const float dotq = qw * gqw + qx * gqx + qy * gqy + qz * gqz;
+    gquat[0] = (gqw - qw * dotq) / qn;
+    gquat[1] = (gqx - qx * dotq) / qn;
+    gquat[2] = (gqy - qy * dotq) / qn;
+    gquat[3] = (gqz - qz * dotq) / qn;
+    // ---- SH colour ----
+    {
+      float dx = mx - V.campos[0], dy = my - V.campos[1], dz = mz - V.campos[2];
+      const float len = sqrtf(dx * dx + dy * dy + dz * dz);
+      const float il = 1.f / len;
+      dx *= il; dy *= il; dz *= il;
+      float Y[16];
+      sh_eval(deg, dx, dy, dz, Y);
+      const size_t shb = (size_t)k * nsh * 3;
+      float raw[3] = {0.5f, 0.5f, 0.5f};
+      float cw[16];
+      for (int j = 0; j < nsh; ++j)
+        for (int c = 0; c < 3; ++c) raw[c] += Y[j] * load_attr<STORAGE>(V.sh, shb + 3 * j + c);
+      float graw[3];
+      for (int c = 0; c < 3; ++c) graw[c] = raw[c] < 0.f ? 0.f : g2[6 + c];
+      for (int j = 0; j < nsh; ++j) {
+        float acc = 0.f;
+        for (int c = 0; c < 3; ++c) {
+          acc += load_attr<STORAGE>(V.sh, shb + 3 * j + c) * graw[c];
+          if (G.sh) G.sh[shb + 3 * j + c] = Y[j] * graw[c];
+        }
+        cw[j] = acc;
+      }
+      float gdx, gdy, gdz;
+      sh_grad(deg, dx, dy, dz, cw, gdx, gdy, gdz);
+      const float dd = dx * gdx + dy * gdy + dz * gdz;
+      gmean[0] += (gdx - dx * dd) * il;
+      gmean[1] += (gdy - dy * dd) * il;
+      gmean[2] += (gdz - dz * dd) * il;
+    }
+    if (G.means) for (int i = 0; i < 3; ++i) G.means[3 * (size_t)k + i] = gmean[i];
+    if (G.scales) for (int i = 0; i < 3; ++i) G.scales[3 * (size_t)k + i] = gscale[i];
+    if (G.quats) for (int i = 0; i < 4; ++i) G.quats[4 * (size_t)k + i] = gquat[i];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Host launchers
+// ------------------------------------------------------------------------------------------
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+template <typename Kern>
+static int persistent_grid(Kern kern, int threads, size_t smem, int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+  return per_sm * sms;
+}
+
+cudaError_t launch_setup(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
+  k_setup<<<1, 256, 0, L.stream>>>(tbl, p);
+  return cudaGetLastError();
+}
+
+template <int K, int ST>
+static cudaError_t launch_pre_t(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
+  static int grid = 0;
+  if (!grid) grid = persistent_grid(k_preprocess<K, ST>, BLOCK, 0, L.sm_count);
+  const int need = (int)((tbl.total_prims + CHUNK - 1) / CHUNK);
+  int g = need < grid ? need : grid;
+  if (g < 1) g = 1;
+  k_preprocess<K, ST><<<g, BLOCK, 0, L.stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <int K, int ST>
+static cudaError_t launch_pre_bwd_t(const FrameTable& tbl, const WsPtrs& p, const gs_prim_grads& g, const Launch& L) {
+  const int n = tbl.v[0].n;
+  int blocks = (n + BLOCK - 1) / BLOCK;
+  if (blocks > L.sm_count * 8) blocks = L.sm_count * 8;
+  if (blocks < 1) blocks = 1;
+  k_preprocess_bwd<K, ST><<<blocks, BLOCK, 0, L.stream>>>(p, g);
+  return cudaGetLastError();
+}
+
+#define GS_DISPATCH_K(K_, ST_, FN, ...)                                 \
+  switch (K_) {                                                         \
+    case 0: return ST_ ? FN<0, 1>(__VA_ARGS__) : FN<0, 0>(__VA_ARGS__); \
+    case 1: return ST_ ? FN<1, 1>(__VA_ARGS__) : FN<1, 0>(__VA_ARGS__); \
+    case 2: return ST_ ? FN<2, 1>(__VA_ARGS__) : FN<2, 0>(__VA_ARGS__); \
+    case 3: return ST_ ? FN<3, 1>(__VA_ARGS__) : FN<3, 0>(__VA_ARGS__); \
+    case 4: return ST_ ? FN<4, 1>(__VA_ARGS__) : FN<4, 0>(__VA_ARGS__); \
+    case 5: return ST_ ? FN<5, 1>(__VA_ARGS__) : FN<5, 0>(__VA_ARGS__); \
+    case 6: return ST_ ? FN<6, 1>(__VA_ARGS__) : FN<6, 0>(__VA_ARGS__); \
+    case 7: return ST_ ? FN<7, 1>(__VA_ARGS__) : FN<7, 0>(__VA_ARGS__); \
+    case 8: return ST_ ? FN<8, 1>(__VA_ARGS__) : FN<8, 0>(__VA_ARGS__); \
+    default: return cudaErrorInvalidValue;                              \
+  }
+
+cudaError_t launch_preprocess(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
+  GS_DISPATCH_K(tbl.K, tbl.storage, launch_pre_t, tbl, p, L)
+}
+
+cudaError_t launch_preprocess_bwd(const FrameTable& tbl, const WsPtrs& p, const gs_prim_grads& g, const Launch& L) {
+  GS_DISPATCH_K(tbl.K, tbl.storage, launch_pre_bwd_t, tbl, p, g, L)
+}
+
+}  // namespace gs

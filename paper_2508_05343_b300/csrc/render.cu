@@ -1,0 +1,440 @@
+// Per-tile compositing of the 2D Gabor primitives (Sec. 3.3.2 Eq. 9, Sec. 3.3.3 Eq. 10) and its
+// reverse-order adjoint.  One CTA of 256 threads owns a 16x16 tile (one pixel per thread) and pulls
+// tiles from an atomic counter.  The tile's depth-sorted pairs are staged into shared memory in
+// batches of 256 records; the evaluation of alpha is a single inlined function with explicit
+// fused-multiply-add intrinsics so the backward kernel reproduces the forward's decisions exactly.
+#include "common.cuh"
+
+namespace gs {
+
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float TWO_PI = 6.283185307179586f;
+
+// Shared-memory record (floats): {mu_x, mu_y, A', B'}, {C', thr, o, 1 - sum w}, {r, g, b, -},
+// {f2D_0x, f2D_0y, ...}, {w_0 ...}; A' = -a/2 log2 e, B' = -b log2 e, C' = -c/2 log2 e so that
+// G = 2^(A' dx^2 + B' dx dy + C' dy^2); thr = log2(alpha_min / o): o G < alpha_min <=> power < thr,
+// and since the filter bank is <= 1 (weights >= 0) such pairs have alpha < alpha_min: skipped early.
+template <int K>
+struct SRec {
+  static constexpr int F = rec_floats(K);
+  static constexpr int F4 = F / 4;
+};
+
+template <int K>
+__device__ __forceinline__ void stage_record(const float* __restrict__ rec, float4* dst, float alpha_min) {
+  const float4* src = reinterpret_cast<const float4*>(rec);
+  const float4 h0 = __ldg(src), h1 = __ldg(src + 1), h2 = __ldg(src + 2);
+  const float o = h1.y;
+  dst[0] = make_float4(h0.x, h0.y, -0.5f * LOG2E * h0.z, -LOG2E * h0.w);
+  dst[1] = make_float4(-0.5f * LOG2E * h1.x, o > 0.f ? log2f(alpha_min / o) : 3.0e38f, o, h1.z);
+  dst[2] = h2;
+#pragma unroll
+  for (int i = 3; i < SRec<K>::F4; ++i) dst[i] = __ldg(src + i);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Exponent (log2 domain) of the 2D Gaussian at offset (dx, dy).
+__device__ __forceinline__ float gauss_power(const float4& h0, const float4& h1, float dx, float dy) {
+  return __fmaf_rn(dx, __fmaf_rn(h0.z, dx, __fmul_rn(h0.w, dy)), __fmul_rn(__fmul_rn(h1.x, dy), dy));
+}
+
+// Phase (cycles) reduced to [-1/2, 1/2]: cos(2 pi x) = cos(2 pi (x - rint(x))).
+__device__ __forceinline__ float reduced_phase(float fx, float fy, float dx, float dy) {
+  const float ph = __fmaf_rn(fx, dx, __fmul_rn(fy, dy));
+  return __fsub_rn(ph, rintf(ph));
+}
+
+// Filter bank (1 - sum w) + sum w_i cos(2 pi f2D_i . d)  (Sec. 3.3.2, Eq. 9)
+template <int K>
+__device__ __forceinline__ float filter_bank(const float* r, float w0, float dx, float dy) {
+  float bank = w0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const float x = reduced_phase(r[2 * i], r[2 * i + 1], dx, dy);
+    bank = __fmaf_rn(r[2 * K + i], __cosf(__fmul_rn(TWO_PI, x)), bank);
+  }
+  return bank;
+}
+
+template <int K>
+__global__ void __launch_bounds__(BLOCK) k_render_fwd(WsPtrs p, const u32* __restrict__ vals, float* out_rgb,
+                                                      float* out_T) {
+  extern __shared__ __align__(16) float4 s_rec[];
+  __shared__ u32 s_tile;
+  WsHeader* hdr = p.hdr;
+  if (read_status(hdr) != 0) return;
+  const FrameTable* tbl = p.tbl;
+  const int tid = threadIdx.x;
+  const u32 ntiles = tbl->total_tiles;
+  const float amax = tbl->alpha_max, amin = tbl->alpha_min, Tmin = tbl->T_min;
+  constexpr int F4 = SRec<K>::F4;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(&hdr->tile_counter_fwd, 1u);
+    __syncthreads();
+    const u32 tile = s_tile;
+    if (tile >= ntiles) break;
+    const int v = view_of_tile(tbl, tile);
+    const ViewDesc& V = tbl->v[v];
+    const u32 local = tile - V.tile_base;
+    const int tx = (int)(local % (u32)V.tiles_x), ty = (int)(local / (u32)V.tiles_x);
+    const int px = tx * TILE + (tid & (TILE - 1)), py = ty * TILE + (tid >> 4);
+    const bool inside = px < V.width && py < V.height;
+    const uint2 rg = p.ranges[tile];
+    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    u32 last = 0;
+    bool done = !inside;
+    for (u32 start = rg.x; start < rg.y; start += BLOCK) {
+      if (__syncthreads_count(done) == BLOCK) break;
+      const u32 idx = start + tid;
+      if (idx < rg.y) stage_record<K>(p.records + (size_t)vals[idx] * rec_floats(K), s_rec + tid * F4, amin);
+      __syncthreads();
+      const int cnt = (int)min((u32)BLOCK, rg.y - start);
+      for (int j = 0; !done && j < cnt; ++j) {
+        const float4* r = s_rec + j * F4;
+        const float4 h0 = r[0], h1 = r[1];
+        const float dx = __fsub_rn(fpx, h0.x), dy = __fsub_rn(fpy, h0.y);
+        const float pw = gauss_power(h0, h1, dx, dy);
+        if (pw < h1.y) continue;
+        const float G = ex2_approx(pw);
+        const float bank = filter_bank<K>(reinterpret_cast<const float*>(r + 3), h1.w, dx, dy);
+        const float alpha = fminf(amax, __fmul_rn(__fmul_rn(h1.z, G), bank));
+        if (alpha < amin) continue;
+        const float test = __fmul_rn(T, __fsub_rn(1.f, alpha));
+        if (test < Tmin) { done = true; break; }
+        const float4 c = r[2];
+        const float wgt = alpha * T;
+        C0 = __fmaf_rn(c.x, wgt, C0);
+        C1 = __fmaf_rn(c.y, wgt, C1);
+        C2 = __fmaf_rn(c.z, wgt, C2);
+        T = test;
+        last = start + (u32)j + 1u - rg.x;
+      }
+    }
+    if (inside) {
+      const size_t hw = (size_t)V.width * V.height, pix = (size_t)py * V.width + px;
+      float* orgb = out_rgb ? out_rgb : V.out_rgb;
+      float* oT = out_rgb ? out_T : V.out_T;
+      if (orgb) {
+        orgb[pix] = C0 + T * tbl->bg[0];
+        orgb[hw + pix] = C1 + T * tbl->bg[1];
+        orgb[2 * hw + pix] = C2 + T * tbl->bg[2];
+      }
+      if (oT) oT[pix] = T;
+      p.T_final[V.pix_base + pix] = T;
+      p.n_contrib[V.pix_base + pix] = last;
+    }
+    __syncthreads();
+  }
+}
+
+// Reduce-scatter of 32 per-lane values across a warp: afterwards lane i holds the warp sum of
+// value i (31 shuffles instead of 32 x 5 for independent butterflies).
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[32], int lane) {
+#pragma unroll
+  for (int level = 16; level >= 1; level >>= 1) {
+    const bool upper = (lane & level) != 0;
+#pragma unroll
+    for (int k = 0; k < level; ++k) {
+      const float send = upper ? v[k] : v[k + level];
+      const float keep = upper ? v[k + level] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, level);
+    }
+  }
+  return v[0];
+}
+
+template <int K>
+__global__ void __launch_bounds__(BLOCK) k_render_bwd(WsPtrs p, const u32* __restrict__ vals,
+                                                      const float* __restrict__ dL_drgb) {
+  constexpr int F4 = SRec<K>::F4;
+  constexpr int NV = 9 + 3 * K;          // gradient values per pair
+  constexpr int NG = g2d_floats(K);      // padded row in global memory
+  constexpr int NS = NV;                 // shared accumulator row (odd stride: conflict-free)
+  constexpr int NVP = (NV + 31) / 32 * 32;
+  extern __shared__ __align__(16) float4 smem4[];
+  float4* s_rec = smem4;                                          // [BLOCK][F4]
+  float* s_acc = reinterpret_cast<float*>(smem4 + BLOCK * F4);    // [BLOCK][NS]
+  u32* s_id = reinterpret_cast<u32*>(s_acc + BLOCK * NS);          // [BLOCK]
+  __shared__ u32 s_tile;
+  __shared__ u32 s_max;
+  WsHeader* hdr = p.hdr;
+  if (read_status(hdr) != 0) return;
+  const FrameTable* tbl = p.tbl;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const u32 ntiles = tbl->total_tiles;
+  const float amax = tbl->alpha_max, amin = tbl->alpha_min;
+  for (;;) {
+    if (tid == 0) {
+      s_tile = atomicAdd(&hdr->tile_counter_bwd, 1u);
+      s_max = 0;
+    }
+    __syncthreads();
+    const u32 tile = s_tile;
+    if (tile >= ntiles) break;
+    const int v = view_of_tile(tbl, tile);
+    const ViewDesc& V = tbl->v[v];
+    const u32 local = tile - V.tile_base;
+    const int tx = (int)(local % (u32)V.tiles_x), ty = (int)(local / (u32)V.tiles_x);
+    const int px = tx * TILE + (tid & (TILE - 1)), py = ty * TILE + (tid >> 4);
+    const bool inside = px < V.width && py < V.height;
+    const uint2 rg = p.ranges[tile];
+    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const float* gsrc = dL_drgb ? dL_drgb : V.dL_drgb;
+    float T = 1.f, Tfin = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    u32 last = 0;
+    if (inside) {
+      const size_t hw = (size_t)V.width * V.height, pix = (size_t)py * V.width + px;
+      T = Tfin = p.T_final[V.pix_base + pix];
+      last = p.n_contrib[V.pix_base + pix];
+      g0 = gsrc[pix];
+      g1 = gsrc[hw + pix];
+      g2 = gsrc[2 * hw + pix];
+    }
+    const float bgdot = tbl->bg[0] * g0 + tbl->bg[1] * g1 + tbl->bg[2] * g2;
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;   // colour of the pairs behind, normalised
+    // the last composited pair over the warp / CTA bounds the reverse walk
+    u32 wlast = last;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
+    if (lane == 0) atomicMax(&s_max, wlast);
+    __syncthreads();
+    const u32 end = rg.x + s_max;
+    for (u32 bend = end; bend > rg.x;) {
+      const u32 bstart = bend - rg.x > (u32)BLOCK ? bend - BLOCK : rg.x;
+      const u32 cnt = bend - bstart;
+      if ((u32)tid < cnt) {
+        const u32 id = vals[bstart + tid];
+        s_id[tid] = id;
+        stage_record<K>(p.records + (size_t)id * rec_floats(K), s_rec + tid * F4, amin);
+      }
+#pragma unroll
+      for (int i = 0; i < NS; ++i) s_acc[tid * NS + i] = 0.f;
+      __syncthreads();
+      for (int j = (int)cnt - 1; j >= 0; --j) {
+        const u32 pos = bstart + (u32)j - rg.x;   // 0-based position in the tile list
+        if (pos >= wlast) continue;                // warp-uniform
+        const float4* r = s_rec + j * F4;
+        const float4 h0 = r[0], h1 = r[1];
+        const float* fw = reinterpret_cast<const float*>(r + 3);
+        float gv[NVP];
+#pragma unroll
+        for (int i = 0; i < NVP; ++i) gv[i] = 0.f;
+        bool contrib = false;
+        const float dx = __fsub_rn(fpx, h0.x), dy = __fsub_rn(fpy, h0.y);
+        const float pw = gauss_power(h0, h1, dx, dy);
+        if (pos < last && pw >= h1.y) {
+          const float G = ex2_approx(pw);
+          float cs[K > 0 ? K : 1], sn[K > 0 ? K : 1];
+          float bank = h1.w;
+#pragma unroll
+          for (int i = 0; i < K; ++i) {
+            const float x = reduced_phase(fw[2 * i], fw[2 * i + 1], dx, dy);
+            const float ang = __fmul_rn(TWO_PI, x);
+            cs[i] = __cosf(ang);
+            sn[i] = __sinf(ang);
+            bank = __fmaf_rn(fw[2 * K + i], cs[i], bank);
+          }
+          const float araw = __fmul_rn(__fmul_rn(h1.z, G), bank);
+          const float alpha = fminf(amax, araw);
+          if (alpha >= amin) {
+            contrib = true;
+            const float oma = 1.f - alpha;
+            T = T / oma;                                   // transmittance before this pair
+            const float4 c = r[2];
+            const float wgt = alpha * T;
+            gv[6] = wgt * g0;
+            gv[7] = wgt * g1;
+            gv[8] = wgt * g2;
+            float dLda = T * ((c.x - acc0) * g0 + (c.y - acc1) * g1 + (c.z - acc2) * g2) - Tfin * bgdot / oma;
+            acc0 = alpha * c.x + oma * acc0;
+            acc1 = alpha * c.y + oma * acc1;
+            acc2 = alpha * c.z + oma * acc2;
+            if (araw > amax) dLda = 0.f;                   // clamped: no gradient through alpha
+            const float o = h1.z;
+            gv[5] = dLda * G * bank;                       // d opacity
+            const float dLdG = dLda * o * bank;
+            const float dLdbank = dLda * o * G;
+            // log2-domain power p2: G = 2^p2, dG/dp2 = G ln 2
+            const float dLdp2 = dLdG * G * 0.6931471805599453f;
+            gv[2] = dLdp2 * dx * dx;                       // w.r.t. A' (converted at flush)
+            gv[3] = dLdp2 * dx * dy;                       // w.r.t. B'
+            gv[4] = dLdp2 * dy * dy;                       // w.r.t. C'
+            float gdx = dLdp2 * (2.f * h0.z * dx + h0.w * dy);
+            float gdy = dLdp2 * (h0.w * dx + 2.f * h1.x * dy);
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+              const float wi = fw[2 * K + i];
+              gv[9 + 2 * K + i] = dLdbank * (cs[i] - 1.f);           // d w_i
+              const float gph = -dLdbank * wi * sn[i] * TWO_PI;       // d phase (cycles)
+              gv[9 + 2 * i] = gph * dx;
+              gv[9 + 2 * i + 1] = gph * dy;
+              gdx += gph * fw[2 * i];
+              gdy += gph * fw[2 * i + 1];
+            }
+            gv[0] = -gdx;                                  // d mu = - d (pixel - mu)
+            gv[1] = -gdy;
+          }
+        }
+        if (__ballot_sync(0xffffffffu, contrib)) {
+#pragma unroll
+          for (int g = 0; g < NVP / 32; ++g) {
+            float part[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) part[i] = gv[32 * g + i];
+            const float red = warp_reduce_scatter(part, lane);
+            if (32 * g + lane < NV) atomicAdd(&s_acc[j * NS + 32 * g + lane], red);
+          }
+        }
+      }
+      __syncthreads();
+      // flush the batch's accumulators: one vector atomic per (pair, 4 values) for the whole tile
+      if ((u32)tid < cnt) {
+        float* dst = p.grad2d + (size_t)s_id[tid] * NG;
+        const float* a = s_acc + tid * NS;
+        const float cA = -0.5f * LOG2E, cB = -LOG2E;
+        float row[NG];
+#pragma unroll
+        for (int i = 0; i < NG; ++i) row[i] = i < NV ? a[i] : 0.f;
+        row[2] *= cA;   // A' = -a/2 log2 e  ->  dL/da
+        row[3] *= cB;   // B' = -b log2 e
+        row[4] *= cA;   // C' = -c/2 log2 e
+#pragma unroll
+        for (int i = 0; i < NG / 4; ++i) {
+          const float4 q = make_float4(row[4 * i], row[4 * i + 1], row[4 * i + 2], row[4 * i + 3]);
+          if (q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f) atomicAdd(reinterpret_cast<float4*>(dst) + i, q);
+        }
+      }
+      __syncthreads();
+      bend = bstart;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_loss_partial(const float* __restrict__ img, const float* __restrict__ tgt, long long count, int kind,
+                               float* __restrict__ dL, double* __restrict__ partials) {
+  __shared__ double s_sum[8];
+  const double invN = 1.0 / (double)count;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    const float d = img[i] - tgt[i];
+    if (kind == GS_LOSS_L1) {
+      acc += fabs((double)d);
+      dL[i] = (float)((d > 0.f ? 1.0 : (d < 0.f ? -1.0 : 0.0)) * invN);
+    } else {
+      acc += (double)d * (double)d;
+      dL[i] = (float)(2.0 * (double)d * invN);
+    }
+  }
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += s_sum[w];
+    partials[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_loss_final(const double* __restrict__ partials, int n, long long count, double* out) {
+  __shared__ double s[256];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += partials[i];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = 128; st; st >>= 1) {
+    if ((int)threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0] / (double)count;
+}
+
+cudaError_t launch_loss(const float* img, const float* tgt, long long count, int kind, double* loss_out, float* dL,
+                        double* partials, int nblocks, cudaStream_t s) {
+  k_loss_partial<<<nblocks, 256, 0, s>>>(img, tgt, count, kind, dL, partials);
+  k_loss_final<<<1, 256, 0, s>>>(partials, nblocks, count, loss_out);
+  return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, const u32* vals, float* rgb, float* T,
+                                const Launch& L) {
+  static int grid = 0;
+  const size_t smem = (size_t)BLOCK * SRec<K>::F * sizeof(float);
+  if (!grid) {
+    cudaError_t e = cudaFuncSetAttribute(k_render_fwd<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<K>, BLOCK, smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    grid = per_sm * L.sm_count;
+  }
+  int g = grid;
+  if ((u32)g > tbl.total_tiles) g = (int)tbl.total_tiles;
+  if (g < 1) g = 1;
+  k_render_fwd<K><<<g, BLOCK, smem, L.stream>>>(p, vals, rgb, T);
+  return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const u32* vals, const float* dL,
+                                const Launch& L) {
+  static int grid = 0;
+  const size_t smem = (size_t)BLOCK * SRec<K>::F * sizeof(float) + (size_t)BLOCK * (9 + 3 * K) * sizeof(float) +
+                      (size_t)BLOCK * sizeof(u32);
+  if (!grid) {
+    cudaError_t e = cudaFuncSetAttribute(k_render_bwd<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<K>, BLOCK, smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    grid = per_sm * L.sm_count;
+  }
+  int g = grid;
+  if ((u32)g > tbl.total_tiles) g = (int)tbl.total_tiles;
+  if (g < 1) g = 1;
+  k_render_bwd<K><<<g, BLOCK, smem, L.stream>>>(p, vals, dL);
+  return cudaGetLastError();
+}
+
+static const u32* sorted_vals(const FrameTable& tbl, const WsPtrs& p) { return (tbl.npasses & 1) ? p.vals1 : p.vals0; }
+
+cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L) {
+  const u32* vals = sorted_vals(tbl, p);
+  switch (tbl.K) {
+    case 0: return launch_fwd_t<0>(tbl, p, vals, out_rgb, out_T, L);
+    case 1: return launch_fwd_t<1>(tbl, p, vals, out_rgb, out_T, L);
+    case 2: return launch_fwd_t<2>(tbl, p, vals, out_rgb, out_T, L);
+    case 3: return launch_fwd_t<3>(tbl, p, vals, out_rgb, out_T, L);
+    case 4: return launch_fwd_t<4>(tbl, p, vals, out_rgb, out_T, L);
+    case 5: return launch_fwd_t<5>(tbl, p, vals, out_rgb, out_T, L);
+    case 6: return launch_fwd_t<6>(tbl, p, vals, out_rgb, out_T, L);
+    case 7: return launch_fwd_t<7>(tbl, p, vals, out_rgb, out_T, L);
+    case 8: return launch_fwd_t<8>(tbl, p, vals, out_rgb, out_T, L);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL, const Launch& L) {
+  const u32* vals = sorted_vals(tbl, p);
+  switch (tbl.K) {
+    case 0: return launch_bwd_t<0>(tbl, p, vals, dL, L);
+    case 1: return launch_bwd_t<1>(tbl, p, vals, dL, L);
+    case 2: return launch_bwd_t<2>(tbl, p, vals, dL, L);
+    case 3: return launch_bwd_t<3>(tbl, p, vals, dL, L);
+    case 4: return launch_bwd_t<4>(tbl, p, vals, dL, L);
+    case 5: return launch_bwd_t<5>(tbl, p, vals, dL, L);
+    case 6: return launch_bwd_t<6>(tbl, p, vals, dL, L);
+    case 7: return launch_bwd_t<7>(tbl, p, vals, dL, L);
+    case 8: return launch_bwd_t<8>(tbl, p, vals, dL, L);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gs
