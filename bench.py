@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the 3D Gabor splatting rasterizer (fwd+bwd ms/iter at 1.5M primitives, 1600x1064).
+
+One step = one training iteration of the rasterizer on one view: gabsplat_preprocess ->
+gabsplat_bin_sort -> gabsplat_render_fwd -> L1 loss -> gabsplat_render_bwd (2D adjoint, then
+the attribute chain rule), on the 1.5M-primitive, K=4, SH-degree-3 synthetic scene cycling through
+its 16 orbit poses.  Primitives (450 MB in float32) are larger than L2, so no flush is needed.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--storage bf16]
+
+Multi-GPU runs (torchrun, one rank per GPU) are independent replicas: each rank renders its own
+poses with no collective on the data path (weak scaling); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd ms/iter @1.5M prims 1600x1064; serve p50/p99 ms & frames/s vs plain"
+UNIT = "ms/iter"
+SM_COUNT_B300 = 148
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["f32", "bf16"], default="f32")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 4])
+    ap.add_argument("--K", type=int, default=None, help="override the number of Gabor components")
+    ap.add_argument("--n", type=int, default=None, help="override the primitive count")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(args, n, K, W, H):
+    st = "bf16-storage" if args.storage == "bf16" else "f32"
+    return f"3DGabSplat train iteration: {n} prims K={K} SH3, {W}x{H}, 16 orbit poses, L1 loss, {st}"
+
+
+# ----------------------------------------------------------------------------------------------
+# clocks sampled with nvidia-smi while the timed region runs
+# ----------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, pci_bus_id):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={pci_bus_id}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        busy = [s for s in sm if s > 0.5 * (max(mx) if mx else 2032)]
+        return {"sm_mhz": float(np.median(busy if busy else sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline / reference arm)
+# ----------------------------------------------------------------------------------------------
+def oracle_sample_ms(scene, cam, n_tiles_sample=6, prim_slice=None, seed=0):
+    """Time the FP64 oracle on a bounded sample of one training iteration and scale it to ms/iter.
+
+    Sample: projection + binning of the primitives (all of them, or a 1/prim_slice contiguous slice
+    scaled back up), forward + backward compositing of n_tiles_sample seeded non-empty tiles scaled
+    to all non-empty tiles, and the backward through the projection of the primitives in those
+    tiles scaled to all primitives."""
+    import torch
+
+    from oracle import gabsplat_oracle as O
+    oc = O.default_config()
+    n = scene["means"].shape[0]
+    keys = ("means", "scales", "quats", "opacity", "sh", "freqs", "weights")
+    t0 = time.perf_counter()
+    if prim_slice:
+        m = n // prim_slice
+        part = {k: scene[k][:m] for k in keys}
+        O.bin_spec(part, cam, oc)
+        with torch.no_grad():
+            O.project(O._to_f64(part), cam, oc)
+        t_proj = (time.perf_counter() - t0) * (n / m)
+    else:
+        t_proj = None
+    spec = O.bin_spec(scene, cam, oc)
+    if t_proj is None:
+        with torch.no_grad():
+            O.project(O._to_f64(scene), cam, oc)
+        t_proj = time.perf_counter() - t0
+    L = spec["ranges"][:, 1].astype(np.int64) - spec["ranges"][:, 0]
+    nonempty = np.nonzero(L > 0)[0]
+    rng = np.random.default_rng(seed)
+    tiles = rng.choice(nonempty, min(n_tiles_sample, len(nonempty)), replace=False)
+    ids = np.unique(np.concatenate([spec["sorted_vals"][spec["ranges"][t, 0]:spec["ranges"][t, 1]] for t in tiles]))
+    sub = {k: scene[k][ids] for k in keys}
+    spec_sub = O.bin_spec(sub, cam, oc)
+    g = torch.zeros(3, cam["height"], cam["width"], dtype=torch.float64)
+    t1 = time.perf_counter()
+    leaves = O._to_f64(sub, requires_grad=True)
+    proj = O.project(leaves, cam, oc)
+    rec = {k: proj[k].detach().clone().requires_grad_(True) for k in O.REC_KEYS}
+    tx = spec["tiles_x"]
+    for t in tiles:
+        ty_, tx_ = divmod(int(t), tx)
+        g[:, ty_ * 16:ty_ * 16 + 16, tx_ * 16:tx_ * 16 + 16] = 1e-3
+    O._render_tiles(rec, spec_sub, cam, oc, dL_dC=g, tiles=[int(t) for t in tiles])
+    t_tiles = time.perf_counter() - t1
+    t2 = time.perf_counter()
+    outs = [proj[k] for k in O.REC_KEYS if proj[k].requires_grad]
+    gouts = [rec[k].grad if rec[k].grad is not None else torch.zeros_like(rec[k]) for k in O.REC_KEYS
+             if proj[k].requires_grad]
+    torch.autograd.backward(outs, gouts)
+    t_pbwd = time.perf_counter() - t2
+    ms = 1e3 * (t_proj + t_tiles * len(nonempty) / len(tiles) + t_pbwd * n / max(len(ids), 1))
+    desc = (f"projection+binning of {'1/%d of ' % prim_slice if prim_slice else 'all '}{n} primitives, "
+            f"fwd+bwd compositing of {len(tiles)} of {len(nonempty)} non-empty tiles and the projection "
+            f"backward of their {len(ids)} primitives, each scaled to the full iteration")
+    return ms, desc, time.perf_counter() - t0
+
+
+def run_reference(args):
+    import torch
+    from paper_2508_05343_b300 import scenes
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    torch.set_num_threads(os.cpu_count() or 1)
+    scene = scenes.config_scene(args.config, n=args.n, K=args.K)
+    cams = scenes.config_cameras(args.config)
+    for i in range(args.warmup):
+        oracle_sample_ms(scene, cams[i % len(cams)], n_tiles_sample=2, prim_slice=16, seed=i)
+    times = []
+    for s in range(args.steps):
+        ms, desc, _ = oracle_sample_ms(scene, cams[s % len(cams)], n_tiles_sample=2, prim_slice=16, seed=100 + s)
+        times.append(ms)
+    v = float(np.mean(times))
+    W, H = cams[0]["width"], cams[0]["height"]
+    cores = torch.get_num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 3), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args, scene["n"], scene["K"], W, H) + " (FP64 CPU oracle)"},
+            "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2508_05343_b300 import binding as B
+    from paper_2508_05343_b300 import raster, scenes
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    storage = B.GS_BF16 if args.storage == "bf16" else B.GS_F32
+
+    scene = scenes.config_scene(args.config, n=args.n, K=args.K)
+    cams = scenes.config_cameras(args.config)
+    W, H = cams[0]["width"], cams[0]["height"]
+    n, K, deg = scene["n"], scene["K"], scene["sh_degree"]
+    pt = raster.to_device(scene, dev, storage)
+    targets = [torch.as_tensor(scenes.make_target(W, H, 5000 + j)).to(dev) for j in range(len(cams))]
+    cfg = B.make_config()
+    rast = raster.Rasterizer(n, K, deg, W, H, device=dev)
+    # size the pair capacity for every pose once (host reads; outside the timed region)
+    pose_stats = []
+    for j, c in enumerate(cams):
+        rast.forward(pt, c, cfg, storage=storage)
+        v = rast.views()
+        pose_stats.append(dict(pairs=v["pairs"], n_eval=int(v["n_eval"].sum().item()),
+                               n_contrib=int(v["n_contrib"].sum().item())))
+    maxP = max(s["pairs"] for s in pose_stats)
+    if rast.capacity < maxP * 1.02:
+        rast._alloc(int(maxP * 1.05) + 4096)
+    frame = rast.frame
+    prims_s = B.make_prims(pt, storage)
+    cams_s = [B.make_camera(c) for c in cams]
+    img = torch.empty(3, H, W, device=dev)
+    dL = torch.empty_like(img)
+    loss_val = torch.zeros(1, dtype=torch.float64, device=dev)
+    scratch = torch.empty(B.gabsplat_loss_scratch_bytes(img.numel()), dtype=torch.uint8, device=dev)
+    grads = {k: torch.empty(pt[k].shape, dtype=torch.float32, device=dev) for k in raster.ATTRS}
+    grads["means2d"] = torch.empty(n, 2, device=dev)
+    g_s = B.gs_prim_grads()
+    for k, t in grads.items():
+        setattr(g_s, k, t.data_ptr() if t.numel() else None)
+    npasses = math.ceil((32 + max(1, math.ceil(math.log2(max(2, rast.views()["tiles_x"] * rast.views()["tiles_y"]))))) / 8)
+    launches_per_step = 1 + 1 + (1 + npasses + 1) + 1 + 2 + 1 + 1   # setup, preprocess, sort, fwd, loss, bwd, pbwd
+    stage_names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd"]
+
+    def pose_of(s):
+        return (s + rank * 7) % len(cams)
+
+    def step(s, evs=None, target=None):
+        j = pose_of(s)
+        if evs: evs[0].record()
+        B.gabsplat_preprocess(frame, prims_s, cams_s[j], cfg)
+        if evs: evs[1].record()
+        B.gabsplat_bin_sort(frame)
+        if evs: evs[2].record()
+        B.gabsplat_render_fwd(frame, img, None)
+        if evs: evs[3].record()
+        B.gabsplat_loss(img, targets[j] if target is None else target, B.GS_LOSS_L1, loss_val, dL, scratch)
+        if evs: evs[4].record()
+        B.gabsplat_render_bwd_2d(frame, dL)
+        if evs: evs[5].record()
+        B.gabsplat_preprocess_bwd(frame, g_s)
+        if evs: evs[6].record()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    sampler = ClockSampler(_pci_id(torch.cuda.get_device_properties(dev)))
+    for s in range(args.warmup):
+        step(s)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    start.record()
+    for s in range(args.steps):
+        step(s, evs[s])
+    end.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    st, _ = rast.status()
+    if st != B.GS_OK:
+        raise RuntimeError(f"device status after timed region: {B.status_string(st)}")
+    ms_step = start.elapsed_time(end) / args.steps
+    t = torch.tensor([ms_step], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step_max = float(t.item())
+    stage_ms = {nm: float(np.mean([evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps)]))
+                for i, nm in enumerate(stage_names)}
+
+    # ---- end to end through the public API with host buffers --------------------------------
+    e2e = None
+    if not args.no_e2e:
+        host_t = [targets[j].cpu().pin_memory() for j in range(len(cams))]
+        loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
+        dev_t = torch.empty_like(img)
+        for s in range(min(3, args.steps)):
+            dev_t.copy_(host_t[pose_of(s)], non_blocking=True)
+            step(s, target=dev_t)
+            loss_host.copy_(loss_val, non_blocking=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s in range(args.steps):
+            dev_t.copy_(host_t[pose_of(s)], non_blocking=True)
+            step(s, target=dev_t)
+            loss_host.copy_(loss_val, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        te = torch.tensor([e0.elapsed_time(e1) / args.steps], device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": round(float(te.item()) / world, 4), "unit": UNIT,
+               "h2d_bytes_per_step": int(img.numel() * 4), "d2h_bytes_per_step": 8}
+
+    # ---- roofline of the dominant kernel ------------------------------------------------------
+    poses = [pose_of(s) for s in range(args.steps)]
+    mean = lambda key: float(np.mean([pose_stats[j][key] for j in poses]))
+    P, n_eval, n_contrib = mean("pairs"), mean("n_eval"), mean("n_contrib")
+    sh_b = (deg + 1) ** 2 * 3 * (2 if storage == B.GS_BF16 else 4)
+    g_b = K * 4 * (2 if storage == B.GS_BF16 else 4)
+    param_b = 12 + 12 + 16 + 4 + sh_b + g_b
+    rec_b = (12 + 4 * ((3 * K + 3) // 4)) * 4
+    g2d_b = 4 * ((9 + 3 * K + 3) // 4) * 4
+    fp32_ops_fwd = 13 + 6 * K      # per evaluated pixel-pair: offset, quadratic form, exp, K (phase, cos, weight), alpha
+    fp32_ops_bwd = 43 + 16 * K     # per composited pixel-pair: recomputation + adjoints of Eq. 9-10
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2032.0
+    alu_peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # FP32 TFLOP/s (FMA = 2 ops)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    work = {
+        "preprocess": ("hbm", n * (param_b + rec_b + 8) + P * 12),
+        "bin_sort": ("hbm", P * (8 + npasses * 24 + 8)),
+        "render_fwd": ("alu", n_eval * fp32_ops_fwd + n_contrib * 7),
+        "loss": ("hbm", img.numel() * 12),
+        "render_bwd": ("alu", n_contrib * fp32_ops_bwd),
+        "preprocess_bwd": ("hbm", n * (param_b + g2d_b + param_b)),
+    }
+    top = max(stage_ms, key=stage_ms.get)
+    bound, amount = work[top]
+    sec = stage_ms[top] * 1e-3
+    if bound == "hbm":
+        achieved, peak, unit = amount / sec / 1e9, hbm_peak, "GB/s"
+    else:
+        achieved, peak, unit = amount / sec / 1e12, alu_peak, "TFLOP/s"
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        rec = json.load(open(tf)).get(top)
+        if rec and rec.get("source_sha") == _kernel_source_sha():
+            traffic = rec.get("dram_bytes_per_launch")
+    roofline = {"kernel": top, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": unit,
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if bound == "hbm" else
+                f"derived: 148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock under load)"}
+    stage_fracs = {}
+    for nm, (bd, amt) in work.items():
+        s_ = stage_ms[nm] * 1e-3
+        stage_fracs[nm] = round((amt / s_ / 1e9 / hbm_peak) if bd == "hbm" else (amt / s_ / 1e12 / alu_peak), 4)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import torch as _t
+        _t.set_num_threads(os.cpu_count() or 1)
+        ms, desc, wall = oracle_sample_ms(scene, cams[0], n_tiles_sample=6)
+        cpu = {"value": round(ms, 1), "unit": UNIT, "cores": _t.get_num_threads(), "kind": "oracle", "sample": desc,
+               "wall_s": round(wall, 1)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(ms_step_max / world, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step_max, 4),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if storage == B.GS_F32 else "f32 (bf16 storage)", "data": "synthetic",
+            "config": {"workload": workload_name(args, n, K, W, H), "n": n, "K": K, "sh_degree": deg,
+                       "width": W, "height": H, "storage": args.storage, "poses": len(cams),
+                       "pairs_per_view": round(P), "evaluated_pixel_pairs": round(n_eval),
+                       "composited_pixel_pairs": round(n_contrib),
+                       "l2": "inputs larger than L2 (primitive arrays %.0f MB)" % (n * param_b / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "stage_roofline_frac": stage_fracs,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _pci_id(props):
+    try:
+        return "%08X:%02X:%02X.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except Exception:
+        return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+
+
+def _kernel_source_sha():
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2508_05343_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -136,7 +136,8 @@ typedef struct {
  * touched/offsets [n] uint32; keys [pairs] uint64 = tile << 32 | float bits of depth;
  * values [pairs] uint32 primitive index; ranges [tiles][2] uint32 [start, end);
  * T_final [H][W] float32; n_contrib [H][W] uint32 (1-based position in the tile's list of
- * the last composited pair); grad2d [n][grad2d_floats] float32
+ * the last composited pair); n_eval [H][W] uint32 pairs the forward pass evaluated at the pixel
+ * (its tile's list length, or up to the pair that ended compositing); grad2d [n][grad2d_floats] float32
  *   {d mu_x, d mu_y, d a, d b, d c, d opacity, d r, d g, d b, d f2D (2K), d w (K), 0 pad}. */
 typedef struct {
   float* records;
@@ -149,6 +150,7 @@ typedef struct {
   unsigned* ranges;
   float* T_final;
   unsigned* n_contrib;
+  unsigned* n_eval;
   float* grad2d;
   int record_floats;
   int grad2d_floats;
@@ -194,6 +196,12 @@ gs_status gabsplat_render_fwd(const gs_frame* frame, float* out_rgb, float* out_
  * this frame (their buffers must still hold the same values). */
 gs_status gabsplat_render_bwd(const gs_frame* frame, const float* dL_drgb, const gs_prim_grads* grads,
                               gs_stream stream);
+
+/* The two halves of gabsplat_render_bwd, callable separately (e.g. to time them):
+ * gabsplat_render_bwd_2d accumulates the per-primitive 2D gradients (workspace grad2d) from
+ * dL/d(rgb); gabsplat_preprocess_bwd chains them to the attributes in gs_prim_grads. */
+gs_status gabsplat_render_bwd_2d(const gs_frame* frame, const float* dL_drgb, gs_stream stream);
+gs_status gabsplat_preprocess_bwd(const gs_frame* frame, const gs_prim_grads* grads, gs_stream stream);
 
 /* Photometric loss of Sec. 3.4.1 (its L1 part; L2 for gradient checks): mean over `count` values
  * of |image - target| or (image - target)^2.  Writes the loss (float64, device, 1 value) and

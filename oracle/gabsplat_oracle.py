@@ -252,18 +252,13 @@ def bin_spec(prims_np: dict, cam, cfg) -> dict:
     offsets = np.concatenate([[0], np.cumsum(touched)[:-1]]) if n else np.zeros(0, np.int64)
     P = int(touched.sum())
     depth_bits = tz.astype(f32).view(np.uint32).astype(np.uint64)
-    keys = np.empty(P, np.uint64)
-    vals = np.empty(P, np.uint32)
-    idx = np.nonzero(touched)[0]
-    pos = 0
-    for k in idx:                      # emission order: primitive ascending, tiles row-major
-        ty_r = np.arange(y0[k], y1[k] + 1)
-        tx_r = np.arange(x0[k], x1[k] + 1)
-        tid = (ty_r[:, None] * tiles_x + tx_r[None, :]).reshape(-1).astype(np.uint64)
-        m = tid.size
-        keys[pos:pos + m] = (tid << np.uint64(32)) | depth_bits[k]
-        vals[pos:pos + m] = k
-        pos += m
+    # emission order: primitive ascending, then the primitive's tiles row-major
+    prim_of = np.repeat(np.arange(n), touched)
+    local = np.arange(P) - np.repeat(offsets, touched)
+    wx = (x1 - x0 + 1)[prim_of]
+    tid = ((y0[prim_of] + local // wx) * tiles_x + x0[prim_of] + local % wx).astype(np.uint64)
+    keys = (tid << np.uint64(32)) | depth_bits[prim_of]
+    vals = prim_of.astype(np.uint32)
     order = np.argsort(keys, kind="stable")
     skeys, svals = keys[order], vals[order]
     ntiles = tiles_x * tiles_y

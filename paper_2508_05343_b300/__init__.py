@@ -5,7 +5,7 @@ without loading the CUDA library.
 """
 import importlib
 
-__all__ = ["scenes", "binding", "autograd", "serve"]
+__all__ = ["scenes", "binding", "raster", "serve", "build"]
 
 
 def __getattr__(name):

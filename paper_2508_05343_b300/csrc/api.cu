@@ -41,6 +41,7 @@ WsLayout make_layout(u32 n_prims, int K, u32 n_tiles, u64 n_pixels, u64 capacity
   L.ranges = take((size_t)n_tiles * 8);
   L.T_final = take((size_t)n_pixels * 4);
   L.n_contrib = take((size_t)n_pixels * 4);
+  L.n_eval = take((size_t)n_pixels * 4);
   L.grad2d = take((size_t)n_prims * L.g2d_f * sizeof(float));
   L.total = off;
   return L;
@@ -64,6 +65,7 @@ WsPtrs make_ptrs(const WsLayout& L, void* ws) {
   p.ranges = reinterpret_cast<uint2*>(b + L.ranges);
   p.T_final = reinterpret_cast<float*>(b + L.T_final);
   p.n_contrib = reinterpret_cast<u32*>(b + L.n_contrib);
+  p.n_eval = reinterpret_cast<u32*>(b + L.n_eval);
   p.grad2d = reinterpret_cast<float*>(b + L.grad2d);
   p.capacity = L.capacity;
   p.n_chunks = L.n_chunks;
@@ -201,19 +203,34 @@ gs_status gabsplat_render_fwd(const gs_frame* frame, float* out_rgb, float* out_
   return from_cuda(launch_render_fwd(t, make_ptrs(L, frame->ws), out_rgb, out_T, make_launch(stream)));
 }
 
-gs_status gabsplat_render_bwd(const gs_frame* frame, const float* dL_drgb, const gs_prim_grads* grads,
-                              gs_stream stream) {
+gs_status gabsplat_render_bwd_2d(const gs_frame* frame, const float* dL_drgb, gs_stream stream) {
   FrameTable t;
   WsLayout L;
   const gs_status s = frame_meta(frame, t, L);
   if (s != GS_OK) return s;
-  if (!dL_drgb || !grads) return GS_ERR_INVALID_ARG;
+  if (!dL_drgb) return GS_ERR_INVALID_ARG;
   const WsPtrs p = make_ptrs(L, frame->ws);
   const Launch lc = make_launch(stream);
   cudaError_t e = cudaMemsetAsync(p.grad2d, 0, (size_t)frame->n * L.g2d_f * sizeof(float), lc.stream);
   if (e == cudaSuccess) e = launch_render_bwd(t, p, dL_drgb, lc);
-  if (e == cudaSuccess) e = launch_preprocess_bwd(t, p, *grads, lc);
   return from_cuda(e);
+}
+
+gs_status gabsplat_preprocess_bwd(const gs_frame* frame, const gs_prim_grads* grads, gs_stream stream) {
+  FrameTable t;
+  WsLayout L;
+  const gs_status s = frame_meta(frame, t, L);
+  if (s != GS_OK) return s;
+  if (!grads) return GS_ERR_INVALID_ARG;
+  return from_cuda(launch_preprocess_bwd(t, make_ptrs(L, frame->ws), *grads, make_launch(stream)));
+}
+
+gs_status gabsplat_render_bwd(const gs_frame* frame, const float* dL_drgb, const gs_prim_grads* grads,
+                              gs_stream stream) {
+  if (!grads) return GS_ERR_INVALID_ARG;
+  const gs_status s = gabsplat_render_bwd_2d(frame, dL_drgb, stream);
+  if (s != GS_OK) return s;
+  return gabsplat_preprocess_bwd(frame, grads, stream);
 }
 
 size_t gabsplat_loss_scratch_bytes(long long count) {
@@ -266,6 +283,7 @@ gs_status gabsplat_workspace_views(const gs_frame* frame, gs_ws_views* out) {
   out->ranges = reinterpret_cast<unsigned*>(p.ranges);
   out->T_final = p.T_final;
   out->n_contrib = p.n_contrib;
+  out->n_eval = p.n_eval;
   out->grad2d = p.grad2d;
   out->record_floats = L.rec_f;
   out->grad2d_floats = L.g2d_f;

@@ -79,7 +79,7 @@ struct WsHeader {
 // Offsets of every region of a workspace (host-computed; all 256-byte aligned).
 struct WsLayout {
   size_t header, table, records, touched, offsets, scan_status, keys0, keys1, vals0, vals1, hist,
-      sort_status, ranges, T_final, n_contrib, grad2d, total;
+      sort_status, ranges, T_final, n_contrib, n_eval, grad2d, total;
   u32 n_prims, n_tiles, n_chunks, n_parts;
   u64 n_pixels, capacity;
   int K, rec_f, g2d_f;
@@ -102,6 +102,7 @@ struct WsPtrs {
   uint2* ranges;      // [n_tiles]
   float* T_final;     // [n_pixels]
   u32* n_contrib;     // [n_pixels]
+  u32* n_eval;        // [n_pixels] pairs the forward pass evaluated per pixel
   float* grad2d;      // [n_prims][g2d_f]
   u64 capacity;
   u32 n_chunks, n_parts;

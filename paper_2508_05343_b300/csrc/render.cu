@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(BLOCK) k_render_fwd(WsPtrs p, const u32* __res
     const uint2 rg = p.ranges[tile];
     const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    u32 last = 0;
+    u32 last = 0, evaluated = rg.y - rg.x;
     bool done = !inside;
     for (u32 start = rg.x; start < rg.y; start += BLOCK) {
       if (__syncthreads_count(done) == BLOCK) break;
@@ -106,7 +106,11 @@ __global__ void __launch_bounds__(BLOCK) k_render_fwd(WsPtrs p, const u32* __res
         const float alpha = fminf(amax, __fmul_rn(__fmul_rn(h1.z, G), bank));
         if (alpha < amin) continue;
         const float test = __fmul_rn(T, __fsub_rn(1.f, alpha));
-        if (test < Tmin) { done = true; break; }
+        if (test < Tmin) {
+          done = true;
+          evaluated = start + (u32)j + 1u - rg.x;
+          break;
+        }
         const float4 c = r[2];
         const float wgt = alpha * T;
         C0 = __fmaf_rn(c.x, wgt, C0);
@@ -128,6 +132,7 @@ __global__ void __launch_bounds__(BLOCK) k_render_fwd(WsPtrs p, const u32* __res
       if (oT) oT[pix] = T;
       p.T_final[V.pix_base + pix] = T;
       p.n_contrib[V.pix_base + pix] = last;
+      p.n_eval[V.pix_base + pix] = evaluated;
     }
     __syncthreads();
   }

@@ -175,8 +175,13 @@ __global__ void k_tile_ranges(WsPtrs p, const u64* __restrict__ keys) {
   if (read_status(p.hdr) != 0) return;
   const u64 Pall = p.hdr->pairs;
   const u64 P = Pall < p.capacity ? Pall : p.capacity;
+  const u32 ntiles = p.tbl->total_tiles;
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (u64)gridDim.x * blockDim.x) {
     const u32 t = (u32)(keys[i] >> 32);
+    if (t >= ntiles) {   // cannot happen for keys this frame emitted; guards the table write
+      set_status(p.hdr, GS_ERR_INVALID_ARG);
+      continue;
+    }
     if (i == 0 || (u32)(keys[i - 1] >> 32) != t) p.ranges[t].x = (u32)i;
     if (i + 1 == P || (u32)(keys[i + 1] >> 32) != t) p.ranges[t].y = (u32)(i + 1);
   }

@@ -1,0 +1,150 @@
+"""Frame-level helpers over the C ABI: a workspace-owning Rasterizer and the autograd Function.
+
+Device memory comes from PyTorch's caching allocator; the library itself never allocates.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+ATTRS = ("means", "scales", "quats", "opacity", "sh", "freqs", "weights")
+
+
+def to_device(prims: dict, device="cuda", storage=B.GS_F32) -> dict:
+    """numpy scene (scenes.make_scene) -> contiguous CUDA tensors; sh/freqs/weights in bf16 if asked."""
+    out = {}
+    for k in ATTRS:
+        a = torch.as_tensor(np.ascontiguousarray(prims[k]), dtype=torch.float32)
+        if storage == B.GS_BF16 and k in ("sh", "freqs", "weights"):
+            a = a.to(torch.bfloat16)     # round-to-nearest-even
+        out[k] = a.to(device).contiguous()
+    return out
+
+
+class Rasterizer:
+    """One frame's workspace: n primitives with K Gabor components, one camera resolution."""
+
+    def __init__(self, n, K, sh_degree, width, height, pair_capacity=None, device="cuda"):
+        self.n, self.K, self.sh_degree, self.width, self.height = n, K, sh_degree, width, height
+        self.device = torch.device(device)
+        self.frame = B.gs_frame()
+        self._alloc(pair_capacity if pair_capacity is not None else max(1 << 16, 8 * n))
+        self._loss_scratch = None
+
+    def _alloc(self, cap):
+        cap = int(cap)
+        nbytes = B.gabsplat_workspace_size(self.n, self.K, self.sh_degree, self.width, self.height, cap)
+        if nbytes == 0:
+            raise ValueError("invalid frame sizes")
+        self.ws = None
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        f = self.frame
+        f.n, f.K, f.sh_degree, f.width, f.height = self.n, self.K, self.sh_degree, self.width, self.height
+        f.reserved, f.pair_capacity, f.ws, f.ws_bytes = 0, cap, self.ws.data_ptr(), nbytes
+        B.gabsplat_workspace_init(f)
+        self.capacity = cap
+
+    # ---- stages -------------------------------------------------------------------------
+    def forward(self, prims_t: dict, camera: dict, cfg: B.gs_config, storage=B.GS_F32, out_rgb=None, out_T=None,
+                auto_capacity=True):
+        """preprocess -> bin_sort -> render_fwd.  With auto_capacity the pair count is read back once
+        (a host synchronisation) and the workspace regrown if it overflowed."""
+        self._prims = B.make_prims(prims_t, storage)
+        self._cam = B.make_camera(camera)
+        self._cfg = cfg
+        self._keep = prims_t
+        if out_rgb is None:
+            out_rgb = torch.empty(3, self.height, self.width, device=self.device)
+        for _ in range(2):
+            B.gabsplat_preprocess(self.frame, self._prims, self._cam, cfg)
+            B.gabsplat_bin_sort(self.frame)
+            B.gabsplat_render_fwd(self.frame, out_rgb, out_T)
+            if not auto_capacity:
+                break
+            st, pairs = B.gabsplat_device_status(self.frame)
+            if st == B.GS_ERR_CAPACITY:
+                self._alloc(int(pairs * 1.25) + 1024)
+                continue
+            if st != B.GS_OK:
+                raise B.GabsplatError("render (device status)", st)
+            break
+        return out_rgb
+
+    def backward(self, dL_drgb: torch.Tensor, grads: dict | None = None):
+        if grads is None:
+            grads = {k: torch.empty(self._keep[k].shape, dtype=torch.float32, device=self.device) for k in ATTRS}
+            grads["means2d"] = torch.empty(self.n, 2, device=self.device)
+        g = B.gs_prim_grads()
+        for k in ATTRS + ("means2d",):
+            t = grads.get(k)
+            setattr(g, k, t.data_ptr() if (t is not None and t.numel() > 0) else None)
+        B.gabsplat_render_bwd(self.frame, dL_drgb.contiguous(), g)
+        return grads
+
+    def loss(self, image, target, kind=B.GS_LOSS_L1):
+        if self._loss_scratch is None:
+            self._loss_scratch = torch.empty(B.gabsplat_loss_scratch_bytes(image.numel()), dtype=torch.uint8,
+                                             device=self.device)
+            self._loss_val = torch.empty(1, dtype=torch.float64, device=self.device)
+        dL = torch.empty_like(image)
+        B.gabsplat_loss(image, target, kind, self._loss_val, dL, self._loss_scratch)
+        return self._loss_val, dL
+
+    def status(self):
+        return B.gabsplat_device_status(self.frame)
+
+    # ---- workspace inspection (tests) ----------------------------------------------------
+    def views(self) -> dict:
+        v = B.gabsplat_workspace_views(self.frame)
+        base = self.ws.data_ptr()
+        _, pairs = self.status()
+        P = min(pairs, self.capacity)
+        ntiles = v.tiles_x * v.tiles_y
+        npix = self.width * self.height
+
+        def sl(ptr, count, dtype):
+            off = ptr - base
+            nb = count * torch.empty(0, dtype=dtype).element_size()
+            return self.ws[off:off + nb].view(dtype)
+
+        return dict(
+            records=sl(v.records, self.n * v.record_floats, torch.float32).view(self.n, v.record_floats),
+            touched=sl(v.touched, self.n, torch.int32), offsets=sl(v.offsets, self.n, torch.int32),
+            keys_sorted=sl(v.keys_sorted, P, torch.int64), values_sorted=sl(v.values_sorted, P, torch.int32),
+            ranges=sl(v.ranges, 2 * ntiles, torch.int32).view(ntiles, 2),
+            T_final=sl(v.T_final, npix, torch.float32).view(self.height, self.width),
+            n_contrib=sl(v.n_contrib, npix, torch.int32).view(self.height, self.width),
+            n_eval=sl(v.n_eval, npix, torch.int32).view(self.height, self.width),
+            grad2d=sl(v.grad2d, self.n * v.grad2d_floats, torch.float32).view(self.n, v.grad2d_floats),
+            pairs=pairs, tiles_x=v.tiles_x, tiles_y=v.tiles_y,
+            record_floats=v.record_floats, grad2d_floats=v.grad2d_floats)
+
+
+class GabSplatRender(torch.autograd.Function):
+    """image = render(primitives, camera); backward via the hand-written adjoint kernels.
+
+    Inputs are activated attributes (exp / sigmoid are applied by the caller in torch)."""
+
+    @staticmethod
+    def forward(ctx, rast: Rasterizer, camera: dict, cfg, means, scales, quats, opacity, sh, freqs, weights):
+        prims = dict(means=means.contiguous(), scales=scales.contiguous(), quats=quats.contiguous(),
+                     opacity=opacity.contiguous(), sh=sh.contiguous(), freqs=freqs.contiguous(),
+                     weights=weights.contiguous())
+        storage = B.GS_BF16 if sh.dtype == torch.bfloat16 else B.GS_F32
+        img = rast.forward(prims, camera, cfg, storage=storage)
+        ctx.rast = rast
+        ctx.dtypes = [t.dtype for t in (means, scales, quats, opacity, sh, freqs, weights)]
+        return img
+
+    @staticmethod
+    def backward(ctx, grad_img):
+        g = ctx.rast.backward(grad_img.contiguous())
+        outs = [g[k] for k in ATTRS]
+        outs = [o.to(dt) if o.dtype != dt else o for o, dt in zip(outs, ctx.dtypes)]
+        return (None, None, None, *outs)
+
+
+def render(rast: Rasterizer, camera: dict, cfg, means, scales, quats, opacity, sh, freqs, weights):
+    return GabSplatRender.apply(rast, camera, cfg, means, scales, quats, opacity, sh, freqs, weights)

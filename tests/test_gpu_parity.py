@@ -1,0 +1,280 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bars: tile lists / sort keys / ranges / touched counts bit-exact; images within 2e-4 max-abs per
+channel (pixels where float32 and float64 may branch differently at alpha_min or T_min get the
+extra allowance of one skipped pair and are counted); gradients within 1e-3 relative L2 per
+attribute group of the oracle's analytic gradients and of its central finite differences.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gabsplat_oracle as O
+from paper_2508_05343_b300 import scenes
+from tests.conftest import cuda_available
+from tests.gpu_util import (AMBIG_EXTRA, ATTRS, GRAD_TOL, IMG_TOL, assert_image_parity, bf16_prims, cfg_pair,
+                            compare_images, gpu_grads, gpu_render, rel_l2)
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_available(), reason="needs a CUDA device")]
+
+
+def check_binning(r, spec):
+    v = r.views()
+    assert v["pairs"] == spec["P"]
+    np.testing.assert_array_equal(v["touched"].cpu().numpy().astype(np.int64), spec["touched"])
+    valid = spec["touched"] > 0
+    np.testing.assert_array_equal(v["offsets"].cpu().numpy().astype(np.int64)[valid], spec["offsets"][valid])
+    np.testing.assert_array_equal(v["keys_sorted"].cpu().numpy().view(np.uint64), spec["sorted_keys"])
+    np.testing.assert_array_equal(v["values_sorted"].cpu().numpy().view(np.uint32), spec["sorted_vals"])
+    np.testing.assert_array_equal(v["ranges"].cpu().numpy().view(np.uint32), spec["ranges"])
+    return v
+
+
+def check_records(v, out, prims):
+    """Projected records vs the float64 projection (valid primitives only)."""
+    spec, proj = out["spec"], out["proj"]
+    valid = spec["valid"]
+    rec = v["records"].cpu().numpy().astype(np.float64)[valid]
+    K = prims["weights"].shape[1]
+    np.testing.assert_allclose(rec[:, 0:2], proj["mu2d"].numpy()[valid], rtol=1e-5, atol=1e-3)
+    conic = proj["conic"].numpy()[valid]
+    scale = np.abs(conic).max(1, keepdims=True)
+    assert np.abs(rec[:, 2:5] - conic).max() <= 1e-3 * scale.max()
+    assert (np.abs(rec[:, 2:5] - conic) / scale).max() < 1e-3
+    np.testing.assert_allclose(rec[:, 5], proj["opacity"].numpy()[valid], rtol=1e-6)
+    np.testing.assert_allclose(rec[:, 8:11], proj["rgb"].numpy()[valid], atol=2e-5)
+    if K:
+        f2d = proj["f2d"].numpy()[valid].reshape(-1, 2 * K)
+        err = np.abs(rec[:, 12:12 + 2 * K] - f2d)
+        assert np.quantile(err / (np.abs(f2d) + 1e-3), 0.999) < 1e-3
+        np.testing.assert_allclose(rec[:, 12 + 2 * K:12 + 3 * K], proj["weights"].numpy()[valid], rtol=1e-6)
+
+
+@pytest.mark.parametrize("eps2d", [0.3, 0.0])
+def test_config0_every_stage(eps2d):
+    prims, cam = scenes.config_scene(0), scenes.config_cameras(0)[0]
+    oc, gc = cfg_pair(eps2d=eps2d)
+    out = O.render(prims, cam, oc)
+    r, _, img, T = gpu_render(prims, cam, gc)
+    v = check_binning(r, out["spec"])
+    check_records(v, out, prims)
+    assert_image_parity(img.cpu().numpy(), out)
+    amb = out["ambiguous"].numpy()
+    np.testing.assert_allclose(T.cpu().numpy()[~amb], out["T"].numpy()[~amb], atol=IMG_TOL)
+    nc = v["n_contrib"].cpu().numpy()
+    assert (nc[~amb] == out["n_contrib"].numpy()[~amb]).mean() > 0.999
+
+
+def test_config1_forward_bitexact_bins_and_image():
+    prims, cam = scenes.config_scene(1), scenes.config_cameras(1)[0]
+    oc, gc = cfg_pair()
+    out = O.render(prims, cam, oc)
+    r, _, img, _ = gpu_render(prims, cam, gc)
+    v = check_binning(r, out["spec"])
+    check_records(v, out, prims)
+    assert_image_parity(img.cpu().numpy(), out)
+
+
+def _masked_l2_grad(img_ref, target, amb_bwd):
+    _, g = O.loss_and_grad(img_ref, target, "l2")
+    g[:, amb_bwd] = 0.0          # pixels whose branch may differ contribute nothing to the loss
+    return g
+
+
+def test_config1_gradients_vs_oracle_analytic():
+    prims, cam = scenes.config_scene(1), scenes.config_cameras(1)[0]
+    oc, gc = cfg_pair()
+    out = O.render(prims, cam, oc)
+    target = scenes.make_target(cam["width"], cam["height"], 1101)
+    dL = _masked_l2_grad(out["image"].numpy(), target, out["ambiguous_bwd"].numpy())
+    ref = O.render_backward(prims, cam, oc, dL)
+    r, _, _, _ = gpu_render(prims, cam, gc)
+    g = gpu_grads(r, dL)
+    errs = {k: rel_l2(g[k], ref[k]) for k in ATTRS}
+    # 2D (per-record) gradients too: mu2d, conic, opacity, rgb, f2d, weights
+    g2 = r.views()["grad2d"].cpu().numpy().astype(np.float64)
+    K = prims["weights"].shape[1]
+    r2 = ref["grad2d"]
+    errs["2d.mu"] = rel_l2(g2[:, 0:2], r2["mu2d"])
+    errs["2d.conic"] = rel_l2(g2[:, 2:5], r2["conic"])
+    errs["2d.opacity"] = rel_l2(g2[:, 5], r2["opacity"])
+    errs["2d.rgb"] = rel_l2(g2[:, 6:9], r2["rgb"])
+    errs["2d.f2d"] = rel_l2(g2[:, 9:9 + 2 * K], r2["f2d"].reshape(-1, 2 * K))
+    errs["2d.w"] = rel_l2(g2[:, 9 + 2 * K:9 + 3 * K], r2["weights"])
+    bad = {k: e for k, e in errs.items() if not e <= GRAD_TOL}
+    assert not bad, f"gradient rel-L2 above {GRAD_TOL}: {bad} (all: {errs})"
+
+
+def test_config1_gradients_vs_oracle_finite_differences():
+    """Directional derivatives of the oracle (central differences in float64) along seeded random
+    directions that move a few primitives, against the GPU's analytic gradient."""
+    prims, cam = scenes.config_scene(1), scenes.config_cameras(1)[0]
+    oc, gc = cfg_pair()
+    out = O.render(prims, cam, oc)
+    spec = out["spec"]
+    target = scenes.make_target(cam["width"], cam["height"], 1102)
+    dL = _masked_l2_grad(out["image"].numpy(), target, out["ambiguous_bwd"].numpy())
+    r, _, _, _ = gpu_render(prims, cam, gc)
+    g = gpu_grads(r, dL)
+    rng = np.random.default_rng(77)
+    cand = np.nonzero((spec["touched"] > 0) & (spec["touched"] <= 6))[0]
+    scale = dict(means=0.01, scales=0.005, quats=0.3, opacity=0.05, sh=0.1, freqs=0.5, weights=0.05)
+    p64 = {k: (np.asarray(v, np.float64) if isinstance(v, np.ndarray) else v) for k, v in prims.items()}
+    for trial in range(3):
+        ids = rng.choice(cand, 6, replace=False)
+        tiles = set()
+        for k in ids:
+            x0, x1, y0, y1 = spec["rect"][k]
+            tiles |= {ty * spec["tiles_x"] + tx for ty in range(y0, y1 + 1) for tx in range(x0, x1 + 1)}
+        tiles = sorted(tiles)
+        u = {k: np.zeros_like(p64[k]) for k in ATTRS}
+        for k in ATTRS:
+            u[k][ids] = rng.standard_normal(u[k][ids].shape) * scale[k]
+        analytic = sum(float((g[k].astype(np.float64) * u[k]).sum()) for k in ATTRS)
+
+        def L(h):
+            q = {k: (p64[k] + h * u[k] if k in ATTRS else p64[k]) for k in p64}
+            o = O.render(q, cam, oc, tiles=tiles)
+            return float((o["image"].numpy() * dL).sum())
+
+        h = 1e-4
+        fd = (L(h) - L(-h)) / (2 * h)
+        assert abs(analytic - fd) <= GRAD_TOL * abs(fd) + 1e-9, (trial, analytic, fd)
+
+
+@pytest.mark.parametrize("K,storage,w,h", [(0, 0, 100, 70), (1, 0, 100, 70), (3, 0, 53, 97), (8, 0, 100, 70),
+                                           (2, 1, 100, 70), (4, 1, 64, 48)])
+def test_components_storage_and_ragged_sizes(K, storage, w, h):
+    spec = scenes.SceneSpec(n=600, K=K, sh_degree=2, layout="uniform", box=1.0, log_scale=(-2.8, 0.5))
+    prims = scenes.make_scene(spec, 4242 + K)
+    cam = scenes.orbit_camera(w, h, 30.0 + 10 * K, 15.0, 3.5)
+    oc, gc = cfg_pair(bg=(0.1, 0.2, 0.3))
+    ref_prims = bf16_prims(prims) if storage == 1 else prims
+    out = O.render(ref_prims, cam, oc)
+    r, _, img, _ = gpu_render(prims, cam, gc, storage=storage)
+    check_binning(r, out["spec"])
+    assert_image_parity(img.cpu().numpy(), out)
+    # gradients for the same storage (the oracle consumes the bf16-rounded values)
+    rng = np.random.default_rng(K)
+    dL = rng.standard_normal((3, h, w)) * 1e-3
+    dL[:, out["ambiguous_bwd"].numpy()] = 0.0
+    ref = O.render_backward(ref_prims, cam, oc, dL)
+    g = gpu_grads(r, dL)
+    errs = {k: rel_l2(g[k], ref[k]) for k in ATTRS if ref[k].size}
+    assert all(e <= GRAD_TOL for e in errs.values()), errs
+
+
+def test_empty_scene_and_all_culled():
+    oc, gc = cfg_pair(bg=(0.25, 0.5, 0.75))
+    cam = scenes.orbit_camera(40, 24, 0.0)
+    prims = scenes.make_scene(scenes.SceneSpec(n=0, K=2, sh_degree=1, layout="uniform"), 1)
+    _, _, img, T = gpu_render(prims, cam, gc)
+    np.testing.assert_allclose(img.cpu().numpy(), np.broadcast_to(np.array(oc["bg"])[:, None, None], (3, 24, 40)))
+    np.testing.assert_array_equal(T.cpu().numpy(), 1.0)
+    # every primitive behind the camera
+    prims = scenes.make_scene(scenes.SceneSpec(n=300, K=2, sh_degree=1, layout="uniform", box=0.5), 2)
+    prims["means"] = (prims["means"] + np.array([0, 0, -6.0], np.float32)).astype(np.float32)
+    r, _, img, _ = gpu_render(prims, cam, gc)
+    assert r.views()["pairs"] == 0
+    np.testing.assert_allclose(img.cpu().numpy(), np.broadcast_to(np.array(oc["bg"])[:, None, None], (3, 24, 40)))
+
+
+def test_single_huge_primitive_covers_every_tile():
+    oc, gc = cfg_pair()
+    cam = scenes.orbit_camera(90, 70, 0.0)
+    prims = dict(means=np.zeros((1, 3), np.float32), scales=np.full((1, 3), 3.0, np.float32),
+                 quats=np.array([[1, 0, 0, 0]], np.float32), opacity=np.array([0.7], np.float32),
+                 sh=np.full((1, 1, 3), 0.3, np.float32), freqs=np.array([[[0.2, 0.1, 0.0]]], np.float32),
+                 weights=np.array([[0.4]], np.float32))
+    out = O.render(prims, cam, oc)
+    r, _, img, _ = gpu_render(prims, cam, gc)
+    v = check_binning(r, out["spec"])
+    assert v["pairs"] == 6 * 5
+    assert_image_parity(img.cpu().numpy(), out)
+
+
+def test_capacity_overflow_is_reported_and_recovered():
+    from paper_2508_05343_b300 import binding as B
+    prims, cam = scenes.config_scene(0), scenes.config_cameras(0)[0]
+    oc, gc = cfg_pair()
+    out = O.render(prims, cam, oc)
+    r, pt, img, _ = gpu_render(prims, cam, gc, capacity=100)      # regrown automatically
+    assert r.capacity >= out["spec"]["P"]
+    assert_image_parity(img.cpu().numpy(), out)
+    from paper_2508_05343_b300 import raster
+    r2 = raster.Rasterizer(256, 2, 0, cam["width"], cam["height"], pair_capacity=100)
+    buf = torch.empty(3, cam["height"], cam["width"], device="cuda")
+    r2.forward(pt, cam, gc, out_rgb=buf, auto_capacity=False)
+    st, pairs = r2.status()
+    assert st == B.GS_ERR_CAPACITY and pairs == out["spec"]["P"]
+
+
+def test_nonfinite_input_sets_device_status():
+    from paper_2508_05343_b300 import binding as B
+    from paper_2508_05343_b300 import raster
+    prims, cam = scenes.config_scene(0), scenes.config_cameras(0)[0]
+    _, gc = cfg_pair()
+    prims["scales"] = prims["scales"].copy()
+    prims["scales"][5] = np.nan
+    r = raster.Rasterizer(256, 2, 0, cam["width"], cam["height"])
+    with pytest.raises(B.GabsplatError) as e:
+        r.forward(raster.to_device(prims), cam, gc)
+    assert e.value.status == B.GS_ERR_NONFINITE
+
+
+def test_bounded_lookback_wait_reports_timeout():
+    """Make a look-back wait run out: the sort's partition counter is advanced past partition 0
+    before bin_sort, so partition 0's prefix is never published.  The waiting CTAs give up after
+    their time limit (about a second), set GS_ERR_TIMEOUT and return; the context stays usable."""
+    from paper_2508_05343_b300 import binding as B
+    prims, cam = scenes.config_scene(1), scenes.config_cameras(1)[0]
+    _, gc = cfg_pair()
+    r, pt, _, _ = gpu_render(prims, cam, gc)
+    assert r.views()["pairs"] > 2 * 4096
+    B.gabsplat_preprocess(r.frame, B.make_prims(pt), B.make_camera(cam), gc)
+    SORT_COUNTER0 = 32     # byte offset of sort_counter[0] in the workspace header
+    r.ws[SORT_COUNTER0:SORT_COUNTER0 + 4].view(torch.int32).fill_(1)
+    B.gabsplat_bin_sort(r.frame)
+    st, _ = r.status()
+    assert st == B.GS_ERR_TIMEOUT
+    # the next frame on the same workspace is clean again
+    img = r.forward(pt, cam, gc)
+    assert r.status()[0] == B.GS_OK and torch.isfinite(img).all()
+
+
+def test_full_size_training_view_sampled():
+    """1.5M primitives at 1600x1064 in the benchmark's launch configuration: bins bit-exact against
+    the oracle's binning, images on a seeded sample of tiles (incl. the longest list) against the
+    oracle, and gradients of the primitives in those tiles for a loss restricted to them."""
+    prims, cam = scenes.config_scene(2), scenes.config_cameras(2)[0]
+    oc, gc = cfg_pair()
+    spec = O.bin_spec(prims, cam, oc)
+    r, _, img, _ = gpu_render(prims, cam, gc)
+    check_binning(r, spec)
+    L = spec["ranges"][:, 1].astype(np.int64) - spec["ranges"][:, 0]
+    rng = np.random.default_rng(2)
+    nonempty = np.nonzero(L > 0)[0]
+    tiles = sorted(set(rng.choice(nonempty, 10, replace=False).tolist()) | {int(L.argmax())})
+    out = O.render(prims, cam, oc, tiles=tiles)
+    gi = img.cpu().numpy()
+    tx = spec["tiles_x"]
+    mask = np.zeros((cam["height"], cam["width"]), bool)
+    for t in tiles:
+        mask[(t // tx) * 16:(t // tx) * 16 + 16, (t % tx) * 16:(t % tx) * 16 + 16] = True
+    amb = out["ambiguous"].numpy()
+    err = np.abs(gi - out["image"].numpy()).max(0)
+    assert err[mask & ~amb].max() <= IMG_TOL
+    assert err[mask & amb].max(initial=0.0) <= IMG_TOL + AMBIG_EXTRA
+    # gradients restricted to the sampled tiles
+    dL = np.zeros((3, cam["height"], cam["width"]))
+    dL[:, mask] = np.random.default_rng(3).standard_normal((3, int(mask.sum()))) * 1e-3
+    dL[:, out["ambiguous_bwd"].numpy()] = 0.0
+    g = gpu_grads(r, dL)
+    ids = np.unique(spec["sorted_vals"][np.concatenate([np.arange(spec["ranges"][t, 0], spec["ranges"][t, 1])
+                                                        for t in tiles])])
+    sub = {k: (np.asarray(prims[k])[ids] if isinstance(prims[k], np.ndarray) and prims[k].ndim and
+               prims[k].shape[0] == prims["means"].shape[0] else prims[k]) for k in prims}
+    ref = O.render_backward(sub, cam, oc, dL)
+    for k in ATTRS:
+        e = rel_l2(g[k][ids], ref[k])
+        assert e <= GRAD_TOL, (k, e)
