@@ -364,11 +364,11 @@ def _render_tiles(proj, spec, cam, cfg, dL_dC=None, tiles=None, max_elems=1 << 2
             img[:, gyi, gxi] = bg[:, None]
             continue
         ids = torch.from_numpy(spec["sorted_vals"][s0:s1].astype(np.int64))
-        rec = {k: proj[k].index_select(0, ids) for k in REC_KEYS}
         L = s1 - s0
         chunk = max(1, max_elems // (L * max(K, 1)))
         for c0 in range(0, gxp.shape[0], chunk):
             sl = slice(c0, c0 + chunk)
+            rec = {k: proj[k].index_select(0, ids) for k in REC_KEYS}   # fresh graph per pixel chunk
             C, T, lst, af, ab = composite(gxp[sl], gyp[sl], rec, cfg)
             out = C + T[:, None] * bg[None, :]
             if dL_dC is not None:

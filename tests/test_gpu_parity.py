@@ -26,7 +26,13 @@ def check_binning(r, spec):
     np.testing.assert_array_equal(v["offsets"].cpu().numpy().astype(np.int64)[valid], spec["offsets"][valid])
     np.testing.assert_array_equal(v["keys_sorted"].cpu().numpy().view(np.uint64), spec["sorted_keys"])
     np.testing.assert_array_equal(v["values_sorted"].cpu().numpy().view(np.uint32), spec["sorted_vals"])
-    np.testing.assert_array_equal(v["ranges"].cpu().numpy().view(np.uint32), spec["ranges"])
+    # tile ranges: identical [start, end) for every non-empty tile; empty tiles empty on both sides
+    rg = v["ranges"].cpu().numpy().view(np.uint32).astype(np.int64)
+    ref = spec["ranges"].astype(np.int64)
+    cnt_gpu, cnt_ref = rg[:, 1] - rg[:, 0], ref[:, 1] - ref[:, 0]
+    np.testing.assert_array_equal(cnt_gpu, cnt_ref)
+    nz = cnt_ref > 0
+    np.testing.assert_array_equal(rg[nz], ref[nz])
     return v
 
 
