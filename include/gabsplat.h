@@ -108,7 +108,7 @@ typedef struct {
  * a workspace must not overlap on the device. */
 typedef struct {
   int n, K, sh_degree, width, height;
-  int reserved;
+  int storage;                      /* gs_dtype of sh/freqs/weights; must equal gs_prims.storage */
   unsigned long long pair_capacity; /* most (tile, primitive) pairs the workspace can hold */
   void* ws;                         /* device pointer, 256-byte aligned */
   size_t ws_bytes;

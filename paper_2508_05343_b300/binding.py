@@ -39,7 +39,7 @@ class gs_config(C.Structure):
 
 class gs_frame(C.Structure):
     _fields_ = [("n", C.c_int), ("K", C.c_int), ("sh_degree", C.c_int), ("width", C.c_int), ("height", C.c_int),
-                ("reserved", C.c_int), ("pair_capacity", C.c_ulonglong), ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
+                ("storage", C.c_int), ("pair_capacity", C.c_ulonglong), ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
 
 
 class gs_prim_grads(C.Structure):

@@ -98,8 +98,10 @@ static bool frame_sizes_ok(int n, int K, int sh_degree, int width, int height, u
 static gs_status frame_meta(const gs_frame* f, FrameTable& t, WsLayout& L) {
   if (!f || !f->ws) return GS_ERR_INVALID_ARG;
   if (!frame_sizes_ok(f->n, f->K, f->sh_degree, f->width, f->height, f->pair_capacity)) return GS_ERR_INVALID_ARG;
+  if (f->storage != GS_F32 && f->storage != GS_BF16) return GS_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(f->ws) & 255) return GS_ERR_WORKSPACE;
   memset(&t, 0, sizeof(t));
+  t.storage = f->storage;   // every stage dispatches on the frame's storage type
   const int tx = (f->width + TILE - 1) / TILE, ty = (f->height + TILE - 1) / TILE;
   t.nviews = 1;
   t.K = f->K;
@@ -148,7 +150,7 @@ gs_status gabsplat_preprocess(const gs_frame* frame, const gs_prims* pr, const g
   if (s != GS_OK) return s;
   if (!pr || !cam || !cfg) return GS_ERR_INVALID_ARG;
   if (pr->n != frame->n || pr->K != frame->K || pr->sh_degree != frame->sh_degree) return GS_ERR_INVALID_ARG;
-  if (pr->storage != GS_F32 && pr->storage != GS_BF16) return GS_ERR_INVALID_ARG;
+  if (pr->storage != frame->storage) return GS_ERR_INVALID_ARG;
   if (cam->width != frame->width || cam->height != frame->height) return GS_ERR_INVALID_ARG;
   if (pr->n > 0 && (!pr->means || !pr->scales || !pr->quats || !pr->opacity || !pr->sh)) return GS_ERR_INVALID_ARG;
   if (pr->n > 0 && pr->K > 0 && (!pr->freqs || !pr->weights)) return GS_ERR_INVALID_ARG;

@@ -42,7 +42,7 @@ class Rasterizer:
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         f = self.frame
         f.n, f.K, f.sh_degree, f.width, f.height = self.n, self.K, self.sh_degree, self.width, self.height
-        f.reserved, f.pair_capacity, f.ws, f.ws_bytes = 0, cap, self.ws.data_ptr(), nbytes
+        f.storage, f.pair_capacity, f.ws, f.ws_bytes = getattr(self, 'storage', B.GS_F32), cap, self.ws.data_ptr(), nbytes
         B.gabsplat_workspace_init(f)
         self.capacity = cap
 
@@ -52,6 +52,8 @@ class Rasterizer:
         """preprocess -> bin_sort -> render_fwd.  With auto_capacity the pair count is read back once
         (a host synchronisation) and the workspace regrown if it overflowed."""
         self._prims = B.make_prims(prims_t, storage)
+        self.storage = storage
+        self.frame.storage = storage        # the frame carries the storage type to every stage
         self._cam = B.make_camera(camera)
         self._cfg = cfg
         self._keep = prims_t

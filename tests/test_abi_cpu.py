@@ -66,10 +66,16 @@ def test_invalid_arguments_rejected_on_host(B):
     f.ws, f.ws_bytes = 0x100000, 16         # too small (never dereferenced)
     assert lib.gabsplat_bin_sort(C.byref(f), None) == B.GS_ERR_WORKSPACE
     f.ws_bytes = B.gabsplat_workspace_size(10, 2, 0, 64, 64, 1000)
+    f.storage = 7                           # unknown storage type
+    assert lib.gabsplat_bin_sort(C.byref(f), None) == B.GS_ERR_INVALID_ARG
+    f.storage = B.GS_F32
     cam, cfg, pr = B.gs_camera(), B.make_config(), B.gs_prims()
     pr.n, pr.K, pr.sh_degree = 11, 2, 0     # n does not match the frame
     assert lib.gabsplat_preprocess(C.byref(f), C.byref(pr), C.byref(cam), C.byref(cfg), None) == B.GS_ERR_INVALID_ARG
     pr.n = 10
+    pr.storage = B.GS_BF16                  # storage differs from the frame's
+    assert lib.gabsplat_preprocess(C.byref(f), C.byref(pr), C.byref(cam), C.byref(cfg), None) == B.GS_ERR_INVALID_ARG
+    pr.storage = B.GS_F32
     cam.width, cam.height = 64, 64          # fx = 0: invalid camera (checked before any launch)
     pr.means = pr.scales = pr.quats = pr.opacity = pr.sh = pr.freqs = pr.weights = 0x100000
     assert lib.gabsplat_preprocess(C.byref(f), C.byref(pr), C.byref(cam), C.byref(cfg), None) == B.GS_ERR_INVALID_ARG
