@@ -211,6 +211,25 @@ size_t gabsplat_loss_scratch_bytes(long long count);
 gs_status gabsplat_loss(const float* image, const float* target, long long count, int kind, double* loss_out,
                         float* dL_dimage, void* scratch, gs_stream stream);
 
+/* The loss above without a scratch argument, for callers that cannot allocate device memory:
+ * e.g. a plug-in running inside another engine's frame loop whose allocator owns the device heap,
+ * or a service under a fixed memory budget that allows no allocation once running.  The paper has
+ * no counterpart; this is a packaging variant of gabsplat_loss with the same results (the loss
+ * may differ in the last bits because the per-block sums are grouped differently).
+ *  - The per-block partial sums live in a fixed 64 KB array inside the library (one double per
+ *    4096 values), held by every GPU that loads the library until the process exits.
+ *  - count must be at most GS_LOSS_NOALLOC_MAX_COUNT (33,554,432 values, e.g. a 3 x 3840 x 2160
+ *    image fits); larger counts return GS_ERR_INVALID_ARG without launching anything.
+ *  - The first call on each device looks up the array's device address (with that device
+ *    current); make that first call before any stream capture.
+ *  - All calls share the one array and each call overwrites the slots it reads, so nothing has to
+ *    be cleared between calls, but calls that overlap on the GPU (different streams, or different
+ *    host threads without ordering) race on it.  Issue them in order on one stream.
+ *  - It never calls cudaMalloc, cudaFree or any allocating routine. */
+#define GS_LOSS_NOALLOC_MAX_COUNT 33554432LL
+gs_status gabsplat_loss_noalloc(const float* image, const float* target, long long count, int kind, double* loss_out,
+                                float* dL_dimage, gs_stream stream);
+
 /* Synchronises `stream`, then reads the workspace status word.  *status = device-side
  * gs_status of the last frame, *pairs = number of (tile, primitive) pairs it produced (the
  * required capacity when *status == GS_ERR_CAPACITY).  Either output pointer may be NULL. */

@@ -67,6 +67,8 @@ SIGNATURES = {
     "gabsplat_loss_scratch_bytes": (C.c_size_t, [C.c_longlong]),
     "gabsplat_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),
+    "gabsplat_loss_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p,
+                                        C.c_void_p]),
     "gabsplat_device_status": (C.c_int, [P_(gs_frame), P_(C.c_int), P_(C.c_ulonglong), C.c_void_p]),
     "gabsplat_workspace_views": (C.c_int, [P_(gs_frame), P_(gs_ws_views)]),
     "gabsplat_status_string": (C.c_char_p, [C.c_int]),
@@ -151,6 +153,11 @@ def gabsplat_loss_scratch_bytes(count):
 def gabsplat_loss(image, target, kind, loss_out, dL_dimage, scratch, stream=None):
     _check("gabsplat_loss", lib.gabsplat_loss(_ptr(image), _ptr(target), image.numel(), kind, _ptr(loss_out),
                                               _ptr(dL_dimage), _ptr(scratch), _stream(stream)))
+
+
+def gabsplat_loss_noalloc(image, target, kind, loss_out, dL_dimage, stream=None):
+    _check("gabsplat_loss_noalloc", lib.gabsplat_loss_noalloc(_ptr(image), _ptr(target), image.numel(), kind,
+                                                              _ptr(loss_out), _ptr(dL_dimage), _stream(stream)))
 
 
 def gabsplat_device_status(frame, stream=None):
