@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the primitive count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement (config 3)")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-only", action="store_true")
     return ap.parse_args()
 
 
@@ -158,6 +161,48 @@ def oracle_sample_ms(scene, cam, n_tiles_sample=6, prim_slice=None, seed=0):
             f"fwd+bwd compositing of {len(tiles)} of {len(nonempty)} non-empty tiles and the projection "
             f"backward of their {len(ids)} primitives, each scaled to the full iteration")
     return ms, desc, time.perf_counter() - t0
+
+
+def run_serve(args):
+    """Config 3: 8 resident scenes (100k..3M primitives, K=4, SH3, BF16 storage), a Poisson stream of
+    novel-view requests at 200 req/s with resolutions from {400x400, 800x800, 1280x720, 1920x1080}.
+    The continuous-batching server (graph replays on 3 slots) against the plain float32 path that
+    renders one request at a time; both replay the stream in real time (latency) and then serve the
+    whole stream offered at once (frames/s at saturation)."""
+    import torch
+
+    from paper_2508_05343_b300 import binding as B
+    from paper_2508_05343_b300 import scenes, serve
+    t0 = time.time()
+    sc = scenes.serve_scenes()
+    reqs = serve.make_requests(n_req=args.serve_requests)
+    res = scenes.SERVE_RESOLUTIONS
+    srv = serve.Server(sc, B.GS_BF16, 4, 3, n_slots=3)
+    est = srv.calibrate(res)
+    warm = serve.make_requests(n_req=64, rate=1e6, seed=2001)
+    srv.run(warm, realtime=False)
+    live = srv.run(reqs, realtime=True)
+    sat = srv.run(reqs, realtime=False)
+    del srv
+    torch.cuda.empty_cache()
+    plain = serve.PlainRenderer(sc, est)
+    plain.prepare(reqs)
+    plain.run(warm, realtime=False)
+    p_live = plain.run(reqs, realtime=True)
+    p_sat = plain.run(reqs, realtime=False)
+    del plain
+    torch.cuda.empty_cache()
+    r3 = lambda x: round(float(x), 3)
+    return {"workload": "8 resident scenes {100k..3M} prims K=4 SH3 BF16; %d Poisson requests at 200 req/s; "
+                        "resolutions 400x400/800x800/1280x720/1920x1080; random orbit poses" % len(reqs),
+            "p50_ms": r3(live["latency_ms_p50"]), "p99_ms": r3(live["latency_ms_p99"]),
+            "frames_per_s": r3(sat["frames_per_s"]), "frames_per_s_at_200rps": r3(live["frames_per_s"]),
+            "mean_batch_saturated": r3(sat["mean_batch"]), "mean_batch_200rps": r3(live["mean_batch"]),
+            "retries": live["retries"] + sat["retries"],
+            "plain": {"p50_ms": r3(p_live["latency_ms_p50"]), "p99_ms": r3(p_live["latency_ms_p99"]),
+                      "frames_per_s": r3(p_sat["frames_per_s"]), "storage": "f32", "mode": "one request at a time"},
+            "speedup_frames_per_s": r3(sat["frames_per_s"] / p_sat["frames_per_s"]),
+            "wall_s": round(time.time() - t0, 1)}
 
 
 def run_reference(args):
@@ -368,6 +413,15 @@ def run_ours(args):
         cpu = {"value": round(ms, 1), "unit": UNIT, "cores": _t.get_num_threads(), "kind": "oracle", "sample": desc,
                "wall_s": round(wall, 1)}
 
+    serve_out = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        del rast, pt, targets, grads, img, dL
+        torch.cuda.empty_cache()
+        try:
+            serve_out = run_serve(args)
+        except Exception as e:          # the training line is still reported
+            serve_out = {"error": f"{type(e).__name__}: {e}"}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(ms_step_max / world, 4), "unit": UNIT, "n_gpus": world,
@@ -387,6 +441,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
+            "serve": serve_out,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -414,6 +469,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve_only:
+        print(json.dumps({"serve": run_serve(args)}), flush=True)
     else:
         run_ours(args)
 

@@ -230,6 +230,57 @@ gs_status gabsplat_loss(const float* image, const float* target, long long count
 gs_status gabsplat_loss_noalloc(const float* image, const float* target, long long count, int kind, double* loss_out,
                                 float* dL_dimage, gs_stream stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched frames (serving).  A batch renders up to GS_MAX_VIEWS views -- each a camera with its own
+ * resolution over one resident scene -- with one launch sequence (forward only): the views'
+ * primitives, tiles and pixels are concatenated, so one sort and one persistent compositing launch
+ * serve all of them, and every view's image is bit-identical to rendering that view alone with
+ * gabsplat_preprocess / gabsplat_bin_sort / gabsplat_render_fwd.  All views of a batch share K,
+ * sh_degree and storage (those of the batch frame) and the gs_config.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct {
+  gs_prims prims;   /* device arrays of the view's scene */
+  gs_camera cam;    /* the view's camera and resolution */
+  float* out_rgb;   /* device [3][cam.height][cam.width], required */
+  float* out_T;     /* device [cam.height][cam.width], may be NULL */
+} gs_view;
+
+/* Capacity of a batched workspace: at most max_views views whose primitive counts sum to at most
+ * max_prims, tile counts to max_tiles and pixel counts to max_pixels, with at most pair_capacity
+ * (tile, primitive) pairs in total. */
+typedef struct {
+  int max_views, K, sh_degree, storage;
+  unsigned long long max_prims, max_tiles, max_pixels, pair_capacity;
+  void* ws;          /* device, 256-byte aligned, zero-filled once (gabsplat_batch_workspace_init) */
+  size_t ws_bytes;
+} gs_batch_frame;
+
+size_t gabsplat_batch_workspace_size(int max_views, int K, int sh_degree, unsigned long long max_prims,
+                                     unsigned long long max_tiles, unsigned long long max_pixels,
+                                     unsigned long long pair_capacity);
+gs_status gabsplat_batch_workspace_init(const gs_batch_frame* frame, gs_stream stream);
+
+/* Render `nviews` views (Sec. 3.3, Eq. 9-10 per view) with direct launches on `stream`.
+ * GS_ERR_CAPACITY (host, nothing launched) if the views exceed the frame's primitive, tile or
+ * pixel capacity; pair overflow is reported on the device as for single frames. */
+gs_status gabsplat_render_batch(const gs_batch_frame* frame, const gs_view* views, int nviews, const gs_config* cfg,
+                                gs_stream stream);
+
+/* Asynchronously copies the 16-byte status record {int status; unsigned epoch; unsigned long long pairs}
+ * of the batch's workspace to `dst` (pinned host or device memory) on `stream`. */
+gs_status gabsplat_batch_status_copy(const gs_batch_frame* frame, void* dst, gs_stream stream);
+
+/* A CUDA graph of the batch launch sequence, captured once per workspace on `stream` (which must
+ * not be the legacy default stream) and replayed per batch: each launch writes the new view table
+ * into the graph's first kernel node, so replays need no re-capture.  The graph executor is host
+ * memory allocated by the library (malloc); destroy it with gabsplat_batch_graph_destroy.  Launches
+ * of one graph must not overlap on the device (they share the workspace). */
+typedef struct gs_batch_graph gs_batch_graph;
+gs_status gabsplat_batch_graph_create(const gs_batch_frame* frame, const gs_config* cfg, gs_stream stream,
+                                      gs_batch_graph** out);
+gs_status gabsplat_batch_graph_launch(gs_batch_graph* graph, const gs_view* views, int nviews, gs_stream stream);
+void gabsplat_batch_graph_destroy(gs_batch_graph* graph);
+
 /* Synchronises `stream`, then reads the workspace status word.  *status = device-side
  * gs_status of the last frame, *pairs = number of (tile, primitive) pairs it produced (the
  * required capacity when *status == GS_ERR_CAPACITY).  Either output pointer may be NULL. */

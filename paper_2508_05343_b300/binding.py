@@ -54,6 +54,16 @@ class gs_ws_views(C.Structure):
                 ("grad2d_floats", C.c_int), ("tiles_x", C.c_int), ("tiles_y", C.c_int)]
 
 
+class gs_view(C.Structure):
+    _fields_ = [("prims", gs_prims), ("cam", gs_camera), ("out_rgb", C.c_void_p), ("out_T", C.c_void_p)]
+
+
+class gs_batch_frame(C.Structure):
+    _fields_ = [("max_views", C.c_int), ("K", C.c_int), ("sh_degree", C.c_int), ("storage", C.c_int),
+                ("max_prims", C.c_ulonglong), ("max_tiles", C.c_ulonglong), ("max_pixels", C.c_ulonglong),
+                ("pair_capacity", C.c_ulonglong), ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
+
+
 P_ = C.POINTER
 SIGNATURES = {
     "gabsplat_workspace_size": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_ulonglong]),
@@ -71,6 +81,14 @@ SIGNATURES = {
                                         C.c_void_p]),
     "gabsplat_device_status": (C.c_int, [P_(gs_frame), P_(C.c_int), P_(C.c_ulonglong), C.c_void_p]),
     "gabsplat_workspace_views": (C.c_int, [P_(gs_frame), P_(gs_ws_views)]),
+    "gabsplat_batch_workspace_size": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.c_ulonglong,
+                                                   C.c_ulonglong, C.c_ulonglong]),
+    "gabsplat_batch_workspace_init": (C.c_int, [P_(gs_batch_frame), C.c_void_p]),
+    "gabsplat_render_batch": (C.c_int, [P_(gs_batch_frame), P_(gs_view), C.c_int, P_(gs_config), C.c_void_p]),
+    "gabsplat_batch_status_copy": (C.c_int, [P_(gs_batch_frame), C.c_void_p, C.c_void_p]),
+    "gabsplat_batch_graph_create": (C.c_int, [P_(gs_batch_frame), P_(gs_config), C.c_void_p, P_(C.c_void_p)]),
+    "gabsplat_batch_graph_launch": (C.c_int, [C.c_void_p, P_(gs_view), C.c_int, C.c_void_p]),
+    "gabsplat_batch_graph_destroy": (None, [C.c_void_p]),
     "gabsplat_status_string": (C.c_char_p, [C.c_int]),
     "gabsplat_version": (C.c_char_p, []),
 }
@@ -170,6 +188,56 @@ def gabsplat_device_status(frame, stream=None):
 def gabsplat_workspace_views(frame):
     v = gs_ws_views()
     _check("gabsplat_workspace_views", lib.gabsplat_workspace_views(C.byref(frame), C.byref(v)))
+    return v
+
+
+def gabsplat_batch_workspace_size(max_views, K, sh_degree, max_prims, max_tiles, max_pixels, pair_capacity):
+    return int(lib.gabsplat_batch_workspace_size(max_views, K, sh_degree, max_prims, max_tiles, max_pixels,
+                                                 pair_capacity))
+
+
+def gabsplat_batch_workspace_init(frame, stream=None):
+    _check("gabsplat_batch_workspace_init", lib.gabsplat_batch_workspace_init(C.byref(frame), _stream(stream)))
+
+
+def _view_array(views):
+    arr = (gs_view * max(1, len(views)))()
+    for i, v in enumerate(views):
+        arr[i] = v
+    return arr
+
+
+def gabsplat_render_batch(frame, views, cfg, stream=None):
+    _check("gabsplat_render_batch", lib.gabsplat_render_batch(C.byref(frame), _view_array(views), len(views),
+                                                              C.byref(cfg), _stream(stream)))
+
+
+def gabsplat_batch_status_copy(frame, dst_ptr, stream=None):
+    _check("gabsplat_batch_status_copy", lib.gabsplat_batch_status_copy(C.byref(frame), C.c_void_p(dst_ptr),
+                                                                        _stream(stream)))
+
+
+def gabsplat_batch_graph_create(frame, cfg, stream=None):
+    g = C.c_void_p()
+    _check("gabsplat_batch_graph_create", lib.gabsplat_batch_graph_create(C.byref(frame), C.byref(cfg),
+                                                                          _stream(stream), C.byref(g)))
+    return g
+
+
+def gabsplat_batch_graph_launch(graph, views, stream=None):
+    _check("gabsplat_batch_graph_launch", lib.gabsplat_batch_graph_launch(graph, _view_array(views), len(views),
+                                                                          _stream(stream)))
+
+
+def gabsplat_batch_graph_destroy(graph):
+    lib.gabsplat_batch_graph_destroy(graph)
+
+
+def make_view(prims: "gs_prims", cam: "gs_camera", out_rgb, out_T=None) -> "gs_view":
+    v = gs_view()
+    v.prims, v.cam = prims, cam
+    v.out_rgb = out_rgb.data_ptr()
+    v.out_T = out_T.data_ptr() if out_T is not None else None
     return v
 
 

@@ -87,7 +87,7 @@ static int tile_bits(u32 ntiles) {
   while (b < 32 && ((u64)1 << b) < (u64)ntiles) ++b;
   return b;
 }
-static int sort_passes(u32 ntiles) { return (32 + tile_bits(ntiles) + RADIX_BITS - 1) / RADIX_BITS; }
+int sort_passes(u32 ntiles) { return (32 + tile_bits(ntiles) + RADIX_BITS - 1) / RADIX_BITS; }
 
 static bool frame_sizes_ok(int n, int K, int sh_degree, int width, int height, u64 cap) {
   return n >= 0 && K >= 0 && K <= GS_MAX_K && sh_degree >= 0 && sh_degree <= GS_MAX_SH_DEGREE && width > 0 &&
@@ -110,6 +110,8 @@ static gs_status frame_meta(const gs_frame* f, FrameTable& t, WsLayout& L) {
   t.total_tiles = (u32)(tx * ty);
   t.total_pixels = (u64)f->width * f->height;
   t.npasses = sort_passes(t.total_tiles);
+  t.launch_prims = t.total_prims;
+  t.launch_tiles = t.total_tiles;
   t.v[0].n = f->n;
   t.v[0].width = f->width;
   t.v[0].height = f->height;

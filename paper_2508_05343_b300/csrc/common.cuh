@@ -59,6 +59,7 @@ struct FrameTable {
   float eps2d, alpha_max, alpha_min, T_min;
   float bg[3];
   int npasses;
+  u32 launch_prims, launch_tiles;   // host-side launch sizing (capacity of the workspace); not read on the device
   ViewDesc v[GS_MAX_VIEWS];
 };
 
@@ -109,6 +110,7 @@ struct WsPtrs {
 };
 
 WsLayout make_layout(u32 n_prims, int K, u32 n_tiles, u64 n_pixels, u64 capacity);
+int sort_passes(u32 ntiles);
 WsPtrs make_ptrs(const WsLayout& L, void* ws);
 
 // ------------------------------------------------------------------------------------------

@@ -19,6 +19,8 @@ namespace gs {
 #define FS __fsub_rn
 #define FDV __fdiv_rn
 
+static_assert(sizeof(FrameTable) + sizeof(WsPtrs) <= 4096, "k_setup parameters must fit the classic 4 KB limit");
+
 __global__ void k_setup(FrameTable tbl, WsPtrs p) {
   const u32* src = reinterpret_cast<const u32*>(&tbl);
   u32* dst = reinterpret_cast<u32*>(const_cast<FrameTable*>(p.tbl));
@@ -671,6 +673,8 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
 // ------------------------------------------------------------------------------------------
 // Host launchers
 // ------------------------------------------------------------------------------------------
+const void* setup_kernel_fn() { return reinterpret_cast<const void*>(k_setup); }
+
 int device_sm_count() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -694,7 +698,7 @@ template <int K, int ST>
 static cudaError_t launch_pre_t(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_preprocess<K, ST>, BLOCK, 0, L.sm_count);
-  const int need = (int)((tbl.total_prims + CHUNK - 1) / CHUNK);
+  const int need = (int)((tbl.launch_prims + CHUNK - 1) / CHUNK);
   int g = need < grid ? need : grid;
   if (g < 1) g = 1;
   k_preprocess<K, ST><<<g, BLOCK, 0, L.stream>>>(p);

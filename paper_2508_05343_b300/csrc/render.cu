@@ -381,7 +381,7 @@ static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, const u3
     grid = per_sm * L.sm_count;
   }
   int g = grid;
-  if ((u32)g > tbl.total_tiles) g = (int)tbl.total_tiles;
+  if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
   if (g < 1) g = 1;
   k_render_fwd<K><<<g, BLOCK, smem, L.stream>>>(p, vals, rgb, T);
   return cudaGetLastError();
@@ -402,7 +402,7 @@ static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const u3
     grid = per_sm * L.sm_count;
   }
   int g = grid;
-  if ((u32)g > tbl.total_tiles) g = (int)tbl.total_tiles;
+  if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
   if (g < 1) g = 1;
   k_render_bwd<K><<<g, BLOCK, smem, L.stream>>>(p, vals, dL);
   return cudaGetLastError();

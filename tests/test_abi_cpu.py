@@ -12,7 +12,7 @@ HEADER = os.path.join(ROOT, "include", "gabsplat.h")
 
 def declared_functions():
     src = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:gs_status|size_t|const char\*)\s+(gabsplat_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:gs_status|size_t|const char\*|void)\s+(gabsplat_\w+)\s*\(", src, re.M)))
 
 
 @pytest.fixture(scope="module")
