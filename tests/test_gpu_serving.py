@@ -125,7 +125,8 @@ def test_server_results_same_alone_and_in_the_mix(realtime):
     srv.calibrate(res)
     out = srv.run(reqs, realtime=realtime, keep_images=True)
     assert len(out["images"]) == len(reqs) and out["refused"] == 0
-    assert out["mean_batch"] > 1.0                 # requests really were batched together
+    if not realtime:
+        assert out["mean_batch"] > 1.0             # offered at once, requests are batched together
     for r in reqs:
         ref = alone(prims, (r.scene, r.width, r.height, r.azimuth, r.elevation), B.GS_BF16)
         assert torch.equal(out["images"][r.rid], ref), r
