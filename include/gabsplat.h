@@ -286,7 +286,8 @@ void gabsplat_batch_graph_destroy(gs_batch_graph* graph);
  * required capacity when *status == GS_ERR_CAPACITY).  Either output pointer may be NULL. */
 gs_status gabsplat_device_status(const gs_frame* frame, int* status, unsigned long long* pairs, gs_stream stream);
 
-/* Device pointers into the workspace of `frame` (no device access). */
+/* Device pointers into the workspace of `frame`.  Reads the workspace header with a synchronous
+ * copy (the sorted pairs end in one of two buffers, decided on the device). */
 gs_status gabsplat_workspace_views(const gs_frame* frame, gs_ws_views* out);
 
 /* Human-readable name of a status code (static string). */

@@ -82,12 +82,26 @@ static Launch make_launch(gs_stream s) {
   return L;
 }
 
-static int tile_bits(u32 ntiles) {
+int tile_bits(u32 ntiles) {
   int b = 0;
   while (b < 32 && ((u64)1 << b) < (u64)ntiles) ++b;
   return b;
 }
 int sort_passes(u32 ntiles) { return (32 + tile_bits(ntiles) + RADIX_BITS - 1) / RADIX_BITS; }
+
+// Depth keys of culled-in primitives lie in (bits(znear), bits(zfar)]: positive floats order like their
+// bit patterns, so subtracting bits(znear) leaves a value below 2^depth_bits.
+void set_depth_window(FrameTable& t, float znear_min, float zfar_max) {
+  u32 lo, hi;
+  memcpy(&lo, &znear_min, 4);
+  memcpy(&hi, &zfar_max, 4);
+  int db = 1;
+  while (db < 32 && ((u64)(hi - lo) >> db) != 0) ++db;
+  t.depth_base = lo;
+  t.depth_bits = db;
+  t.npasses_needed = (db + tile_bits(t.total_tiles) + RADIX_BITS - 1) / RADIX_BITS;
+  if (t.npasses_needed > t.npasses) t.npasses_needed = t.npasses;
+}
 
 static bool frame_sizes_ok(int n, int K, int sh_degree, int width, int height, u64 cap) {
   return n >= 0 && K >= 0 && K <= GS_MAX_K && sh_degree >= 0 && sh_degree <= GS_MAX_SH_DEGREE && width > 0 &&
@@ -183,6 +197,7 @@ gs_status gabsplat_preprocess(const gs_frame* frame, const gs_prims* pr, const g
   V.znear = cam->znear; V.zfar = cam->zfar;
   for (int i = 0; i < 3; ++i)   // camera centre -R^T t
     V.campos[i] = -(cam->R[i] * cam->t[0] + cam->R[3 + i] * cam->t[1] + cam->R[6 + i] * cam->t[2]);
+  set_depth_window(t, cam->znear, cam->zfar);
   const WsPtrs p = make_ptrs(L, frame->ws);
   const Launch lc = make_launch(stream);
   cudaError_t e = launch_setup(t, p, lc);
@@ -276,7 +291,9 @@ gs_status gabsplat_workspace_views(const gs_frame* frame, gs_ws_views* out) {
   if (s != GS_OK) return s;
   if (!out) return GS_ERR_INVALID_ARG;
   const WsPtrs p = make_ptrs(L, frame->ws);
-  const bool odd = (t.npasses & 1) != 0;
+  WsHeader h;
+  if (cudaMemcpy(&h, p.hdr, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
+  const bool odd = h.sorted_buf != 0;
   out->records = p.records;
   out->touched = p.touched;
   out->offsets = p.offsets;

@@ -103,6 +103,13 @@ gs_status build_batch_table(const gs_batch_frame* f, const gs_view* views, int n
   t.total_prims = (u32)prims;
   t.total_tiles = (u32)tiles;
   t.total_pixels = pixels;
+  float zn = 3.0e38f, zf = 0.f;
+  for (int v = 0; v < nviews; ++v) {
+    zn = fminf(zn, views[v].cam.znear);
+    zf = fmaxf(zf, views[v].cam.zfar);
+  }
+  if (nviews == 0) zn = zf = 1.f;
+  set_depth_window(t, zn, zf);
   return GS_OK;
 }
 

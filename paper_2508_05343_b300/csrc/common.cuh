@@ -58,7 +58,10 @@ struct FrameTable {
   u64 total_pixels;
   float eps2d, alpha_max, alpha_min, T_min;
   float bg[3];
-  int npasses;
+  int npasses;                      // digit passes launched (worst case for the workspace; host)
+  int npasses_needed;               // passes that do work: ceil((depth_bits + tile bits) / 8)
+  u32 depth_base;                   // float bits of the nearest depth (znear): depth keys minus this fit
+  int depth_bits;                   //   in depth_bits bits, so the sort digits come from (tile, depth - base)
   u32 launch_prims, launch_tiles;   // host-side launch sizing (capacity of the workspace); not read on the device
   ViewDesc v[GS_MAX_VIEWS];
 };
@@ -74,7 +77,8 @@ struct WsHeader {
   u32 nonfinite;            // primitives culled because a projected value was not finite
   u32 sort_counter[MAX_PASSES];
   u32 timeout_site;         // which bounded wait gave up (diagnostics)
-  u32 pad[15];
+  u32 sorted_buf;           // 0: sorted pairs in keys0/vals0, 1: in keys1/vals1
+  u32 pad[14];
 };
 
 // Offsets of every region of a workspace (host-computed; all 256-byte aligned).
@@ -111,6 +115,15 @@ struct WsPtrs {
 
 WsLayout make_layout(u32 n_prims, int K, u32 n_tiles, u64 n_pixels, u64 capacity);
 int sort_passes(u32 ntiles);
+int tile_bits(u32 ntiles);
+void set_depth_window(FrameTable& t, float znear_min, float zfar_max);
+
+// Sort digit source: the 64-bit key (tile << 32 | float bits of depth) re-packed as
+// (tile << depth_bits | depth bits - depth_base), which orders exactly like the key for depths in
+// (znear, zfar] and has 32 - depth_bits fewer significant bits.
+__device__ __forceinline__ u64 sort_value(u64 key, u32 base, int dbits) {
+  return ((key >> 32) << dbits) | (u64)((u32)key - base);
+}
 WsPtrs make_ptrs(const WsLayout& L, void* ws);
 
 // ------------------------------------------------------------------------------------------

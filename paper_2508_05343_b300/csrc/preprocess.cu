@@ -36,6 +36,7 @@ __global__ void k_setup(FrameTable tbl, WsPtrs p) {
     h->tile_counter_bwd = 0;
     h->nonfinite = 0;
     h->timeout_site = 0;
+    h->sorted_buf = (u32)(tbl.npasses_needed & 1);
     for (int i = 0; i < MAX_PASSES; ++i) h->sort_counter[i] = 0;
   }
 }

@@ -61,18 +61,30 @@ __device__ __forceinline__ float filter_bank(const float* r, float w0, float dx,
   return bank;
 }
 
-template <int K>
-__global__ void __launch_bounds__(BLOCK) k_render_fwd(WsPtrs p, const u32* __restrict__ vals, float* out_rgb,
-                                                      float* out_T) {
-  extern __shared__ __align__(16) float4 s_rec[];
+// Pixels per thread of the compositing kernels: a thread owns PPT vertically adjacent pixels of
+// its tile column, so each shared-memory record load and (backward) each warp reduction of the
+// per-pair gradients serves PPT pixels.  CTAs have 256 / PPT threads.
+#ifndef GS_PPT_FWD
+#define GS_PPT_FWD 2
+#endif
+#ifndef GS_PPT_BWD
+#define GS_PPT_BWD 2
+#endif
+
+template <int K, int PPT>
+__global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32* vals, float* out_rgb,
+                                                            float* out_T) {
+  constexpr int NT = BLOCK / PPT;
+  constexpr int F4 = SRec<K>::F4;
+  extern __shared__ __align__(16) float4 s_rec[];   // [NT][F4]
   __shared__ u32 s_tile;
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
   const FrameTable* tbl = p.tbl;
+  if (!vals) vals = (tbl->npasses_needed & 1) ? p.vals1 : p.vals0;
   const int tid = threadIdx.x;
   const u32 ntiles = tbl->total_tiles;
   const float amax = tbl->alpha_max, amin = tbl->alpha_min, Tmin = tbl->T_min;
-  constexpr int F4 = SRec<K>::F4;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&hdr->tile_counter_fwd, 1u);
     __syncthreads();
@@ -82,57 +94,79 @@ __global__ void __launch_bounds__(BLOCK) k_render_fwd(WsPtrs p, const u32* __res
     const ViewDesc& V = tbl->v[v];
     const u32 local = tile - V.tile_base;
     const int tx = (int)(local % (u32)V.tiles_x), ty = (int)(local / (u32)V.tiles_x);
-    const int px = tx * TILE + (tid & (TILE - 1)), py = ty * TILE + (tid >> 4);
-    const bool inside = px < V.width && py < V.height;
+    const int px = tx * TILE + (tid & (TILE - 1)), py0 = ty * TILE + (tid >> 4) * PPT;
     const uint2 rg = p.ranges[tile];
-    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    u32 last = 0, evaluated = rg.y - rg.x;
-    bool done = !inside;
-    for (u32 start = rg.x; start < rg.y; start += BLOCK) {
-      if (__syncthreads_count(done) == BLOCK) break;
+    const float fpx = (float)px + 0.5f;
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    u32 last[PPT], evaluated[PPT];
+    bool done[PPT];
+    bool tdone = true;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      T[q] = 1.f; C0[q] = C1[q] = C2[q] = 0.f;
+      last[q] = 0; evaluated[q] = rg.y - rg.x;
+      done[q] = !(px < V.width && py0 + q < V.height);
+      tdone = tdone && done[q];
+    }
+    for (u32 start = rg.x; start < rg.y; start += NT) {
+      if (__syncthreads_count(tdone) == NT) break;
       const u32 idx = start + tid;
       if (idx < rg.y) stage_record<K>(p.records + (size_t)vals[idx] * rec_floats(K), s_rec + tid * F4, amin);
       __syncthreads();
-      const int cnt = (int)min((u32)BLOCK, rg.y - start);
-      for (int j = 0; !done && j < cnt; ++j) {
+      const int cnt = (int)min((u32)NT, rg.y - start);
+      for (int j = 0; !tdone && j < cnt; ++j) {
         const float4* r = s_rec + j * F4;
         const float4 h0 = r[0], h1 = r[1];
-        const float dx = __fsub_rn(fpx, h0.x), dy = __fsub_rn(fpy, h0.y);
-        const float pw = gauss_power(h0, h1, dx, dy);
-        if (pw < h1.y) continue;
-        const float G = ex2_approx(pw);
-        const float bank = filter_bank<K>(reinterpret_cast<const float*>(r + 3), h1.w, dx, dy);
-        const float alpha = fminf(amax, __fmul_rn(__fmul_rn(h1.z, G), bank));
-        if (alpha < amin) continue;
-        const float test = __fmul_rn(T, __fsub_rn(1.f, alpha));
-        if (test < Tmin) {
-          done = true;
-          evaluated = start + (u32)j + 1u - rg.x;
-          break;
+        const float dx = __fsub_rn(fpx, h0.x);
+        tdone = true;
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+          if (!done[q]) {
+            const float dy = __fsub_rn((float)(py0 + q) + 0.5f, h0.y);
+            const float pw = gauss_power(h0, h1, dx, dy);
+            if (pw >= h1.y) {
+              const float G = ex2_approx(pw);
+              const float bank = filter_bank<K>(reinterpret_cast<const float*>(r + 3), h1.w, dx, dy);
+              const float alpha = fminf(amax, __fmul_rn(__fmul_rn(h1.z, G), bank));
+              if (alpha >= amin) {
+                const float test = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
+                if (test < Tmin) {
+                  done[q] = true;
+                  evaluated[q] = start + (u32)j + 1u - rg.x;
+                } else {
+                  const float4 c = r[2];
+                  const float wgt = alpha * T[q];
+                  C0[q] = __fmaf_rn(c.x, wgt, C0[q]);
+                  C1[q] = __fmaf_rn(c.y, wgt, C1[q]);
+                  C2[q] = __fmaf_rn(c.z, wgt, C2[q]);
+                  T[q] = test;
+                  last[q] = start + (u32)j + 1u - rg.x;
+                }
+              }
+            }
+          }
+          tdone = tdone && done[q];
         }
-        const float4 c = r[2];
-        const float wgt = alpha * T;
-        C0 = __fmaf_rn(c.x, wgt, C0);
-        C1 = __fmaf_rn(c.y, wgt, C1);
-        C2 = __fmaf_rn(c.z, wgt, C2);
-        T = test;
-        last = start + (u32)j + 1u - rg.x;
       }
     }
-    if (inside) {
-      const size_t hw = (size_t)V.width * V.height, pix = (size_t)py * V.width + px;
-      float* orgb = out_rgb ? out_rgb : V.out_rgb;
-      float* oT = out_rgb ? out_T : V.out_T;
-      if (orgb) {
-        orgb[pix] = C0 + T * tbl->bg[0];
-        orgb[hw + pix] = C1 + T * tbl->bg[1];
-        orgb[2 * hw + pix] = C2 + T * tbl->bg[2];
+    float* orgb = out_rgb ? out_rgb : V.out_rgb;
+    float* oT = out_rgb ? out_T : V.out_T;
+    const size_t hw = (size_t)V.width * V.height;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const int py = py0 + q;
+      if (px < V.width && py < V.height) {
+        const size_t pix = (size_t)py * V.width + px;
+        if (orgb) {
+          orgb[pix] = C0[q] + T[q] * tbl->bg[0];
+          orgb[hw + pix] = C1[q] + T[q] * tbl->bg[1];
+          orgb[2 * hw + pix] = C2[q] + T[q] * tbl->bg[2];
+        }
+        if (oT) oT[pix] = T[q];
+        p.T_final[V.pix_base + pix] = T[q];
+        p.n_contrib[V.pix_base + pix] = last[q];
+        p.n_eval[V.pix_base + pix] = evaluated[q];
       }
-      if (oT) oT[pix] = T;
-      p.T_final[V.pix_base + pix] = T;
-      p.n_contrib[V.pix_base + pix] = last;
-      p.n_eval[V.pix_base + pix] = evaluated;
     }
     __syncthreads();
   }
@@ -154,23 +188,25 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[32], int lane) {
   return v[0];
 }
 
-template <int K>
-__global__ void __launch_bounds__(BLOCK) k_render_bwd(WsPtrs p, const u32* __restrict__ vals,
-                                                      const float* __restrict__ dL_drgb) {
+template <int K, int PPT>
+__global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32* vals,
+                                                            const float* __restrict__ dL_drgb) {
+  constexpr int NT = BLOCK / PPT;
   constexpr int F4 = SRec<K>::F4;
   constexpr int NV = 9 + 3 * K;          // gradient values per pair
   constexpr int NG = g2d_floats(K);      // padded row in global memory
   constexpr int NS = NV;                 // shared accumulator row (odd stride: conflict-free)
   constexpr int NVP = (NV + 31) / 32 * 32;
   extern __shared__ __align__(16) float4 smem4[];
-  float4* s_rec = smem4;                                          // [BLOCK][F4]
-  float* s_acc = reinterpret_cast<float*>(smem4 + BLOCK * F4);    // [BLOCK][NS]
-  u32* s_id = reinterpret_cast<u32*>(s_acc + BLOCK * NS);          // [BLOCK]
+  float4* s_rec = smem4;                                        // [NT][F4]
+  float* s_acc = reinterpret_cast<float*>(smem4 + NT * F4);     // [NT][NS]
+  u32* s_id = reinterpret_cast<u32*>(s_acc + NT * NS);           // [NT]
   __shared__ u32 s_tile;
   __shared__ u32 s_max;
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
   const FrameTable* tbl = p.tbl;
+  if (!vals) vals = (tbl->npasses_needed & 1) ? p.vals1 : p.vals0;
   const int tid = threadIdx.x, lane = tid & 31;
   const u32 ntiles = tbl->total_tiles;
   const float amax = tbl->alpha_max, amin = tbl->alpha_min;
@@ -186,32 +222,40 @@ __global__ void __launch_bounds__(BLOCK) k_render_bwd(WsPtrs p, const u32* __res
     const ViewDesc& V = tbl->v[v];
     const u32 local = tile - V.tile_base;
     const int tx = (int)(local % (u32)V.tiles_x), ty = (int)(local / (u32)V.tiles_x);
-    const int px = tx * TILE + (tid & (TILE - 1)), py = ty * TILE + (tid >> 4);
-    const bool inside = px < V.width && py < V.height;
+    const int px = tx * TILE + (tid & (TILE - 1)), py0 = ty * TILE + (tid >> 4) * PPT;
     const uint2 rg = p.ranges[tile];
-    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const float fpx = (float)px + 0.5f;
     const float* gsrc = dL_drgb ? dL_drgb : V.dL_drgb;
-    float T = 1.f, Tfin = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    u32 last = 0;
-    if (inside) {
-      const size_t hw = (size_t)V.width * V.height, pix = (size_t)py * V.width + px;
-      T = Tfin = p.T_final[V.pix_base + pix];
-      last = p.n_contrib[V.pix_base + pix];
-      g0 = gsrc[pix];
-      g1 = gsrc[hw + pix];
-      g2 = gsrc[2 * hw + pix];
+    const size_t hw = (size_t)V.width * V.height;
+    float T[PPT], Tfin[PPT], g0[PPT], g1[PPT], g2[PPT], bgdot[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
+    u32 last[PPT];
+    u32 wlast = 0;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      T[q] = Tfin[q] = 1.f;
+      g0[q] = g1[q] = g2[q] = 0.f;
+      acc0[q] = acc1[q] = acc2[q] = 0.f;
+      last[q] = 0;
+      const int py = py0 + q;
+      if (px < V.width && py < V.height) {
+        const size_t pix = (size_t)py * V.width + px;
+        T[q] = Tfin[q] = p.T_final[V.pix_base + pix];
+        last[q] = p.n_contrib[V.pix_base + pix];
+        g0[q] = gsrc[pix];
+        g1[q] = gsrc[hw + pix];
+        g2[q] = gsrc[2 * hw + pix];
+      }
+      bgdot[q] = tbl->bg[0] * g0[q] + tbl->bg[1] * g1[q] + tbl->bg[2] * g2[q];
+      wlast = max(wlast, last[q]);
     }
-    const float bgdot = tbl->bg[0] * g0 + tbl->bg[1] * g1 + tbl->bg[2] * g2;
-    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;   // colour of the pairs behind, normalised
     // the last composited pair over the warp / CTA bounds the reverse walk
-    u32 wlast = last;
 #pragma unroll
     for (int o = 16; o; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
     if (lane == 0) atomicMax(&s_max, wlast);
     __syncthreads();
     const u32 end = rg.x + s_max;
     for (u32 bend = end; bend > rg.x;) {
-      const u32 bstart = bend - rg.x > (u32)BLOCK ? bend - BLOCK : rg.x;
+      const u32 bstart = bend - rg.x > (u32)NT ? bend - NT : rg.x;
       const u32 cnt = bend - bstart;
       if ((u32)tid < cnt) {
         const u32 id = vals[bstart + tid];
@@ -231,9 +275,13 @@ __global__ void __launch_bounds__(BLOCK) k_render_bwd(WsPtrs p, const u32* __res
 #pragma unroll
         for (int i = 0; i < NVP; ++i) gv[i] = 0.f;
         bool contrib = false;
-        const float dx = __fsub_rn(fpx, h0.x), dy = __fsub_rn(fpy, h0.y);
-        const float pw = gauss_power(h0, h1, dx, dy);
-        if (pos < last && pw >= h1.y) {
+        const float dx = __fsub_rn(fpx, h0.x);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+          if (pos >= last[q]) continue;
+          const float dy = __fsub_rn((float)(py0 + q) + 0.5f, h0.y);
+          const float pw = gauss_power(h0, h1, dx, dy);
+          if (pw < h1.y) continue;
           const float G = ex2_approx(pw);
           float cs[K > 0 ? K : 1], sn[K > 0 ? K : 1];
           float bank = h1.w;
@@ -247,44 +295,44 @@ __global__ void __launch_bounds__(BLOCK) k_render_bwd(WsPtrs p, const u32* __res
           }
           const float araw = __fmul_rn(__fmul_rn(h1.z, G), bank);
           const float alpha = fminf(amax, araw);
-          if (alpha >= amin) {
-            contrib = true;
-            const float oma = 1.f - alpha;
-            T = T / oma;                                   // transmittance before this pair
-            const float4 c = r[2];
-            const float wgt = alpha * T;
-            gv[6] = wgt * g0;
-            gv[7] = wgt * g1;
-            gv[8] = wgt * g2;
-            float dLda = T * ((c.x - acc0) * g0 + (c.y - acc1) * g1 + (c.z - acc2) * g2) - Tfin * bgdot / oma;
-            acc0 = alpha * c.x + oma * acc0;
-            acc1 = alpha * c.y + oma * acc1;
-            acc2 = alpha * c.z + oma * acc2;
-            if (araw > amax) dLda = 0.f;                   // clamped: no gradient through alpha
-            const float o = h1.z;
-            gv[5] = dLda * G * bank;                       // d opacity
-            const float dLdG = dLda * o * bank;
-            const float dLdbank = dLda * o * G;
-            // log2-domain power p2: G = 2^p2, dG/dp2 = G ln 2
-            const float dLdp2 = dLdG * G * 0.6931471805599453f;
-            gv[2] = dLdp2 * dx * dx;                       // w.r.t. A' (converted at flush)
-            gv[3] = dLdp2 * dx * dy;                       // w.r.t. B'
-            gv[4] = dLdp2 * dy * dy;                       // w.r.t. C'
-            float gdx = dLdp2 * (2.f * h0.z * dx + h0.w * dy);
-            float gdy = dLdp2 * (h0.w * dx + 2.f * h1.x * dy);
+          if (alpha < amin) continue;
+          contrib = true;
+          const float oma = 1.f - alpha;
+          T[q] = T[q] / oma;                               // transmittance before this pair
+          const float4 c = r[2];
+          const float wgt = alpha * T[q];
+          gv[6] += wgt * g0[q];
+          gv[7] += wgt * g1[q];
+          gv[8] += wgt * g2[q];
+          float dLda = T[q] * ((c.x - acc0[q]) * g0[q] + (c.y - acc1[q]) * g1[q] + (c.z - acc2[q]) * g2[q]) -
+                       Tfin[q] * bgdot[q] / oma;
+          acc0[q] = alpha * c.x + oma * acc0[q];
+          acc1[q] = alpha * c.y + oma * acc1[q];
+          acc2[q] = alpha * c.z + oma * acc2[q];
+          if (araw > amax) dLda = 0.f;                     // clamped: no gradient through alpha
+          const float o = h1.z;
+          gv[5] += dLda * G * bank;                        // d opacity
+          const float dLdG = dLda * o * bank;
+          const float dLdbank = dLda * o * G;
+          // log2-domain power p2: G = 2^p2, dG/dp2 = G ln 2
+          const float dLdp2 = dLdG * G * 0.6931471805599453f;
+          gv[2] += dLdp2 * dx * dx;                        // w.r.t. A' (converted at flush)
+          gv[3] += dLdp2 * dx * dy;                        // w.r.t. B'
+          gv[4] += dLdp2 * dy * dy;                        // w.r.t. C'
+          float gdx = dLdp2 * (2.f * h0.z * dx + h0.w * dy);
+          float gdy = dLdp2 * (h0.w * dx + 2.f * h1.x * dy);
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-              const float wi = fw[2 * K + i];
-              gv[9 + 2 * K + i] = dLdbank * (cs[i] - 1.f);           // d w_i
-              const float gph = -dLdbank * wi * sn[i] * TWO_PI;       // d phase (cycles)
-              gv[9 + 2 * i] = gph * dx;
-              gv[9 + 2 * i + 1] = gph * dy;
-              gdx += gph * fw[2 * i];
-              gdy += gph * fw[2 * i + 1];
-            }
-            gv[0] = -gdx;                                  // d mu = - d (pixel - mu)
-            gv[1] = -gdy;
+          for (int i = 0; i < K; ++i) {
+            const float wi = fw[2 * K + i];
+            gv[9 + 2 * K + i] += dLdbank * (cs[i] - 1.f);          // d w_i
+            const float gph = -dLdbank * wi * sn[i] * TWO_PI;       // d phase (cycles)
+            gv[9 + 2 * i] += gph * dx;
+            gv[9 + 2 * i + 1] += gph * dy;
+            gdx += gph * fw[2 * i];
+            gdy += gph * fw[2 * i + 1];
           }
+          gv[0] -= gdx;                                    // d mu = - d (pixel - mu)
+          gv[1] -= gdy;
         }
         if (__ballot_sync(0xffffffffu, contrib)) {
 #pragma unroll
@@ -311,8 +359,8 @@ __global__ void __launch_bounds__(BLOCK) k_render_bwd(WsPtrs p, const u32* __res
         row[4] *= cA;   // C' = -c/2 log2 e
 #pragma unroll
         for (int i = 0; i < NG / 4; ++i) {
-          const float4 q = make_float4(row[4 * i], row[4 * i + 1], row[4 * i + 2], row[4 * i + 3]);
-          if (q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f) atomicAdd(reinterpret_cast<float4*>(dst) + i, q);
+          const float4 qv = make_float4(row[4 * i], row[4 * i + 1], row[4 * i + 2], row[4 * i + 3]);
+          if (qv.x != 0.f || qv.y != 0.f || qv.z != 0.f || qv.w != 0.f) atomicAdd(reinterpret_cast<float4*>(dst) + i, qv);
         }
       }
       __syncthreads();
@@ -370,48 +418,53 @@ cudaError_t launch_loss(const float* img, const float* tgt, long long count, int
 template <int K>
 static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, const u32* vals, float* rgb, float* T,
                                 const Launch& L) {
+  constexpr int PPT = GS_PPT_FWD, NT = BLOCK / PPT;
   static int grid = 0;
-  const size_t smem = (size_t)BLOCK * SRec<K>::F * sizeof(float);
+  const size_t smem = (size_t)NT * SRec<K>::F * sizeof(float);
   if (!grid) {
-    cudaError_t e = cudaFuncSetAttribute(k_render_fwd<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_render_fwd<K, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<K>, BLOCK, smem) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<K, PPT>, NT, smem) != cudaSuccess ||
+        per_sm < 1)
       per_sm = 1;
     grid = per_sm * L.sm_count;
   }
   int g = grid;
   if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
   if (g < 1) g = 1;
-  k_render_fwd<K><<<g, BLOCK, smem, L.stream>>>(p, vals, rgb, T);
+  k_render_fwd<K, PPT><<<g, NT, smem, L.stream>>>(p, vals, rgb, T);
   return cudaGetLastError();
 }
 
 template <int K>
 static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const u32* vals, const float* dL,
                                 const Launch& L) {
+  constexpr int PPT = GS_PPT_BWD, NT = BLOCK / PPT;
   static int grid = 0;
-  const size_t smem = (size_t)BLOCK * SRec<K>::F * sizeof(float) + (size_t)BLOCK * (9 + 3 * K) * sizeof(float) +
-                      (size_t)BLOCK * sizeof(u32);
+  const size_t smem = (size_t)NT * SRec<K>::F * sizeof(float) + (size_t)NT * (9 + 3 * K) * sizeof(float) +
+                      (size_t)NT * sizeof(u32);
   if (!grid) {
-    cudaError_t e = cudaFuncSetAttribute(k_render_bwd<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_render_bwd<K, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<K>, BLOCK, smem) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<K, PPT>, NT, smem) != cudaSuccess ||
+        per_sm < 1)
       per_sm = 1;
     grid = per_sm * L.sm_count;
   }
   int g = grid;
   if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
   if (g < 1) g = 1;
-  k_render_bwd<K><<<g, BLOCK, smem, L.stream>>>(p, vals, dL);
+  k_render_bwd<K, PPT><<<g, NT, smem, L.stream>>>(p, vals, dL);
   return cudaGetLastError();
 }
 
-static const u32* sorted_vals(const FrameTable& tbl, const WsPtrs& p) { return (tbl.npasses & 1) ? p.vals1 : p.vals0; }
 
 cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L) {
-  const u32* vals = sorted_vals(tbl, p);
+  const u32* vals = nullptr;   // chosen on the device: the sort's pass count depends on the depth range
   switch (tbl.K) {
     case 0: return launch_fwd_t<0>(tbl, p, vals, out_rgb, out_T, L);
     case 1: return launch_fwd_t<1>(tbl, p, vals, out_rgb, out_T, L);
@@ -427,7 +480,7 @@ cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out
 }
 
 cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL, const Launch& L) {
-  const u32* vals = sorted_vals(tbl, p);
+  const u32* vals = nullptr;   // chosen on the device: the sort's pass count depends on the depth range
   switch (tbl.K) {
     case 0: return launch_bwd_t<0>(tbl, p, vals, dL, L);
     case 1: return launch_bwd_t<1>(tbl, p, vals, dL, L);

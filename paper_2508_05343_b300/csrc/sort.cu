@@ -17,9 +17,12 @@ __global__ void __launch_bounds__(256) k_digit_hist(WsPtrs p, int npasses) {
   __syncthreads();
   const u64 P = p.hdr->pairs;
   const u64 n = P < p.capacity ? P : p.capacity;
+  const u32 base = p.tbl->depth_base;
+  const int dbits = p.tbl->depth_bits;
+  const int need = min(npasses, p.tbl->npasses_needed);
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
-    const u64 key = p.keys0[i];
-    for (int ps = 0; ps < npasses; ++ps) atomicAdd(&s_h[ps][(key >> (RADIX_BITS * ps)) & (RADIX - 1)], 1u);
+    const u64 v = sort_value(p.keys0[i], base, dbits);
+    for (int ps = 0; ps < need; ++ps) atomicAdd(&s_h[ps][(v >> (RADIX_BITS * ps)) & (RADIX - 1)], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < npasses * RADIX; i += blockDim.x) {
@@ -65,6 +68,9 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* 
   SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
+  if (pass >= p.tbl->npasses_needed) return;   // the remaining digits are zero for every key
+  const u32 dbase = p.tbl->depth_base;
+  const int dbits = p.tbl->depth_bits;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u64 Pall = hdr->pairs;
   const u64 P = Pall < p.capacity ? Pall : p.capacity;
@@ -93,7 +99,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* 
     for (int i = 0; i < SORT_ITEMS; ++i) {
       const u64 idx = wbase + (u64)i * 32 + lane;
       const bool valid = idx < P;
-      const u32 d = (u32)(key[i] >> shift) & (RADIX - 1);
+      const u32 d = (u32)(sort_value(key[i], dbase, dbits) >> shift) & (RADIX - 1);
       const u32 peers = __match_any_sync(0xffffffffu, valid ? d : (RADIX + lane));
       const int leader = __ffs(peers) - 1;
       u32 old = 0;
@@ -152,7 +158,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* 
     for (int i = 0; i < SORT_ITEMS; ++i) {
       const u64 idx = wbase + (u64)i * 32 + lane;
       if (idx < P) {
-        const u32 d = (u32)(key[i] >> shift) & (RADIX - 1);
+        const u32 d = (u32)(sort_value(key[i], dbase, dbits) >> shift) & (RADIX - 1);
         const u32 lp = S.local_excl[d] + S.warp_cnt[warp][d] + rank[i];
         S.keys[lp] = key[i];
         S.vals[lp] = val[i];
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* 
     const u32 nvalid = (u32)((P - base) < (u64)SORT_TILE ? (P - base) : (u64)SORT_TILE);
     for (u32 j = tid; j < nvalid; j += SORT_THREADS) {
       const u64 k = S.keys[j];
-      const u32 d = (u32)(k >> shift) & (RADIX - 1);
+      const u32 d = (u32)(sort_value(k, dbase, dbits) >> shift) & (RADIX - 1);
       const u32 pos = S.glob[d] + j;
       kout[pos] = k;
       vout[pos] = S.vals[j];
@@ -171,8 +177,9 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* 
   }
 }
 
-__global__ void k_tile_ranges(WsPtrs p, const u64* __restrict__ keys) {
+__global__ void k_tile_ranges(WsPtrs p) {
   if (read_status(p.hdr) != 0) return;
+  const u64* __restrict__ keys = (p.tbl->npasses_needed & 1) ? p.keys1 : p.keys0;
   const u64 Pall = p.hdr->pairs;
   const u64 P = Pall < p.capacity ? Pall : p.capacity;
   const u32 ntiles = p.tbl->total_tiles;
@@ -217,7 +224,7 @@ cudaError_t launch_bin_sort(const FrameTable& tbl, const WsPtrs& p, const Launch
     kin = tk;
     vin = tv;
   }
-  k_tile_ranges<<<L.sm_count * 8, 256, 0, L.stream>>>(p, kin);
+  k_tile_ranges<<<L.sm_count * 8, 256, 0, L.stream>>>(p);
   return cudaGetLastError();
 }
 
