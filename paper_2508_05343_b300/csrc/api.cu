@@ -31,6 +31,7 @@ WsLayout make_layout(u32 n_prims, int K, u32 n_tiles, u64 n_pixels, u64 capacity
   L.records = take((size_t)n_prims * L.rec_f * sizeof(float));
   L.touched = take((size_t)n_prims * 4);
   L.offsets = take((size_t)n_prims * 4);
+  L.active = take((size_t)n_prims * 4);
   L.scan_status = take((size_t)(L.n_chunks ? L.n_chunks : 1) * 8);
   L.keys0 = take((size_t)capacity * 8);
   L.keys1 = take((size_t)capacity * 8);
@@ -55,6 +56,7 @@ WsPtrs make_ptrs(const WsLayout& L, void* ws) {
   p.records = reinterpret_cast<float*>(b + L.records);
   p.touched = reinterpret_cast<u32*>(b + L.touched);
   p.offsets = reinterpret_cast<u32*>(b + L.offsets);
+  p.active = reinterpret_cast<u32*>(b + L.active);
   p.scan_status = reinterpret_cast<u64*>(b + L.scan_status);
   p.keys0 = reinterpret_cast<u64*>(b + L.keys0);
   p.keys1 = reinterpret_cast<u64*>(b + L.keys1);

@@ -78,12 +78,13 @@ struct WsHeader {
   u32 sort_counter[MAX_PASSES];
   u32 timeout_site;         // which bounded wait gave up (diagnostics)
   u32 sorted_buf;           // 0: sorted pairs in keys0/vals0, 1: in keys1/vals1
-  u32 pad[14];
+  u32 n_active;             // primitives that touch at least one tile (entries of the active list)
+  u32 pad[13];
 };
 
 // Offsets of every region of a workspace (host-computed; all 256-byte aligned).
 struct WsLayout {
-  size_t header, table, records, touched, offsets, scan_status, keys0, keys1, vals0, vals1, hist,
+  size_t header, table, records, touched, offsets, active, scan_status, keys0, keys1, vals0, vals1, hist,
       sort_status, ranges, T_final, n_contrib, n_eval, grad2d, total;
   u32 n_prims, n_tiles, n_chunks, n_parts;
   u64 n_pixels, capacity;
@@ -97,6 +98,7 @@ struct WsPtrs {
   float* records;
   u32* touched;
   u32* offsets;
+  u32* active;        // [n_prims] indices of primitives that touch a tile (any order)
   u64* scan_status;
   u64* keys0;
   u64* keys1;

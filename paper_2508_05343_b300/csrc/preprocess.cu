@@ -37,6 +37,7 @@ __global__ void k_setup(FrameTable tbl, WsPtrs p) {
     h->nonfinite = 0;
     h->timeout_site = 0;
     h->sorted_buf = (u32)(tbl.npasses_needed & 1);
+    h->n_active = 0;
     for (int i = 0; i < MAX_PASSES; ++i) h->sort_counter[i] = 0;
   }
 }
@@ -217,9 +218,8 @@ __device__ __forceinline__ void bin_spec(const ViewDesc& V, float eps2d, float m
   }
 }
 
-// Project one primitive: binning + the 2D Gabor record.  Returns the touched-tile count.
-template <int K, int STORAGE>
-__device__ __forceinline__ u32 project_one(const FrameTable* tbl, u32 gi, const WsPtrs& p, int& x0, int& y0, int& wx,
+// Bin one primitive (the float32 binning specification).  Returns the touched-tile count.
+__device__ __forceinline__ u32 bin_one(const FrameTable* tbl, u32 gi, const WsPtrs& p, int& x0, int& y0, int& wx,
                                            u32& dbits, u32& tile_base, int& tiles_x, bool& nonfinite) {
   const int v = view_of_prim(tbl, gi);
   const ViewDesc& V = tbl->v[v];
@@ -242,8 +242,23 @@ __device__ __forceinline__ u32 project_one(const FrameTable* tbl, u32 gi, const 
   y0 = b.y0;
   wx = b.x1 - b.x0 + 1;
   dbits = __float_as_uint(b.tz);
-  const u32 cnt = (u32)wx * (u32)(b.y1 - b.y0 + 1);
+  return (u32)wx * (u32)(b.y1 - b.y0 + 1);
+}
 
+// The 2D record of one primitive that touches at least one tile: conic from the float64
+// determinant, colour, splatted frequencies.  Recomputes the binning quantities (bit-identical).
+template <int K, int STORAGE>
+__device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, const WsPtrs& p) {
+  const int v = view_of_prim(tbl, gi);
+  const ViewDesc& V = tbl->v[v];
+  const u32 k = gi - V.prim_base;
+  const float mx = __ldg(V.means + 3 * (size_t)k), my = __ldg(V.means + 3 * (size_t)k + 1),
+              mz = __ldg(V.means + 3 * (size_t)k + 2);
+  const float s0 = __ldg(V.scales + 3 * (size_t)k), s1 = __ldg(V.scales + 3 * (size_t)k + 1),
+              s2 = __ldg(V.scales + 3 * (size_t)k + 2);
+  const float4 q = __ldg(reinterpret_cast<const float4*>(V.quats) + k);
+  BinSpec b;
+  bin_spec(V, tbl->eps2d, mx, my, mz, s0, s1, s2, q, b);
   // ---- 2D record: conic from the float64 determinant, colour, splatted frequencies ----
   const double inv_det = 1.0 / b.det;
   const double da = (double)FA(b.A00, tbl->eps2d), db = (double)b.A01, dc = (double)FA(b.A11, tbl->eps2d);
@@ -309,13 +324,11 @@ __device__ __forceinline__ u32 project_one(const FrameTable* tbl, u32 gi, const 
   float4* dst = reinterpret_cast<float4*>(p.records + (size_t)gi * rec_floats(K));
 #pragma unroll
   for (int i = 0; i < rec_floats(K) / 4; ++i) dst[i] = make_float4(rec[4 * i], rec[4 * i + 1], rec[4 * i + 2], rec[4 * i + 3]);
-  return cnt;
 }
 
 // Preprocess + single-pass (decoupled look-back) exclusive scan of touched-tile counts + key emission.
 // Persistent CTAs take 256-primitive chunks in increasing order from an atomic counter, so every chunk
 // a CTA waits on is held by a CTA that is already running.
-template <int K, int STORAGE>
 __global__ void __launch_bounds__(BLOCK) k_preprocess(WsPtrs p) {
   __shared__ u32 s_chunk;
   __shared__ u32 s_warp[BLOCK / 32];
@@ -336,7 +349,14 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess(WsPtrs p) {
     int x0 = 0, y0 = 0, wx = 1, tiles_x = 1;
     u32 dbits = 0, tile_base = 0, cnt = 0;
     bool nonfinite = false;
-    if (gi < total) cnt = project_one<K, STORAGE>(tbl, gi, p, x0, y0, wx, dbits, tile_base, tiles_x, nonfinite);
+    if (gi < total) cnt = bin_one(tbl, gi, p, x0, y0, wx, dbits, tile_base, tiles_x, nonfinite);
+    {   // append the primitives that touch a tile to the active list (warp-aggregated atomic)
+      const u32 ballot = __ballot_sync(0xffffffffu, cnt > 0);
+      u32 base = 0;
+      if (lane == 0 && ballot) base = atomicAdd(&hdr->n_active, (u32)__popc(ballot));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (cnt > 0) p.active[base + __popc(ballot & ((1u << lane) - 1u))] = gi;
+    }
     if (__syncthreads_or(nonfinite)) {
       if (tid == 0) { atomicAdd(&hdr->nonfinite, 1u); set_status(hdr, GS_ERR_NONFINITE); }
     }
@@ -438,6 +458,38 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess(WsPtrs p) {
   }
 }
 
+// 2D records of the active primitives (full warps: culled primitives are not in the list).
+template <int K, int STORAGE>
+__global__ void __launch_bounds__(BLOCK) k_records(WsPtrs p) {
+  if (read_status(p.hdr) != 0) return;
+  const u32 n = p.hdr->n_active;
+  for (u32 i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) record_one<K, STORAGE>(p.tbl, p.active[i], p);
+}
+
+// Zero every attribute gradient (culled primitives keep zeros; active ones are overwritten).
+__device__ __forceinline__ void zero_fill(float* a, size_t count, size_t tid, size_t nthreads) {
+  if (!a) return;
+  size_t head = (16 - (reinterpret_cast<uintptr_t>(a) & 15)) / 4 % 4;   // floats before 16-byte alignment
+  if (head > count) head = count;
+  for (size_t i = tid; i < head; i += nthreads) a[i] = 0.f;
+  float4* v = reinterpret_cast<float4*>(a + head);
+  const size_t n4 = (count - head) / 4;
+  for (size_t i = tid; i < n4; i += nthreads) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (size_t i = head + 4 * n4 + tid; i < count; i += nthreads) a[i] = 0.f;
+}
+
+__global__ void k_zero_grads(gs_prim_grads G, int n, int K, int nsh) {
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
+  zero_fill(G.means, 3 * (size_t)n, tid, nt);
+  zero_fill(G.scales, 3 * (size_t)n, tid, nt);
+  zero_fill(G.quats, 4 * (size_t)n, tid, nt);
+  zero_fill(G.opacity, (size_t)n, tid, nt);
+  zero_fill(G.sh, (size_t)n * nsh * 3, tid, nt);
+  zero_fill(G.freqs, (size_t)n * K * 3, tid, nt);
+  zero_fill(G.weights, (size_t)n * K, tid, nt);
+  zero_fill(G.means2d, 2 * (size_t)n, tid, nt);
+}
+
 // ------------------------------------------------------------------------------------------
 // Backward: 2D record gradients -> primitive attribute gradients (exact chain rule of the
 // forward above; clamps pass zero gradient).
@@ -447,12 +499,13 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
   const FrameTable* tbl = p.tbl;
   if (read_status(p.hdr) != 0) return;
   const ViewDesc& V = tbl->v[0];
-  const int n = V.n;
   const int deg = V.sh_degree;
   const int nsh = (deg + 1) * (deg + 1);
-  for (int k = blockIdx.x * BLOCK + threadIdx.x; k < n; k += gridDim.x * BLOCK) {
-    const u32 gi = V.prim_base + k;
-    const bool active = p.touched[gi] != 0;
+  const u32 n_act = p.hdr->n_active;
+  for (u32 ia = blockIdx.x * BLOCK + threadIdx.x; ia < n_act; ia += gridDim.x * BLOCK) {
+    const u32 gi = p.active[ia];
+    const int k = (int)(gi - V.prim_base);
+    const bool active = true;
     float g2[g2d_floats(K)];
     if (active) {
       const float4* src = reinterpret_cast<const float4*>(p.grad2d + (size_t)gi * g2d_floats(K));
@@ -697,20 +750,28 @@ cudaError_t launch_setup(const FrameTable& tbl, const WsPtrs& p, const Launch& L
 
 template <int K, int ST>
 static cudaError_t launch_pre_t(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
-  static int grid = 0;
-  if (!grid) grid = persistent_grid(k_preprocess<K, ST>, BLOCK, 0, L.sm_count);
+  static int grid = 0, rgrid = 0;
+  if (!grid) grid = persistent_grid(k_preprocess, BLOCK, 0, L.sm_count);
+  if (!rgrid) rgrid = persistent_grid(k_records<K, ST>, BLOCK, 0, L.sm_count);
   const int need = (int)((tbl.launch_prims + CHUNK - 1) / CHUNK);
   int g = need < grid ? need : grid;
   if (g < 1) g = 1;
-  k_preprocess<K, ST><<<g, BLOCK, 0, L.stream>>>(p);
+  k_preprocess<<<g, BLOCK, 0, L.stream>>>(p);
+  int rg = need < rgrid ? need : rgrid;
+  if (rg < 1) rg = 1;
+  k_records<K, ST><<<rg, BLOCK, 0, L.stream>>>(p);
   return cudaGetLastError();
 }
 
 template <int K, int ST>
 static cudaError_t launch_pre_bwd_t(const FrameTable& tbl, const WsPtrs& p, const gs_prim_grads& g, const Launch& L) {
+  static int grid = 0;
+  if (!grid) grid = persistent_grid(k_preprocess_bwd<K, ST>, BLOCK, 0, L.sm_count);
   const int n = tbl.v[0].n;
+  const int nsh = (tbl.sh_degree + 1) * (tbl.sh_degree + 1);
+  k_zero_grads<<<L.sm_count * 4, 256, 0, L.stream>>>(g, n, K, nsh);
   int blocks = (n + BLOCK - 1) / BLOCK;
-  if (blocks > L.sm_count * 8) blocks = L.sm_count * 8;
+  if (blocks > grid) blocks = grid;
   if (blocks < 1) blocks = 1;
   k_preprocess_bwd<K, ST><<<blocks, BLOCK, 0, L.stream>>>(p, g);
   return cudaGetLastError();

@@ -298,14 +298,15 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
           if (alpha < amin) continue;
           contrib = true;
           const float oma = 1.f - alpha;
-          T[q] = T[q] / oma;                               // transmittance before this pair
+          const float ioma = __frcp_rn(oma);
+          T[q] = T[q] * ioma;                              // transmittance before this pair
           const float4 c = r[2];
           const float wgt = alpha * T[q];
           gv[6] += wgt * g0[q];
           gv[7] += wgt * g1[q];
           gv[8] += wgt * g2[q];
           float dLda = T[q] * ((c.x - acc0[q]) * g0[q] + (c.y - acc1[q]) * g1[q] + (c.z - acc2[q]) * g2[q]) -
-                       Tfin[q] * bgdot[q] / oma;
+                       Tfin[q] * bgdot[q] * ioma;
           acc0[q] = alpha * c.x + oma * acc0[q];
           acc1[q] = alpha * c.y + oma * acc1[q];
           acc2[q] = alpha * c.z + oma * acc2[q];
