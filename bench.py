@@ -48,12 +48,16 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement (config 3)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="config 4: K in {0,1,2,4,8} x {f32, bf16}, one line each, with the oracle crop error")
+    ap.add_argument("--oracle-crop", action="store_true",
+                    help="also compare pose 0 with the FP64 oracle on the 256x256 centre crop")
     return ap.parse_args()
 
 
-def workload_name(args, n, K, W, H):
+def workload_name(args, n, K, W, H, poses=16):
     st = "bf16-storage" if args.storage == "bf16" else "f32"
-    return f"3DGabSplat train iteration: {n} prims K={K} SH3, {W}x{H}, 16 orbit poses, L1 loss, {st}"
+    return f"3DGabSplat train iteration: {n} prims K={K} SH3, {W}x{H}, {poses} orbit poses, L1 loss, {st}"
 
 
 # ----------------------------------------------------------------------------------------------
@@ -205,6 +209,40 @@ def run_serve(args):
             "wall_s": round(time.time() - t0, 1)}
 
 
+def oracle_crop_error(scene, cam, gpu_img, storage_bf16):
+    """Error of the GPU image against the FP64 oracle on the 256x256 centre crop of a 1920x1080 view
+    (pixels [832,1088) x [412,668)): evaluation error against the oracle on the same (BF16-rounded
+    when stored so) values, and for BF16 storage the quantisation error against float32 values."""
+    import torch
+
+    from oracle import gabsplat_oracle as O
+    from paper_2508_05343_b300 import scenes
+    torch.set_num_threads(os.cpu_count() or 1)
+    W, H = cam["width"], cam["height"]
+    x0, y0 = (W - 256) // 2, (H - 256) // 2
+    x1, y1 = x0 + 256, y0 + 256
+    tx = (W + 15) // 16
+    tiles = [ty * tx + t for ty in range(y0 // 16, (y1 - 1) // 16 + 1) for t in range(x0 // 16, (x1 - 1) // 16 + 1)]
+    oc = O.default_config()
+    psnr = lambda e: float(10 * np.log10(1.0 / max(float(np.mean(e ** 2)), 1e-30)))
+    out = {}
+    variants = [("eval", {k: scenes.bf16_round(scene[k]) if storage_bf16 and k in ("sh", "freqs", "weights")
+                          else scene[k] for k in scene})]
+    if storage_bf16:
+        variants.append(("quant", scene))
+    t0 = time.time()
+    for name, prims in variants:
+        ref = O.render(prims, cam, oc, tiles=tiles)
+        e = (gpu_img[:, y0:y1, x0:x1] - ref["image"].numpy()[:, y0:y1, x0:x1])
+        amb = ref["ambiguous"].numpy()[y0:y1, x0:x1]
+        err = np.abs(e).max(0)
+        out[name] = {"max_abs_unambiguous": float(err[~amb].max()), "max_abs": float(err.max()), "psnr_db": round(psnr(e), 2),
+                     "ambiguous_px": int(amb.sum())}
+    out["crop"] = f"[{x0},{x1})x[{y0},{y1})"
+    out["oracle_wall_s"] = round(time.time() - t0, 1)
+    return out
+
+
 def run_reference(args):
     import torch
     from paper_2508_05343_b300 import scenes
@@ -226,7 +264,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 3), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args, scene["n"], scene["K"], W, H) + " (FP64 CPU oracle)"},
+            "config": {"workload": workload_name(args, scene["n"], scene["K"], W, H, len(cams)) + " (FP64 CPU oracle)"},
             "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -265,6 +303,7 @@ def run_ours(args):
         rast.forward(pt, c, cfg, storage=storage)
         v = rast.views()
         pose_stats.append(dict(pairs=v["pairs"], n_eval=int(v["n_eval"].sum().item()),
+                               active=int((v["touched"] > 0).sum().item()),
                                n_contrib=int(v["n_contrib"].sum().item())))
     maxP = max(s["pairs"] for s in pose_stats)
     if rast.capacity < maxP * 1.02:
@@ -281,8 +320,15 @@ def run_ours(args):
     g_s = B.gs_prim_grads()
     for k, t in grads.items():
         setattr(g_s, k, t.data_ptr() if t.numel() else None)
-    npasses = math.ceil((32 + max(1, math.ceil(math.log2(max(2, rast.views()["tiles_x"] * rast.views()["tiles_y"]))))) / 8)
-    launches_per_step = 1 + 1 + (1 + npasses + 1) + 1 + 2 + 1 + 1   # setup, preprocess, sort, fwd, loss, bwd, pbwd
+    vv = rast.views()
+    tbits = max(0, math.ceil(math.log2(max(1, vv["tiles_x"] * vv["tiles_y"]))))
+    npasses = math.ceil((32 + tbits) / 8)                    # launched
+    zb = lambda z: int(np.float32(z).view(np.uint32))
+    dbits = max(1, (zb(cams[0]["zfar"]) - zb(cams[0]["znear"])).bit_length())
+    npasses_needed = min(npasses, math.ceil((dbits + tbits) / 8))   # passes that do work
+    # my kernels per step: setup, preprocess + records, histogram + passes + ranges, render_fwd,
+    # loss (2), render_bwd, zero-fill + preprocess_bwd
+    launches_per_step = 1 + 2 + (1 + npasses + 1) + 1 + 2 + 1 + 2
     stage_names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd"]
 
     def pose_of(s):
@@ -362,12 +408,13 @@ def run_ours(args):
     # ---- roofline of the dominant kernel ------------------------------------------------------
     poses = [pose_of(s) for s in range(args.steps)]
     mean = lambda key: float(np.mean([pose_stats[j][key] for j in poses]))
-    P, n_eval, n_contrib = mean("pairs"), mean("n_eval"), mean("n_contrib")
+    P, n_eval, n_contrib, n_act = mean("pairs"), mean("n_eval"), mean("n_contrib"), mean("active")
     sh_b = (deg + 1) ** 2 * 3 * (2 if storage == B.GS_BF16 else 4)
     g_b = K * 4 * (2 if storage == B.GS_BF16 else 4)
     param_b = 12 + 12 + 16 + 4 + sh_b + g_b
     rec_b = (12 + 4 * ((3 * K + 3) // 4)) * 4
     g2d_b = 4 * ((9 + 3 * K + 3) // 4) * 4
+    grad_b = 4 * (3 + 3 + 4 + 1 + (deg + 1) ** 2 * 3 + 3 * K + K + 2)
     fp32_ops_fwd = 13 + 6 * K      # per evaluated pixel-pair: offset, quadratic form, exp, K (phase, cos, weight), alpha
     fp32_ops_bwd = 43 + 16 * K     # per composited pixel-pair: recomputation + adjoints of Eq. 9-10
     sm_mhz = (clocks or {}).get("sm_mhz") or 2032.0
@@ -376,12 +423,14 @@ def run_ours(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
     work = {
-        "preprocess": ("hbm", n * (param_b + rec_b + 8) + P * 12),
-        "bin_sort": ("hbm", P * (8 + npasses * 24 + 8)),
+        # all primitives: mean/scale/quat read, counts written; active ones: attributes read, record written
+        "preprocess": ("hbm", n * (40 + 8) + n_act * (4 + param_b + rec_b) + P * 12),
+        "bin_sort": ("hbm", P * (8 + npasses_needed * 24 + 8)),
         "render_fwd": ("alu", n_eval * fp32_ops_fwd + n_contrib * 7),
         "loss": ("hbm", img.numel() * 12),
         "render_bwd": ("alu", n_contrib * fp32_ops_bwd),
-        "preprocess_bwd": ("hbm", n * (param_b + g2d_b + param_b)),
+        # gradients of every primitive written (zeros for culled ones), active ones read their inputs
+        "preprocess_bwd": ("hbm", n * grad_b + n_act * (4 + param_b + g2d_b + grad_b)),
     }
     top = max(stage_ms, key=stage_ms.get)
     bound, amount = work[top]
@@ -404,6 +453,13 @@ def run_ours(args):
     for nm, (bd, amt) in work.items():
         s_ = stage_ms[nm] * 1e-3
         stage_fracs[nm] = round((amt / s_ / 1e9 / hbm_peak) if bd == "hbm" else (amt / s_ / 1e12 / alu_peak), 4)
+
+    crop = None
+    if rank == 0 and args.oracle_crop:
+        img0 = rast.forward(pt, cams[0], cfg, storage=storage)
+        torch.cuda.synchronize()
+        crop = oracle_crop_error({k: scene[k] for k in raster.ATTRS}, cams[0], img0.cpu().numpy().astype(np.float64),
+                                 storage == B.GS_BF16)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -428,7 +484,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step_max, 4),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if storage == B.GS_F32 else "f32 (bf16 storage)", "data": "synthetic",
-            "config": {"workload": workload_name(args, n, K, W, H), "n": n, "K": K, "sh_degree": deg,
+            "config": {"workload": workload_name(args, n, K, W, H, len(cams)), "n": n, "K": K, "sh_degree": deg,
                        "width": W, "height": H, "storage": args.storage, "poses": len(cams),
                        "pairs_per_view": round(P), "evaluated_pixel_pairs": round(n_eval),
                        "composited_pixel_pairs": round(n_contrib),
@@ -442,6 +498,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "serve": serve_out,
+            "oracle_crop": crop,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -469,6 +526,15 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        base = list(sys.argv[1:])
+        for K in (0, 1, 2, 4, 8):
+            for st in ("f32", "bf16"):
+                sys.argv = [sys.argv[0], "--config", "4", "--K", str(K), "--storage", st, "--steps", str(args.steps),
+                            "--warmup", str(args.warmup), "--no-cpu-baseline", "--no-e2e", "--no-serve",
+                            "--oracle-crop"]
+                run_ours(parse())
+        sys.argv = [sys.argv[0]] + base
     elif args.serve_only:
         print(json.dumps({"serve": run_serve(args)}), flush=True)
     else:

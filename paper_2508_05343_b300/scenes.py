@@ -72,7 +72,7 @@ CONFIGS = {
         CameraSpec(1600, 1064, poses=[(22.5 * j, 0.0) for j in range(16)])),
     4: (SceneSpec(n=3_000_000, K=4, sh_degree=3, layout="mixture+shell", box=4.0, n_clusters=64,
                   shell_frac=0.2, log_scale=(-4.0, 0.7)),
-        CameraSpec(1920, 1080)),
+        CameraSpec(1920, 1080, poses=[(22.5 * j, 0.0) for j in range(16)])),
 }
 SERVE_SCENE_SIZES = [100_000, 250_000, 500_000, 1_000_000, 1_500_000, 2_000_000, 2_500_000, 3_000_000]
 SERVE_RESOLUTIONS = [(400, 400), (800, 800), (1280, 720), (1920, 1080)]
