@@ -177,13 +177,61 @@ def project(prims: dict, cam, cfg, third_row: str = "z") -> dict:
 # ----------------------------------------------------------------------------------------------
 # Binning specification (float32, fixed op order; integer results must match the GPU bit for bit)
 # ----------------------------------------------------------------------------------------------
-def bin_spec(prims_np: dict, cam, cfg) -> dict:
+LN2_UP = np.float32(0.693147182464599609375)   # the float32 just above ln 2
+
+
+def _tile_reachable(prims_np, prim_of, tile_x, tile_y, mux, muy, ca, cb, cc, det, cfg):
+    """Which (primitive, tile) pairs of the 3-sigma squares can give some pixel alpha >= alpha_min.
+
+    alpha = o G(x) bank(x) <= o G(x) because the filter bank is at most 1, so a pixel needs
+    q(x) = (x - mu)^T Sigma2D^-1 (x - mu) <= 2 ln(o / alpha_min).  A tile is kept if the minimum of q
+    over the box spanned by its pixel centres is at most an upper bound of that threshold; dropping
+    the other tiles removes only pairs that every pixel skips, so the image is unchanged.  All in
+    float32, single correctly rounded operations in the written order:
+      conic = (c, -b, a) / float32(det);  x = o / alpha_min = m 2^e (frexp, m in [0.5, 1));
+      m2 = 2 m, t = (e - 1) LN2_UP + (m2 - 1) / sqrt(m2)  (>= ln x since ln m2 <= (m2 - 1)/sqrt m2);
+      thr = (2 t) (1 + 2^-10) + 2^-6  (margin for float32 evaluation);  o < alpha_min reaches nothing;
+      box: xl = (16 tx + 0.5) - mu_x, xh = (16 tx + 15.5) - mu_x (same for y); q_min = 0 if the box
+      holds the mean, else the least of the four edge minima, edge x = e: s = clip(-(B e) / C, lo, hi),
+      q = ((A e) e + ((2 B) e) s) + (C s) s, and the same with A, C and x, y swapped for y-edges.
+    """
+    f32 = np.float32
+    with np.errstate(all="ignore"):
+        op = np.asarray(prims_np["opacity"], f32)
+        amin = f32(cfg["alpha_min"])
+        det32 = det.astype(f32)
+        A, B, Cc = (cc / det32)[prim_of], (-cb / det32)[prim_of], (ca / det32)[prim_of]
+        xq = op / amin
+        mq, eq = np.frexp(xq)
+        m2 = mq * f32(2)
+        t = (eq - 1).astype(f32) * LN2_UP + (m2 - f32(1)) / np.sqrt(m2)
+        thr = ((f32(2) * t) * f32(1 + 2 ** -10) + f32(2 ** -6))[prim_of]
+        reach = (op >= amin)[prim_of]
+        mx, my = mux[prim_of], muy[prim_of]
+        bx, by = (tile_x * 16).astype(f32), (tile_y * 16).astype(f32)
+        xl, xh = (bx + f32(0.5)) - mx, (bx + f32(15.5)) - mx
+        yl, yh = (by + f32(0.5)) - my, (by + f32(15.5)) - my
+
+        def edge(a_, b_, c_, e, lo, hi):
+            s = np.minimum(np.maximum(-(b_ * e) / c_, lo), hi)
+            return ((a_ * e) * e + ((f32(2) * b_) * e) * s) + (c_ * s) * s
+
+        qmin = np.minimum(np.minimum(edge(A, B, Cc, xl, yl, yh), edge(A, B, Cc, xh, yl, yh)),
+                          np.minimum(edge(Cc, B, A, yl, xl, xh), edge(Cc, B, A, yh, xl, xh)))
+        inside = (xl <= 0) & (xh >= 0) & (yl <= 0) & (yh >= 0)
+        qmin = np.where(inside, f32(0), qmin)
+    return reach & (qmin <= thr)
+
+
+def bin_spec(prims_np: dict, cam, cfg, cull: bool = True) -> dict:
     """Tile binning per the written float32 specification.
 
     Every float32 operation below is a single IEEE round-to-nearest operation in the stated order
     (numpy never fuses multiply-add).  Determinant, eigenvalue and radius are float64 functions of
-    the float32 covariance entries.  Returns per-primitive depth/mean/covariance/radius/rect,
-    the emitted (key, value) pairs in emission order, the stably sorted pairs and tile ranges.
+    the float32 covariance entries.  A primitive's tiles are those of its 3-sigma square that some
+    pixel can reach (see _tile_reachable; cull=False keeps the whole square, which renders the same
+    image).  Returns per-primitive depth/mean/covariance/radius/rect, the emitted (key, value) pairs
+    in emission order, the stably sorted pairs and tile ranges.
     """
     f32 = np.float32
     mu = np.asarray(prims_np["means"], f32)
@@ -248,15 +296,22 @@ def bin_spec(prims_np: dict, cam, cfg) -> dict:
     x1 = np.where(valid, np.clip(x1, 0, tiles_x - 1), -1).astype(np.int64)
     y0 = np.where(valid, np.clip(y0, 0, tiles_y - 1), 0).astype(np.int64)
     y1 = np.where(valid, np.clip(y1, 0, tiles_y - 1), -1).astype(np.int64)
-    touched = np.where(valid, (x1 - x0 + 1) * (y1 - y0 + 1), 0).astype(np.int64)
+    # tiles of the 3-sigma square, in emission order: primitive ascending, then row-major
+    sq_count = np.where(valid, (x1 - x0 + 1) * (y1 - y0 + 1), 0).astype(np.int64)
+    sq_off = np.concatenate([[0], np.cumsum(sq_count)[:-1]]) if n else np.zeros(0, np.int64)
+    prim_of = np.repeat(np.arange(n), sq_count)
+    local = np.arange(int(sq_count.sum())) - np.repeat(sq_off, sq_count)
+    wx = (x1 - x0 + 1)[prim_of]
+    tile_y = y0[prim_of] + local // wx
+    tile_x = x0[prim_of] + local % wx
+    if cull:
+        keep = _tile_reachable(prims_np, prim_of, tile_x, tile_y, mux, muy, ca, cb, cc, det, cfg)
+        prim_of, tile_x, tile_y = prim_of[keep], tile_x[keep], tile_y[keep]
+    touched = np.bincount(prim_of, minlength=n).astype(np.int64)
     offsets = np.concatenate([[0], np.cumsum(touched)[:-1]]) if n else np.zeros(0, np.int64)
     P = int(touched.sum())
     depth_bits = tz.astype(f32).view(np.uint32).astype(np.uint64)
-    # emission order: primitive ascending, then the primitive's tiles row-major
-    prim_of = np.repeat(np.arange(n), touched)
-    local = np.arange(P) - np.repeat(offsets, touched)
-    wx = (x1 - x0 + 1)[prim_of]
-    tid = ((y0[prim_of] + local // wx) * tiles_x + x0[prim_of] + local % wx).astype(np.uint64)
+    tid = (tile_y * tiles_x + tile_x).astype(np.uint64)
     keys = (tid << np.uint64(32)) | depth_bits[prim_of]
     vals = prim_of.astype(np.uint32)
     order = np.argsort(keys, kind="stable")
@@ -268,6 +323,7 @@ def bin_spec(prims_np: dict, cam, cfg) -> dict:
     ranges = np.stack([starts, ends], -1).astype(np.uint32)
     return dict(depth=tz, mu2d=np.stack([mux, muy], -1), cov2d=np.stack([ca, cb, cc], -1), radius=rad,
                 valid=valid, rect=np.stack([x0, x1, y0, y1], -1), touched=touched, offsets=offsets, P=P,
+                square_count=sq_count,
                 keys=keys, vals=vals, sorted_keys=skeys, sorted_vals=svals, ranges=ranges,
                 tiles_x=tiles_x, tiles_y=tiles_y)
 
@@ -382,9 +438,9 @@ def _render_tiles(proj, spec, cam, cfg, dL_dC=None, tiles=None, max_elems=1 << 2
     return dict(image=img, T=Tf, n_contrib=last, ambiguous=amb_f, ambiguous_bwd=amb_b)
 
 
-def render(prims: dict, cam, cfg, tiles=None, third_row="z") -> dict:
+def render(prims: dict, cam, cfg, tiles=None, third_row="z", cull=True) -> dict:
     """Forward render in float64.  prims: numpy arrays (means, scales, quats, opacity, sh, freqs, weights)."""
-    spec = bin_spec(prims, cam, cfg)
+    spec = bin_spec(prims, cam, cfg, cull=cull)
     with torch.no_grad():
         proj = project(_to_f64(prims), cam, cfg, third_row)
     out = _render_tiles(proj, spec, cam, cfg, tiles=tiles)

@@ -329,35 +329,68 @@ def test_brute_force_matches_tiled_oracle(seed, n, K):
     cfg = O.default_config(bg=(0.2, 0.0, 0.5))
     prims = tiny_scene(seed, n=n, K=K, log_scale=(-2.2, 0.4))
     prims["opacity"] = np.clip(prims["opacity"] * 1.4, 0, 0.999).astype(np.float32)   # exercise the stop rule
-    out = O.render(prims, cam, cfg)
-    img, T, last = _brute_force(prims, cam, cfg)
+    out = O.render(prims, cam, cfg)                     # tiles culled to those a pixel can reach
+    img, T, last = _brute_force(prims, cam, cfg)        # every tile of the 3-sigma squares
     np.testing.assert_allclose(out["image"].numpy(), img, atol=1e-12)
     np.testing.assert_allclose(out["T"].numpy(), T, atol=1e-12)
-    np.testing.assert_array_equal(out["n_contrib"].numpy(), last)
+    full = O.render(prims, cam, cfg, cull=False)       # list positions refer to the full squares
+    np.testing.assert_array_equal(full["n_contrib"].numpy(), last)
 
 
 def test_binning_rects_and_sorted_keys_brute_force():
+    """Pairs = tiles of each primitive's 3-sigma square (interval overlap, brute force) that some pixel
+    centre can reach with o G >= alpha_min (float64 over the 256 centres): every such pair must be
+    emitted, and every emitted pair must be within the specification's margin of reaching; the
+    sorted keys must be Python's sort of the emission list."""
     cam = tiny_camera(72, 56, dist=2.0)
     cfg = O.default_config()
     prims = tiny_scene(14, n=60, K=1, log_scale=(-2.0, 0.6))
     spec = O.bin_spec(prims, cam, cfg)
     tx_n, ty_n = spec["tiles_x"], spec["tiles_y"]
-    pairs = []
+    emitted = {(int(k) >> 32, int(v)) for k, v in zip(spec["keys"], spec["vals"])}
+    must, may = set(), set()
     for k in range(60):
         if not spec["valid"][k]:
             continue
         mx, my, r = float(spec["mu2d"][k, 0]), float(spec["mu2d"][k, 1]), float(spec["radius"][k])
+        a, b, c = (float(x) for x in spec["cov2d"][k])
+        det = a * c - b * b
+        Qa, Qb, Qc = c / det, -b / det, a / det
+        o = float(np.float32(prims["opacity"][k]))
+        thr = 2 * math.log(o / cfg["alpha_min"]) if o >= cfg["alpha_min"] else -1.0
         for ty in range(ty_n):
             for tx in range(tx_n):
-                if 16 * tx <= mx + r and 16 * tx + 16 > mx - r and 16 * ty <= my + r and 16 * ty + 16 > my - r:
-                    pairs.append(((ty * tx_n + tx) << 32 | int(np.float32(spec["depth"][k]).view(np.uint32)), k))
-    assert len(pairs) == spec["P"] and spec["P"] > 0
+                if not (16 * tx <= mx + r and 16 * tx + 16 > mx - r and 16 * ty <= my + r and 16 * ty + 16 > my - r):
+                    continue
+                px = 16 * tx + 0.5 + np.arange(16) - mx
+                py = 16 * ty + 0.5 + np.arange(16) - my
+                q = (Qa * px[None] ** 2 + 2 * Qb * px[None] * py[:, None] + Qc * py[:, None] ** 2).min()
+                if q <= thr:
+                    must.add((ty * tx_n + tx, k))
+                if q <= thr * 1.01 + 0.1 and thr > 0:
+                    may.add((ty * tx_n + tx, k))
+    assert must and must <= emitted <= may, (len(must), len(emitted), len(may))
+    pairs = [(int(key), int(v)) for key, v in zip(spec["keys"], spec["vals"])]
     ref = sorted(enumerate(pairs), key=lambda e: (e[1][0], e[0]))
     np.testing.assert_array_equal(spec["sorted_keys"], np.array([p[1][0] for p in ref], np.uint64))
     np.testing.assert_array_equal(spec["sorted_vals"], np.array([p[1][1] for p in ref], np.uint32))
     for tid in range(tx_n * ty_n):
         cnt = sum(1 for p in pairs if p[0] >> 32 == tid)
         assert spec["ranges"][tid, 1] - spec["ranges"][tid, 0] == cnt
+
+
+@pytest.mark.parametrize("cfgi", [0, 1])
+def test_tile_culling_leaves_the_image_unchanged(cfgi):
+    """Dropping the tiles no pixel can reach changes no pixel: culled and full 3-sigma lists render the
+    same float64 image and transmittance up to summation order (config 1 on a block of tiles)."""
+    prims, cam = scenes.config_scene(cfgi), scenes.config_cameras(cfgi)[0]
+    cfg = O.default_config()
+    tiles = None if cfgi == 0 else [ty * 50 + tx for ty in range(20, 26) for tx in range(20, 28)]
+    a = O.render(prims, cam, cfg, tiles=tiles)
+    b = O.render(prims, cam, cfg, tiles=tiles, cull=False)
+    assert a["spec"]["P"] < 0.8 * b["spec"]["P"]
+    np.testing.assert_allclose(a["image"].numpy(), b["image"].numpy(), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(a["T"].numpy(), b["T"].numpy(), rtol=0, atol=1e-13)
 
 
 def test_binning_float32_close_to_float64():
