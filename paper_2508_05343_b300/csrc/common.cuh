@@ -15,8 +15,14 @@ typedef unsigned int u32;
 constexpr int TILE = GS_TILE;
 constexpr int BLOCK = 256;            // threads per CTA for every tile / chunk kernel
 constexpr int CHUNK = BLOCK;          // primitives per preprocess chunk (one per thread)
-constexpr int SORT_THREADS = 256;
-constexpr int SORT_ITEMS = 16;
+#ifndef GS_SORT_THREADS
+#define GS_SORT_THREADS 256
+#endif
+#ifndef GS_SORT_ITEMS
+#define GS_SORT_ITEMS 16
+#endif
+constexpr int SORT_THREADS = GS_SORT_THREADS;   // >= 256: the first 256 threads own one digit each
+constexpr int SORT_ITEMS = GS_SORT_ITEMS;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // keys per onesweep partition
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;

@@ -218,9 +218,55 @@ __device__ __forceinline__ void bin_spec(const ViewDesc& V, float eps2d, float m
   }
 }
 
+// Tiles a pixel can reach (binning specification): alpha = o G bank <= o G, so a pixel needs the
+// squared Mahalanobis distance q <= 2 ln(o / alpha_min).  thr is a float32 upper bound of that
+// (frexp and ln m <= (m - 1)/sqrt(m), plus a margin for float32 evaluation); a tile of the 3-sigma
+// square is kept when the minimum of q over the box of its pixel centres is <= thr.  Dropped tiles
+// hold only pairs that every pixel skips, so no pixel changes.  Single correctly rounded float32
+// operations in the order the oracle's specification states.
+struct Reach {
+  float mux, muy, A, C, kx, ky, B2, thr;
+};
+constexpr float LN2_UP = 0.693147182464599609375f;   // the float32 just above ln 2
+
+__device__ __forceinline__ bool reach_params(const BinSpec& b, float eps2d, float o, float amin, Reach& r) {
+  if (!(o >= amin)) return false;
+  const float ca = FA(b.A00, eps2d), cb = b.A01, cc = FA(b.A11, eps2d);
+  const float det32 = __double2float_rn(b.det);
+  const float A = FDV(cc, det32), B = FDV(-cb, det32), C = FDV(ca, det32);
+  int e = 0;
+  const float m = frexpf(FDV(o, amin), &e);
+  const float m2 = FM(m, 2.f);
+  const float t = FA(FM((float)(e - 1), LN2_UP), FDV(FS(m2, 1.f), __fsqrt_rn(m2)));
+  r.thr = FA(FM(FM(2.f, t), 1.0009765625f), 0.015625f);
+  r.A = A;
+  r.C = C;
+  r.kx = FDV(-B, C);
+  r.ky = FDV(-B, A);
+  r.B2 = FM(2.f, B);
+  r.mux = b.mux;
+  r.muy = b.muy;
+  return true;
+}
+
+__device__ __forceinline__ float reach_edge(float a, float c, float k, float b2, float e, float lo, float hi) {
+  const float s = fminf(fmaxf(FM(k, e), lo), hi);
+  return FA(FA(FM(FM(a, e), e), FM(FM(b2, e), s)), FM(FM(c, s), s));
+}
+
+__device__ __forceinline__ bool tile_reached(const Reach& r, int tx, int ty) {
+  const float bx = (float)(16 * tx), by = (float)(16 * ty);
+  const float xl = FS(FA(bx, 0.5f), r.mux), xh = FS(FA(bx, 15.5f), r.mux);
+  const float yl = FS(FA(by, 0.5f), r.muy), yh = FS(FA(by, 15.5f), r.muy);
+  if (xl <= 0.f && xh >= 0.f && yl <= 0.f && yh >= 0.f) return true;
+  const float q = fminf(fminf(reach_edge(r.A, r.C, r.kx, r.B2, xl, yl, yh), reach_edge(r.A, r.C, r.kx, r.B2, xh, yl, yh)),
+                        fminf(reach_edge(r.C, r.A, r.ky, r.B2, yl, xl, xh), reach_edge(r.C, r.A, r.ky, r.B2, yh, xl, xh)));
+  return q <= r.thr;
+}
+
 // Bin one primitive (the float32 binning specification).  Returns the touched-tile count.
 __device__ __forceinline__ u32 bin_one(const FrameTable* tbl, u32 gi, const WsPtrs& p, int& x0, int& y0, int& wx,
-                                           u32& dbits, u32& tile_base, int& tiles_x, bool& nonfinite) {
+                                       u32& dbits, u32& tile_base, int& tiles_x, bool& nonfinite, Reach& r) {
   const int v = view_of_prim(tbl, gi);
   const ViewDesc& V = tbl->v[v];
   const u32 k = gi - V.prim_base;
@@ -234,7 +280,7 @@ __device__ __forceinline__ u32 bin_one(const FrameTable* tbl, u32 gi, const WsPt
   tile_base = V.tile_base;
   tiles_x = V.tiles_x;
   nonfinite = (b.tz > V.znear) && (b.tz <= V.zfar) && !b.finite;
-  if (!b.valid) {
+  if (!b.valid || !reach_params(b, tbl->eps2d, __ldg(V.opacity + k), tbl->alpha_min, r)) {
     x0 = 0; y0 = 0; wx = 1; dbits = 0;
     return 0;
   }
@@ -242,7 +288,7 @@ __device__ __forceinline__ u32 bin_one(const FrameTable* tbl, u32 gi, const WsPt
   y0 = b.y0;
   wx = b.x1 - b.x0 + 1;
   dbits = __float_as_uint(b.tz);
-  return (u32)wx * (u32)(b.y1 - b.y0 + 1);
+  return (u32)wx * (u32)(b.y1 - b.y0 + 1);   // tiles of the 3-sigma square (culled per tile later)
 }
 
 // The 2D record of one primitive that touches at least one tile: conic from the float64
@@ -329,8 +375,60 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, const 
 // Preprocess + single-pass (decoupled look-back) exclusive scan of touched-tile counts + key emission.
 // Persistent CTAs take 256-primitive chunks in increasing order from an atomic counter, so every chunk
 // a CTA waits on is held by a CTA that is already running.
+// Entry j of a warp's flat tile list: the owner lane (largest lane whose exclusive start <= j),
+// the tile coordinates and the owner's reach parameters (every lane takes part in the shuffles).
+struct FlatTile {
+  int owner, tx, ty;
+  Reach r;
+};
+constexpr int KEPT_ROUNDS = 128;   // rounds of 32 flat tiles whose ballots are kept in shared memory
+__device__ __forceinline__ void flat_tile(u32 j, u32 my_excl, int x0, int y0, int wx, const Reach& rr, FlatTile& f) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const int cand = lo + step;
+    if (__shfl_sync(0xffffffffu, my_excl, cand) <= j) lo = cand;
+  }
+  const u32 o_excl = __shfl_sync(0xffffffffu, my_excl, lo);
+  const int ox0 = __shfl_sync(0xffffffffu, x0, lo), oy0 = __shfl_sync(0xffffffffu, y0, lo);
+  const int owx = __shfl_sync(0xffffffffu, wx, lo);
+  f.r.mux = __shfl_sync(0xffffffffu, rr.mux, lo);
+  f.r.muy = __shfl_sync(0xffffffffu, rr.muy, lo);
+  f.r.A = __shfl_sync(0xffffffffu, rr.A, lo);
+  f.r.C = __shfl_sync(0xffffffffu, rr.C, lo);
+  f.r.kx = __shfl_sync(0xffffffffu, rr.kx, lo);
+  f.r.ky = __shfl_sync(0xffffffffu, rr.ky, lo);
+  f.r.B2 = __shfl_sync(0xffffffffu, rr.B2, lo);
+  f.r.thr = __shfl_sync(0xffffffffu, rr.thr, lo);
+  const u32 local = j - o_excl;
+  const u32 ry = local / (u32)owx;
+  f.owner = lo;
+  f.ty = oy0 + (int)ry;
+  f.tx = ox0 + (int)(local - ry * (u32)owx);
+}
+
+// Owner and tile coordinates only (no reach parameters).
+__device__ __forceinline__ void flat_owner(u32 j, u32 my_excl, int x0, int y0, int wx, FlatTile& f) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const int cand = lo + step;
+    if (__shfl_sync(0xffffffffu, my_excl, cand) <= j) lo = cand;
+  }
+  const u32 o_excl = __shfl_sync(0xffffffffu, my_excl, lo);
+  const int ox0 = __shfl_sync(0xffffffffu, x0, lo), oy0 = __shfl_sync(0xffffffffu, y0, lo);
+  const int owx = __shfl_sync(0xffffffffu, wx, lo);
+  const u32 local = j - o_excl;
+  const u32 ry = local / (u32)owx;
+  f.owner = lo;
+  f.ty = oy0 + (int)ry;
+  f.tx = ox0 + (int)(local - ry * (u32)owx);
+}
+
 __global__ void __launch_bounds__(BLOCK) k_preprocess(WsPtrs p) {
   __shared__ u32 s_chunk;
+  __shared__ u32 s_cnt[BLOCK / 32][32];
+  __shared__ u32 s_kept[BLOCK / 32][KEPT_ROUNDS];   // ballots of the counting pass, reused by emission
   __shared__ u32 s_warp[BLOCK / 32];
   __shared__ u64 s_excl;
   const FrameTable* tbl = p.tbl;
@@ -347,15 +445,41 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess(WsPtrs p) {
     if ((u64)chunk * CHUNK >= total) break;
     const u32 gi = chunk * CHUNK + tid;
     int x0 = 0, y0 = 0, wx = 1, tiles_x = 1;
-    u32 dbits = 0, tile_base = 0, cnt = 0;
+    u32 dbits = 0, tile_base = 0, sq = 0;
     bool nonfinite = false;
-    if (gi < total) cnt = bin_one(tbl, gi, p, x0, y0, wx, dbits, tile_base, tiles_x, nonfinite);
+    Reach rr;
+    rr.mux = rr.muy = rr.A = rr.C = rr.kx = rr.ky = rr.B2 = rr.thr = 0.f;
+    if (gi < total) sq = bin_one(tbl, gi, p, x0, y0, wx, dbits, tile_base, tiles_x, nonfinite, rr);
+    // the warp's 3-sigma-square tiles form one flat list (owner lanes in order, tiles row-major)
+    u32 sq_incl = sq;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 t = __shfl_up_sync(0xffffffffu, sq_incl, o);
+      if (lane >= o) sq_incl += t;
+    }
+    const u32 my_sq_excl = sq_incl - sq;
+    const u32 wsq_total = __shfl_sync(0xffffffffu, sq_incl, 31);
+    // counting pass: how many of each owner's tiles some pixel can reach
+    s_cnt[warp][lane] = 0;
+    __syncwarp();
+    for (u32 base = 0; base < wsq_total; base += 32) {
+      const u32 j = base + lane;
+      FlatTile ft;
+      flat_tile(j, my_sq_excl, x0, y0, wx, rr, ft);
+      const bool kept = j < wsq_total && tile_reached(ft.r, ft.tx, ft.ty);
+      const u32 ballot = __ballot_sync(0xffffffffu, kept);
+      if (lane == 0 && base / 32 < (u32)KEPT_ROUNDS) s_kept[warp][base / 32] = ballot;
+      const u32 peers = __match_any_sync(0xffffffffu, j < wsq_total ? ft.owner : 32 + lane);
+      if (j < wsq_total && lane == __ffs(peers) - 1) s_cnt[warp][ft.owner] += __popc(ballot & peers);
+      __syncwarp();
+    }
+    const u32 cnt = s_cnt[warp][lane];
     {   // append the primitives that touch a tile to the active list (warp-aggregated atomic)
       const u32 ballot = __ballot_sync(0xffffffffu, cnt > 0);
-      u32 base = 0;
-      if (lane == 0 && ballot) base = atomicAdd(&hdr->n_active, (u32)__popc(ballot));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (cnt > 0) p.active[base + __popc(ballot & ((1u << lane) - 1u))] = gi;
+      u32 abase = 0;
+      if (lane == 0 && ballot) abase = atomicAdd(&hdr->n_active, (u32)__popc(ballot));
+      abase = __shfl_sync(0xffffffffu, abase, 0);
+      if (cnt > 0) p.active[abase + __popc(ballot & ((1u << lane) - 1u))] = gi;
     }
     if (__syncthreads_or(nonfinite)) {
       if (tid == 0) { atomicAdd(&hdr->nonfinite, 1u); set_status(hdr, GS_ERR_NONFINITE); }
@@ -420,39 +544,35 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess(WsPtrs p) {
       p.touched[gi] = cnt;
       p.offsets[gi] = (u32)off;
     }
-    // warp-cooperative emission: the warp's pairs are contiguous, so lane j of each round writes
-    // pair (round * 32 + j) -> coalesced 8-byte key and 4-byte value stores
+    // emission: the warp's kept pairs are contiguous in the output (primitives in lane order, tiles
+    // row-major), so each round compacts its kept tiles with a ballot -> coalesced key/value stores
     const u64 warp_off = __shfl_sync(0xffffffffu, off, 0);
-    const u32 my_excl = (u32)(off - warp_off);
-    const u32 warp_total = __shfl_sync(0xffffffffu, my_excl + cnt, 31);
-    for (u32 base = 0; base < warp_total; base += 32) {
+    u32 running = 0;
+    const u32 lt = (1u << lane) - 1u;
+    for (u32 base = 0; base < wsq_total; base += 32) {
       const u32 j = base + lane;
-      int lo = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int cand = lo + step;
-        const u32 e = __shfl_sync(0xffffffffu, my_excl, cand);
-        if (e <= j) lo = cand;
+      FlatTile ft;
+      u32 ballot;
+      if (base / 32 < (u32)KEPT_ROUNDS) {   // the counting pass already decided these tiles
+        flat_owner(j, my_sq_excl, x0, y0, wx, ft);
+        ballot = s_kept[warp][base / 32];
+      } else {
+        flat_tile(j, my_sq_excl, x0, y0, wx, rr, ft);
+        ballot = __ballot_sync(0xffffffffu, j < wsq_total && tile_reached(ft.r, ft.tx, ft.ty));
       }
-      const u32 o_excl = __shfl_sync(0xffffffffu, my_excl, lo);
-      const int ox0 = __shfl_sync(0xffffffffu, x0, lo);
-      const int oy0 = __shfl_sync(0xffffffffu, y0, lo);
-      const int owx = __shfl_sync(0xffffffffu, wx, lo);
-      const u32 odb = __shfl_sync(0xffffffffu, dbits, lo);
-      const u32 ogi = __shfl_sync(0xffffffffu, gi, lo);
-      const u32 otb = __shfl_sync(0xffffffffu, tile_base, lo);
-      const int otx = __shfl_sync(0xffffffffu, tiles_x, lo);
-      if (j < warp_total) {
-        const u32 local = j - o_excl;
-        const u32 ry = local / (u32)owx;
-        const u32 rx = local - ry * (u32)owx;
-        const u32 tile = otb + (u32)(oy0 + (int)ry) * (u32)otx + (u32)(ox0 + (int)rx);
-        const u64 pos = warp_off + j;
+      const bool kept = (ballot >> lane) & 1u;
+      const u32 odb = __shfl_sync(0xffffffffu, dbits, ft.owner);
+      const u32 ogi = __shfl_sync(0xffffffffu, gi, ft.owner);
+      const u32 otb = __shfl_sync(0xffffffffu, tile_base, ft.owner);
+      const int otx = __shfl_sync(0xffffffffu, tiles_x, ft.owner);
+      if (kept) {
+        const u64 pos = warp_off + running + __popc(ballot & lt);
         if (pos < p.capacity) {
-          p.keys0[pos] = ((u64)tile << 32) | odb;
+          p.keys0[pos] = ((u64)(otb + (u32)ft.ty * (u32)otx + (u32)ft.tx) << 32) | odb;
           p.vals0[pos] = ogi;
         }
       }
+      running += __popc(ballot);
     }
     __syncthreads();
   }

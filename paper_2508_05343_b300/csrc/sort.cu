@@ -31,6 +31,8 @@ __global__ void __launch_bounds__(256) k_digit_hist(WsPtrs p, int npasses) {
   }
 }
 
+static_assert(SORT_THREADS >= RADIX && SORT_THREADS % 32 == 0, "one digit per thread of the first RADIX threads");
+
 struct SortSmem {
   u32 warp_cnt[SORT_THREADS / 32][RADIX];
   u32 local_excl[RADIX];
@@ -42,8 +44,8 @@ struct SortSmem {
   u32 vals[SORT_TILE];
 };
 
-// Exclusive scan of one value per thread over a 256-thread CTA (contains two barriers).
-__device__ __forceinline__ u32 block_excl_scan_256(u32 v, u32* scratch /*8*/) {
+// Exclusive scan of one value per thread over the CTA (two barriers); threads >= RADIX pass 0.
+__device__ __forceinline__ u32 block_excl_scan(u32 v, u32* scratch /*SORT_THREADS / 32*/) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u32 incl = v;
 #pragma unroll
@@ -75,7 +77,10 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* 
   const u64 Pall = hdr->pairs;
   const u64 P = Pall < p.capacity ? Pall : p.capacity;
   const u32 tag = hdr->epoch * (u32)MAX_PASSES + (u32)pass;
-  S.hist_excl[tid] = block_excl_scan_256(p.hist[pass * RADIX + tid], S.scratch);
+  {
+    const u32 hx = block_excl_scan(tid < RADIX ? p.hist[pass * RADIX + tid] : 0u, S.scratch);
+    if (tid < RADIX) S.hist_excl[tid] = hx;
+  }
   const u32 lt_mask = (1u << lane) - 1u;
   for (;;) {
     if (tid == 0) S.part = atomicAdd(&hdr->sort_counter[pass], 1u);
@@ -112,17 +117,16 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* 
       __syncwarp();
     }
     __syncthreads();
-    // digit `tid`: exclusive prefix over warps, partition count
+    // digit `tid` (first RADIX threads): exclusive prefix over warps, partition count, look-back
     u32 cnt = 0;
-#pragma unroll
-    for (int w = 0; w < SORT_THREADS / 32; ++w) {
-      const u32 c = S.warp_cnt[w][tid];
-      S.warp_cnt[w][tid] = cnt;
-      cnt += c;
-    }
-    // decoupled look-back for digit `tid`
     u64 excl = 0;
-    {
+    if (tid < RADIX) {
+#pragma unroll
+      for (int w = 0; w < SORT_THREADS / 32; ++w) {
+        const u32 c = S.warp_cnt[w][tid];
+        S.warp_cnt[w][tid] = cnt;
+        cnt += c;
+      }
       u64* st = p.sort_status + (u64)part * RADIX + tid;
       if (part == 0) {
         st_relaxed(st, lb_pack(LB_FLAG_PREFIX, tag, cnt));
@@ -149,9 +153,11 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* 
         st_relaxed(st, lb_pack(LB_FLAG_PREFIX, tag, excl + cnt));
       }
     }
-    const u32 lex = block_excl_scan_256(cnt, S.scratch);
-    S.local_excl[tid] = lex;
-    S.glob[tid] = S.hist_excl[tid] + (u32)excl - lex;
+    const u32 lex = block_excl_scan(tid < RADIX ? cnt : 0u, S.scratch);
+    if (tid < RADIX) {
+      S.local_excl[tid] = lex;
+      S.glob[tid] = S.hist_excl[tid] + (u32)excl - lex;
+    }
     __syncthreads();
     // local scatter into shared memory (stable: warp order, round order, lane order)
 #pragma unroll

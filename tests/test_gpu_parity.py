@@ -37,9 +37,9 @@ def check_binning(r, spec):
 
 
 def check_records(v, out, prims):
-    """Projected records vs the float64 projection (valid primitives only)."""
+    """Projected records vs the float64 projection (primitives that reach at least one tile)."""
     spec, proj = out["spec"], out["proj"]
-    valid = spec["valid"]
+    valid = spec["valid"] & (spec["touched"] > 0)
     rec = v["records"].cpu().numpy().astype(np.float64)[valid]
     K = prims["weights"].shape[1]
     np.testing.assert_allclose(rec[:, 0:2], proj["mu2d"].numpy()[valid], rtol=1e-5, atol=1e-3)
