@@ -326,9 +326,9 @@ def run_ours(args):
     zb = lambda z: int(np.float32(z).view(np.uint32))
     dbits = max(1, (zb(cams[0]["zfar"]) - zb(cams[0]["znear"])).bit_length())
     npasses_needed = min(npasses, math.ceil((dbits + tbits) / 8))   # passes that do work
-    # my kernels per step: setup, preprocess + records, histogram + passes + ranges, render_fwd,
+    # my kernels per step: setup, bin + scan + emit + records, histogram + passes + ranges, render_fwd,
     # loss (2), render_bwd, zero-fill + preprocess_bwd
-    launches_per_step = 1 + 2 + (1 + npasses + 1) + 1 + 2 + 1 + 2
+    launches_per_step = 1 + 4 + (1 + npasses + 1) + 1 + 2 + 1 + 2
     stage_names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd"]
 
     def pose_of(s):

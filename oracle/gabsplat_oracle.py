@@ -191,9 +191,10 @@ def _tile_reachable(prims_np, prim_of, tile_x, tile_y, mux, muy, ca, cb, cc, det
       conic = (c, -b, a) / float32(det);  x = o / alpha_min = m 2^e (frexp, m in [0.5, 1));
       m2 = 2 m, t = (e - 1) LN2_UP + (m2 - 1) / sqrt(m2)  (>= ln x since ln m2 <= (m2 - 1)/sqrt m2);
       thr = (2 t) (1 + 2^-10) + 2^-6  (margin for float32 evaluation);  o < alpha_min reaches nothing;
+      per primitive kx = (-B) / C, ky = (-B) / A, B2 = 2 B;
       box: xl = (16 tx + 0.5) - mu_x, xh = (16 tx + 15.5) - mu_x (same for y); q_min = 0 if the box
-      holds the mean, else the least of the four edge minima, edge x = e: s = clip(-(B e) / C, lo, hi),
-      q = ((A e) e + ((2 B) e) s) + (C s) s, and the same with A, C and x, y swapped for y-edges.
+      holds the mean, else the least of the four edge minima, edge x = e: s = clip(kx e, yl, yh),
+      q = ((A e) e + (B2 e) s) + (C s) s; edge y = e: s = clip(ky e, xl, xh), q = ((C e) e + (B2 e) s) + (A s) s.
     """
     f32 = np.float32
     with np.errstate(all="ignore"):
@@ -212,12 +213,14 @@ def _tile_reachable(prims_np, prim_of, tile_x, tile_y, mux, muy, ca, cb, cc, det
         xl, xh = (bx + f32(0.5)) - mx, (bx + f32(15.5)) - mx
         yl, yh = (by + f32(0.5)) - my, (by + f32(15.5)) - my
 
-        def edge(a_, b_, c_, e, lo, hi):
-            s = np.minimum(np.maximum(-(b_ * e) / c_, lo), hi)
-            return ((a_ * e) * e + ((f32(2) * b_) * e) * s) + (c_ * s) * s
+        kx, ky, B2 = (-B) / Cc, (-B) / A, f32(2) * B
 
-        qmin = np.minimum(np.minimum(edge(A, B, Cc, xl, yl, yh), edge(A, B, Cc, xh, yl, yh)),
-                          np.minimum(edge(Cc, B, A, yl, xl, xh), edge(Cc, B, A, yh, xl, xh)))
+        def edge(a_, c_, k_, e, lo, hi):
+            s = np.minimum(np.maximum(k_ * e, lo), hi)
+            return ((a_ * e) * e + (B2 * e) * s) + (c_ * s) * s
+
+        qmin = np.minimum(np.minimum(edge(A, Cc, kx, xl, yl, yh), edge(A, Cc, kx, xh, yl, yh)),
+                          np.minimum(edge(Cc, A, ky, yl, xl, xh), edge(Cc, A, ky, yh, xl, xh)))
         inside = (xl <= 0) & (xh >= 0) & (yl <= 0) & (yh >= 0)
         qmin = np.where(inside, f32(0), qmin)
     return reach & (qmin <= thr)
@@ -227,8 +230,9 @@ def bin_spec(prims_np: dict, cam, cfg, cull: bool = True) -> dict:
     """Tile binning per the written float32 specification.
 
     Every float32 operation below is a single IEEE round-to-nearest operation in the stated order
-    (numpy never fuses multiply-add).  Determinant, eigenvalue and radius are float64 functions of
-    the float32 covariance entries.  A primitive's tiles are those of its 3-sigma square that some
+    (numpy never fuses multiply-add).  The determinant of the dilated 2D covariance is a float64
+    function of its float32 entries; eigenvalue and radius are float32 from the rounded determinant;
+    the tile rectangle is integer arithmetic.  A primitive's tiles are those of its 3-sigma square that some
     pixel can reach (see _tile_reachable; cull=False keeps the whole square, which renders the same
     image).  Returns per-primitive depth/mean/covariance/radius/rect, the emitted (key, value) pairs
     in emission order, the stably sorted pairs and tile ranges.
@@ -278,19 +282,25 @@ def bin_spec(prims_np: dict, cam, cfg, cull: bool = True) -> dict:
     A01 = (U[0][0] * T[1][0] + U[0][1] * T[1][1]) + U[0][2] * T[1][2]
     A11 = (U[1][0] * T[1][0] + U[1][1] * T[1][1]) + U[1][2] * T[1][2]
     ca, cb, cc = A00 + eps, A01, A11 + eps
-    # float64 determinant / largest eigenvalue / 3-sigma radius
+    # float64 determinant of the dilated 2D covariance (where near-degenerate footprints cancel)
     da, db, dc = ca.astype(np.float64), cb.astype(np.float64), cc.astype(np.float64)
     det = da * dc - db * db
-    mid = 0.5 * (da + dc)
-    lam = mid + np.sqrt(np.maximum(0.0, mid * mid - det))
-    with np.errstate(invalid="ignore"):
-        rad = np.ceil(3.0 * np.sqrt(np.maximum(lam, 0.0)))
-    finite = np.isfinite(mux) & np.isfinite(muy) & np.isfinite(det) & np.isfinite(rad)
+    # largest eigenvalue and 3-sigma radius in float32 from the rounded determinant
+    with np.errstate(invalid="ignore", over="ignore"):
+        det32 = det.astype(f32)
+        mid = f32(0.5) * (ca + cc)
+        lam = mid + np.sqrt(np.maximum(mid * mid - det32, f32(0)))
+        rad = np.ceil(f32(3) * np.sqrt(np.maximum(lam, f32(0))))
+    lim = f32(2.0 ** 30)
+    finite = (np.isfinite(mux) & np.isfinite(muy) & np.isfinite(det) & np.isfinite(rad) &
+              (np.abs(mux) < lim) & (np.abs(muy) < lim) & (rad < lim))
     valid = (tz > znear) & (tz <= zfar) & (det > 0.0) & finite
-    mx, my = mux.astype(np.float64), muy.astype(np.float64)
-    with np.errstate(invalid="ignore"):
-        x0 = np.floor((mx - rad) / TILE); x1 = np.floor((mx + rad) / TILE)
-        y0 = np.floor((my - rad) / TILE); y1 = np.floor((my + rad) / TILE)
+    # rectangle: floor((mu -+ r) / 16) = floor_div(floor(mu) -+ r, 16) exactly, r being an integer
+    ix = np.where(finite, np.floor(mux), 0).astype(np.int64)
+    iy = np.where(finite, np.floor(muy), 0).astype(np.int64)
+    ir = np.where(finite, rad, 0).astype(np.int64)
+    x0, x1 = (ix - ir) // TILE, (ix + ir) // TILE
+    y0, y1 = (iy - ir) // TILE, (iy + ir) // TILE
     valid &= (x1 >= 0) & (x0 <= tiles_x - 1) & (y1 >= 0) & (y0 <= tiles_y - 1)
     x0 = np.where(valid, np.clip(x0, 0, tiles_x - 1), 0).astype(np.int64)
     x1 = np.where(valid, np.clip(x1, 0, tiles_x - 1), -1).astype(np.int64)

@@ -191,28 +191,31 @@ __device__ __forceinline__ void bin_spec(const ViewDesc& V, float eps2d, float m
   b.A01 = FA(FA(FM(U0[0], b.T1[0]), FM(U0[1], b.T1[1])), FM(U0[2], b.T1[2]));
   b.A11 = FA(FA(FM(U1[0], b.T1[0]), FM(U1[1], b.T1[1])), FM(U1[2], b.T1[2]));
   const float ca = FA(b.A00, eps2d), cb = b.A01, cc = FA(b.A11, eps2d);
+  // float64 determinant (where near-degenerate footprints cancel); the rest in float32
   const double da = ca, db = cb, dc = cc;
   const double det = __dsub_rn(__dmul_rn(da, dc), __dmul_rn(db, db));
-  const double mid = __dmul_rn(0.5, __dadd_rn(da, dc));
-  const double lam = __dadd_rn(mid, __dsqrt_rn(fmax(0.0, __dsub_rn(__dmul_rn(mid, mid), det))));
-  const double rad = ceil(__dmul_rn(3.0, __dsqrt_rn(fmax(lam, 0.0))));
+  const float det32 = __double2float_rn(det);
+  const float mid = FM(0.5f, FA(ca, cc));
+  const float lam = FA(mid, __fsqrt_rn(fmaxf(FS(FM(mid, mid), det32), 0.f)));
+  const float rad = ceilf(FM(3.f, __fsqrt_rn(fmaxf(lam, 0.f))));
   b.det = det;
-  b.finite = isfinite(b.mux) && isfinite(b.muy) && isfinite(det) && isfinite(rad);
+  const float lim = 1073741824.f;   // 2^30
+  b.finite = isfinite(b.mux) && isfinite(b.muy) && isfinite(det) && isfinite(rad) && fabsf(b.mux) < lim &&
+             fabsf(b.muy) < lim && rad < lim;
   bool valid = (tz > V.znear) && (tz <= V.zfar) && (det > 0.0) && b.finite;
-  const double mxd = b.mux, myd = b.muy;
-  // division by the tile size 16 is exact, so it is written as a multiplication by 1/16
-  const double fx0 = floor(__dmul_rn(__dsub_rn(mxd, rad), 0.0625));
-  const double fx1 = floor(__dmul_rn(__dadd_rn(mxd, rad), 0.0625));
-  const double fy0 = floor(__dmul_rn(__dsub_rn(myd, rad), 0.0625));
-  const double fy1 = floor(__dmul_rn(__dadd_rn(myd, rad), 0.0625));
-  valid = valid && (fx1 >= 0.0) && (fx0 <= (double)(V.tiles_x - 1)) && (fy1 >= 0.0) &&
-          (fy0 <= (double)(V.tiles_y - 1));
+  long long fx0 = 0, fx1 = -1, fy0 = 0, fy1 = -1;
+  if (b.finite) {   // floor((mu -+ r) / 16) = floor_div(floor(mu) -+ r, 16), r an integer
+    const long long ix = (long long)floorf(b.mux), iy = (long long)floorf(b.muy), ir = (long long)rad;
+    fx0 = (ix - ir) >> 4; fx1 = (ix + ir) >> 4;
+    fy0 = (iy - ir) >> 4; fy1 = (iy + ir) >> 4;
+  }
+  valid = valid && fx1 >= 0 && fx0 <= V.tiles_x - 1 && fy1 >= 0 && fy0 <= V.tiles_y - 1;
   b.valid = valid;
   if (valid) {
-    b.x0 = (int)fmax(fx0, 0.0);
-    b.x1 = (int)fmin(fx1, (double)(V.tiles_x - 1));
-    b.y0 = (int)fmax(fy0, 0.0);
-    b.y1 = (int)fmin(fy1, (double)(V.tiles_y - 1));
+    b.x0 = (int)(fx0 > 0 ? fx0 : 0);
+    b.x1 = (int)(fx1 < V.tiles_x - 1 ? fx1 : V.tiles_x - 1);
+    b.y0 = (int)(fy0 > 0 ? fy0 : 0);
+    b.y1 = (int)(fy1 < V.tiles_y - 1 ? fy1 : V.tiles_y - 1);
   } else {
     b.x0 = 0; b.x1 = -1; b.y0 = 0; b.y1 = -1;
   }
@@ -372,16 +375,13 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, const 
   for (int i = 0; i < rec_floats(K) / 4; ++i) dst[i] = make_float4(rec[4 * i], rec[4 * i + 1], rec[4 * i + 2], rec[4 * i + 3]);
 }
 
-// Preprocess + single-pass (decoupled look-back) exclusive scan of touched-tile counts + key emission.
-// Persistent CTAs take 256-primitive chunks in increasing order from an atomic counter, so every chunk
-// a CTA waits on is held by a CTA that is already running.
-// Entry j of a warp's flat tile list: the owner lane (largest lane whose exclusive start <= j),
-// the tile coordinates and the owner's reach parameters (every lane takes part in the shuffles).
+// Entry j of a warp's flat list of 3-sigma-square tiles (owner lanes in order, tiles row-major):
+// the owner lane (largest lane whose exclusive start <= j), the tile and the owner's reach
+// parameters.  Every lane takes part in the shuffles.
 struct FlatTile {
   int owner, tx, ty;
   Reach r;
 };
-constexpr int KEPT_ROUNDS = 128;   // rounds of 32 flat tiles whose ballots are kept in shared memory
 __device__ __forceinline__ void flat_tile(u32 j, u32 my_excl, int x0, int y0, int wx, const Reach& rr, FlatTile& f) {
   int lo = 0;
 #pragma unroll
@@ -407,28 +407,78 @@ __device__ __forceinline__ void flat_tile(u32 j, u32 my_excl, int x0, int y0, in
   f.tx = ox0 + (int)(local - ry * (u32)owx);
 }
 
-// Owner and tile coordinates only (no reach parameters).
-__device__ __forceinline__ void flat_owner(u32 j, u32 my_excl, int x0, int y0, int wx, FlatTile& f) {
-  int lo = 0;
-#pragma unroll
-  for (int step = 16; step > 0; step >>= 1) {
-    const int cand = lo + step;
-    if (__shfl_sync(0xffffffffu, my_excl, cand) <= j) lo = cand;
+// Binning in three launches: (1) bin every primitive and count the tiles of its 3-sigma square
+// that a pixel can reach (warp-cooperative, no CTA barriers), appending primitives with at least one
+// tile to the active list; (2) exclusive scan of the counts (single pass, decoupled look-back over
+// 4096-element chunks); (3) emission of the kept pairs, warp-cooperative over the active list.
+
+// Per-owner counts of kept tiles over a warp's flat tile list; returns this lane's count.
+__device__ __forceinline__ u32 count_kept(u32 wsq_total, u32 my_sq_excl, int x0, int y0, int wx, const Reach& rr,
+                                          u32* s_cnt, int lane) {
+  s_cnt[lane] = 0;
+  __syncwarp();
+  for (u32 base = 0; base < wsq_total; base += 32) {
+    const u32 j = base + lane;
+    FlatTile ft;
+    flat_tile(j, my_sq_excl, x0, y0, wx, rr, ft);
+    const bool kept = j < wsq_total && tile_reached(ft.r, ft.tx, ft.ty);
+    const u32 ballot = __ballot_sync(0xffffffffu, kept);
+    const u32 peers = __match_any_sync(0xffffffffu, j < wsq_total ? ft.owner : 32 + lane);
+    if (j < wsq_total && lane == __ffs(peers) - 1) s_cnt[ft.owner] += __popc(ballot & peers);
+    __syncwarp();
   }
-  const u32 o_excl = __shfl_sync(0xffffffffu, my_excl, lo);
-  const int ox0 = __shfl_sync(0xffffffffu, x0, lo), oy0 = __shfl_sync(0xffffffffu, y0, lo);
-  const int owx = __shfl_sync(0xffffffffu, wx, lo);
-  const u32 local = j - o_excl;
-  const u32 ry = local / (u32)owx;
-  f.owner = lo;
-  f.ty = oy0 + (int)ry;
-  f.tx = ox0 + (int)(local - ry * (u32)owx);
+  return s_cnt[lane];
 }
 
-__global__ void __launch_bounds__(BLOCK) k_preprocess(WsPtrs p) {
-  __shared__ u32 s_chunk;
+__device__ __forceinline__ u32 warp_excl_scan(u32 v, int lane, u32& total) {
+  u32 incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  total = __shfl_sync(0xffffffffu, incl, 31);
+  return incl - v;
+}
+
+__global__ void __launch_bounds__(BLOCK) k_bin(WsPtrs p) {
   __shared__ u32 s_cnt[BLOCK / 32][32];
-  __shared__ u32 s_kept[BLOCK / 32][KEPT_ROUNDS];   // ballots of the counting pass, reused by emission
+  const FrameTable* tbl = p.tbl;
+  WsHeader* hdr = p.hdr;
+  if (read_status(hdr) != 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u32 total = tbl->total_prims;
+  for (u32 i = blockIdx.x * BLOCK + threadIdx.x; i < tbl->total_tiles; i += gridDim.x * BLOCK) p.ranges[i] = make_uint2(0u, 0u);
+  const u32 nwarps = gridDim.x * (BLOCK / 32);
+  for (u32 grp = blockIdx.x * (BLOCK / 32) + warp; (u64)grp * 32 < total; grp += nwarps) {
+    const u32 gi = grp * 32 + lane;
+    int x0 = 0, y0 = 0, wx = 1, tiles_x = 1;
+    u32 dbits = 0, tile_base = 0, sq = 0;
+    bool nonfinite = false;
+    Reach rr;
+    rr.mux = rr.muy = rr.A = rr.C = rr.kx = rr.ky = rr.B2 = rr.thr = 0.f;
+    if (gi < total) sq = bin_one(tbl, gi, p, x0, y0, wx, dbits, tile_base, tiles_x, nonfinite, rr);
+    if (__any_sync(0xffffffffu, nonfinite) && lane == 0) {
+      atomicAdd(&hdr->nonfinite, 1u);
+      set_status(hdr, GS_ERR_NONFINITE);
+    }
+    u32 wsq_total;
+    const u32 my_sq_excl = warp_excl_scan(sq, lane, wsq_total);
+    const u32 cnt = count_kept(wsq_total, my_sq_excl, x0, y0, wx, rr, s_cnt[warp], lane);
+    if (gi < total) p.touched[gi] = cnt;
+    const u32 ballot = __ballot_sync(0xffffffffu, cnt > 0);
+    u32 abase = 0;
+    if (lane == 0 && ballot) abase = atomicAdd(&hdr->n_active, (u32)__popc(ballot));
+    abase = __shfl_sync(0xffffffffu, abase, 0);
+    if (cnt > 0) p.active[abase + __popc(ballot & ((1u << lane) - 1u))] = gi;
+  }
+}
+
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_CHUNK = BLOCK * SCAN_ITEMS;   // counts per look-back partition
+
+__global__ void __launch_bounds__(BLOCK) k_scan_touched(WsPtrs p) {
+  __shared__ u32 s_chunk;
   __shared__ u32 s_warp[BLOCK / 32];
   __shared__ u64 s_excl;
   const FrameTable* tbl = p.tbl;
@@ -437,73 +487,31 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess(WsPtrs p) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u32 total = tbl->total_prims;
   const u32 tag = hdr->epoch;
-  for (u32 i = blockIdx.x * BLOCK + tid; i < tbl->total_tiles; i += gridDim.x * BLOCK) p.ranges[i] = make_uint2(0u, 0u);
   for (;;) {
     if (tid == 0) s_chunk = atomicAdd(&hdr->chunk_counter, 1u);
     __syncthreads();
     const u32 chunk = s_chunk;
-    if ((u64)chunk * CHUNK >= total) break;
-    const u32 gi = chunk * CHUNK + tid;
-    int x0 = 0, y0 = 0, wx = 1, tiles_x = 1;
-    u32 dbits = 0, tile_base = 0, sq = 0;
-    bool nonfinite = false;
-    Reach rr;
-    rr.mux = rr.muy = rr.A = rr.C = rr.kx = rr.ky = rr.B2 = rr.thr = 0.f;
-    if (gi < total) sq = bin_one(tbl, gi, p, x0, y0, wx, dbits, tile_base, tiles_x, nonfinite, rr);
-    // the warp's 3-sigma-square tiles form one flat list (owner lanes in order, tiles row-major)
-    u32 sq_incl = sq;
+    const u64 base = (u64)chunk * SCAN_CHUNK;
+    if (base >= total) break;
+    // thread t owns SCAN_ITEMS consecutive counts
+    u32 v[SCAN_ITEMS], sum = 0;
+    const u64 my0 = base + (u64)tid * SCAN_ITEMS;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const u32 t = __shfl_up_sync(0xffffffffu, sq_incl, o);
-      if (lane >= o) sq_incl += t;
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      v[i] = (my0 + i < total) ? p.touched[my0 + i] : 0u;
+      sum += v[i];
     }
-    const u32 my_sq_excl = sq_incl - sq;
-    const u32 wsq_total = __shfl_sync(0xffffffffu, sq_incl, 31);
-    // counting pass: how many of each owner's tiles some pixel can reach
-    s_cnt[warp][lane] = 0;
-    __syncwarp();
-    for (u32 base = 0; base < wsq_total; base += 32) {
-      const u32 j = base + lane;
-      FlatTile ft;
-      flat_tile(j, my_sq_excl, x0, y0, wx, rr, ft);
-      const bool kept = j < wsq_total && tile_reached(ft.r, ft.tx, ft.ty);
-      const u32 ballot = __ballot_sync(0xffffffffu, kept);
-      if (lane == 0 && base / 32 < (u32)KEPT_ROUNDS) s_kept[warp][base / 32] = ballot;
-      const u32 peers = __match_any_sync(0xffffffffu, j < wsq_total ? ft.owner : 32 + lane);
-      if (j < wsq_total && lane == __ffs(peers) - 1) s_cnt[warp][ft.owner] += __popc(ballot & peers);
-      __syncwarp();
-    }
-    const u32 cnt = s_cnt[warp][lane];
-    {   // append the primitives that touch a tile to the active list (warp-aggregated atomic)
-      const u32 ballot = __ballot_sync(0xffffffffu, cnt > 0);
-      u32 abase = 0;
-      if (lane == 0 && ballot) abase = atomicAdd(&hdr->n_active, (u32)__popc(ballot));
-      abase = __shfl_sync(0xffffffffu, abase, 0);
-      if (cnt > 0) p.active[abase + __popc(ballot & ((1u << lane) - 1u))] = gi;
-    }
-    if (__syncthreads_or(nonfinite)) {
-      if (tid == 0) { atomicAdd(&hdr->nonfinite, 1u); set_status(hdr, GS_ERR_NONFINITE); }
-    }
-    // block scan of cnt
-    u32 incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_warp[warp] = incl;
+    u32 wtot;
+    const u32 wex = warp_excl_scan(sum, lane, wtot);
+    if (lane == 31) s_warp[warp] = wex + sum;
     __syncthreads();
     if (warp == 0) {
       const u32 wv = lane < BLOCK / 32 ? s_warp[lane] : 0u;
-      u32 wi = wv;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const u32 t = __shfl_up_sync(0xffffffffu, wi, o);
-        if (lane >= o) wi += t;
-      }
-      const u32 agg = __shfl_sync(0xffffffffu, wi, 31);
-      if (lane < BLOCK / 32) s_warp[lane] = wi - wv;
+      u32 wt;
+      const u32 wx = warp_excl_scan(wv, lane, wt);
+      if (lane < BLOCK / 32) s_warp[lane] = wx;
       if (lane == 0) {
+        const u32 agg = wt;
         u64* st = p.scan_status + chunk;
         u64 excl = 0;
         if (chunk == 0) {
@@ -518,7 +526,7 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess(WsPtrs p) {
             if (lb_flag(w) != 0 && lb_tag(w) == (tag & 0x3FFFFFu)) {
               excl += lb_value(w);
               if (lb_flag(w) == LB_FLAG_PREFIX) break;
-              --pidx;  // chunk 0 always publishes a prefix, so pidx never underflows
+              --pidx;  // chunk 0 always publishes a prefix
               continue;
             }
             if (++polls > SPIN_LIMIT_POLLS || ((polls & 1023u) == 0 && global_timer_ns() - t0 > SPIN_LIMIT_NS)) {
@@ -531,7 +539,7 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess(WsPtrs p) {
           st_relaxed(st, lb_pack(LB_FLAG_PREFIX, tag, excl + agg));
         }
         s_excl = excl;
-        if ((u64)(chunk + 1) * CHUNK >= total) {  // last chunk: publish the pair count
+        if (base + SCAN_CHUNK >= total) {   // last chunk: publish the pair count
           const u64 P = excl + agg;
           hdr->pairs = P;
           if (P > p.capacity) set_status(hdr, GS_ERR_CAPACITY);
@@ -539,42 +547,66 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess(WsPtrs p) {
       }
     }
     __syncthreads();
-    const u64 off = s_excl + s_warp[warp] + (incl - cnt);
-    if (gi < total) {
-      p.touched[gi] = cnt;
-      p.offsets[gi] = (u32)off;
+    u32 run = (u32)s_excl + s_warp[warp] + wex;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      if (my0 + i < total) p.offsets[my0 + i] = run;
+      run += v[i];
     }
-    // emission: the warp's kept pairs are contiguous in the output (primitives in lane order, tiles
-    // row-major), so each round compacts its kept tiles with a ballot -> coalesced key/value stores
-    const u64 warp_off = __shfl_sync(0xffffffffu, off, 0);
-    u32 running = 0;
-    const u32 lt = (1u << lane) - 1u;
+    __syncthreads();
+  }
+}
+
+// Emission over the active list: 32 primitives per warp, each lane re-bins its own (bit-identical),
+// the warp walks the owners' squares and writes each kept tile at offset(owner) + its rank among
+// the owner's kept tiles (row-major), i.e. in the order of the specification.
+__global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
+  __shared__ u32 s_run[BLOCK / 32][32];
+  const FrameTable* tbl = p.tbl;
+  WsHeader* hdr = p.hdr;
+  if (read_status(hdr) != 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u32 nact = hdr->n_active;
+  const u32 lt = (1u << lane) - 1u;
+  const u32 nwarps = gridDim.x * (BLOCK / 32);
+  for (u32 grp = blockIdx.x * (BLOCK / 32) + warp; (u64)grp * 32 < nact; grp += nwarps) {
+    const u32 ia = grp * 32 + lane;
+    const u32 gi = ia < nact ? p.active[ia] : 0u;
+    int x0 = 0, y0 = 0, wx = 1, tiles_x = 1;
+    u32 dbits = 0, tile_base = 0, sq = 0;
+    bool nonfinite = false;
+    Reach rr;
+    rr.mux = rr.muy = rr.A = rr.C = rr.kx = rr.ky = rr.B2 = rr.thr = 0.f;
+    if (ia < nact) sq = bin_one(tbl, gi, p, x0, y0, wx, dbits, tile_base, tiles_x, nonfinite, rr);
+    const u32 off = ia < nact ? p.offsets[gi] : 0u;
+    u32 wsq_total;
+    const u32 my_sq_excl = warp_excl_scan(sq, lane, wsq_total);
+    s_run[warp][lane] = 0;
+    __syncwarp();
     for (u32 base = 0; base < wsq_total; base += 32) {
       const u32 j = base + lane;
       FlatTile ft;
-      u32 ballot;
-      if (base / 32 < (u32)KEPT_ROUNDS) {   // the counting pass already decided these tiles
-        flat_owner(j, my_sq_excl, x0, y0, wx, ft);
-        ballot = s_kept[warp][base / 32];
-      } else {
-        flat_tile(j, my_sq_excl, x0, y0, wx, rr, ft);
-        ballot = __ballot_sync(0xffffffffu, j < wsq_total && tile_reached(ft.r, ft.tx, ft.ty));
-      }
-      const bool kept = (ballot >> lane) & 1u;
+      flat_tile(j, my_sq_excl, x0, y0, wx, rr, ft);
+      const bool kept = j < wsq_total && tile_reached(ft.r, ft.tx, ft.ty);
+      const u32 ballot = __ballot_sync(0xffffffffu, kept);
+      const u32 peers = __match_any_sync(0xffffffffu, j < wsq_total ? ft.owner : 32 + lane);
+      const u32 ooff = __shfl_sync(0xffffffffu, off, ft.owner);
       const u32 odb = __shfl_sync(0xffffffffu, dbits, ft.owner);
       const u32 ogi = __shfl_sync(0xffffffffu, gi, ft.owner);
       const u32 otb = __shfl_sync(0xffffffffu, tile_base, ft.owner);
       const int otx = __shfl_sync(0xffffffffu, tiles_x, ft.owner);
+      const u32 run = j < wsq_total ? s_run[warp][ft.owner] : 0u;
       if (kept) {
-        const u64 pos = warp_off + running + __popc(ballot & lt);
+        const u64 pos = (u64)ooff + run + __popc(ballot & peers & lt);
         if (pos < p.capacity) {
           p.keys0[pos] = ((u64)(otb + (u32)ft.ty * (u32)otx + (u32)ft.tx) << 32) | odb;
           p.vals0[pos] = ogi;
         }
       }
-      running += __popc(ballot);
+      __syncwarp();
+      if (j < wsq_total && lane == __ffs(peers) - 1) s_run[warp][ft.owner] = run + __popc(ballot & peers);
+      __syncwarp();
     }
-    __syncthreads();
   }
 }
 
@@ -870,16 +902,18 @@ cudaError_t launch_setup(const FrameTable& tbl, const WsPtrs& p, const Launch& L
 
 template <int K, int ST>
 static cudaError_t launch_pre_t(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
-  static int grid = 0, rgrid = 0;
-  if (!grid) grid = persistent_grid(k_preprocess, BLOCK, 0, L.sm_count);
+  static int bgrid = 0, sgrid = 0, egrid = 0, rgrid = 0;
+  if (!bgrid) bgrid = persistent_grid(k_bin, BLOCK, 0, L.sm_count);
+  if (!sgrid) sgrid = persistent_grid(k_scan_touched, BLOCK, 0, L.sm_count);
+  if (!egrid) egrid = persistent_grid(k_emit, BLOCK, 0, L.sm_count);
   if (!rgrid) rgrid = persistent_grid(k_records<K, ST>, BLOCK, 0, L.sm_count);
-  const int need = (int)((tbl.launch_prims + CHUNK - 1) / CHUNK);
-  int g = need < grid ? need : grid;
-  if (g < 1) g = 1;
-  k_preprocess<<<g, BLOCK, 0, L.stream>>>(p);
-  int rg = need < rgrid ? need : rgrid;
-  if (rg < 1) rg = 1;
-  k_records<K, ST><<<rg, BLOCK, 0, L.stream>>>(p);
+  const int need = (int)((tbl.launch_prims + BLOCK - 1) / BLOCK);
+  const int schunks = (int)((tbl.launch_prims + SCAN_CHUNK - 1) / SCAN_CHUNK);
+  auto clampg = [](int g, int cap) { return g < 1 ? 1 : (g > cap ? cap : g); };
+  k_bin<<<clampg(need, bgrid), BLOCK, 0, L.stream>>>(p);
+  k_scan_touched<<<clampg(schunks, sgrid), BLOCK, 0, L.stream>>>(p);
+  k_emit<<<clampg(need, egrid), BLOCK, 0, L.stream>>>(p);
+  k_records<K, ST><<<clampg(need, rgrid), BLOCK, 0, L.stream>>>(p);
   return cudaGetLastError();
 }
 
