@@ -304,6 +304,7 @@ def run_ours(args):
         v = rast.views()
         pose_stats.append(dict(pairs=v["pairs"], n_eval=int(v["n_eval"].sum().item()),
                                active=int((v["touched"] > 0).sum().item()),
+                               n_reach=int(v["n_reach"].sum().item()), n_comp=int(v["n_comp"].sum().item()),
                                n_contrib=int(v["n_contrib"].sum().item())))
     maxP = max(s["pairs"] for s in pose_stats)
     if rast.capacity < maxP * 1.02:
@@ -409,14 +410,18 @@ def run_ours(args):
     poses = [pose_of(s) for s in range(args.steps)]
     mean = lambda key: float(np.mean([pose_stats[j][key] for j in poses]))
     P, n_eval, n_contrib, n_act = mean("pairs"), mean("n_eval"), mean("n_contrib"), mean("active")
+    n_reach, n_comp = mean("n_reach"), mean("n_comp")
     sh_b = (deg + 1) ** 2 * 3 * (2 if storage == B.GS_BF16 else 4)
     g_b = K * 4 * (2 if storage == B.GS_BF16 else 4)
     param_b = 12 + 12 + 16 + 4 + sh_b + g_b
     rec_b = (12 + 4 * ((3 * K + 3) // 4)) * 4
     g2d_b = 4 * ((9 + 3 * K + 3) // 4) * 4
     grad_b = 4 * (3 + 3 + 4 + 1 + (deg + 1) ** 2 * 3 + 3 * K + K + 2)
-    fp32_ops_fwd = 13 + 6 * K      # per evaluated pixel-pair: offset, quadratic form, exp, K (phase, cos, weight), alpha
-    fp32_ops_bwd = 43 + 16 * K     # per composited pixel-pair: recomputation + adjoints of Eq. 9-10
+    # algorithmic FP32 operations (Eq. 9-10): every walked pixel-pair needs the offset and the
+    # quadratic form of the envelope (7); pairs whose envelope passes o G >= alpha_min need exp, the
+    # K-term filter bank and alpha (6 + 6K); composited pairs the blend (7).  The backward walks the
+    # same positions (7) and, per composited pair, recomputes Eq. 9 and forms its adjoints (43 + 16K).
+    ops_walk, ops_reach, ops_comp, ops_bwd = 7, 6 + 6 * K, 7, 43 + 16 * K
     sm_mhz = (clocks or {}).get("sm_mhz") or 2032.0
     alu_peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # FP32 TFLOP/s (FMA = 2 ops)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -426,9 +431,9 @@ def run_ours(args):
         # all primitives: mean/scale/quat read, counts written; active ones: attributes read, record written
         "preprocess": ("hbm", n * (40 + 8) + n_act * (4 + param_b + rec_b) + P * 12),
         "bin_sort": ("hbm", P * (8 + npasses_needed * 24 + 8)),
-        "render_fwd": ("alu", n_eval * fp32_ops_fwd + n_contrib * 7),
+        "render_fwd": ("alu", n_eval * ops_walk + n_reach * ops_reach + n_comp * ops_comp),
         "loss": ("hbm", img.numel() * 12),
-        "render_bwd": ("alu", n_contrib * fp32_ops_bwd),
+        "render_bwd": ("alu", n_contrib * ops_walk + n_comp * ops_bwd),
         # gradients of every primitive written (zeros for culled ones), active ones read their inputs
         "preprocess_bwd": ("hbm", n * grad_b + n_act * (4 + param_b + g2d_b + grad_b)),
     }
@@ -487,7 +492,8 @@ def run_ours(args):
             "config": {"workload": workload_name(args, n, K, W, H, len(cams)), "n": n, "K": K, "sh_degree": deg,
                        "width": W, "height": H, "storage": args.storage, "poses": len(cams),
                        "pairs_per_view": round(P), "evaluated_pixel_pairs": round(n_eval),
-                       "composited_pixel_pairs": round(n_contrib),
+                       "walked_pixel_pairs_bwd": round(n_contrib), "reached_pixel_pairs": round(n_reach),
+                       "composited_pixel_pairs": round(n_comp),
                        "l2": "inputs larger than L2 (primitive arrays %.0f MB)" % (n * param_b / 1e6),
                        "parallelism": f"replicas x{world}"},
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},

@@ -137,7 +137,8 @@ typedef struct {
  * values [pairs] uint32 primitive index; ranges [tiles][2] uint32 [start, end);
  * T_final [H][W] float32; n_contrib [H][W] uint32 (1-based position in the tile's list of
  * the last composited pair); n_eval [H][W] uint32 pairs the forward pass evaluated at the pixel
- * (its tile's list length, or up to the pair that ended compositing); grad2d [n][grad2d_floats] float32
+ * (its tile's list length, or up to the pair that ended compositing); n_reach [H][W] uint32 of those,
+ * pairs whose envelope passed o G >= alpha_min; n_comp [H][W] uint32 pairs composited; grad2d [n][grad2d_floats] float32
  *   {d mu_x, d mu_y, d a, d b, d c, d opacity, d r, d g, d b, d f2D (2K), d w (K), 0 pad}. */
 typedef struct {
   float* records;
@@ -151,6 +152,8 @@ typedef struct {
   float* T_final;
   unsigned* n_contrib;
   unsigned* n_eval;
+  unsigned* n_reach;
+  unsigned* n_comp;
   float* grad2d;
   int record_floats;
   int grad2d_floats;

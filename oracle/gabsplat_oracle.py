@@ -364,7 +364,8 @@ def composite(px, py, rec, cfg):
     """Front-to-back compositing of L depth-ordered pairs at P pixels (Eq. 10).
 
     Returns colour [P,3], final transmittance [P], the 1-based list position of the last
-    composited pair [P] (0 if none) and ambiguity flags for forward / backward comparisons.
+    composited pair [P] (0 if none), ambiguity flags for forward / backward comparisons and the
+    number of composited pairs [P].
     """
     L = rec["mu2d"].shape[0]
     alpha_raw = gabor_alpha(px, py, rec, cfg)
@@ -391,7 +392,7 @@ def composite(px, py, rec, cfg):
     C = weight @ rec["rgb"]
     T_ext = torch.cat([T_before, T_after[:, -1:]], 1) if L > 0 else ones
     T_final = torch.gather(T_ext, 1, s[:, None])[:, 0]
-    return C, T_final, last, amb_f, amb_b
+    return C, T_final, last, amb_f, amb_b, include.sum(1)
 
 
 def _tile_pixels(tx, ty, width, height):
@@ -419,6 +420,7 @@ def _render_tiles(proj, spec, cam, cfg, dL_dC=None, tiles=None, max_elems=1 << 2
     img = torch.zeros(3, height, width, dtype=F64)
     Tf = torch.ones(height, width, dtype=F64)
     last = torch.zeros(height, width, dtype=torch.long)
+    comp = torch.zeros(height, width, dtype=torch.long)
     amb_f = torch.zeros(height, width, dtype=torch.bool)
     amb_b = torch.zeros(height, width, dtype=torch.bool)
     K = proj["weights"].shape[1]
@@ -435,7 +437,7 @@ def _render_tiles(proj, spec, cam, cfg, dL_dC=None, tiles=None, max_elems=1 << 2
         for c0 in range(0, gxp.shape[0], chunk):
             sl = slice(c0, c0 + chunk)
             rec = {k: proj[k].index_select(0, ids) for k in REC_KEYS}   # fresh graph per pixel chunk
-            C, T, lst, af, ab = composite(gxp[sl], gyp[sl], rec, cfg)
+            C, T, lst, af, ab, nc = composite(gxp[sl], gyp[sl], rec, cfg)
             out = C + T[:, None] * bg[None, :]
             if dL_dC is not None:
                 g = dL_dC[:, gyi[sl], gxi[sl]].T
@@ -443,9 +445,10 @@ def _render_tiles(proj, spec, cam, cfg, dL_dC=None, tiles=None, max_elems=1 << 2
             img[:, gyi[sl], gxi[sl]] = out.detach().T
             Tf[gyi[sl], gxi[sl]] = T.detach()
             last[gyi[sl], gxi[sl]] = lst
+            comp[gyi[sl], gxi[sl]] = nc
             amb_f[gyi[sl], gxi[sl]] = af
             amb_b[gyi[sl], gxi[sl]] = ab
-    return dict(image=img, T=Tf, n_contrib=last, ambiguous=amb_f, ambiguous_bwd=amb_b)
+    return dict(image=img, T=Tf, n_contrib=last, n_comp=comp, ambiguous=amb_f, ambiguous_bwd=amb_b)
 
 
 def render(prims: dict, cam, cfg, tiles=None, third_row="z", cull=True) -> dict:

@@ -43,6 +43,8 @@ WsLayout make_layout(u32 n_prims, int K, u32 n_tiles, u64 n_pixels, u64 capacity
   L.T_final = take((size_t)n_pixels * 4);
   L.n_contrib = take((size_t)n_pixels * 4);
   L.n_eval = take((size_t)n_pixels * 4);
+  L.n_reach = take((size_t)n_pixels * 4);
+  L.n_comp = take((size_t)n_pixels * 4);
   L.grad2d = take((size_t)n_prims * L.g2d_f * sizeof(float));
   L.total = off;
   return L;
@@ -68,6 +70,8 @@ WsPtrs make_ptrs(const WsLayout& L, void* ws) {
   p.T_final = reinterpret_cast<float*>(b + L.T_final);
   p.n_contrib = reinterpret_cast<u32*>(b + L.n_contrib);
   p.n_eval = reinterpret_cast<u32*>(b + L.n_eval);
+  p.n_reach = reinterpret_cast<u32*>(b + L.n_reach);
+  p.n_comp = reinterpret_cast<u32*>(b + L.n_comp);
   p.grad2d = reinterpret_cast<float*>(b + L.grad2d);
   p.capacity = L.capacity;
   p.n_chunks = L.n_chunks;
@@ -307,6 +311,8 @@ gs_status gabsplat_workspace_views(const gs_frame* frame, gs_ws_views* out) {
   out->T_final = p.T_final;
   out->n_contrib = p.n_contrib;
   out->n_eval = p.n_eval;
+  out->n_reach = p.n_reach;
+  out->n_comp = p.n_comp;
   out->grad2d = p.grad2d;
   out->record_floats = L.rec_f;
   out->grad2d_floats = L.g2d_f;

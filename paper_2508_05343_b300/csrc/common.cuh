@@ -91,7 +91,7 @@ struct WsHeader {
 // Offsets of every region of a workspace (host-computed; all 256-byte aligned).
 struct WsLayout {
   size_t header, table, records, touched, offsets, active, scan_status, keys0, keys1, vals0, vals1, hist,
-      sort_status, ranges, T_final, n_contrib, n_eval, grad2d, total;
+      sort_status, ranges, T_final, n_contrib, n_eval, n_reach, n_comp, grad2d, total;
   u32 n_prims, n_tiles, n_chunks, n_parts;
   u64 n_pixels, capacity;
   int K, rec_f, g2d_f;
@@ -116,6 +116,8 @@ struct WsPtrs {
   float* T_final;     // [n_pixels]
   u32* n_contrib;     // [n_pixels]
   u32* n_eval;        // [n_pixels] pairs the forward pass evaluated per pixel
+  u32* n_reach;       // [n_pixels] of those, pairs that passed the footprint test (o G >= alpha_min)
+  u32* n_comp;        // [n_pixels] pairs composited
   float* grad2d;      // [n_prims][g2d_f]
   u64 capacity;
   u32 n_chunks, n_parts;

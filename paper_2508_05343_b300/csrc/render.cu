@@ -98,13 +98,13 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
     const uint2 rg = p.ranges[tile];
     const float fpx = (float)px + 0.5f;
     float T[PPT], C0[PPT], C1[PPT], C2[PPT];
-    u32 last[PPT], evaluated[PPT];
+    u32 last[PPT], evaluated[PPT], reached[PPT], composited[PPT];
     bool done[PPT];
     bool tdone = true;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
       T[q] = 1.f; C0[q] = C1[q] = C2[q] = 0.f;
-      last[q] = 0; evaluated[q] = rg.y - rg.x;
+      last[q] = 0; evaluated[q] = rg.y - rg.x; reached[q] = 0; composited[q] = 0;
       done[q] = !(px < V.width && py0 + q < V.height);
       tdone = tdone && done[q];
     }
@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
             const float dy = __fsub_rn((float)(py0 + q) + 0.5f, h0.y);
             const float pw = gauss_power(h0, h1, dx, dy);
             if (pw >= h1.y) {
+              ++reached[q];
               const float G = ex2_approx(pw);
               const float bank = filter_bank<K>(reinterpret_cast<const float*>(r + 3), h1.w, dx, dy);
               const float alpha = fminf(amax, __fmul_rn(__fmul_rn(h1.z, G), bank));
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
                   C2[q] = __fmaf_rn(c.z, wgt, C2[q]);
                   T[q] = test;
                   last[q] = start + (u32)j + 1u - rg.x;
+                  ++composited[q];
                 }
               }
             }
@@ -166,6 +168,8 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
         p.T_final[V.pix_base + pix] = T[q];
         p.n_contrib[V.pix_base + pix] = last[q];
         p.n_eval[V.pix_base + pix] = evaluated[q];
+        p.n_reach[V.pix_base + pix] = reached[q];
+        p.n_comp[V.pix_base + pix] = composited[q];
       }
     }
     __syncthreads();

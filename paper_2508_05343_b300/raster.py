@@ -119,6 +119,8 @@ class Rasterizer:
             T_final=sl(v.T_final, npix, torch.float32).view(self.height, self.width),
             n_contrib=sl(v.n_contrib, npix, torch.int32).view(self.height, self.width),
             n_eval=sl(v.n_eval, npix, torch.int32).view(self.height, self.width),
+            n_reach=sl(v.n_reach, npix, torch.int32).view(self.height, self.width),
+            n_comp=sl(v.n_comp, npix, torch.int32).view(self.height, self.width),
             grad2d=sl(v.grad2d, self.n * v.grad2d_floats, torch.float32).view(self.n, v.grad2d_floats),
             pairs=pairs, tiles_x=v.tiles_x, tiles_y=v.tiles_y,
             record_floats=v.record_floats, grad2d_floats=v.grad2d_floats)

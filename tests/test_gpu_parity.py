@@ -69,6 +69,8 @@ def test_config0_every_stage(eps2d):
     np.testing.assert_allclose(T.cpu().numpy()[~amb], out["T"].numpy()[~amb], atol=IMG_TOL)
     nc = v["n_contrib"].cpu().numpy()
     assert (nc[~amb] == out["n_contrib"].numpy()[~amb]).mean() > 0.999
+    ncomp = v["n_comp"].cpu().numpy()
+    assert (ncomp[~amb] == out["n_comp"].numpy()[~amb]).mean() > 0.999
 
 
 def test_config1_forward_bitexact_bins_and_image():
