@@ -497,3 +497,44 @@ def loss_and_grad(image, target, kind="l1"):
     if kind == "l1":
         return float(np.abs(diff).sum() / N), np.sign(diff) / N
     return float((diff * diff).sum() / N), 2.0 * diff / N
+
+
+# ----------------------------------------------------------------------------------------------
+# Training loss with the structural term (Sec. 3.4.1, Eq. 11): L = (1 - lambda) L1 + lambda D-SSIM
+# ----------------------------------------------------------------------------------------------
+SSIM_WINDOW = 11       # Gaussian window of the SSIM index (Wang et al. 2004, the paper's metric)
+SSIM_SIGMA = 1.5
+SSIM_C1 = 0.01 ** 2    # (K1 L)^2 with K1 = 0.01, dynamic range L = 1
+SSIM_C2 = 0.03 ** 2    # (K2 L)^2 with K2 = 0.03
+
+
+def ssim_window() -> torch.Tensor:
+    """The 11 x 11 circular Gaussian window (sigma 1.5) normalised to unit sum."""
+    i = torch.arange(SSIM_WINDOW, dtype=F64) - SSIM_WINDOW // 2
+    g = torch.exp(-(i * i) / (2.0 * SSIM_SIGMA ** 2))
+    g = g / g.sum()
+    return torch.outer(g, g)
+
+
+def ssim_map(x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
+    """Per-pixel SSIM of two [C][H][W] images, channels separately: local means, variances and
+    covariance are window-weighted moments with zeros outside the image, and
+    SSIM = (2 mu_x mu_y + C1)(2 cov_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(var_x + var_y + C2))."""
+    C = x.shape[0]
+    w = ssim_window()[None, None].expand(C, 1, SSIM_WINDOW, SSIM_WINDOW).contiguous()
+    filt = lambda t: torch.nn.functional.conv2d(t[None], w, padding=SSIM_WINDOW // 2, groups=C)[0]
+    mx, my = filt(x), filt(y)
+    vx = filt(x * x) - mx * mx
+    vy = filt(y * y) - my * my
+    cxy = filt(x * y) - mx * my
+    return ((2 * mx * my + SSIM_C1) * (2 * cxy + SSIM_C2)) / ((mx * mx + my * my + SSIM_C1) * (vx + vy + SSIM_C2))
+
+
+def l1_dssim_loss_and_grad(image, target, lam=0.2):
+    """L = (1 - lam) mean|x - y| + lam (1 - mean SSIM(x, y)) over all pixels and channels (D-SSIM
+    read as 1 - SSIM), and dL/dimage by autodiff in float64 (|.| has derivative sign, 0 at 0)."""
+    x = torch.tensor(np.asarray(image, np.float64), requires_grad=True)
+    y = torch.tensor(np.asarray(target, np.float64))
+    L = (1.0 - lam) * (x - y).abs().mean() + lam * (1.0 - ssim_map(x, y).mean())
+    L.backward()
+    return float(L.detach()), x.grad.numpy()

@@ -453,3 +453,97 @@ def test_loss_gradients():
         im2 = img.copy(); im2[i, j, k] += h
         L2, _ = O.loss_and_grad(im2, tgt, kind)
         assert abs((L2 - L) / h - g[i, j, k]) < 1e-6
+
+
+# ---- training loss with the structural term (Sec. 3.4.1, Eq. 11) ------------------------------
+def _window_1d():
+    g = [math.exp(-((i - 5) ** 2) / (2 * 1.5 ** 2)) for i in range(11)]
+    s = sum(g)
+    return [v / s for v in g]
+
+
+def _moments_brute(x, y, c, i, j):
+    """Window-weighted moments at pixel (i, j) of channel c by explicit sums (zeros outside)."""
+    g = _window_1d()
+    H, W = x.shape[1:]
+    m = [0.0] * 5
+    for a in range(-5, 6):
+        for b in range(-5, 6):
+            r, q = i + a, j + b
+            if 0 <= r < H and 0 <= q < W:
+                w = g[a + 5] * g[b + 5]
+                u, v = float(x[c, r, q]), float(y[c, r, q])
+                m[0] += w * u; m[1] += w * v; m[2] += w * u * u; m[3] += w * v * v; m[4] += w * u * v
+    return m
+
+
+def test_ssim_brute_force_tiny():
+    """Every pixel of a 2 x 9 x 13 image pair (smaller than the window in one direction, so every
+    pixel sees the zero border): explicit windowed sums, then the SSIM index."""
+    rng = np.random.default_rng(41)
+    x, y = rng.random((2, 9, 13)), rng.random((2, 9, 13))
+    got = O.ssim_map(torch.tensor(x), torch.tensor(y)).numpy()
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    for c in range(2):
+        for i in range(9):
+            for j in range(13):
+                mx, my, exx, eyy, exy = _moments_brute(x, y, c, i, j)
+                vx, vy, cv = exx - mx * mx, eyy - my * my, exy - mx * my
+                ref = (2 * mx * my + C1) * (2 * cv + C2) / ((mx * mx + my * my + C1) * (vx + vy + C2))
+                assert abs(got[c, i, j] - ref) < 1e-12, (c, i, j)
+
+
+def test_ssim_closed_forms():
+    rng = np.random.default_rng(42)
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    x = rng.random((3, 24, 30))
+    # identical images: 1 everywhere, zero loss
+    np.testing.assert_allclose(O.ssim_map(torch.tensor(x), torch.tensor(x)).numpy(), 1.0, atol=1e-12)
+    assert O.l1_dssim_loss_and_grad(x, x)[0] == 0.0
+    # constant images a, b: away from the border only the luminance factor is left
+    a, b = 0.7, 0.2
+    s = O.ssim_map(torch.full((1, 24, 30), a, dtype=torch.float64), torch.full((1, 24, 30), b, dtype=torch.float64))
+    np.testing.assert_allclose(s[0, 5:-5, 5:-5].numpy(), (2 * a * b + C1) / (a * a + b * b + C1), rtol=1e-12)
+    # y = x + c: equal variances and covariance, so the contrast-structure factor is 1
+    s = O.ssim_map(torch.tensor(x), torch.tensor(x + 0.3)).numpy()
+    for (c, i, j) in [(0, 7, 9), (1, 12, 20), (2, 18, 6)]:
+        mx = _moments_brute(x, x, c, i, j)[0]
+        my = mx + 0.3
+        assert abs(s[c, i, j] - (2 * mx * my + C1) / (mx * mx + my * my + C1)) < 1e-12
+    # y = 1 - x: covariance = -variance, so the contrast-structure factor is (C2 - 2 var)/(C2 + 2 var)
+    s = O.ssim_map(torch.tensor(x), torch.tensor(1.0 - x)).numpy()
+    for (c, i, j) in [(0, 6, 11), (2, 15, 24)]:
+        mx, _, exx, _, _ = _moments_brute(x, x, c, i, j)
+        var, my = exx - mx * mx, 1.0 - mx
+        ref = (2 * mx * my + C1) / (mx * mx + my * my + C1) * (C2 - 2 * var) / (C2 + 2 * var)
+        assert abs(s[c, i, j] - ref) < 1e-12
+
+
+def test_l1_dssim_is_the_weighted_sum_and_its_gradient():
+    """lambda = 0 is the mean L1 loss with gradient sign(x - y)/N; lambda = 1 is 1 - mean SSIM;
+    the value is affine in lambda; the gradient matches central finite differences."""
+    rng = np.random.default_rng(43)
+    x, y = rng.random((2, 12, 15)), rng.random((2, 12, 15))
+    N = x.size
+    l0, g0 = O.l1_dssim_loss_and_grad(x, y, lam=0.0)
+    assert abs(l0 - np.abs(x - y).mean()) < 1e-14
+    np.testing.assert_allclose(g0, np.sign(x - y) / N, atol=1e-18)
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    ssum = 0.0
+    for c in range(2):
+        for i in range(12):
+            for j in range(15):
+                mx, my, exx, eyy, exy = _moments_brute(x, y, c, i, j)
+                ssum += (2 * mx * my + C1) * (2 * (exy - mx * my) + C2) / (
+                    (mx * mx + my * my + C1) * (exx - mx * mx + eyy - my * my + C2))
+    l1, _ = O.l1_dssim_loss_and_grad(x, y, lam=1.0)
+    assert abs(l1 - (1.0 - ssum / N)) < 1e-12
+    l2, g2 = O.l1_dssim_loss_and_grad(x, y, lam=0.2)
+    assert abs(l2 - (0.8 * l0 + 0.2 * l1)) < 1e-14
+    h = 1e-6
+    for (c, i, j) in [(0, 0, 0), (1, 5, 7), (0, 11, 14), (1, 3, 12)]:
+        xp, xm = x.copy(), x.copy()
+        xp[c, i, j] += h
+        xm[c, i, j] -= h
+        fd = (O.l1_dssim_loss_and_grad(xp, y)[0] - O.l1_dssim_loss_and_grad(xm, y)[0]) / (2 * h)
+        assert abs(fd - g2[c, i, j]) < 1e-8 * max(1.0, abs(g2[c, i, j]) * N), (c, i, j, fd, g2[c, i, j])
