@@ -233,6 +233,23 @@ gs_status gabsplat_loss(const float* image, const float* target, long long count
 gs_status gabsplat_loss_noalloc(const float* image, const float* target, long long count, int kind, double* loss_out,
                                 float* dL_dimage, gs_stream stream);
 
+/* Training objective of Sec. 3.4.1 (Eq. 11): L = (1 - lambda) L1 + lambda D-SSIM, the paper's
+ * lambda being 0.2.  D-SSIM is 1 - mean SSIM, with SSIM the structural similarity index (Wang et
+ * al. 2004, the metric of the paper's Sec. 4) computed per channel from window-weighted local
+ * moments: an 11 x 11 Gaussian window of standard deviation 1.5 normalised to unit sum, zeros
+ * outside the image, C1 = 0.01^2 and C2 = 0.03^2 (intensities in [0, 1]).  Both means run over all
+ * channels x height x width values.
+ *   image, target: [channels][height][width] float32, device; dL_dimage: the same shape, written
+ *   with dL/dimage (the derivative of |d| is taken as 0 at d = 0); loss_out: one float64, device;
+ *   scratch: device memory of gabsplat_loss_l1_dssim_scratch_bytes(channels, height, width) bytes.
+ * The caller owns every buffer.  One fused kernel computes the loss and its gradient (float32
+ * arithmetic, float64 for the final sums) plus a one-block reduction; both run on `stream`.
+ * Returns GS_ERR_INVALID_ARG for a null pointer, channels outside [1, 64], a height or width
+ * outside [1, 32768], or lambda outside [0, 1]. */
+size_t gabsplat_loss_l1_dssim_scratch_bytes(int channels, int height, int width);
+gs_status gabsplat_loss_l1_dssim(const float* image, const float* target, int channels, int height, int width,
+                                 float lambda, double* loss_out, float* dL_dimage, void* scratch, gs_stream stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Batched frames (serving).  A batch renders up to GS_MAX_VIEWS views -- each a camera with its own
  * resolution over one resident scene -- with one launch sequence (forward only): the views'

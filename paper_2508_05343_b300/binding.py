@@ -77,6 +77,9 @@ SIGNATURES = {
     "gabsplat_loss_scratch_bytes": (C.c_size_t, [C.c_longlong]),
     "gabsplat_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),
+    "gabsplat_loss_l1_dssim_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+    "gabsplat_loss_l1_dssim": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_float, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]),
     "gabsplat_loss_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p,
                                         C.c_void_p]),
     "gabsplat_device_status": (C.c_int, [P_(gs_frame), P_(C.c_int), P_(C.c_ulonglong), C.c_void_p]),
@@ -171,6 +174,18 @@ def gabsplat_loss_scratch_bytes(count):
 def gabsplat_loss(image, target, kind, loss_out, dL_dimage, scratch, stream=None):
     _check("gabsplat_loss", lib.gabsplat_loss(_ptr(image), _ptr(target), image.numel(), kind, _ptr(loss_out),
                                               _ptr(dL_dimage), _ptr(scratch), _stream(stream)))
+
+
+def gabsplat_loss_l1_dssim_scratch_bytes(channels, height, width):
+    return int(lib.gabsplat_loss_l1_dssim_scratch_bytes(channels, height, width))
+
+
+def gabsplat_loss_l1_dssim(image, target, lam, loss_out, dL_dimage, scratch, stream=None):
+    """image, target: [C][H][W] float32 device tensors; lam: the D-SSIM weight (0.2 in the paper)."""
+    Cc, H, W = image.shape
+    _check("gabsplat_loss_l1_dssim", lib.gabsplat_loss_l1_dssim(_ptr(image), _ptr(target), Cc, H, W, lam,
+                                                                _ptr(loss_out), _ptr(dL_dimage), _ptr(scratch),
+                                                                _stream(stream)))
 
 
 def gabsplat_loss_noalloc(image, target, kind, loss_out, dL_dimage, stream=None):

@@ -274,6 +274,24 @@ gs_status gabsplat_loss(const float* image, const float* target, long long count
                                blocks, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+static bool l1_dssim_sizes_ok(int channels, int height, int width) {
+  return channels >= 1 && channels <= 64 && height >= 1 && width >= 1 && height <= 32768 && width <= 32768;
+}
+
+size_t gabsplat_loss_l1_dssim_scratch_bytes(int channels, int height, int width) {
+  if (!l1_dssim_sizes_ok(channels, height, width)) return 0;
+  return l1_dssim_partials(channels, height, width) * sizeof(double);
+}
+
+gs_status gabsplat_loss_l1_dssim(const float* image, const float* target, int channels, int height, int width,
+                                 float lambda, double* loss_out, float* dL_dimage, void* scratch, gs_stream stream) {
+  if (!image || !target || !loss_out || !dL_dimage || !scratch) return GS_ERR_INVALID_ARG;
+  if (!l1_dssim_sizes_ok(channels, height, width)) return GS_ERR_INVALID_ARG;
+  if (!(lambda >= 0.f && lambda <= 1.f)) return GS_ERR_INVALID_ARG;
+  return from_cuda(launch_l1_dssim(image, target, channels, height, width, lambda, loss_out, dL_dimage,
+                                   reinterpret_cast<double*>(scratch), reinterpret_cast<cudaStream_t>(stream)));
+}
+
 gs_status gabsplat_device_status(const gs_frame* frame, int* status, unsigned long long* pairs, gs_stream stream) {
   FrameTable t;
   WsLayout L;

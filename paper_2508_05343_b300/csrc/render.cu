@@ -395,51 +395,6 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
   }
 }
 
-__global__ void k_loss_partial(const float* __restrict__ img, const float* __restrict__ tgt, long long count, int kind,
-                               float* __restrict__ dL, double* __restrict__ partials) {
-  __shared__ double s_sum[8];
-  const double invN = 1.0 / (double)count;
-  double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
-    const float d = img[i] - tgt[i];
-    if (kind == GS_LOSS_L1) {
-      acc += fabs((double)d);
-      dL[i] = (float)((d > 0.f ? 1.0 : (d < 0.f ? -1.0 : 0.0)) * invN);
-    } else {
-      acc += (double)d * (double)d;
-      dL[i] = (float)(2.0 * (double)d * invN);
-    }
-  }
-  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += s_sum[w];
-    partials[blockIdx.x] = s;
-  }
-}
-
-__global__ void k_loss_final(const double* __restrict__ partials, int n, long long count, double* out) {
-  __shared__ double s[256];
-  double a = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a += partials[i];
-  s[threadIdx.x] = a;
-  __syncthreads();
-  for (int st = 128; st; st >>= 1) {
-    if ((int)threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = s[0] / (double)count;
-}
-
-cudaError_t launch_loss(const float* img, const float* tgt, long long count, int kind, double* loss_out, float* dL,
-                        double* partials, int nblocks, cudaStream_t s) {
-  k_loss_partial<<<nblocks, 256, 0, s>>>(img, tgt, count, kind, dL, partials);
-  k_loss_final<<<1, 256, 0, s>>>(partials, nblocks, count, loss_out);
-  return cudaGetLastError();
-}
-
 template <int K>
 static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, const u32* vals, float* rgb, float* T,
                                 const Launch& L) {
