@@ -30,6 +30,9 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+bwd ms/iter @1.5M prims 1600x1064; serve p50/p99 ms & frames/s vs plain"
 UNIT = "ms/iter"
 SM_COUNT_B300 = 148
+# fused L1 + D-SSIM per image value: five windowed moments and three windowed adjoint maps, each
+# separable (2 x 11 taps, an FMA = 2 flops), the SSIM index and its partials (~25), the gradient (5)
+SSIM_FLOPS_PER_VALUE = 2 * 11 * 2 * (5 + 3) + 25 + 5
 FP32_LANES_PER_SM = 128
 
 
@@ -43,6 +46,9 @@ def parse():
     ap.add_argument("--config", type=int, default=2, choices=[2, 4])
     ap.add_argument("--K", type=int, default=None, help="override the number of Gabor components")
     ap.add_argument("--n", type=int, default=None, help="override the primitive count")
+    ap.add_argument("--loss", choices=["l1", "l1-dssim"], default="l1",
+                    help="loss in the step: mean L1 (the training-iteration configuration) or Eq. 11's "
+                         "0.8 L1 + 0.2 D-SSIM")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement (config 3)")
@@ -57,7 +63,8 @@ def parse():
 
 def workload_name(args, n, K, W, H, poses=16):
     st = "bf16-storage" if args.storage == "bf16" else "f32"
-    return f"3DGabSplat train iteration: {n} prims K={K} SH3, {W}x{H}, {poses} orbit poses, L1 loss, {st}"
+    loss = "L1 loss" if getattr(args, "loss", "l1") == "l1" else "0.8 L1 + 0.2 D-SSIM loss"
+    return f"3DGabSplat train iteration: {n} prims K={K} SH3, {W}x{H}, {poses} orbit poses, {loss}, {st}"
 
 
 # ----------------------------------------------------------------------------------------------
@@ -340,7 +347,8 @@ def run_ours(args):
     img = torch.empty(3, H, W, device=dev)
     dL = torch.empty_like(img)
     loss_val = torch.zeros(1, dtype=torch.float64, device=dev)
-    scratch = torch.empty(B.gabsplat_loss_scratch_bytes(img.numel()), dtype=torch.uint8, device=dev)
+    scratch = torch.empty(max(B.gabsplat_loss_scratch_bytes(img.numel()),
+                              B.gabsplat_loss_l1_dssim_scratch_bytes(3, H, W)), dtype=torch.uint8, device=dev)
     grads = {k: torch.empty(pt[k].shape, dtype=torch.float32, device=dev) for k in raster.ATTRS}
     grads["means2d"] = torch.empty(n, 2, device=dev)
     g_s = B.gs_prim_grads()
@@ -369,7 +377,11 @@ def run_ours(args):
         if evs: evs[2].record()
         B.gabsplat_render_fwd(frame, img, None)
         if evs: evs[3].record()
-        B.gabsplat_loss(img, targets[j] if target is None else target, B.GS_LOSS_L1, loss_val, dL, scratch)
+        tj = targets[j] if target is None else target
+        if args.loss == "l1":
+            B.gabsplat_loss(img, tj, B.GS_LOSS_L1, loss_val, dL, scratch)
+        else:
+            B.gabsplat_loss_l1_dssim(img, tj, 0.2, loss_val, dL, scratch)
         if evs: evs[4].record()
         B.gabsplat_render_bwd_2d(frame, dL)
         if evs: evs[5].record()
@@ -451,7 +463,7 @@ def run_ours(args):
         "preprocess": ("hbm", n * (40 + 8) + n_act * (4 + param_b + rec_b) + P * 12),
         "bin_sort": ("hbm", P * (8 + npasses_needed * 24 + 8)),
         "render_fwd": ("alu", n_eval * ops_walk + n_reach * ops_reach + n_comp * ops_comp),
-        "loss": ("hbm", img.numel() * 12),
+        "loss": ("hbm", img.numel() * 12) if args.loss == "l1" else ("alu", img.numel() * SSIM_FLOPS_PER_VALUE),
         "render_bwd": ("alu", n_contrib * ops_walk + n_comp * ops_bwd),
         # gradients of every primitive written (zeros for culled ones), active ones read their inputs
         "preprocess_bwd": ("hbm", n * grad_b + n_act * (4 + param_b + g2d_b + grad_b)),
@@ -477,6 +489,21 @@ def run_ours(args):
     for nm, (bd, amt) in work.items():
         s_ = stage_ms[nm] * 1e-3
         stage_fracs[nm] = round((amt / s_ / 1e9 / hbm_peak) if bd == "hbm" else (amt / s_ / 1e12 / alu_peak), 4)
+
+    # the fused L1 + D-SSIM loss (Eq. 11) timed on its own on the same images, whatever --loss is
+    ssim_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for r in range(3):
+        B.gabsplat_loss_l1_dssim(img, targets[0], 0.2, loss_val, dL, scratch)
+    ssim_ev[0].record()
+    for r in range(20):
+        B.gabsplat_loss_l1_dssim(img, targets[r % len(targets)], 0.2, loss_val, dL, scratch)
+    ssim_ev[1].record()
+    torch.cuda.synchronize()
+    ssim_ms = ssim_ev[0].elapsed_time(ssim_ev[1]) / 20
+    ssim_tf = img.numel() * SSIM_FLOPS_PER_VALUE / (ssim_ms * 1e-3) / 1e12
+    l1_dssim = {"ms": round(ssim_ms, 4), "bound": "alu", "achieved": round(ssim_tf, 3), "peak": round(alu_peak, 3),
+                "unit": "TFLOP/s", "frac": round(ssim_tf / alu_peak, 4),
+                "hbm_frac": round(img.numel() * 12 / (ssim_ms * 1e-3) / 1e9 / hbm_peak, 4)}
 
     crop = None
     if rank == 0 and args.oracle_crop:
@@ -517,6 +544,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "stage_roofline_frac": stage_fracs,
+            "l1_dssim": l1_dssim,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

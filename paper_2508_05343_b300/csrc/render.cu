@@ -32,6 +32,12 @@ __device__ __forceinline__ void stage_record(const float* __restrict__ rec, floa
   for (int i = 3; i < SRec<K>::F4; ++i) dst[i] = __ldg(src + i);
 }
 
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -211,6 +217,26 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[32], int lane) {
   return v[0];
 }
 
+// One pair's accumulated 2D gradients, converted from the log2-domain conic (A' = -a/2 log2 e,
+// B' = -b log2 e, C' = -c/2 log2 e) to (a, b, c), added to its grad2d row with one vector atomic
+// per 4 values (zero groups skipped).
+template <int K>
+__device__ __forceinline__ void flush_pair_grads(const float* a, float* dst) {
+  constexpr int NV = 9 + 3 * K, NG = g2d_floats(K);
+  const float cA = -0.5f * LOG2E, cB = -LOG2E;
+  float row[NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) row[i] = i < NV ? a[i] : 0.f;
+  row[2] *= cA;
+  row[3] *= cB;
+  row[4] *= cA;
+#pragma unroll
+  for (int i = 0; i < NG / 4; ++i) {
+    const float4 qv = make_float4(row[4 * i], row[4 * i + 1], row[4 * i + 2], row[4 * i + 3]);
+    if (qv.x != 0.f || qv.y != 0.f || qv.z != 0.f || qv.w != 0.f) atomicAdd(reinterpret_cast<float4*>(dst) + i, qv);
+  }
+}
+
 template <int K, int PPT>
 __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32* vals,
                                                             const float* __restrict__ dL_drgb) {
@@ -278,7 +304,13 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
     if (lane == 0) atomicMax(&s_max, wlast);
     __syncthreads();
     const u32 end = rg.x + s_max;
-    for (u32 bend = end; bend > rg.x;) {
+    u32 flush_cnt = 0;   // pairs of the previous batch whose accumulators are still to be flushed
+    for (u32 bend = end;;) {
+      // Thread tid owns row tid of the batch buffers: it flushes the previous batch's pair tid,
+      // clears its accumulator row and stages this batch's pair tid, so one barrier separates
+      // this phase from the processing that reads every row.
+      if ((u32)tid < flush_cnt) flush_pair_grads<K>(s_acc + tid * NS, p.grad2d + (size_t)s_id[tid] * NG);
+      if (bend <= rg.x) break;                  // CTA-uniform
       const u32 bstart = bend - rg.x > (u32)NT ? bend - NT : rg.x;
       const u32 cnt = bend - bstart;
       if ((u32)tid < cnt) {
@@ -322,7 +354,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
           if (alpha < amin) continue;
           contrib = true;
           const float oma = 1.f - alpha;
-          const float ioma = __frcp_rn(oma);
+          const float ioma = rcp_approx(oma);
           T[q] = T[q] * ioma;                              // transmittance before this pair
           const float4 c = r[2];
           const float wgt = alpha * T[q];
@@ -371,24 +403,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
         }
       }
       __syncthreads();
-      // flush the batch's accumulators: one vector atomic per (pair, 4 values) for the whole tile
-      if ((u32)tid < cnt) {
-        float* dst = p.grad2d + (size_t)s_id[tid] * NG;
-        const float* a = s_acc + tid * NS;
-        const float cA = -0.5f * LOG2E, cB = -LOG2E;
-        float row[NG];
-#pragma unroll
-        for (int i = 0; i < NG; ++i) row[i] = i < NV ? a[i] : 0.f;
-        row[2] *= cA;   // A' = -a/2 log2 e  ->  dL/da
-        row[3] *= cB;   // B' = -b log2 e
-        row[4] *= cA;   // C' = -c/2 log2 e
-#pragma unroll
-        for (int i = 0; i < NG / 4; ++i) {
-          const float4 qv = make_float4(row[4 * i], row[4 * i + 1], row[4 * i + 2], row[4 * i + 3]);
-          if (qv.x != 0.f || qv.y != 0.f || qv.z != 0.f || qv.w != 0.f) atomicAdd(reinterpret_cast<float4*>(dst) + i, qv);
-        }
-      }
-      __syncthreads();
+      flush_cnt = cnt;
       bend = bstart;
     }
     __syncthreads();
