@@ -13,7 +13,8 @@ __device__ __forceinline__ void add_compensated(float& s, float& c, float x) {
   s = t;
 }
 
-// Sum of one double per thread over a CTA of LOSS_THREADS threads; the result is valid on thread 0.
+// Sum of one double per thread over a CTA of NTHREADS threads; the result is valid on thread 0.
+template <int NTHREADS>
 __device__ __forceinline__ double cta_sum(double v, double* s_warp) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -21,7 +22,7 @@ __device__ __forceinline__ double cta_sum(double v, double* s_warp) {
   __syncthreads();
   double t = 0.0;
   if (threadIdx.x == 0)
-    for (int w = 0; w < LOSS_THREADS / 32; ++w) t += s_warp[w];
+    for (int w = 0; w < NTHREADS / 32; ++w) t += s_warp[w];
   return t;
 }
 
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_loss_partial(const float* __re
       dL[i] = (float)(2.0 * (double)d * invN);
     }
   }
-  const double t = cta_sum((double)s + (double)c, s_warp);
+  const double t = cta_sum<LOSS_THREADS>((double)s + (double)c, s_warp);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
@@ -84,19 +85,32 @@ cudaError_t launch_loss(const float* img, const float* tgt, long long count, int
 //   ds/dmx = s (2 my/a1 - 2 mx/b1),
 // the window being symmetric and A = B = C = 0 at pixels outside the image.
 //
-// One CTA per 32 x 32 output tile of one channel, everything in shared memory: the inputs over the
-// tile and a 10-pixel ring, the five moments and then A, B, C over the tile and a 5-pixel ring,
-// and the window applied to A, B, C over the tile.  Each separable pass keeps a run of outputs per
-// thread in registers, so one shared-memory load feeds up to 11 FMAs.
+// One CTA per 32 x 32 output tile of one channel, everything in shared memory:
+//   1. the inputs over the tile and a 10-pixel ring;
+//   2-3. the five moments, then SSIM and A, B, C, over the tile and a 5-pixel ring;
+//   4-5. the window applied to A, B, C over the tile, and the gradient.
+// Each separable pass keeps a run of outputs per thread in registers, so one shared-memory load
+// feeds up to 11 FMAs.  Row strides are odd and horizontal passes give consecutive lanes
+// consecutive rows, so no pass has bank conflicts.  A, B, C overwrite the inputs (step 5 reads x
+// and y at the tile's pixels again from global memory), which keeps three CTAs per SM.
 // ------------------------------------------------------------------------------------------------
 constexpr int SS_T = 32;                      // output tile edge
 constexpr int SS_R = 5;                       // window radius
 constexpr int SS_K = 2 * SS_R + 1;            // window taps
-constexpr int SS_IN = SS_T + 4 * SS_R;        // 52: inputs
-constexpr int SS_MID = SS_T + 2 * SS_R;       // 42: moments and adjoint maps
-constexpr int SS_THREADS = 256;
-constexpr size_t SS_SMEM = sizeof(float) * (2 * SS_IN * SS_IN + 5 * SS_IN * SS_MID + 3 * SS_MID * SS_MID);
-static_assert(3 * SS_MID * SS_T <= 5 * SS_IN * SS_MID, "backward rows reuse the moment rows");
+constexpr int SS_IN = SS_T + 4 * SS_R;        // 52: input rows and columns
+constexpr int SS_MID = SS_T + 2 * SS_R;       // 42: rows and columns of the moments and of A, B, C
+constexpr int SX = SS_IN + 1;                 // odd row strides (floats)
+constexpr int SH = SS_MID + 1;
+constexpr int SB = SS_T + 1;
+#ifndef GS_SSIM_THREADS
+#define GS_SSIM_THREADS 320
+#endif
+constexpr int SS_THREADS = GS_SSIM_THREADS;
+constexpr int SS_IN_FLOATS = 2 * SS_IN * SX;          // x, y; later A, B, C
+constexpr int SS_HM_FLOATS = 5 * SS_IN * SH;          // horizontal moments; later the horizontal A, B, C
+constexpr size_t SS_SMEM = sizeof(float) * (SS_IN_FLOATS + SS_HM_FLOATS);
+static_assert(3 * SS_MID * SH <= SS_IN_FLOATS, "A, B, C reuse the input rows");
+static_assert(3 * SS_MID * SB <= SS_HM_FLOATS, "the horizontal pass of A, B, C reuses the moment rows");
 
 struct SsimWindow {
   float w[SS_K];
@@ -106,11 +120,11 @@ __global__ void __launch_bounds__(SS_THREADS) k_l1_dssim(const float* __restrict
                                                         int H, int W, float lambda, double invN, SsimWindow win,
                                                         float* __restrict__ dL, double* __restrict__ partials) {
   extern __shared__ __align__(16) float sm[];
-  float* sx = sm;                                  // [IN][IN]
-  float* sy = sx + SS_IN * SS_IN;                  // [IN][IN]
-  float* hm = sy + SS_IN * SS_IN;                  // [5][IN][MID] horizontal moments
-  float* am = hm + 5 * SS_IN * SS_MID;             // [3][MID][MID] A, B, C
-  float* hb = hm;                                  // [3][MID][T] horizontal pass of A, B, C
+  float* sx = sm;                                  // [IN][SX]
+  float* sy = sx + SS_IN * SX;                     // [IN][SX]
+  float* am = sm;                                  // [3][MID][SH] A, B, C (after step 2)
+  float* hm = sm + SS_IN_FLOATS;                   // [5][IN][SH] horizontal moments
+  float* hb = hm;                                  // [3][MID][SB] horizontal pass of A, B, C (after step 3)
   __shared__ double s_warp[SS_THREADS / 32];
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * SS_T, y0 = blockIdx.y * SS_T;
@@ -119,21 +133,38 @@ __global__ void __launch_bounds__(SS_THREADS) k_l1_dssim(const float* __restrict
   const float* Y = tgt + blockIdx.z * plane;
   constexpr float C1 = 0.0001f, C2 = 0.0009f;
 
-  // 1. inputs over the tile and a 10-pixel ring, zero outside the image
-  for (int i = tid; i < SS_IN * SS_IN; i += SS_THREADS) {
-    const int r = i / SS_IN, q = i - r * SS_IN;
-    const int gy = y0 - 2 * SS_R + r, gx = x0 - 2 * SS_R + q;
-    const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-    sx[i] = in ? __ldg(X + (size_t)gy * W + gx) : 0.f;
-    sy[i] = in ? __ldg(Y + (size_t)gy * W + gx) : 0.f;
+  // 1. inputs over the tile and a 10-pixel ring, zero outside the image (every load of a thread
+  //    issued before the first store, so their latencies overlap)
+  {
+    constexpr int NL = (SS_IN * SS_IN + SS_THREADS - 1) / SS_THREADS;
+    float lx[NL], ly[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int i = tid + k * SS_THREADS;
+      const int r = i / SS_IN, q = i - r * SS_IN;
+      const int gy = y0 - 2 * SS_R + r, gx = x0 - 2 * SS_R + q;
+      const bool in = i < SS_IN * SS_IN && gy >= 0 && gy < H && gx >= 0 && gx < W;
+      lx[k] = in ? __ldg(X + (size_t)gy * W + gx) : 0.f;
+      ly[k] = in ? __ldg(Y + (size_t)gy * W + gx) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int i = tid + k * SS_THREADS;
+      if (i < SS_IN * SS_IN) {
+        const int r = i / SS_IN, q = i - r * SS_IN;
+        sx[r * SX + q] = lx[k];
+        sy[r * SX + q] = ly[k];
+      }
+    }
   }
   __syncthreads();
 
-  // 2. horizontal window over x, y, x^2, y^2, xy: IN rows x MID columns, 7 outputs per item
+  // 2. horizontal window over x, y, x^2, y^2, xy: IN rows x MID columns, 7 outputs per item,
+  //    consecutive lanes on consecutive rows
   for (int it = tid; it < SS_IN * 6; it += SS_THREADS) {
-    const int r = it / 6, c0 = (it - r * 6) * 7;
-    const float* px = sx + r * SS_IN + c0;
-    const float* py = sy + r * SS_IN + c0;
+    const int c0 = (it / SS_IN) * 7, r = it - (it / SS_IN) * SS_IN;
+    const float* px = sx + r * SX + c0;
+    const float* py = sy + r * SX + c0;
     float acc[5][7];
 #pragma unroll
     for (int m = 0; m < 5; ++m)
@@ -159,11 +190,12 @@ __global__ void __launch_bounds__(SS_THREADS) k_l1_dssim(const float* __restrict
 #pragma unroll
     for (int m = 0; m < 5; ++m)
 #pragma unroll
-      for (int o = 0; o < 7; ++o) hm[m * SS_IN * SS_MID + r * SS_MID + c0 + o] = acc[m][o];
+      for (int o = 0; o < 7; ++o) hm[(m * SS_IN + r) * SH + c0 + o] = acc[m][o];
   }
   __syncthreads();
 
-  // 3. vertical window -> moments over MID x MID, then SSIM and A, B, C (6 rows per item)
+  // 3. vertical window -> moments over MID x MID, then SSIM and A, B, C (6 rows per item,
+  //    consecutive lanes on consecutive columns)
   float dssim = 0.f;
   for (int it = tid; it < SS_MID * 7; it += SS_THREADS) {
     const int r0 = (it / SS_MID) * 6, q = it - (it / SS_MID) * SS_MID;
@@ -176,7 +208,7 @@ __global__ void __launch_bounds__(SS_THREADS) k_l1_dssim(const float* __restrict
     for (int j = 0; j < 6 + 2 * SS_R; ++j) {
       float val[5];
 #pragma unroll
-      for (int m = 0; m < 5; ++m) val[m] = hm[m * SS_IN * SS_MID + (r0 + j) * SS_MID + q];
+      for (int m = 0; m < 5; ++m) val[m] = hm[(m * SS_IN + r0 + j) * SH + q];
 #pragma unroll
       for (int o = 0; o < 6; ++o) {
         const int k = j - o;
@@ -203,14 +235,15 @@ __global__ void __launch_bounds__(SS_THREADS) k_l1_dssim(const float* __restrict
         A = s * (2.f * my / a1 - 2.f * mx / b1) - 2.f * mx * Bv - my * Cv;
         if (r >= SS_R && r < SS_R + SS_T && q >= SS_R && q < SS_R + SS_T) dssim += 1.f - s;
       }
-      am[r * SS_MID + q] = A;
-      am[SS_MID * SS_MID + r * SS_MID + q] = Bv;
-      am[2 * SS_MID * SS_MID + r * SS_MID + q] = Cv;
+      am[(0 * SS_MID + r) * SH + q] = A;
+      am[(1 * SS_MID + r) * SH + q] = Bv;
+      am[(2 * SS_MID + r) * SH + q] = Cv;
     }
   }
   __syncthreads();
 
-  // 4. horizontal window over A, B, C: MID rows x T columns, 8 outputs per item
+  // 4. horizontal window over A, B, C: MID rows x T columns, 8 outputs per item, consecutive
+  //    lanes on consecutive rows
   for (int it = tid; it < SS_MID * 4; it += SS_THREADS) {
     const int c0 = (it / SS_MID) * 8, r = it - (it / SS_MID) * SS_MID;
     float acc[3][8];
@@ -222,7 +255,7 @@ __global__ void __launch_bounds__(SS_THREADS) k_l1_dssim(const float* __restrict
     for (int j = 0; j < 8 + 2 * SS_R; ++j) {
       float val[3];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) val[m] = am[m * SS_MID * SS_MID + r * SS_MID + c0 + j];
+      for (int m = 0; m < 3; ++m) val[m] = am[(m * SS_MID + r) * SH + c0 + j];
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
         const int k = j - o;
@@ -236,7 +269,7 @@ __global__ void __launch_bounds__(SS_THREADS) k_l1_dssim(const float* __restrict
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
-      for (int o = 0; o < 8; ++o) hb[m * SS_MID * SS_T + r * SS_T + c0 + o] = acc[m][o];
+      for (int o = 0; o < 8; ++o) hb[(m * SS_MID + r) * SB + c0 + o] = acc[m][o];
   }
   __syncthreads();
 
@@ -254,7 +287,7 @@ __global__ void __launch_bounds__(SS_THREADS) k_l1_dssim(const float* __restrict
     for (int j = 0; j < 4 + 2 * SS_R; ++j) {
       float val[3];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) val[m] = hb[m * SS_MID * SS_T + (r0 + j) * SS_T + q];
+      for (int m = 0; m < 3; ++m) val[m] = hb[(m * SS_MID + r0 + j) * SB + q];
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
         const int k = j - o;
@@ -267,18 +300,19 @@ __global__ void __launch_bounds__(SS_THREADS) k_l1_dssim(const float* __restrict
     }
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
-      const int r = r0 + o, gy = y0 + r, gx = x0 + q;
+      const int gy = y0 + r0 + o, gx = x0 + q;
       if (gy < H && gx < W) {
-        const float x = sx[(r + 2 * SS_R) * SS_IN + q + 2 * SS_R], y = sy[(r + 2 * SS_R) * SS_IN + q + 2 * SS_R];
+        const size_t pix = (size_t)gy * W + gx;
+        const float x = __ldg(X + pix), y = __ldg(Y + pix);
         const float d = x - y;
         const float dS = acc[0][o] + 2.f * x * acc[1][o] + y * acc[2][o];
         const float g1 = d > 0.f ? l1w : (d < 0.f ? -l1w : 0.f);
-        dL[blockIdx.z * plane + (size_t)gy * W + gx] = fmaf(-ssw, dS, g1);
+        dL[blockIdx.z * plane + pix] = fmaf(-ssw, dS, g1);
         l1 += fabsf(d);
       }
     }
   }
-  const double t = cta_sum((1.0 - (double)lambda) * (double)l1 + (double)lambda * (double)dssim, s_warp);
+  const double t = cta_sum<SS_THREADS>((1.0 - (double)lambda) * (double)l1 + (double)lambda * (double)dssim, s_warp);
   if (tid == 0) partials[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
 }
 
