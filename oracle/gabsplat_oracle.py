@@ -462,6 +462,28 @@ def render(prims: dict, cam, cfg, tiles=None, third_row="z", cull=True) -> dict:
     return out
 
 
+def frequency_features(proj: dict) -> torch.Tensor:
+    """Per primitive [n, 3]: sum_i w_i |f2D_i|, sum_i w_i |f2D_i,x|, sum_i w_i |f2D_i,y| -- the
+    weighted Gabor frequencies (cycles per pixel) that the frequency maps blend (Sec. 4)."""
+    f, w = proj["f2d"], proj["weights"]
+    if w.shape[1] == 0:
+        return torch.zeros(w.shape[0], 3, dtype=F64)
+    mag = torch.sqrt((f * f).sum(-1))
+    return torch.stack([(w * mag).sum(-1), (w * f[..., 0].abs()).sum(-1), (w * f[..., 1].abs()).sum(-1)], -1)
+
+
+def render_frequency_map(prims: dict, cam, cfg) -> dict:
+    """Frequency maps: the compositing of render() (same pairs, same weights alpha T) with each
+    primitive's colour replaced by its frequency features and no background."""
+    spec = bin_spec(prims, cam, cfg)
+    with torch.no_grad():
+        proj = project(_to_f64(prims), cam, cfg)
+    proj = dict(proj, rgb=frequency_features(proj))
+    out = _render_tiles(proj, spec, cam, dict(cfg, bg=(0.0, 0.0, 0.0)))
+    out["map"] = out.pop("image")
+    return out
+
+
 def render_backward(prims: dict, cam, cfg, dL_dC) -> dict:
     """Gradients of sum(dL_dC * image) w.r.t. every primitive attribute (float64, exact adjoint).
 

@@ -277,10 +277,11 @@ def test_transmittance_monotone_and_bounded():
     assert (out["image"].numpy() >= 0).all()
 
 
-def _brute_force(prims, cam, cfg):
+def _brute_force(prims, cam, cfg, feature=None):
     """Sequential per-pixel compositing with scalar math, independent of the tile vectorisation:
     gather every primitive whose 3-sigma square overlaps the pixel's tile, order by (float32 depth
-    bits, index) with Python's sort, and walk front to back."""
+    bits, index) with Python's sort, and walk front to back.  feature(P, k) replaces the colour
+    (and the background is then zero)."""
     spec = O.bin_spec(prims, cam, cfg)
     proj = O.project(O._to_f64(prims), cam, cfg)
     P = {k: v.detach().numpy() for k, v in proj.items()}
@@ -314,10 +315,10 @@ def _brute_force(prims, cam, cfg):
                     continue
                 if T * (1 - alpha) < cfg["T_min"]:
                     break
-                C += P["rgb"][k] * alpha * T
+                C += (P["rgb"][k] if feature is None else feature(P, k)) * alpha * T
                 T *= (1 - alpha)
                 lst = pos + 1
-            img[:, py, px] = C + T * np.array(cfg["bg"])
+            img[:, py, px] = C + (T * np.array(cfg["bg"]) if feature is None else 0.0)
             Tf[py, px] = T
             last[py, px] = lst
     return img, Tf, last
@@ -547,3 +548,47 @@ def test_l1_dssim_is_the_weighted_sum_and_its_gradient():
         xm[c, i, j] -= h
         fd = (O.l1_dssim_loss_and_grad(xp, y)[0] - O.l1_dssim_loss_and_grad(xm, y)[0]) / (2 * h)
         assert abs(fd - g2[c, i, j]) < 1e-8 * max(1.0, abs(g2[c, i, j]) * N), (c, i, j, fd, g2[c, i, j])
+
+
+# ---- frequency maps (the visualisation of Sec. 4) --------------------------------------------
+def _weighted_frequencies(P, k):
+    m = mx = my = 0.0
+    for i in range(P["weights"].shape[1]):
+        fx, fy, w = P["f2d"][k, i, 0], P["f2d"][k, i, 1], P["weights"][k, i]
+        m += w * math.hypot(fx, fy)
+        mx += w * abs(fx)
+        my += w * abs(fy)
+    return np.array([m, mx, my])
+
+
+@pytest.mark.parametrize("seed,n,K", [(5, 24, 2), (6, 30, 3)])
+def test_frequency_map_brute_force(seed, n, K):
+    """The maps are the compositing of the image with each primitive's colour replaced by its
+    weighted |f2D|, |f2D_x|, |f2D_y| and no background: brute-force sequential compositing."""
+    cam = tiny_camera(40, 32, dist=2.0)
+    cfg = O.default_config(bg=(0.3, 0.2, 0.1))
+    prims = tiny_scene(seed, n=n, K=K, log_scale=(-2.2, 0.4))
+    got = O.render_frequency_map(prims, cam, cfg)["map"].numpy()
+    ref, _, _ = _brute_force(prims, cam, cfg, feature=_weighted_frequencies)
+    np.testing.assert_allclose(got, ref, atol=1e-12)
+    assert np.abs(ref).max() > 1e-3                       # the maps are not trivially zero
+
+
+def test_frequency_map_special_cases():
+    cam = tiny_camera(40, 32, dist=2.0)
+    cfg = O.default_config()
+    # K = 0 (or all weights zero): a pure Gaussian scene has no frequency content
+    p0 = tiny_scene(7, n=20, K=0)
+    assert np.all(O.render_frequency_map(p0, cam, cfg)["map"].numpy() == 0.0)
+    # one primitive: map = alpha * features, alpha read off the image of a constant colour
+    p1 = tiny_scene(8, n=1, K=2, log_scale=(-1.0, 0.0))
+    p1["means"][:] = 0.0
+    p1["sh"][:] = 0.0
+    p1["sh"][0, 0, :] = 0.5 / 0.28209479177387814     # SH band 0 -> colour 1.0 in every channel
+    out = O.render(p1, cam, cfg)
+    alpha = out["image"].numpy()[0]                     # colour 1, background 0: image = alpha
+    proj = {k: v.numpy() for k, v in out["proj"].items()}
+    feat = _weighted_frequencies(proj, 0)
+    got = O.render_frequency_map(p1, cam, cfg)["map"].numpy()
+    np.testing.assert_allclose(got, alpha[None] * feat[:, None, None], atol=1e-14)
+    assert alpha.max() > 0.1
