@@ -191,6 +191,16 @@ gs_status gabsplat_bin_sort(const gs_frame* frame, gs_stream stream);
  * transmittance and the last contributor per pixel in the workspace for the backward pass. */
 gs_status gabsplat_render_fwd(const gs_frame* frame, float* out_rgb, float* out_T, gs_stream stream);
 
+/* Frequency maps (the visualisation of Sec. 4: the weighted Gabor frequencies of the primitives
+ * blended into the image): the compositing of stage 3 with each primitive's colour replaced by
+ * three frequency features of its splatted components (Eq. 8) and no background:
+ *   out_map[0] = sum over pairs of alpha T (sum_i w_i |f2D_i|),
+ *   out_map[1] = ... (sum_i w_i |f2D_i,x|),  out_map[2] = ... (sum_i w_i |f2D_i,y|),
+ * f2D in cycles per pixel.  out_map [3][H][W] float32, device, required.  Runs after
+ * gabsplat_bin_sort like gabsplat_render_fwd (before or after it: both make the same per-pixel
+ * decisions and leave the same per-pixel state for the backward pass).  All zero for K = 0. */
+gs_status gabsplat_render_freq_map(const gs_frame* frame, float* out_map, gs_stream stream);
+
 /* Stage 4, reverse-order backward pass of the differentiable rasterizer (Sec. 3.3.3, trained by
  * the photometric loss of Sec. 3.4.1).  Given dL/d(rgb) [3][H][W] (device), walks each pixel's
  * pairs back to front from its last contributor, recomputing transmittance by division instead of

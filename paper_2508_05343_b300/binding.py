@@ -71,6 +71,7 @@ SIGNATURES = {
     "gabsplat_preprocess": (C.c_int, [P_(gs_frame), P_(gs_prims), P_(gs_camera), P_(gs_config), C.c_void_p]),
     "gabsplat_bin_sort": (C.c_int, [P_(gs_frame), C.c_void_p]),
     "gabsplat_render_fwd": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gabsplat_render_freq_map": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p]),
     "gabsplat_render_bwd": (C.c_int, [P_(gs_frame), C.c_void_p, P_(gs_prim_grads), C.c_void_p]),
     "gabsplat_render_bwd_2d": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p]),
     "gabsplat_preprocess_bwd": (C.c_int, [P_(gs_frame), P_(gs_prim_grads), C.c_void_p]),
@@ -152,6 +153,10 @@ def gabsplat_bin_sort(frame, stream=None):
 
 def gabsplat_render_fwd(frame, out_rgb, out_T=None, stream=None):
     _check("gabsplat_render_fwd", lib.gabsplat_render_fwd(C.byref(frame), _ptr(out_rgb), _ptr(out_T), _stream(stream)))
+
+
+def gabsplat_render_freq_map(frame, out_map, stream=None):
+    _check("gabsplat_render_freq_map", lib.gabsplat_render_freq_map(C.byref(frame), _ptr(out_map), _stream(stream)))
 
 
 def gabsplat_render_bwd(frame, dL_drgb, grads, stream=None):

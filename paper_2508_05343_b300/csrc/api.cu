@@ -228,6 +228,15 @@ gs_status gabsplat_render_fwd(const gs_frame* frame, float* out_rgb, float* out_
   return from_cuda(launch_render_fwd(t, make_ptrs(L, frame->ws), out_rgb, out_T, make_launch(stream)));
 }
 
+gs_status gabsplat_render_freq_map(const gs_frame* frame, float* out_map, gs_stream stream) {
+  FrameTable t;
+  WsLayout L;
+  const gs_status s = frame_meta(frame, t, L);
+  if (s != GS_OK) return s;
+  if (!out_map) return GS_ERR_INVALID_ARG;
+  return from_cuda(launch_render_freq_map(t, make_ptrs(L, frame->ws), out_map, make_launch(stream)));
+}
+
 gs_status gabsplat_render_bwd_2d(const gs_frame* frame, const float* dL_drgb, gs_stream stream) {
   FrameTable t;
   WsLayout L;

@@ -85,7 +85,8 @@ struct WsHeader {
   u32 timeout_site;         // which bounded wait gave up (diagnostics)
   u32 sorted_buf;           // 0: sorted pairs in keys0/vals0, 1: in keys1/vals1
   u32 n_active;             // primitives that touch at least one tile (entries of the active list)
-  u32 pad[13];
+  u32 fwd_exits, bwd_exits; // CTAs of the current compositing launch that have finished
+  u32 pad[11];
 };
 
 // Offsets of every region of a workspace (host-computed; all 256-byte aligned).
@@ -204,6 +205,7 @@ cudaError_t launch_setup(const FrameTable& tbl, const WsPtrs& p, const Launch& L
 cudaError_t launch_preprocess(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
 cudaError_t launch_bin_sort(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
 cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L);
+cudaError_t launch_render_freq_map(const FrameTable& tbl, const WsPtrs& p, float* out_map, const Launch& L);
 cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL_drgb, const Launch& L);
 cudaError_t launch_preprocess_bwd(const FrameTable& tbl, const WsPtrs& p, const gs_prim_grads& g, const Launch& L);
 cudaError_t launch_loss(const float* img, const float* tgt, long long count, int kind, double* loss_out, float* dL,

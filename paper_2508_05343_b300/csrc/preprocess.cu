@@ -38,6 +38,8 @@ __global__ void k_setup(FrameTable tbl, WsPtrs p) {
     h->timeout_site = 0;
     h->sorted_buf = (u32)(tbl.npasses_needed & 1);
     h->n_active = 0;
+    h->fwd_exits = 0;
+    h->bwd_exits = 0;
     for (int i = 0; i < MAX_PASSES; ++i) h->sort_counter[i] = 0;
   }
 }

@@ -32,6 +32,20 @@ __device__ __forceinline__ void stage_record(const float* __restrict__ rec, floa
   for (int i = 3; i < SRec<K>::F4; ++i) dst[i] = __ldg(src + i);
 }
 
+// Frequency features of one record: sum_i w_i |f2D_i|, sum_i w_i |f2D_i,x|, sum_i w_i |f2D_i,y|.
+template <int K>
+__device__ __forceinline__ float4 frequency_features(const float* __restrict__ rec) {
+  float m = 0.f, mx = 0.f, my = 0.f;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const float fx = __ldg(rec + 12 + 2 * i), fy = __ldg(rec + 13 + 2 * i), w = __ldg(rec + 12 + 2 * K + i);
+    m = fmaf(w, sqrtf(fx * fx + fy * fy), m);
+    mx = fmaf(w, fabsf(fx), mx);
+    my = fmaf(w, fabsf(fy), my);
+  }
+  return make_float4(m, mx, my, 0.f);
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -84,6 +98,16 @@ __device__ __forceinline__ float filter_bank(const float* r, float w0, float dx,
 #define GS_WARP_SQUARE 1
 #endif
 
+// Called by thread 0 of every CTA after it has left its tile loop: the last CTA of the launch
+// resets the tile allocator, so each compositing launch of a frame starts from tile 0.
+__device__ __forceinline__ void release_tile_counter(u32* counter, u32* exits) {
+  __threadfence();
+  if (atomicAdd(exits, 1u) == gridDim.x - 1) {
+    *counter = 0;
+    *exits = 0;
+  }
+}
+
 // First pixel (x, y) of thread tid in tile (tx, ty); the thread owns rows y .. y + PPT - 1.
 template <int PPT>
 __device__ __forceinline__ int2 thread_pixel(int tx, int ty, int tid) {
@@ -95,7 +119,9 @@ __device__ __forceinline__ int2 thread_pixel(int tx, int ty, int tid) {
 #endif
 }
 
-template <int K, int PPT>
+// FMAP: composite the frequency features of each primitive (sum_i w_i |f2D_i|, sum_i w_i |f2D_i,x|,
+// sum_i w_i |f2D_i,y|, cycles per pixel) in place of its colour, with no background.
+template <int K, int PPT, bool FMAP>
 __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32* vals, float* out_rgb,
                                                             float* out_T) {
   constexpr int NT = BLOCK / PPT;
@@ -136,7 +162,11 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
     for (u32 start = rg.x; start < rg.y; start += NT) {
       if (__syncthreads_count(tdone) == NT) break;
       const u32 idx = start + tid;
-      if (idx < rg.y) stage_record<K>(p.records + (size_t)vals[idx] * rec_floats(K), s_rec + tid * F4, amin);
+      if (idx < rg.y) {
+        const float* rec = p.records + (size_t)vals[idx] * rec_floats(K);
+        stage_record<K>(rec, s_rec + tid * F4, amin);
+        if (FMAP) s_rec[tid * F4 + 2] = frequency_features<K>(rec);
+      }
       __syncthreads();
       const int cnt = (int)min((u32)NT, rg.y - start);
       for (int j = 0; !tdone && j < cnt; ++j) {
@@ -185,9 +215,9 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
       if (px < V.width && py < V.height) {
         const size_t pix = (size_t)py * V.width + px;
         if (orgb) {
-          orgb[pix] = C0[q] + T[q] * tbl->bg[0];
-          orgb[hw + pix] = C1[q] + T[q] * tbl->bg[1];
-          orgb[2 * hw + pix] = C2[q] + T[q] * tbl->bg[2];
+          orgb[pix] = FMAP ? C0[q] : C0[q] + T[q] * tbl->bg[0];
+          orgb[hw + pix] = FMAP ? C1[q] : C1[q] + T[q] * tbl->bg[1];
+          orgb[2 * hw + pix] = FMAP ? C2[q] : C2[q] + T[q] * tbl->bg[2];
         }
         if (oT) oT[pix] = T[q];
         p.T_final[V.pix_base + pix] = T[q];
@@ -199,6 +229,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
     }
     __syncthreads();
   }
+  if (tid == 0) release_tile_counter(&hdr->tile_counter_fwd, &hdr->fwd_exits);
 }
 
 // Reduce-scatter of 32 per-lane values across a warp: afterwards lane i holds the warp sum of
@@ -408,9 +439,10 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
     }
     __syncthreads();
   }
+  if (tid == 0) release_tile_counter(&hdr->tile_counter_bwd, &hdr->bwd_exits);
 }
 
-template <int K>
+template <int K, bool FMAP>
 static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, const u32* vals, float* rgb, float* T,
                                 const Launch& L) {
   constexpr int PPT = GS_PPT_FWD, NT = BLOCK / PPT;
@@ -418,10 +450,10 @@ static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, const u3
   const size_t smem = (size_t)NT * SRec<K>::F * sizeof(float);
   if (!grid) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_render_fwd<K, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_render_fwd<K, PPT, FMAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<K, PPT>, NT, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<K, PPT, FMAP>, NT, smem) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     grid = per_sm * L.sm_count;
@@ -429,7 +461,7 @@ static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, const u3
   int g = grid;
   if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
   if (g < 1) g = 1;
-  k_render_fwd<K, PPT><<<g, NT, smem, L.stream>>>(p, vals, rgb, T);
+  k_render_fwd<K, PPT, FMAP><<<g, NT, smem, L.stream>>>(p, vals, rgb, T);
   return cudaGetLastError();
 }
 
@@ -458,20 +490,29 @@ static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const u3
 }
 
 
-cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L) {
+template <bool FMAP>
+static cudaError_t launch_fwd_k(const FrameTable& tbl, const WsPtrs& p, float* out, float* out_T, const Launch& L) {
   const u32* vals = nullptr;   // chosen on the device: the sort's pass count depends on the depth range
   switch (tbl.K) {
-    case 0: return launch_fwd_t<0>(tbl, p, vals, out_rgb, out_T, L);
-    case 1: return launch_fwd_t<1>(tbl, p, vals, out_rgb, out_T, L);
-    case 2: return launch_fwd_t<2>(tbl, p, vals, out_rgb, out_T, L);
-    case 3: return launch_fwd_t<3>(tbl, p, vals, out_rgb, out_T, L);
-    case 4: return launch_fwd_t<4>(tbl, p, vals, out_rgb, out_T, L);
-    case 5: return launch_fwd_t<5>(tbl, p, vals, out_rgb, out_T, L);
-    case 6: return launch_fwd_t<6>(tbl, p, vals, out_rgb, out_T, L);
-    case 7: return launch_fwd_t<7>(tbl, p, vals, out_rgb, out_T, L);
-    case 8: return launch_fwd_t<8>(tbl, p, vals, out_rgb, out_T, L);
+    case 0: return launch_fwd_t<0, FMAP>(tbl, p, vals, out, out_T, L);
+    case 1: return launch_fwd_t<1, FMAP>(tbl, p, vals, out, out_T, L);
+    case 2: return launch_fwd_t<2, FMAP>(tbl, p, vals, out, out_T, L);
+    case 3: return launch_fwd_t<3, FMAP>(tbl, p, vals, out, out_T, L);
+    case 4: return launch_fwd_t<4, FMAP>(tbl, p, vals, out, out_T, L);
+    case 5: return launch_fwd_t<5, FMAP>(tbl, p, vals, out, out_T, L);
+    case 6: return launch_fwd_t<6, FMAP>(tbl, p, vals, out, out_T, L);
+    case 7: return launch_fwd_t<7, FMAP>(tbl, p, vals, out, out_T, L);
+    case 8: return launch_fwd_t<8, FMAP>(tbl, p, vals, out, out_T, L);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L) {
+  return launch_fwd_k<false>(tbl, p, out_rgb, out_T, L);
+}
+
+cudaError_t launch_render_freq_map(const FrameTable& tbl, const WsPtrs& p, float* out_map, const Launch& L) {
+  return launch_fwd_k<true>(tbl, p, out_map, nullptr, L);
 }
 
 cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL, const Launch& L) {

@@ -74,6 +74,14 @@ class Rasterizer:
             break
         return out_rgb
 
+    def frequency_map(self, out_map=None):
+        """The [3][H][W] frequency maps of the frame that forward() last rendered: weighted
+        |f2D|, |f2D_x| and |f2D_y| blended like colours, without background."""
+        if out_map is None:
+            out_map = torch.empty(3, self.height, self.width, device=self.device)
+        B.gabsplat_render_freq_map(self.frame, out_map)
+        return out_map
+
     def backward(self, dL_drgb: torch.Tensor, grads: dict | None = None):
         if grads is None:
             grads = {k: torch.empty(self._keep[k].shape, dtype=torch.float32, device=self.device) for k in ATTRS}
