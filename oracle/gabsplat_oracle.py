@@ -560,3 +560,94 @@ def l1_dssim_loss_and_grad(image, target, lam=0.2):
     L = (1.0 - lam) * (x - y).abs().mean() + lam * (1.0 - ssim_map(x, y).mean())
     L.backward()
     return float(L.detach()), x.grad.numpy()
+
+
+# ----------------------------------------------------------------------------------------------
+# Frequency-adaptive density control (Sec. 3.4.2; supplement B), on top of the 3DGS rules
+# ----------------------------------------------------------------------------------------------
+def densify_defaults(dense_scale=0.05):
+    """Constants: 3DGS's gradient threshold, split into two children whose scales are divided by
+    0.8 x 2; the paper's opacity threshold 0.01 and the reset values of new primitives' frequencies
+    (0.001 per coordinate) and weights (0.01)."""
+    return dict(grad_threshold=2e-4, dense_scale=dense_scale, min_opacity=0.01, max_scale=0.0,
+                split_divisor=1.6, child_freq=1e-3, child_weight=1e-2)
+
+
+def densify_accumulate(grad_accum, denom, means2d_grad, visible):
+    """One training view's statistics: every primitive visible in the view (at least one tile)
+    adds the norm of dL/dmu2D (pixels) to grad_accum and 1 to denom.  float32, single correctly
+    rounded operations: sqrt((gx gx) + (gy gy)), then the sum."""
+    f32 = np.float32
+    g = np.asarray(means2d_grad, f32)
+    norm = np.sqrt(g[:, 0] * g[:, 0] + g[:, 1] * g[:, 1])
+    vis = np.asarray(visible, bool)
+    acc = np.asarray(grad_accum, f32).copy()
+    den = np.asarray(denom, f32).copy()
+    acc[vis] = acc[vis] + norm[vis]
+    den[vis] = den[vis] + f32(1.0)
+    return acc, den
+
+
+def densify_decisions(prims, grad_accum, denom, cfg):
+    """Per primitive, in float32 with correctly rounded operations:
+      mean gradient  g = grad_accum / denom (0 where denom = 0);
+      candidate      g >= grad_threshold;  s_max = the largest scale;
+      clone          candidate and s_max <= dense_scale;  split: candidate and s_max > dense_scale;
+      pruned         opacity < min_opacity, or max_scale > 0 and s_max > max_scale (children of a
+                     split are tested with their own scale s / split_divisor).
+    Returns (keep_original, keep_clone, keep_children) boolean arrays."""
+    f32 = np.float32
+    acc, den = np.asarray(grad_accum, f32), np.asarray(denom, f32)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        g = np.where(den > 0, acc / np.where(den > 0, den, f32(1)), f32(0))
+    sc = np.asarray(prims["scales"], f32)
+    smax = sc.max(1)
+    cand = g >= f32(cfg["grad_threshold"])
+    clone = cand & (smax <= f32(cfg["dense_scale"]))
+    split = cand & (smax > f32(cfg["dense_scale"]))
+    low = np.asarray(prims["opacity"], f32) < f32(cfg["min_opacity"])
+    ms = f32(cfg["max_scale"])
+    big = (ms > 0) & (smax > ms)
+    child_big = (ms > 0) & ((sc / f32(cfg["split_divisor"])).max(1) > ms)
+    return ~split & ~low & ~big, clone & ~low & ~big, split & ~low & ~child_big
+
+
+def densify(prims, grad_accum, denom, split_noise, cfg):
+    """Clone / split / prune with the frequency-adaptive reset of new primitives.
+
+    Output rows, in this order: the kept originals (index order), then one clone per kept clone
+    (index order), then two children per kept split (index order; child c at
+    mu + R(q) (s * z_c) with z = split_noise[i, c], scale s / split_divisor).  Clones and children
+    copy rotation, opacity and SH; every frequency coordinate of a new primitive is child_freq and
+    every weight child_weight.  Returns the output attribute arrays (float64 means, float32 scales)
+    and the three segment counts."""
+    keep_o, keep_c, keep_s = densify_decisions(prims, grad_accum, denom, cfg)
+    f32 = np.float32
+    K = prims["weights"].shape[1]
+    io, ic, isp = np.nonzero(keep_o)[0], np.nonzero(keep_c)[0], np.nonzero(keep_s)[0]
+    isp2 = np.repeat(isp, 2)
+    which = np.tile([0, 1], isp.shape[0])
+    src = np.concatenate([io, ic, isp2])
+    out = {k: np.asarray(prims[k])[src].copy() for k in ("means", "scales", "quats", "opacity", "sh", "freqs", "weights")}
+    out["means"] = out["means"].astype(np.float64)
+    new = slice(io.shape[0], src.shape[0])
+    out["freqs"][new] = f32(cfg["child_freq"])
+    out["weights"][new] = f32(cfg["child_weight"])
+    if isp.shape[0]:
+        s = np.asarray(prims["scales"], f32)[isp2]
+        R = rotation_from_quaternion(torch.tensor(np.asarray(prims["quats"], np.float64)[isp2])).numpy()
+        z = np.asarray(split_noise, np.float64)[isp2, which]
+        off = np.einsum("nij,nj->ni", R, s.astype(np.float64) * z)
+        ch = slice(io.shape[0] + ic.shape[0], src.shape[0])
+        out["means"][ch] = np.asarray(prims["means"], np.float64)[isp2] + off
+        out["scales"][ch] = s / f32(cfg["split_divisor"])
+    counts = dict(originals=int(io.shape[0]), clones=int(ic.shape[0]), children=int(2 * isp.shape[0]))
+    return out, counts
+
+
+def reset_opacity_weights(prims, opacity_cap=0.02, weight=0.01):
+    """The periodic reset (every 3000 iterations in the paper): opacity capped, every weight set."""
+    out = dict(prims)
+    out["opacity"] = np.minimum(np.asarray(prims["opacity"], np.float32), np.float32(opacity_cap))
+    out["weights"] = np.full_like(np.asarray(prims["weights"], np.float32), np.float32(weight))
+    return out

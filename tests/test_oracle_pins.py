@@ -592,3 +592,100 @@ def test_frequency_map_special_cases():
     got = O.render_frequency_map(p1, cam, cfg)["map"].numpy()
     np.testing.assert_allclose(got, alpha[None] * feat[:, None, None], atol=1e-14)
     assert alpha.max() > 0.1
+
+
+# ---- frequency-adaptive density control (Sec. 3.4.2) -----------------------------------------
+def _densify_loop(prims, acc, den, noise, cfg):
+    """The rules written per primitive with float32 scalars, output segments built by appending."""
+    f32 = np.float32
+    orig, clones, kids = [], [], []
+    for i in range(prims["means"].shape[0]):
+        g = f32(acc[i]) / f32(den[i]) if den[i] > 0 else f32(0)
+        s = [f32(v) for v in prims["scales"][i]]
+        smax = max(s)
+        cand = g >= f32(cfg["grad_threshold"])
+        low = f32(prims["opacity"][i]) < f32(cfg["min_opacity"])
+        ms = f32(cfg["max_scale"])
+        too_big = lambda m: ms > 0 and m > ms
+        split = cand and smax > f32(cfg["dense_scale"])
+        if not split and not low and not too_big(smax):
+            orig.append(i)
+            if cand:
+                clones.append(i)
+        if split and not low and not too_big(max(v / f32(cfg["split_divisor"]) for v in s)):
+            kids.append(i)
+    return orig, clones, kids
+
+
+def _densify_inputs(seed, n=80):
+    rng = np.random.default_rng(seed)
+    prims = tiny_scene(seed, n=n, K=2, log_scale=(-3.0, 0.5))
+    prims["opacity"][: n // 8] = rng.random(n // 8).astype(np.float32) * 0.02   # some below 0.01
+    acc = (rng.random(n) * 2e-3).astype(np.float32)
+    den = rng.integers(0, 4, n).astype(np.float32)
+    return prims, acc, den, rng.standard_normal((n, 2, 3))
+
+
+@pytest.mark.parametrize("seed,max_scale", [(21, 0.0), (22, 0.12)])
+def test_densify_matches_per_primitive_loop(seed, max_scale):
+    prims, acc, den, noise = _densify_inputs(seed)
+    cfg = dict(O.densify_defaults(dense_scale=0.06), max_scale=max_scale)
+    out, cnt = O.densify(prims, acc, den, noise, cfg)
+    orig, clones, kids = _densify_loop(prims, acc, den, noise, cfg)
+    assert (cnt["originals"], cnt["clones"], cnt["children"]) == (len(orig), len(clones), 2 * len(kids))
+    assert len(orig) and len(clones) and len(kids) and len(orig) < prims["means"].shape[0]
+    src = orig + clones + [i for i in kids for _ in (0, 1)]
+    for k in ("quats", "opacity", "sh"):
+        np.testing.assert_array_equal(out[k], np.asarray(prims[k])[src])
+    no = len(orig)
+    np.testing.assert_array_equal(out["freqs"][:no], prims["freqs"][orig])
+    np.testing.assert_array_equal(out["weights"][:no], prims["weights"][orig])
+    assert np.all(out["freqs"][no:] == np.float32(1e-3)) and np.all(out["weights"][no:] == np.float32(1e-2))
+    nc = no + len(clones)
+    np.testing.assert_array_equal(out["means"][:nc], np.asarray(prims["means"], np.float64)[orig + clones])
+    np.testing.assert_array_equal(out["scales"][:nc], prims["scales"][orig + clones])
+    np.testing.assert_array_equal(out["scales"][nc:], np.repeat(prims["scales"][kids], 2, 0) / np.float32(1.6))
+
+
+def test_densify_split_children_geometry():
+    """Children sit at mu + R(q) (s * z): with antithetic noise (z, -z) they average to the parent,
+    and R^T (child - mu) / s recovers z (R from scipy's quaternion convention, scalar last)."""
+    from scipy.spatial.transform import Rotation
+    prims, acc, den, noise = _densify_inputs(23)
+    noise[:, 1] = -noise[:, 0]
+    cfg = O.densify_defaults(dense_scale=0.06)
+    out, cnt = O.densify(prims, acc, den, noise, cfg)
+    _, _, kids = _densify_loop(prims, acc, den, noise, cfg)
+    ch = out["means"][cnt["originals"] + cnt["clones"]:].reshape(-1, 2, 3)
+    mu = np.asarray(prims["means"], np.float64)[kids]
+    np.testing.assert_allclose(ch.mean(1), mu, atol=1e-12)
+    q = np.asarray(prims["quats"], np.float64)[kids]
+    R = Rotation.from_quat(q[:, [1, 2, 3, 0]]).as_matrix()
+    z = np.einsum("nji,nj->ni", R, ch[:, 0] - mu) / prims["scales"][kids].astype(np.float64)
+    np.testing.assert_allclose(z, noise[kids, 0], atol=1e-9)
+
+
+def test_densify_special_cases_accumulate_and_reset():
+    prims, acc, den, noise = _densify_inputs(24)
+    cfg = O.densify_defaults(dense_scale=0.06)
+    n = prims["means"].shape[0]
+    # no statistics: nothing is densified, only low-opacity primitives go
+    out, cnt = O.densify(prims, np.zeros(n, np.float32), np.zeros(n, np.float32), noise, cfg)
+    keep = prims["opacity"] >= np.float32(0.01)
+    assert cnt == dict(originals=int(keep.sum()), clones=0, children=0)
+    np.testing.assert_array_equal(out["sh"], prims["sh"][keep])
+    # everything below the opacity threshold: nothing survives
+    out, cnt = O.densify(dict(prims, opacity=np.zeros(n, np.float32)), acc, den, noise, cfg)
+    assert cnt == dict(originals=0, clones=0, children=0)
+    # accumulation: visible primitives add |g| and one visit, the others are unchanged
+    rng = np.random.default_rng(5)
+    g = rng.standard_normal((n, 2)).astype(np.float32)
+    vis = rng.random(n) < 0.5
+    a2, d2 = O.densify_accumulate(acc, den, g, vis)
+    np.testing.assert_allclose(a2[vis], acc[vis] + np.hypot(g[vis, 0], g[vis, 1]), rtol=1e-6)
+    np.testing.assert_array_equal(a2[~vis], acc[~vis])
+    np.testing.assert_array_equal(d2, den + vis)
+    # periodic reset
+    r = O.reset_opacity_weights(prims)
+    np.testing.assert_array_equal(r["opacity"], np.minimum(prims["opacity"], np.float32(0.02)))
+    assert np.all(r["weights"] == np.float32(0.01))
