@@ -505,6 +505,32 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": round(ssim_tf / alu_peak, 4),
                 "hbm_frac": round(img.numel() * 12 / (ssim_ms * 1e-3) / 1e9 / hbm_peak, 4)}
 
+    # frequency-adaptive density control on the same scene: about 10% of the primitives reach the
+    # gradient threshold, half of them small (cloned) and half large (split); 20 timed compactions
+    rng_d = np.random.default_rng(77)
+    d_acc = torch.tensor((rng_d.random(n) * 2.22e-4).astype(np.float32), device=dev)
+    d_den = torch.ones(n, device=dev)
+    d_noise = torch.tensor(rng_d.standard_normal((n, 2, 3)).astype(np.float32), device=dev)
+    d_cfg = B.make_densify_config(dense_scale=float(np.median(scene["scales"].max(1))))
+    d_out = {k: torch.empty((2 * n,) + tuple(v.shape[1:]), dtype=v.dtype, device=dev) for k, v in pt.items()}
+    d_counts = torch.zeros(4, dtype=torch.int32, device=dev)
+    d_scr = torch.empty(B.gabsplat_densify_scratch_bytes(n), dtype=torch.uint8, device=dev)
+    d_args = (prims_s, d_acc, d_den, d_noise, d_cfg, B.make_prim_arrays(d_out), 2 * n, d_counts, d_scr)
+    B.gabsplat_densify(*d_args)
+    d_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    d_ev[0].record()
+    for r in range(20):
+        B.gabsplat_densify(*d_args)
+    d_ev[1].record()
+    torch.cuda.synchronize()
+    d_ms = d_ev[0].elapsed_time(d_ev[1]) / 20
+    dc = d_counts.cpu().tolist()
+    d_bytes = n * (param_b + 8) + (dc[3] // 2) * 24 + dc[0] * param_b
+    densify = {"ms": round(d_ms, 4), "rows_in": n, "rows_out": dc[0], "clones": dc[2], "split_children": dc[3],
+               "bound": "hbm", "achieved": round(d_bytes / (d_ms * 1e-3) / 1e9, 1), "peak": hbm_peak, "unit": "GB/s",
+               "frac": round(d_bytes / (d_ms * 1e-3) / 1e9 / hbm_peak, 4)}
+    del d_out, d_noise, d_scr
+
     crop = None
     if rank == 0 and args.oracle_crop:
         img0 = rast.forward(pt, cams[0], cfg, storage=storage)
@@ -545,6 +571,7 @@ def run_ours(args):
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "stage_roofline_frac": stage_fracs,
             "l1_dssim": l1_dssim,
+            "densify": densify,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -261,6 +261,67 @@ gs_status gabsplat_loss_l1_dssim(const float* image, const float* target, int ch
                                  float lambda, double* loss_out, float* dL_dimage, void* scratch, gs_stream stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Frequency-adaptive density control (Sec. 3.4.2 and supplement B), on top of the adaptive density
+ * control of 3DGS that the paper keeps: primitives whose mean screen-space positional gradient
+ * reaches a threshold are cloned (small ones) or split into two (large ones), low-opacity and
+ * (optionally) over-large ones are pruned, and every new primitive starts with its frequencies
+ * and weights reset to small values, so it does not inherit its parent's high frequencies.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct {
+  float grad_threshold; /* mean |dL/dmu2D| (pixels) over the views that saw a primitive, at or
+                           above which it is densified */
+  float dense_scale;    /* largest scale up to which a candidate is cloned; larger ones are split */
+  float min_opacity;    /* primitives with opacity below are pruned (the paper: 0.01) */
+  float max_scale;      /* primitives whose largest scale exceeds it are pruned; <= 0: no such rule */
+  float split_divisor;  /* scales of split children = parent's / split_divisor (3DGS: 0.8 x 2 = 1.6) */
+  float child_freq;     /* every frequency coordinate of a new primitive (the paper: 0.001) */
+  float child_weight;   /* every weight of a new primitive (the paper: 0.01) */
+} gs_densify_config;
+
+/* Writable attribute arrays, laid out as in gs_prims (sh/freqs/weights in the storage type). */
+typedef struct {
+  float* means;
+  float* scales;
+  float* quats;
+  float* opacity;
+  void* sh;
+  void* freqs;
+  void* weights;
+} gs_prim_arrays;
+
+/* One training view's statistics, after gabsplat_preprocess_bwd: every primitive that reached at
+ * least one tile of the frame's view adds sqrt(gx^2 + gy^2) of its means2d gradient (pixels,
+ * [n][2] float32, the gs_prim_grads.means2d output) to grad_accum[i] and 1 to denom[i] ([n]
+ * float32, device, caller-owned; start them at zero and zero them after gabsplat_densify).
+ * Single correctly rounded float32 operations. */
+gs_status gabsplat_densify_accumulate(const gs_frame* frame, const float* means2d_grad, float* grad_accum,
+                                      float* denom, gs_stream stream);
+
+/* Clone / split / prune in one compaction.  Per primitive i, in float32:
+ *   g = grad_accum[i] / denom[i] (0 if denom is 0); candidate if g >= grad_threshold;
+ *   s_max = largest scale; candidates with s_max <= dense_scale are cloned, the others split;
+ *   pruned: opacity < min_opacity, or max_scale > 0 and s_max > max_scale (split children are
+ *   tested with their own scales).
+ * Output rows (out, capacity out_capacity >= 2 n rows), in this order: the kept originals, the
+ * clones, then two children per split, each segment in index order.  Clones and children copy
+ * rotation, opacity and SH; their frequencies are child_freq and weights child_weight.  Child c
+ * of primitive i sits at mu + R(q) (s * z) with z = split_noise[i][c][0..2] (float32 [n][2][3],
+ * standard normal samples drawn by the caller) and has scale s / split_divisor.
+ * counts (device, 4 ints): {rows written, originals, clones, split children}; the count never
+ * leaves the device.  n <= 2^30 - 1.  scratch: gabsplat_densify_scratch_bytes(n) bytes of device
+ * memory.  Input and output arrays must not overlap; out->quats 16-byte aligned. */
+size_t gabsplat_densify_scratch_bytes(int n);
+gs_status gabsplat_densify(const gs_prims* in, const float* grad_accum, const float* denom, const float* split_noise,
+                           const gs_densify_config* cfg, const gs_prim_arrays* out, long long out_capacity,
+                           int* counts, void* scratch, gs_stream stream);
+
+/* The periodic reset (the paper: every 3000 iterations, with the opacity reset): opacity =
+ * min(opacity, opacity_cap) and every weight = weight, in place on n primitives with K
+ * components stored as `storage`. */
+gs_status gabsplat_reset_opacity_weights(const gs_prim_arrays* prims, int n, int K, int storage, float opacity_cap,
+                                         float weight, gs_stream stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Batched frames (serving).  A batch renders up to GS_MAX_VIEWS views -- each a camera with its own
  * resolution over one resident scene -- with one launch sequence (forward only): the views'
  * primitives, tiles and pixels are concatenated, so one sort and one persistent compositing launch

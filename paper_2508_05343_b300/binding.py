@@ -46,6 +46,15 @@ class gs_prim_grads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("means", "scales", "quats", "opacity", "sh", "freqs", "weights", "means2d")]
 
 
+class gs_densify_config(C.Structure):
+    _fields_ = [(k, C.c_float) for k in ("grad_threshold", "dense_scale", "min_opacity", "max_scale", "split_divisor",
+                                          "child_freq", "child_weight")]
+
+
+class gs_prim_arrays(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("means", "scales", "quats", "opacity", "sh", "freqs", "weights")]
+
+
 class gs_ws_views(C.Structure):
     _fields_ = [("records", C.c_void_p), ("touched", C.c_void_p), ("offsets", C.c_void_p),
                 ("keys_sorted", C.c_void_p), ("values_sorted", C.c_void_p), ("keys_unsorted", C.c_void_p),
@@ -72,6 +81,12 @@ SIGNATURES = {
     "gabsplat_bin_sort": (C.c_int, [P_(gs_frame), C.c_void_p]),
     "gabsplat_render_fwd": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p, C.c_void_p]),
     "gabsplat_render_freq_map": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p]),
+    "gabsplat_densify_accumulate": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gabsplat_densify_scratch_bytes": (C.c_size_t, [C.c_int]),
+    "gabsplat_densify": (C.c_int, [P_(gs_prims), C.c_void_p, C.c_void_p, C.c_void_p, P_(gs_densify_config),
+                                   P_(gs_prim_arrays), C.c_longlong, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gabsplat_reset_opacity_weights": (C.c_int, [P_(gs_prim_arrays), C.c_int, C.c_int, C.c_int, C.c_float, C.c_float,
+                                                 C.c_void_p]),
     "gabsplat_render_bwd": (C.c_int, [P_(gs_frame), C.c_void_p, P_(gs_prim_grads), C.c_void_p]),
     "gabsplat_render_bwd_2d": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p]),
     "gabsplat_preprocess_bwd": (C.c_int, [P_(gs_frame), P_(gs_prim_grads), C.c_void_p]),
@@ -310,3 +325,41 @@ def make_prims(t: dict, storage=GS_F32) -> gs_prims:
     p.freqs = t["freqs"].data_ptr() if K > 0 else None
     p.weights = t["weights"].data_ptr() if K > 0 else None
     return p
+
+
+def make_densify_config(grad_threshold=2e-4, dense_scale=0.05, min_opacity=0.01, max_scale=0.0, split_divisor=1.6,
+                        child_freq=1e-3, child_weight=1e-2) -> gs_densify_config:
+    c = gs_densify_config()
+    c.grad_threshold, c.dense_scale, c.min_opacity, c.max_scale = grad_threshold, dense_scale, min_opacity, max_scale
+    c.split_divisor, c.child_freq, c.child_weight = split_divisor, child_freq, child_weight
+    return c
+
+
+def make_prim_arrays(t: dict) -> gs_prim_arrays:
+    """Writable arrays from a dict of contiguous CUDA tensors (means, scales, quats, opacity, sh, freqs, weights)."""
+    a = gs_prim_arrays()
+    for k in ("means", "scales", "quats", "opacity", "sh", "freqs", "weights"):
+        v = t.get(k)
+        setattr(a, k, v.data_ptr() if v is not None and v.numel() > 0 else None)
+    return a
+
+
+def gabsplat_densify_accumulate(frame, means2d_grad, grad_accum, denom, stream=None):
+    _check("gabsplat_densify_accumulate", lib.gabsplat_densify_accumulate(
+        C.byref(frame), _ptr(means2d_grad), _ptr(grad_accum), _ptr(denom), _stream(stream)))
+
+
+def gabsplat_densify_scratch_bytes(n):
+    return int(lib.gabsplat_densify_scratch_bytes(n))
+
+
+def gabsplat_densify(prims, grad_accum, denom, split_noise, cfg, out, out_capacity, counts, scratch, stream=None):
+    """prims: gs_prims; out: gs_prim_arrays with room for out_capacity (>= 2 n) rows; counts: int32[4] on the device."""
+    _check("gabsplat_densify", lib.gabsplat_densify(C.byref(prims), _ptr(grad_accum), _ptr(denom), _ptr(split_noise),
+                                                    C.byref(cfg), C.byref(out), out_capacity, _ptr(counts),
+                                                    _ptr(scratch), _stream(stream)))
+
+
+def gabsplat_reset_opacity_weights(arrays, n, K, storage, opacity_cap=0.02, weight=0.01, stream=None):
+    _check("gabsplat_reset_opacity_weights", lib.gabsplat_reset_opacity_weights(
+        C.byref(arrays), n, K, storage, opacity_cap, weight, _stream(stream)))

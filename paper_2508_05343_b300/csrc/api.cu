@@ -301,6 +301,19 @@ gs_status gabsplat_loss_l1_dssim(const float* image, const float* target, int ch
                                    reinterpret_cast<double*>(scratch), reinterpret_cast<cudaStream_t>(stream)));
 }
 
+gs_status gabsplat_densify_accumulate(const gs_frame* frame, const float* means2d_grad, float* grad_accum,
+                                      float* denom, gs_stream stream) {
+  FrameTable t;
+  WsLayout L;
+  const gs_status s = frame_meta(frame, t, L);
+  if (s != GS_OK) return s;
+  if (frame->n > 0 && (!means2d_grad || !grad_accum || !denom)) return GS_ERR_INVALID_ARG;
+  if (!g_sms) g_sms = device_sm_count();
+  const WsPtrs p = make_ptrs(L, frame->ws);
+  return from_cuda(launch_densify_accumulate(p.touched, frame->n, means2d_grad, grad_accum, denom, g_sms,
+                                             reinterpret_cast<cudaStream_t>(stream)));
+}
+
 gs_status gabsplat_device_status(const gs_frame* frame, int* status, unsigned long long* pairs, gs_stream stream) {
   FrameTable t;
   WsLayout L;

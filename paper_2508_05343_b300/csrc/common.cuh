@@ -211,6 +211,8 @@ cudaError_t launch_preprocess_bwd(const FrameTable& tbl, const WsPtrs& p, const 
 cudaError_t launch_loss(const float* img, const float* tgt, long long count, int kind, double* loss_out, float* dL,
                         double* partials, int nblocks, cudaStream_t s);
 size_t l1_dssim_partials(int C, int H, int W);
+cudaError_t launch_densify_accumulate(const u32* touched, int n, const float* grad, float* acc, float* den,
+                                      int sm_count, cudaStream_t s);
 cudaError_t launch_l1_dssim(const float* img, const float* tgt, int C, int H, int W, float lambda, double* loss_out,
                             float* dL, double* partials, cudaStream_t s);
 
