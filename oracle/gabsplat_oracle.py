@@ -43,11 +43,12 @@ F64 = torch.float64
 TILE = 16
 
 
-def default_config(eps2d=0.3, bg=(0.0, 0.0, 0.0)):
-    """Rasterizer constants (float32 values, so both sides compare against identical thresholds)."""
+def default_config(eps2d=0.3, bg=(0.0, 0.0, 0.0), z_atten=False):
+    """Rasterizer constants (float32 values, so both sides compare against identical thresholds).
+    z_atten selects the z-attenuation variant (see z_attenuation)."""
     f = lambda v: float(np.float32(v))
     return dict(eps2d=f(eps2d), alpha_max=f(0.99), alpha_min=f(1.0 / 255.0), T_min=f(1e-4),
-                bg=tuple(f(b) for b in bg))
+                bg=tuple(f(b) for b in bg), z_atten=bool(z_atten))
 
 
 # ----------------------------------------------------------------------------------------------
@@ -144,6 +145,14 @@ def splat_frequency(f_proj: torch.Tensor, sigma_ray: torch.Tensor) -> torch.Tens
     return f_proj[..., 0:2] - ratio[:, None, :] * f_proj[..., 2:3]
 
 
+def z_attenuation(f_proj: torch.Tensor, sigma_ray: torch.Tensor) -> torch.Tensor:
+    """The variant that keeps the z-integration constant C2 (supplement A.2): integrating a cosine
+    component over z multiplies it, relative to the envelope, by C2 = exp(-2 pi^2 f_proj_z^2 / S_22)
+    with S = inverse(ray-space covariance).  [n,K,3], [n,3,3] -> [n,K]."""
+    S = torch.linalg.inv(sigma_ray)
+    return torch.exp(-2.0 * math.pi ** 2 * f_proj[..., 2] ** 2 / S[:, 2:3, 2])
+
+
 def project(prims: dict, cam, cfg, third_row: str = "z") -> dict:
     """Per-primitive 2D Gabor parameters in float64 (differentiable in every attribute)."""
     W, tc = camera_tensors(cam)
@@ -159,9 +168,12 @@ def project(prims: dict, cam, cfg, third_row: str = "z") -> dict:
     conic = torch.stack([conic_m[:, 0, 0], conic_m[:, 0, 1], conic_m[:, 1, 1]], -1)
     mu2d = torch.stack([cam["fx"] * t[:, 0] / t[:, 2] + cam["cx"], cam["fy"] * t[:, 1] / t[:, 2] + cam["cy"]], -1)
     K = prims["weights"].shape[1]
+    cos_weights = prims["weights"]
     if K > 0:
         f_proj = torch.einsum("nji,nkj->nki", torch.linalg.inv(M), prims["freqs"])   # ((JW)^-1)^T f  (Eq. 7)
         f2d = splat_frequency(f_proj, sigma_ray)
+        if cfg.get("z_atten"):
+            cos_weights = prims["weights"] * z_attenuation(f_proj, sigma_ray)
     else:
         f2d = torch.zeros(means.shape[0], 0, 2, dtype=F64)
     campos = -(W.T @ tc)
@@ -171,7 +183,7 @@ def project(prims: dict, cam, cfg, third_row: str = "z") -> dict:
     basis = sh_basis(dirs, deg)                                 # [n, (d+1)^2]
     rgb = torch.clamp_min(torch.einsum("nc,ncj->nj", basis, prims["sh"]) + 0.5, 0.0)
     return dict(mu2d=mu2d, conic=conic, opacity=prims["opacity"], rgb=rgb, f2d=f2d,
-                weights=prims["weights"], depth=t[:, 2], cov2d=cov2d)
+                weights=prims["weights"], cos_weights=cos_weights, depth=t[:, 2], cov2d=cov2d)
 
 
 # ----------------------------------------------------------------------------------------------
@@ -346,7 +358,8 @@ AMBIG_T = 1e-8         # |T (1 - alpha) - T_min| below this: likewise
 
 
 def gabor_alpha(px, py, rec, cfg):
-    """alpha_raw = o * G2D(x) * [(1 - sum w) + sum w cos(2 pi f2D . (x - mu2D))] for pixels x pairs."""
+    """alpha_raw = o * G2D(x) * [(1 - sum w) + sum w' cos(2 pi f2D . (x - mu2D))] for pixels x pairs,
+    w' = w (the method) or w C2 (the z-attenuation variant)."""
     dx = px[:, None] - rec["mu2d"][None, :, 0]
     dy = py[:, None] - rec["mu2d"][None, :, 1]
     a, b, c = rec["conic"][:, 0], rec["conic"][:, 1], rec["conic"][:, 2]
@@ -354,7 +367,7 @@ def gabor_alpha(px, py, rec, cfg):
     w = rec["weights"]
     if w.shape[1] > 0:
         phase = 2.0 * math.pi * (dx[..., None] * rec["f2d"][None, :, :, 0] + dy[..., None] * rec["f2d"][None, :, :, 1])
-        bank = (1.0 - w.sum(-1))[None, :] + (w[None] * torch.cos(phase)).sum(-1)
+        bank = (1.0 - w.sum(-1))[None, :] + (rec["cos_weights"][None] * torch.cos(phase)).sum(-1)
     else:
         bank = torch.ones_like(G)
     return rec["opacity"][None, :] * G * bank
@@ -402,7 +415,7 @@ def _tile_pixels(tx, ty, width, height):
     return gx.reshape(-1) + 0.5, gy.reshape(-1) + 0.5, gx.reshape(-1).long(), gy.reshape(-1).long()
 
 
-REC_KEYS = ("mu2d", "conic", "opacity", "rgb", "f2d", "weights")
+REC_KEYS = ("mu2d", "conic", "opacity", "rgb", "f2d", "weights", "cos_weights")
 
 
 def _to_f64(prims, requires_grad=False):
@@ -465,7 +478,7 @@ def render(prims: dict, cam, cfg, tiles=None, third_row="z", cull=True) -> dict:
 def frequency_features(proj: dict) -> torch.Tensor:
     """Per primitive [n, 3]: sum_i w_i |f2D_i|, sum_i w_i |f2D_i,x|, sum_i w_i |f2D_i,y| -- the
     weighted Gabor frequencies (cycles per pixel) that the frequency maps blend (Sec. 4)."""
-    f, w = proj["f2d"], proj["weights"]
+    f, w = proj["f2d"], proj["cos_weights"]
     if w.shape[1] == 0:
         return torch.zeros(w.shape[0], 3, dtype=F64)
     mag = torch.sqrt((f * f).sum(-1))

@@ -309,7 +309,8 @@ def _brute_force(prims, cam, cfg, feature=None):
                 bank = 1.0
                 for i in range(P["weights"].shape[1]):
                     wi = P["weights"][k, i]
-                    bank += wi * (math.cos(2 * math.pi * (P["f2d"][k, i, 0] * dx + P["f2d"][k, i, 1] * dy)) - 1.0)
+                    wc = P["cos_weights"][k, i]
+                    bank += wc * math.cos(2 * math.pi * (P["f2d"][k, i, 0] * dx + P["f2d"][k, i, 1] * dy)) - wi
                 alpha = min(cfg["alpha_max"], P["opacity"][k] * G * bank)
                 if alpha < cfg["alpha_min"]:
                     continue
@@ -689,3 +690,47 @@ def test_densify_special_cases_accumulate_and_reset():
     r = O.reset_opacity_weights(prims)
     np.testing.assert_array_equal(r["opacity"], np.minimum(prims["opacity"], np.float32(0.02)))
     assert np.all(r["weights"] == np.float32(0.01))
+
+
+
+# ---- the z-attenuation variant (supplement A.2 with C2 kept) ---------------------------------
+@pytest.mark.parametrize("seed", [3, 4])
+def test_z_attenuation_variant_is_the_z_integral(seed):
+    """With C2 kept, the 2D bank (1 - w) + w C2 cos(2 pi f2D.(x, y)) is the z-integral of the 3D
+    primitive's bank weighted by its envelope, divided by the z-integral of the envelope
+    (adaptive quadrature), so C1 cancels and only C2 remains."""
+    from scipy.integrate import quad
+    rng = np.random.default_rng(200 + seed)
+    A = rng.standard_normal((3, 3))
+    sigma = A @ A.T + 0.3 * np.eye(3)
+    f = rng.normal(0, 0.4, 3)
+    S22 = np.linalg.inv(sigma)[2, 2]
+    f *= math.sqrt(0.7 * S22 / (2 * math.pi ** 2 * f[2] ** 2))   # 2 pi^2 f_z^2 / S22 = 0.7
+    w = 0.7
+    f2d = O.splat_frequency(t64(f[None, None, :]), t64(sigma[None])).numpy()[0, 0]
+    C2 = float(O.z_attenuation(t64(f[None, None, :]), t64(sigma[None])).numpy()[0, 0])
+    S = np.linalg.inv(sigma)
+    assert abs(C2 - math.exp(-0.7)) < 1e-12
+    for _ in range(5):
+        x, y = rng.normal(0, 1.0, 2)
+        env = lambda z: math.exp(-0.5 * np.array([x, y, z]) @ S @ np.array([x, y, z]))
+        num, _ = quad(lambda z: env(z) * ((1 - w) + w * math.cos(2 * math.pi * (f @ np.array([x, y, z])))),
+                      -np.inf, np.inf, epsabs=1e-14, epsrel=1e-12, limit=400)
+        den, _ = quad(env, -np.inf, np.inf, epsabs=1e-14, epsrel=1e-12, limit=400)
+        bank = (1 - w) + w * C2 * math.cos(2 * math.pi * (f2d @ np.array([x, y])))
+        assert abs(num / den - bank) < 1e-9, (num / den, bank)
+
+
+def test_z_attenuation_variant_render_brute_force():
+    cam = tiny_camera(40, 32, dist=2.0)
+    cfg = O.default_config(z_atten=True)
+    prims = tiny_scene(9, n=24, K=2, log_scale=(-2.2, 0.4))
+    prims["freqs"] = prims["freqs"] * 6.0                  # frequencies high enough to be attenuated
+    out = O.render(prims, cam, cfg)
+    img, T, _ = _brute_force(prims, cam, cfg)
+    np.testing.assert_allclose(out["image"].numpy(), img, atol=1e-12)
+    plain = O.render(prims, cam, O.default_config())["image"].numpy()
+    assert np.abs(plain - img).max() > 1e-3                # and it differs from the method
+    proj = O.project(O._to_f64(prims), cam, cfg)
+    c2 = (proj["cos_weights"] / proj["weights"]).detach().numpy()
+    assert np.all(c2 <= 1.0) and c2.min() < 0.9
