@@ -94,7 +94,12 @@ typedef struct {
  * eps2d is added to the diagonal of the 2D covariance, alpha = min(alpha_max, o Gabor2D(x)),
  * pairs with alpha < alpha_min are skipped, compositing stops before the pair whose
  * T (1 - alpha) would drop below T_min, and bg is added with the final transmittance.
- * Defaults: 0.3, 0.99, 1/255, 1e-4, (0,0,0).  flags must be 0. */
+ * Defaults: 0.3, 0.99, 1/255, 1e-4, (0,0,0).  flags: 0 (the method as the paper renders it) or
+ * GS_FLAG_Z_ATTENUATION: the variant that keeps the z-integration constant C2 of supplement A.2,
+ * so the 2D filter bank is (1 - sum w_i) + sum w_i C2_i cos(2 pi f2D_i . d) with
+ * C2_i = exp(-2 pi^2 f_proj,z,i^2 / S_22), S the inverse of the ray-space covariance J W Sigma
+ * W^T J^T (undilated).  Other bits are rejected. */
+#define GS_FLAG_Z_ATTENUATION 1u
 typedef struct {
   float eps2d, alpha_max, alpha_min, T_min;
   float bg[3];
@@ -139,7 +144,10 @@ typedef struct {
  * the last composited pair); n_eval [H][W] uint32 pairs the forward pass evaluated at the pixel
  * (its tile's list length, or up to the pair that ended compositing); n_reach [H][W] uint32 of those,
  * pairs whose envelope passed o G >= alpha_min; n_comp [H][W] uint32 pairs composited; grad2d [n][grad2d_floats] float32
- *   {d mu_x, d mu_y, d a, d b, d c, d opacity, d r, d g, d b, d f2D (2K), d w (K), 0 pad}. */
+ *   {d mu_x, d mu_y, d a, d b, d c, d opacity, d r, d g, d b, d f2D (2K), d (cosine weight) (K),
+ *    d (1 - sum w), 0 pad}: the filter bank (1 - sum w) + sum w'_i cos(.) is differentiated in its
+ *    two weight terms separately (w' = w, or w C2 in the z-attenuation variant, whose records hold
+ *    w' in the weight slots). */
 typedef struct {
   float* records;
   unsigned* touched;

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libgabsplat.so")
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_NONFINITE, GS_ERR_WORKSPACE = range(7)
 GS_F32, GS_BF16 = 0, 1
 GS_LOSS_L1, GS_LOSS_L2 = 0, 1
+GS_FLAG_Z_ATTENUATION = 1
 GS_TILE, GS_MAX_K, GS_MAX_SH_DEGREE, GS_MAX_VIEWS = 16, 8, 3, 16
 
 
@@ -303,12 +304,13 @@ def make_camera(cam: dict) -> gs_camera:
     return c
 
 
-def make_config(eps2d=0.3, alpha_max=0.99, alpha_min=1.0 / 255.0, T_min=1e-4, bg=(0.0, 0.0, 0.0)) -> gs_config:
+def make_config(eps2d=0.3, alpha_max=0.99, alpha_min=1.0 / 255.0, T_min=1e-4, bg=(0.0, 0.0, 0.0),
+                flags=0) -> gs_config:
     g = gs_config()
     g.eps2d, g.alpha_max, g.alpha_min, g.T_min = eps2d, alpha_max, alpha_min, T_min
     for i in range(3):
         g.bg[i] = float(bg[i])
-    g.flags = 0
+    g.flags = flags
     return g
 
 

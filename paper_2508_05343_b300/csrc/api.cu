@@ -179,7 +179,7 @@ gs_status gabsplat_preprocess(const gs_frame* frame, const gs_prims* pr, const g
   if (reinterpret_cast<uintptr_t>(pr->quats) & 15) return GS_ERR_INVALID_ARG;
   if (!(cam->fx > 0.f) || !(cam->fy > 0.f) || !(cam->znear > 0.f) || !(cam->zfar > cam->znear))
     return GS_ERR_INVALID_ARG;
-  if (cfg->flags != 0 || !(cfg->eps2d >= 0.f) || !(cfg->alpha_max > 0.f) || !(cfg->alpha_max < 1.f) ||
+  if ((cfg->flags & ~(unsigned)GS_FLAG_Z_ATTENUATION) != 0 || !(cfg->eps2d >= 0.f) || !(cfg->alpha_max > 0.f) || !(cfg->alpha_max < 1.f) ||
       !(cfg->alpha_min > 0.f) || !(cfg->T_min > 0.f))
     return GS_ERR_INVALID_ARG;
   t.storage = pr->storage;
@@ -187,6 +187,7 @@ gs_status gabsplat_preprocess(const gs_frame* frame, const gs_prims* pr, const g
   t.alpha_max = cfg->alpha_max;
   t.alpha_min = cfg->alpha_min;
   t.T_min = cfg->T_min;
+  t.flags = cfg->flags;
   for (int i = 0; i < 3; ++i) t.bg[i] = cfg->bg[i];
   ViewDesc& V = t.v[0];
   V.means = pr->means;

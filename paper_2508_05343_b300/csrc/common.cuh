@@ -31,7 +31,7 @@ constexpr int MAX_PASSES = 8;
 // Number of floats of a projected 2D record and of a per-primitive 2D gradient row.
 __host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
 __host__ __device__ constexpr int rec_floats(int K) { return 12 + round4(3 * K); }
-__host__ __device__ constexpr int g2d_floats(int K) { return round4(9 + 3 * K); }
+__host__ __device__ constexpr int g2d_floats(int K) { return round4(10 + 3 * K); }
 
 // ------------------------------------------------------------------------------------------
 // Frame description on the device: up to GS_MAX_VIEWS views, each one camera over one scene.
@@ -64,6 +64,7 @@ struct FrameTable {
   u64 total_pixels;
   float eps2d, alpha_max, alpha_min, T_min;
   float bg[3];
+  u32 flags;                        // gs_config.flags (GS_FLAG_*)
   int npasses;                      // digit passes launched (worst case for the workspace; host)
   int npasses_needed;               // passes that do work: ceil((depth_bits + tile bits) / 8)
   u32 depth_base;                   // float bits of the nearest depth (znear): depth keys minus this fit

@@ -233,6 +233,7 @@ struct Reach {
   float mux, muy, A, C, kx, ky, B2, thr;
 };
 constexpr float LN2_UP = 0.693147182464599609375f;   // the float32 just above ln 2
+constexpr float PI_SQ = 9.869604401089358f;          // pi^2
 
 __device__ __forceinline__ bool reach_params(const BinSpec& b, float eps2d, float o, float amin, Reach& r) {
   if (!(o >= amin)) return false;
@@ -353,6 +354,10 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, const 
       r1 = (float)n1 * idet;
     }
     const float tzfx = b.tz / V.fx, tzfy = b.tz / V.fy;
+    // z-attenuation variant: 1/S_22 = c - b^T A^-1 b (the Schur complement of the ray-space
+    // covariance [[A, b], [b^T, c]]), the conditional variance along the ray
+    const bool zatt = (tbl->flags & GS_FLAG_Z_ATTENUATION) != 0;
+    const float sz = zatt ? fmaxf(W[6] * Sw0 + W[7] * Sw1 + W[8] * Sw2 - (bv0 * r0 + bv1 * r1), 0.f) : 0.f;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       const size_t fb = ((size_t)k * K + i) * 3;
@@ -365,7 +370,7 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, const 
       rec[12 + 2 * i] = fpx + r0 * fpz;
       rec[12 + 2 * i + 1] = fpy + r1 * fpz;
       const float wi = load_attr<STORAGE>(V.weights, (size_t)k * K + i);
-      rec[12 + 2 * K + i] = wi;
+      rec[12 + 2 * K + i] = zatt ? wi * expf(-2.f * PI_SQ * fpz * fpz * sz) : wi;
       wsum += wi;
     }
 #pragma unroll
@@ -675,10 +680,6 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
     float gmean[3] = {0.f, 0.f, 0.f}, gscale[3] = {0.f, 0.f, 0.f}, gquat[4] = {0.f, 0.f, 0.f, 0.f};
     if (G.opacity) G.opacity[k] = g2[5];
     if (G.means2d) { G.means2d[2 * (size_t)k] = g2[0]; G.means2d[2 * (size_t)k + 1] = g2[1]; }
-    if (K > 0 && G.weights) {
-#pragma unroll
-      for (int i = 0; i < K; ++i) G.weights[(size_t)k * K + i] = g2[9 + 2 * K + i];
-    }
     if (!active) {
       if (G.means) for (int i = 0; i < 3; ++i) G.means[3 * (size_t)k + i] = 0.f;
       if (G.scales) for (int i = 0; i < 3; ++i) G.scales[3 * (size_t)k + i] = 0.f;
@@ -744,7 +745,7 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
     float gA11 = -(QG10 * Qb + QG11 * Qc);
     float gA01 = -2.f * (QG00 * Qb + QG01 * Qc);   // the off-diagonal entry appears twice
     float gtx = 0.f, gty = 0.f, gtz = 0.f, gux = 0.f, guy = 0.f;
-    float gb0 = 0.f, gb1 = 0.f;
+    float gb0 = 0.f, gb1 = 0.f, gcz = 0.f;   // gcz: dL/d(w3^T Sigma w3), the variant only
     if (K > 0) {
       const double detA = (double)A00 * (double)A11 - (double)A01 * (double)A01;
       float iA00 = 0.f, iA01 = 0.f, iA11 = 0.f, r0 = 0.f, r1 = 0.f;
@@ -756,6 +757,14 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
       }
       float gr0 = 0.f, gr1 = 0.f;
       const float tzfx = tz / V.fx, tzfy = tz / V.fy;
+      // the bank's weight terms: G_i = dL/d(cosine weight i), G0 = dL/d(1 - sum w); in the
+      // z-attenuation variant the cosine weight is w_i C2_i, C2_i = exp(-2 pi^2 fpz_i^2 sz) with
+      // sz = c - b^T A^-1 b (clamped at 0), else C2_i = 1
+      const float G0 = g2[9 + 3 * K];
+      const bool zatt = (tbl->flags & GS_FLAG_Z_ATTENUATION) != 0;
+      const float sz_raw = zatt ? (w3[0] * Sw[0] + w3[1] * Sw[1] + w3[2] * Sw[2]) - (bv0 * r0 + bv1 * r1) : 0.f;
+      const float sz = fmaxf(sz_raw, 0.f);
+      float gsz = 0.f;
       for (int i = 0; i < K; ++i) {
         const size_t fb = ((size_t)k * K + i) * 3;
         const float f0 = load_attr<STORAGE>(V.freqs, fb), f1 = load_attr<STORAGE>(V.freqs, fb + 1),
@@ -765,7 +774,16 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
         const float gg2 = W[6] * f0 + W[7] * f1 + W[8] * f2;
         const float fpz = gg2 + ux * g0 + uy * g1;
         const float gfx = g2[9 + 2 * i], gfy = g2[9 + 2 * i + 1];
-        const float gpz = r0 * gfx + r1 * gfy;
+        float gpz = r0 * gfx + r1 * gfy;
+        const float Gi = g2[9 + 2 * K + i];
+        const float wi = load_attr<STORAGE>(V.weights, (size_t)k * K + i);
+        const float c2 = zatt ? expf(-2.f * PI_SQ * fpz * fpz * sz) : 1.f;
+        if (G.weights) G.weights[(size_t)k * K + i] = c2 * Gi - G0;
+        if (zatt) {
+          const float garg = Gi * wi * c2;                 // dL/d(-2 pi^2 fpz^2 sz)
+          gpz += garg * (-4.f * PI_SQ * fpz * sz);
+          gsz += garg * (-2.f * PI_SQ * fpz * fpz);
+        }
         gr0 += fpz * gfx;
         gr1 += fpz * gfy;
         const float gg0 = gfx * tzfx + gpz * ux;
@@ -786,13 +804,22 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
       gA00 -= u0 * r0;
       gA11 -= u1 * r1;
       gA01 -= u0 * r1 + u1 * r0;
+      // sz = c - b^T A^-1 b: d/dc = 1, d/db = -2 r, d/dA = r r^T
+      if (zatt && sz_raw > 0.f) {
+        gcz = gsz;
+        gb0 -= 2.f * r0 * gsz;
+        gb1 -= 2.f * r1 * gsz;
+        gA00 += r0 * r0 * gsz;
+        gA11 += r1 * r1 * gsz;
+        gA01 += 2.f * r0 * r1 * gsz;
+      }
     }
     // ---- A = T Sigma T^T, b = T Sigma w3 ----
     float gS[9];
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j)
         gS[3 * i + j] = gA00 * T0[i] * T0[j] + gA01 * T0[i] * T1[j] + gA11 * T1[i] * T1[j] +
-                        (gb0 * T0[i] + gb1 * T1[i]) * w3[j];
+                        (gb0 * T0[i] + gb1 * T1[i]) * w3[j] + gcz * w3[i] * w3[j];
     float gT0[3], gT1[3];
     for (int j = 0; j < 3; ++j) {
       gT0[j] = 2.f * gA00 * U0[j] + gA01 * U1[j] + gb0 * Sw[j];

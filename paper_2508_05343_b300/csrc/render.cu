@@ -253,7 +253,7 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[32], int lane) {
 // per 4 values (zero groups skipped).
 template <int K>
 __device__ __forceinline__ void flush_pair_grads(const float* a, float* dst) {
-  constexpr int NV = 9 + 3 * K, NG = g2d_floats(K);
+  constexpr int NV = 10 + 3 * K, NG = g2d_floats(K);
   const float cA = -0.5f * LOG2E, cB = -LOG2E;
   float row[NG];
 #pragma unroll
@@ -273,9 +273,9 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
                                                             const float* __restrict__ dL_drgb) {
   constexpr int NT = BLOCK / PPT;
   constexpr int F4 = SRec<K>::F4;
-  constexpr int NV = 9 + 3 * K;          // gradient values per pair
+  constexpr int NV = 10 + 3 * K;         // gradient values per pair
   constexpr int NG = g2d_floats(K);      // padded row in global memory
-  constexpr int NS = NV;                 // shared accumulator row (odd stride: conflict-free)
+  constexpr int NS = NV | 1;             // shared accumulator row (odd stride: conflict-free)
   constexpr int NVP = (NV + 31) / 32 * 32;
   extern __shared__ __align__(16) float4 smem4[];
   float4* s_rec = smem4;                                        // [NT][F4]
@@ -412,13 +412,14 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
 #pragma unroll
           for (int i = 0; i < K; ++i) {
             const float wi = fw[2 * K + i];
-            gv[9 + 2 * K + i] += dLdbank * (cs[i] - 1.f);          // d w_i
+            gv[9 + 2 * K + i] += dLdbank * cs[i];                  // d (cosine weight i)
             const float gph = -dLdbank * wi * sn[i] * TWO_PI;       // d phase (cycles)
             gv[9 + 2 * i] += gph * dx;
             gv[9 + 2 * i + 1] += gph * dy;
             gdx += gph * fw[2 * i];
             gdy += gph * fw[2 * i + 1];
           }
+          gv[9 + 3 * K] += dLdbank;                        // d (1 - sum w)
           gv[0] -= gdx;                                    // d mu = - d (pixel - mu)
           gv[1] -= gdy;
         }
@@ -470,7 +471,7 @@ static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const u3
                                 const Launch& L) {
   constexpr int PPT = GS_PPT_BWD, NT = BLOCK / PPT;
   static int grid = 0;
-  const size_t smem = (size_t)NT * SRec<K>::F * sizeof(float) + (size_t)NT * (9 + 3 * K) * sizeof(float) +
+  const size_t smem = (size_t)NT * SRec<K>::F * sizeof(float) + (size_t)NT * ((10 + 3 * K) | 1) * sizeof(float) +
                       (size_t)NT * sizeof(u32);
   if (!grid) {
     cudaError_t e =

@@ -11,11 +11,11 @@ AMBIG_EXTRA = 1e-2  # extra allowance at pixels where float32/float64 may take a
 ATTRS = ("means", "scales", "quats", "opacity", "sh", "freqs", "weights")
 
 
-def cfg_pair(eps2d=0.3, bg=(0.0, 0.0, 0.0)):
+def cfg_pair(eps2d=0.3, bg=(0.0, 0.0, 0.0), z_atten=False):
     from paper_2508_05343_b300 import binding as B
-    oc = O.default_config(eps2d=eps2d, bg=bg)
+    oc = O.default_config(eps2d=eps2d, bg=bg, z_atten=z_atten)
     return oc, B.make_config(eps2d=oc["eps2d"], alpha_max=oc["alpha_max"], alpha_min=oc["alpha_min"],
-                             T_min=oc["T_min"], bg=oc["bg"])
+                             T_min=oc["T_min"], bg=oc["bg"], flags=B.GS_FLAG_Z_ATTENUATION if z_atten else 0)
 
 
 def gpu_render(prims, cam, gcfg, storage=0, capacity=None):

@@ -148,7 +148,39 @@ def test_config1_gradients_vs_oracle_analytic():
     errs["2d.opacity"] = rel_l2(g2[:, 5], r2["opacity"])
     errs["2d.rgb"] = rel_l2(g2[:, 6:9], r2["rgb"])
     errs["2d.f2d"] = rel_l2(g2[:, 9:9 + 2 * K], r2["f2d"].reshape(-1, 2 * K))
-    errs["2d.w"] = rel_l2(g2[:, 9 + 2 * K:9 + 3 * K], r2["weights"])
+    errs["2d.cos_w"] = rel_l2(g2[:, 9 + 2 * K:9 + 3 * K], r2["cos_weights"])
+    errs["2d.1-sum_w"] = rel_l2(g2[:, 9 + 3 * K], -r2["weights"][:, 0])   # each weight enters 1 - sum w
+    bad = {k: e for k, e in errs.items() if not e <= GRAD_TOL}
+    assert not bad, f"gradient rel-L2 above {GRAD_TOL}: {bad} (all: {errs})"
+
+
+def _variant_scene():
+    spec = scenes.SceneSpec(n=1500, K=3, sh_degree=2, layout="uniform", box=1.0, log_scale=(-3.0, 0.5))
+    p = scenes.make_scene(spec, 61)
+    p["freqs"] = (p["freqs"] * 2.0).astype(np.float32)     # C2 from ~1e-7 to ~1 across the scene
+    return p, scenes.orbit_camera(160, 120, 40.0, 15.0, 3.5)
+
+
+def test_z_attenuation_variant_image_records_and_gradients():
+    """The variant that keeps C2 = exp(-2 pi^2 f_proj,z^2 / S_22) on each cosine weight: same
+    bars as the method (bit-exact bins, 2e-4 images, 1e-3 gradients); records carry w C2."""
+    prims, cam = _variant_scene()
+    oc, gc = cfg_pair(z_atten=True)
+    out = O.render(prims, cam, oc)
+    r, _, img, _ = gpu_render(prims, cam, gc)
+    v = check_binning(r, out["spec"])
+    assert_image_parity(img.cpu().numpy(), out)
+    K = prims["weights"].shape[1]
+    valid = out["spec"]["valid"] & (out["spec"]["touched"] > 0)
+    rec = v["records"].cpu().numpy().astype(np.float64)[valid]
+    cw = out["proj"]["cos_weights"].numpy()[valid]
+    np.testing.assert_allclose(rec[:, 12 + 2 * K:12 + 3 * K], cw, rtol=1e-4, atol=1e-6)
+    np.testing.assert_allclose(rec[:, 6], 1.0 - prims["weights"][valid].astype(np.float64).sum(1), atol=1e-6)
+    target = scenes.make_target(cam["width"], cam["height"], 1201)
+    dL = _masked_l2_grad(out["image"].numpy(), target, out["ambiguous_bwd"].numpy())
+    ref = O.render_backward(prims, cam, oc, dL)
+    g = gpu_grads(r, dL)
+    errs = {k: rel_l2(g[k], ref[k]) for k in ATTRS}
     bad = {k: e for k, e in errs.items() if not e <= GRAD_TOL}
     assert not bad, f"gradient rel-L2 above {GRAD_TOL}: {bad} (all: {errs})"
 
