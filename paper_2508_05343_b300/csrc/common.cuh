@@ -193,6 +193,44 @@ __device__ __forceinline__ float load_attr(const void* p, size_t i) {
   return __ldg(reinterpret_cast<const float*>(p) + i);
 }
 
+// The 3 nsh SH coefficients of primitive k ([k][nsh][3] in the storage type) as float32.  A full
+// degree-3 row (192 B in float32, 96 B in BF16) is read with 16-byte loads, all issued before use.
+template <int STORAGE>
+__device__ __forceinline__ void load_sh_row(const void* sh, size_t k, int nsh, float* c) {
+  const size_t base = k * (size_t)nsh * 3;
+  if (nsh == 16 && (reinterpret_cast<uintptr_t>(sh) & 15) == 0) {
+    if (STORAGE == GS_BF16) {
+      const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(sh) + base);
+      uint4 t[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) t[i] = __ldg(src + i);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&t[i]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float2 f = __bfloat1622float2(h[j]);
+          c[8 * i + 2 * j] = f.x;
+          c[8 * i + 2 * j + 1] = f.y;
+        }
+      }
+    } else {
+      const float4* src = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(sh) + base);
+      float4 t[12];
+#pragma unroll
+      for (int i = 0; i < 12; ++i) t[i] = __ldg(src + i);
+#pragma unroll
+      for (int i = 0; i < 12; ++i) {
+        c[4 * i] = t[i].x; c[4 * i + 1] = t[i].y; c[4 * i + 2] = t[i].z; c[4 * i + 3] = t[i].w;
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 48; ++i)
+    if (i < 3 * nsh) c[i] = load_attr<STORAGE>(sh, base + i);
+}
+
 // ------------------------------------------------------------------------------------------
 // Launch helpers (defined in the kernel translation units).
 // ------------------------------------------------------------------------------------------

@@ -326,10 +326,14 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, const 
   sh_eval(deg, dxv, dyv, dzv, Y);
   const int nsh = (deg + 1) * (deg + 1);
   float rgb[3] = {0.5f, 0.5f, 0.5f};
-  const size_t shb = (size_t)k * nsh * 3;
-  for (int j = 0; j < nsh; ++j) {
+  float shc[48];
+  load_sh_row<STORAGE>(V.sh, k, nsh, shc);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) rgb[c] += Y[j] * load_attr<STORAGE>(V.sh, shb + 3 * j + c);
+  for (int j = 0; j < 16; ++j) {
+    if (j < nsh) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) rgb[c] += Y[j] * shc[3 * j + c];
+    }
   }
   float rec[rec_floats(K)];
   rec[0] = b.mux; rec[1] = b.muy; rec[2] = ca; rec[3] = cb;
@@ -880,17 +884,36 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
       const size_t shb = (size_t)k * nsh * 3;
       float raw[3] = {0.5f, 0.5f, 0.5f};
       float cw[16];
-      for (int j = 0; j < nsh; ++j)
-        for (int c = 0; c < 3; ++c) raw[c] += Y[j] * load_attr<STORAGE>(V.sh, shb + 3 * j + c);
+      float shc[48];
+      load_sh_row<STORAGE>(V.sh, k, nsh, shc);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (j < nsh)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) raw[c] += Y[j] * shc[3 * j + c];
       float graw[3];
+#pragma unroll
       for (int c = 0; c < 3; ++c) graw[c] = raw[c] < 0.f ? 0.f : g2[6 + c];
-      for (int j = 0; j < nsh; ++j) {
-        float acc = 0.f;
-        for (int c = 0; c < 3; ++c) {
-          acc += load_attr<STORAGE>(V.sh, shb + 3 * j + c) * graw[c];
-          if (G.sh) G.sh[shb + 3 * j + c] = Y[j] * graw[c];
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        cw[j] = j < nsh ? shc[3 * j] * graw[0] + shc[3 * j + 1] * graw[1] + shc[3 * j + 2] * graw[2] : 0.f;
+      if (G.sh) {
+        if (nsh == 16 && (reinterpret_cast<uintptr_t>(G.sh) & 15) == 0) {
+          float4* dst = reinterpret_cast<float4*>(G.sh + shb);
+#pragma unroll
+          for (int i = 0; i < 12; ++i) {
+            float v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = Y[(4 * i + e) / 3] * graw[(4 * i + e) % 3];
+            dst[i] = make_float4(v[0], v[1], v[2], v[3]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (j < nsh)
+#pragma unroll
+              for (int c = 0; c < 3; ++c) G.sh[shb + 3 * j + c] = Y[j] * graw[c];
         }
-        cw[j] = acc;
       }
       float gdx, gdy, gdz;
       sh_grad(deg, dx, dy, dz, cw, gdx, gdy, gdz);
