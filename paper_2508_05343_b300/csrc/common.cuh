@@ -193,6 +193,63 @@ __device__ __forceinline__ float load_attr(const void* p, size_t i) {
   return __ldg(reinterpret_cast<const float*>(p) + i);
 }
 
+// Row `row` of N values ([rows][N] in the storage type) as float32, with the widest loads that the
+// row length and the address allow.
+template <int STORAGE, int N>
+__device__ __forceinline__ void load_row(const void* p, size_t row, float* out) {
+  if (N == 0) return;
+  if (STORAGE == GS_BF16) {
+    const __nv_bfloat16* src = reinterpret_cast<const __nv_bfloat16*>(p) + row * N;
+    if (N % 2 == 0 && (reinterpret_cast<uintptr_t>(src) & 3) == 0) {
+#pragma unroll
+      for (int i = 0; i < N / 2; ++i) {
+        const float2 f = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(src)[i]);
+        out[2 * i] = f.x;
+        out[2 * i + 1] = f.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) out[i] = __bfloat162float(src[i]);
+    }
+  } else {
+    const float* src = reinterpret_cast<const float*>(p) + row * N;
+    if (N % 4 == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+#pragma unroll
+      for (int i = 0; i < N / 4; ++i) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(src) + i);
+        out[4 * i] = t.x; out[4 * i + 1] = t.y; out[4 * i + 2] = t.z; out[4 * i + 3] = t.w;
+      }
+    } else if (N % 2 == 0 && (reinterpret_cast<uintptr_t>(src) & 7) == 0) {
+#pragma unroll
+      for (int i = 0; i < N / 2; ++i) {
+        const float2 t = __ldg(reinterpret_cast<const float2*>(src) + i);
+        out[2 * i] = t.x; out[2 * i + 1] = t.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) out[i] = __ldg(src + i);
+    }
+  }
+}
+
+// N float32 values to row `row` of p ([rows][N]), with the widest stores the row and address allow.
+template <int N>
+__device__ __forceinline__ void store_row(float* p, size_t row, const float* v) {
+  if (N == 0) return;
+  float* dst = p + row * N;
+  if (N % 4 == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i)
+      reinterpret_cast<float4*>(dst)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else if (N % 2 == 0 && (reinterpret_cast<uintptr_t>(dst) & 7) == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) reinterpret_cast<float2*>(dst)[i] = make_float2(v[2 * i], v[2 * i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) dst[i] = v[i];
+  }
+}
+
 // The 3 nsh SH coefficients of primitive k ([k][nsh][3] in the storage type) as float32.  A full
 // degree-3 row (192 B in float32, 96 B in BF16) is read with 16-byte loads, all issued before use.
 template <int STORAGE>

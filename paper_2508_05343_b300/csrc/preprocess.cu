@@ -362,18 +362,19 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, const 
     // covariance [[A, b], [b^T, c]]), the conditional variance along the ray
     const bool zatt = (tbl->flags & GS_FLAG_Z_ATTENUATION) != 0;
     const float sz = zatt ? fmaxf(W[6] * Sw0 + W[7] * Sw1 + W[8] * Sw2 - (bv0 * r0 + bv1 * r1), 0.f) : 0.f;
+    float fr[3 * (K > 0 ? K : 1)], wr[K > 0 ? K : 1];
+    load_row<STORAGE, 3 * K>(V.freqs, k, fr);
+    load_row<STORAGE, K>(V.weights, k, wr);
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      const size_t fb = ((size_t)k * K + i) * 3;
-      const float f0 = load_attr<STORAGE>(V.freqs, fb), f1 = load_attr<STORAGE>(V.freqs, fb + 1),
-                  f2 = load_attr<STORAGE>(V.freqs, fb + 2);
+      const float f0 = fr[3 * i], f1 = fr[3 * i + 1], f2 = fr[3 * i + 2];
       const float g0 = W[0] * f0 + W[1] * f1 + W[2] * f2;
       const float g1 = W[3] * f0 + W[4] * f1 + W[5] * f2;
       const float g2 = W[6] * f0 + W[7] * f1 + W[8] * f2;
       const float fpx = g0 * tzfx, fpy = g1 * tzfy, fpz = g2 + b.ux * g0 + b.uy * g1;
       rec[12 + 2 * i] = fpx + r0 * fpz;
       rec[12 + 2 * i + 1] = fpy + r1 * fpz;
-      const float wi = load_attr<STORAGE>(V.weights, (size_t)k * K + i);
+      const float wi = wr[i];
       rec[12 + 2 * K + i] = zatt ? wi * expf(-2.f * PI_SQ * fpz * fpz * sz) : wi;
       wsum += wi;
     }
@@ -683,7 +684,7 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
     }
     float gmean[3] = {0.f, 0.f, 0.f}, gscale[3] = {0.f, 0.f, 0.f}, gquat[4] = {0.f, 0.f, 0.f, 0.f};
     if (G.opacity) G.opacity[k] = g2[5];
-    if (G.means2d) { G.means2d[2 * (size_t)k] = g2[0]; G.means2d[2 * (size_t)k + 1] = g2[1]; }
+    if (G.means2d) store_row<2>(G.means2d, k, g2);
     if (!active) {
       if (G.means) for (int i = 0; i < 3; ++i) G.means[3 * (size_t)k + i] = 0.f;
       if (G.scales) for (int i = 0; i < 3; ++i) G.scales[3 * (size_t)k + i] = 0.f;
@@ -769,10 +770,13 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
       const float sz_raw = zatt ? (w3[0] * Sw[0] + w3[1] * Sw[1] + w3[2] * Sw[2]) - (bv0 * r0 + bv1 * r1) : 0.f;
       const float sz = fmaxf(sz_raw, 0.f);
       float gsz = 0.f;
+      constexpr int KA = K > 0 ? K : 1;   // array extent (the loop is empty for K = 0)
+      float fr[3 * KA], wr[KA], gfr[3 * KA], gwr[KA];
+      load_row<STORAGE, 3 * K>(V.freqs, k, fr);
+      if (zatt) load_row<STORAGE, K>(V.weights, k, wr);
+#pragma unroll
       for (int i = 0; i < K; ++i) {
-        const size_t fb = ((size_t)k * K + i) * 3;
-        const float f0 = load_attr<STORAGE>(V.freqs, fb), f1 = load_attr<STORAGE>(V.freqs, fb + 1),
-                    f2 = load_attr<STORAGE>(V.freqs, fb + 2);
+        const float f0 = fr[3 * i], f1 = fr[3 * i + 1], f2 = fr[3 * i + 2];
         const float g0 = W[0] * f0 + W[1] * f1 + W[2] * f2;
         const float g1 = W[3] * f0 + W[4] * f1 + W[5] * f2;
         const float gg2 = W[6] * f0 + W[7] * f1 + W[8] * f2;
@@ -780,11 +784,10 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
         const float gfx = g2[9 + 2 * i], gfy = g2[9 + 2 * i + 1];
         float gpz = r0 * gfx + r1 * gfy;
         const float Gi = g2[9 + 2 * K + i];
-        const float wi = load_attr<STORAGE>(V.weights, (size_t)k * K + i);
         const float c2 = zatt ? expf(-2.f * PI_SQ * fpz * fpz * sz) : 1.f;
-        if (G.weights) G.weights[(size_t)k * K + i] = c2 * Gi - G0;
+        gwr[i] = c2 * Gi - G0;
         if (zatt) {
-          const float garg = Gi * wi * c2;                 // dL/d(-2 pi^2 fpz^2 sz)
+          const float garg = Gi * wr[i] * c2;              // dL/d(-2 pi^2 fpz^2 sz)
           gpz += garg * (-4.f * PI_SQ * fpz * sz);
           gsz += garg * (-2.f * PI_SQ * fpz * fpz);
         }
@@ -796,12 +799,12 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
         gtz += gfx * g0 / V.fx + gfy * g1 / V.fy;
         gux += gpz * g0;
         guy += gpz * g1;
-        if (G.freqs) {
-          G.freqs[fb] = W[0] * gg0 + W[3] * gg1 + W[6] * ggz;
-          G.freqs[fb + 1] = W[1] * gg0 + W[4] * gg1 + W[7] * ggz;
-          G.freqs[fb + 2] = W[2] * gg0 + W[5] * gg1 + W[8] * ggz;
-        }
+        gfr[3 * i] = W[0] * gg0 + W[3] * gg1 + W[6] * ggz;
+        gfr[3 * i + 1] = W[1] * gg0 + W[4] * gg1 + W[7] * ggz;
+        gfr[3 * i + 2] = W[2] * gg0 + W[5] * gg1 + W[8] * ggz;
       }
+      if (G.freqs) store_row<3 * K>(G.freqs, k, gfr);
+      if (G.weights) store_row<K>(G.weights, k, gwr);
       // r = A^-1 b: gb = A^-1 gr, gA = -gb r^T (A symmetric, off-diagonal counted twice)
       const float u0 = iA00 * gr0 + iA01 * gr1, u1 = iA01 * gr0 + iA11 * gr1;
       gb0 = u0; gb1 = u1;
@@ -924,7 +927,7 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
     }
     if (G.means) for (int i = 0; i < 3; ++i) G.means[3 * (size_t)k + i] = gmean[i];
     if (G.scales) for (int i = 0; i < 3; ++i) G.scales[3 * (size_t)k + i] = gscale[i];
-    if (G.quats) for (int i = 0; i < 4; ++i) G.quats[4 * (size_t)k + i] = gquat[i];
+    if (G.quats) store_row<4>(G.quats, k, gquat);
   }
 }
 
