@@ -90,6 +90,11 @@ __device__ __forceinline__ float filter_bank(const float* r, float w0, float dx,
 #ifndef GS_PPT_BWD
 #define GS_PPT_BWD 2
 #endif
+// Backward per-pair reduction: 1 = transpose through shared memory, 0 = warp reduce-scatter.
+#ifndef GS_BWD_SMEM_REDUCE
+#define GS_BWD_SMEM_REDUCE 1
+#endif
+
 // Warp footprint inside the 16x16 tile: 1 = 8 pixels wide and 4 PPT rows high (two warp columns),
 // 0 = the full tile width and 2 PPT rows high.  A compact footprint means fewer warps overlap a
 // small splat, so fewer warps run the per-pair gradient block and its reduction (8x8 at PPT = 2:
@@ -281,6 +286,10 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
   float4* s_rec = smem4;                                        // [NT][F4]
   float* s_acc = reinterpret_cast<float*>(smem4 + NT * F4);     // [NT][NS]
   u32* s_id = reinterpret_cast<u32*>(s_acc + NT * NS);           // [NT]
+#if GS_BWD_SMEM_REDUCE
+  constexpr int RS = 36;                                         // row stride of the transpose buffer
+  float* s_red = reinterpret_cast<float*>(smem4 + NT * F4) + NT * NS + NT + (threadIdx.x >> 5) * (NV * RS + 4);
+#endif
   __shared__ u32 s_tile;
   __shared__ u32 s_max;
   WsHeader* hdr = p.hdr;
@@ -424,6 +433,28 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
           gv[1] -= gdy;
         }
         if (__ballot_sync(0xffffffffu, contrib)) {
+#if GS_BWD_SMEM_REDUCE
+          // transpose through shared memory: lane l stores value v at row v, column l; lane v
+          // then adds up its row with eight 16-byte loads
+#pragma unroll
+          for (int v = 0; v < NV; ++v) s_red[v * RS + lane] = gv[v];
+          __syncwarp();
+#pragma unroll
+          for (int g = 0; g < NVP / 32; ++g) {
+            const int v = 32 * g + lane;
+            if (v < NV) {
+              const float4* row = reinterpret_cast<const float4*>(s_red + v * RS);
+              float4 a = row[0];
+#pragma unroll
+              for (int c = 1; c < 8; ++c) {
+                const float4 t = row[c];
+                a.x += t.x; a.y += t.y; a.z += t.z; a.w += t.w;
+              }
+              atomicAdd(&s_acc[j * NS + v], (a.x + a.y) + (a.z + a.w));
+            }
+          }
+          __syncwarp();
+#else
 #pragma unroll
           for (int g = 0; g < NVP / 32; ++g) {
             float part[32];
@@ -432,6 +463,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
             const float red = warp_reduce_scatter(part, lane);
             if (32 * g + lane < NV) atomicAdd(&s_acc[j * NS + 32 * g + lane], red);
           }
+#endif
         }
       }
       __syncthreads();
@@ -472,7 +504,8 @@ static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const u3
   constexpr int PPT = GS_PPT_BWD, NT = BLOCK / PPT;
   static int grid = 0;
   const size_t smem = (size_t)NT * SRec<K>::F * sizeof(float) + (size_t)NT * ((10 + 3 * K) | 1) * sizeof(float) +
-                      (size_t)NT * sizeof(u32);
+                      (size_t)NT * sizeof(u32) +
+                      (GS_BWD_SMEM_REDUCE ? (size_t)(NT / 32) * ((10 + 3 * K) * 36 + 4) * sizeof(float) : 0);
   if (!grid) {
     cudaError_t e =
         cudaFuncSetAttribute(k_render_bwd<K, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
