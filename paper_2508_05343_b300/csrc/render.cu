@@ -408,21 +408,22 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
           acc2[q] = alpha * c.z + oma * acc2[q];
           if (araw > amax) dLda = 0.f;                     // clamped: no gradient through alpha
           const float o = h1.z;
-          gv[5] += dLda * G * bank;                        // d opacity
-          const float dLdG = dLda * o * bank;
           const float dLdbank = dLda * o * G;
-          // log2-domain power p2: G = 2^p2, dG/dp2 = G ln 2
-          const float dLdp2 = dLdG * G * 0.6931471805599453f;
-          gv[2] += dLdp2 * dx * dx;                        // w.r.t. A' (converted at flush)
-          gv[3] += dLdp2 * dx * dy;                        // w.r.t. B'
-          gv[4] += dLdp2 * dy * dy;                        // w.r.t. C'
-          float gdx = dLdp2 * (2.f * h0.z * dx + h0.w * dy);
-          float gdy = dLdp2 * (h0.w * dx + 2.f * h1.x * dy);
+          gv[5] += dLda * G * bank;                        // d opacity
+          // log2-domain power p2: G = 2^p2, dG/dp2 = G ln 2, so dL/dp2 = dLda o bank G ln 2
+          const float dLdp2 = dLdbank * bank * 0.6931471805599453f;
+          const float ex = dLdp2 * dx, ey = dLdp2 * dy;
+          gv[2] += ex * dx;                                // w.r.t. A' (converted at flush)
+          gv[3] += ex * dy;                                // w.r.t. B'
+          gv[4] += ey * dy;                                // w.r.t. C'
+          float gdx = 2.f * h0.z * ex + h0.w * ey;
+          float gdy = h0.w * ex + 2.f * h1.x * ey;
+          const float mph = -TWO_PI * dLdbank;
 #pragma unroll
           for (int i = 0; i < K; ++i) {
             const float wi = fw[2 * K + i];
             gv[9 + 2 * K + i] += dLdbank * cs[i];                  // d (cosine weight i)
-            const float gph = -dLdbank * wi * sn[i] * TWO_PI;       // d phase (cycles)
+            const float gph = mph * wi * sn[i];                     // d phase (cycles)
             gv[9 + 2 * i] += gph * dx;
             gv[9 + 2 * i + 1] += gph * dy;
             gdx += gph * fw[2 * i];
