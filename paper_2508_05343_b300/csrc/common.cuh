@@ -27,6 +27,7 @@ constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // keys per onesweep part
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int MAX_PASSES = 8;
+constexpr int CMASK_PLANES = 8;   // warps of a compositing CTA (one pixel per thread at most 8 warps)
 
 // Number of floats of a projected 2D record and of a per-primitive 2D gradient row.
 __host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
@@ -93,7 +94,7 @@ struct WsHeader {
 // Offsets of every region of a workspace (host-computed; all 256-byte aligned).
 struct WsLayout {
   size_t header, table, records, touched, offsets, active, scan_status, keys0, keys1, vals0, vals1, hist,
-      sort_status, ranges, T_final, n_contrib, n_eval, n_reach, n_comp, grad2d, total;
+      sort_status, ranges, cmask, T_final, n_contrib, n_eval, n_reach, n_comp, grad2d, total;
   u32 n_prims, n_tiles, n_chunks, n_parts;
   u64 n_pixels, capacity;
   int K, rec_f, g2d_f;
@@ -115,6 +116,8 @@ struct WsPtrs {
   u32* hist;          // [MAX_PASSES][RADIX]
   u64* sort_status;   // [n_parts][RADIX]
   uint2* ranges;      // [n_tiles]
+  u32* cmask;         // [CMASK_PLANES][cmask_plane] per compositing warp slot: bit (pos & 31) of word
+                      // (pos >> 5) + tile set if a pixel of that warp composited the pair at sorted position pos
   float* T_final;     // [n_pixels]
   u32* n_contrib;     // [n_pixels]
   u32* n_eval;        // [n_pixels] pairs the forward pass evaluated per pixel
@@ -123,6 +126,7 @@ struct WsPtrs {
   float* grad2d;      // [n_prims][g2d_f]
   u64 capacity;
   u32 n_chunks, n_parts;
+  u32 cmask_plane;     // words per plane: capacity / 32 + tiles + 2 (each tile owns whole words)
 };
 
 WsLayout make_layout(u32 n_prims, int K, u32 n_tiles, u64 n_pixels, u64 capacity);

@@ -90,6 +90,7 @@ __device__ __forceinline__ float filter_bank(const float* r, float w0, float dx,
 #ifndef GS_PPT_BWD
 #define GS_PPT_BWD 2
 #endif
+static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-warp composited-pair bits: same warp footprints");
 // Backward per-pair reduction: 1 = transpose through shared memory, 0 = warp reduce-scatter.
 #ifndef GS_BWD_SMEM_REDUCE
 #define GS_BWD_SMEM_REDUCE 1
@@ -164,6 +165,10 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
       done[q] = !(px < V.width && py0 + q < V.height);
       tdone = tdone && done[q];
     }
+    // composited-pair bits of this warp (warp-uniform), one word per 32 sorted positions, for the
+    // backward pass to skip the pairs no pixel of the warp composited
+    u32* cplane = p.cmask + (size_t)(tid >> 5) * p.cmask_plane;
+    u32 cword = 0, cword_idx = 0xffffffffu;
     for (u32 start = rg.x; start < rg.y; start += NT) {
       if (__syncthreads_count(tdone) == NT) break;
       const u32 idx = start + tid;
@@ -174,10 +179,12 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
       }
       __syncthreads();
       const int cnt = (int)min((u32)NT, rg.y - start);
-      for (int j = 0; !tdone && j < cnt; ++j) {
+      for (int j = 0; j < cnt; ++j) {
+        if (!__any_sync(0xffffffffu, !tdone)) break;   // warp-uniform: the ballot below needs every lane
         const float4* r = s_rec + j * F4;
         const float4 h0 = r[0], h1 = r[1];
         const float dx = __fsub_rn(fpx, h0.x);
+        bool comp = false;
         tdone = true;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
@@ -203,14 +210,25 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
                   T[q] = test;
                   last[q] = start + (u32)j + 1u - rg.x;
                   ++composited[q];
+                  comp = true;
                 }
               }
             }
           }
           tdone = tdone && done[q];
         }
+        const u32 b = __ballot_sync(0xffffffffu, comp);
+        const u32 gpos = start + (u32)j;
+        const u32 wi = (gpos >> 5) + tile;             // each tile owns whole words
+        if (wi != cword_idx) {
+          if (cword_idx != 0xffffffffu && (tid & 31) == 0) cplane[cword_idx] = cword;
+          cword_idx = wi;
+          cword = 0;
+        }
+        if (b) cword |= 1u << (gpos & 31);
       }
     }
+    if (cword_idx != 0xffffffffu && (tid & 31) == 0) cplane[cword_idx] = cword;
     float* orgb = out_rgb ? out_rgb : V.out_rgb;
     float* oT = out_rgb ? out_T : V.out_T;
     const size_t hw = (size_t)V.width * V.height;
@@ -361,9 +379,20 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
 #pragma unroll
       for (int i = 0; i < NS; ++i) s_acc[tid * NS + i] = 0.f;
       __syncthreads();
-      for (int j = (int)cnt - 1; j >= 0; --j) {
-        const u32 pos = bstart + (u32)j - rg.x;   // 0-based position in the tile list
-        if (pos >= wlast) continue;                // warp-uniform
+      // back to front over the pairs the forward recorded as composited by a pixel of this warp,
+      // below the warp's last contributor (the words are read uniformly by the warp)
+      const u32* cplane = p.cmask + (size_t)(tid >> 5) * p.cmask_plane;
+      const u32 hi = min(bend, rg.x + wlast);    // sorted positions [bstart, hi)
+      for (int wk = hi > bstart ? (int)((hi - 1) >> 5) : -1; wk >= (int)(bstart >> 5); --wk) {
+        const u32 w0 = (u32)wk << 5;
+        u32 m = cplane[(u32)wk + tile];
+        if (w0 < bstart) m &= ~0u << (bstart - w0);
+        if (hi - w0 < 32u) m &= (1u << (hi - w0)) - 1u;
+        while (m) {
+        const int bit = 31 - __clz(m);
+        m &= ~(1u << bit);
+        const int j = (int)(w0 + (u32)bit - bstart);
+        const u32 pos = w0 + (u32)bit - rg.x;     // 0-based position in the tile list
         const float4* r = s_rec + j * F4;
         const float4 h0 = r[0], h1 = r[1];
         const float* fw = reinterpret_cast<const float*>(r + 3);
@@ -465,6 +494,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
             if (32 * g + lane < NV) atomicAdd(&s_acc[j * NS + 32 * g + lane], red);
           }
 #endif
+        }
         }
       }
       __syncthreads();
