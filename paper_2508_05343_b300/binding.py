@@ -18,6 +18,7 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_
 GS_F32, GS_BF16 = 0, 1
 GS_LOSS_L1, GS_LOSS_L2 = 0, 1
 GS_FLAG_Z_ATTENUATION = 1
+GS_FLAG_FORWARD_ONLY = 2
 GS_TILE, GS_MAX_K, GS_MAX_SH_DEGREE, GS_MAX_VIEWS = 16, 8, 3, 16
 
 

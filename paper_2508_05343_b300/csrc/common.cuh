@@ -304,7 +304,9 @@ int device_sm_count();
 cudaError_t launch_setup(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
 cudaError_t launch_preprocess(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
 cudaError_t launch_bin_sort(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
-cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L);
+// masks: record the composited-pair bits the backward pass reads (off for forward-only rendering)
+cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L,
+                              bool masks);
 cudaError_t launch_render_freq_map(const FrameTable& tbl, const WsPtrs& p, float* out_map, const Launch& L);
 cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL_drgb, const Launch& L);
 cudaError_t launch_preprocess_bwd(const FrameTable& tbl, const WsPtrs& p, const gs_prim_grads& g, const Launch& L);

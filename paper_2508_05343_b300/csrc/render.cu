@@ -127,7 +127,9 @@ __device__ __forceinline__ int2 thread_pixel(int tx, int ty, int tid) {
 
 // FMAP: composite the frequency features of each primitive (sum_i w_i |f2D_i|, sum_i w_i |f2D_i,x|,
 // sum_i w_i |f2D_i,y|, cycles per pixel) in place of its colour, with no background.
-template <int K, int PPT, bool FMAP>
+// MASKS: record per warp which pairs its pixels composited (for the backward pass); forward-only
+// uses (serving, frequency maps) skip it and keep the per-thread early exit.
+template <int K, int PPT, bool FMAP, bool MASKS>
 __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32* vals, float* out_rgb,
                                                             float* out_T) {
   constexpr int NT = BLOCK / PPT;
@@ -169,6 +171,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
     // backward pass to skip the pairs no pixel of the warp composited
     u32* cplane = p.cmask + (size_t)(tid >> 5) * p.cmask_plane;
     u32 cword = 0, cword_idx = 0xffffffffu;
+    const bool masks = MASKS && !(tbl->flags & GS_FLAG_FORWARD_ONLY);   // uniform over the launch
     for (u32 start = rg.x; start < rg.y; start += NT) {
       if (__syncthreads_count(tdone) == NT) break;
       const u32 idx = start + tid;
@@ -180,7 +183,11 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
       __syncthreads();
       const int cnt = (int)min((u32)NT, rg.y - start);
       for (int j = 0; j < cnt; ++j) {
-        if (!__any_sync(0xffffffffu, !tdone)) break;   // warp-uniform: the ballot below needs every lane
+        if (masks) {
+          if (!__any_sync(0xffffffffu, !tdone)) break;   // warp-uniform: the ballot below needs every lane
+        } else if (tdone) {
+          break;
+        }
         const float4* r = s_rec + j * F4;
         const float4 h0 = r[0], h1 = r[1];
         const float dx = __fsub_rn(fpx, h0.x);
@@ -217,18 +224,20 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
           }
           tdone = tdone && done[q];
         }
-        const u32 b = __ballot_sync(0xffffffffu, comp);
-        const u32 gpos = start + (u32)j;
-        const u32 wi = (gpos >> 5) + tile;             // each tile owns whole words
-        if (wi != cword_idx) {
-          if (cword_idx != 0xffffffffu && (tid & 31) == 0) cplane[cword_idx] = cword;
-          cword_idx = wi;
-          cword = 0;
+        if (masks) {
+          const u32 b = __ballot_sync(0xffffffffu, comp);
+          const u32 gpos = start + (u32)j;
+          const u32 wi = (gpos >> 5) + tile;             // each tile owns whole words
+          if (wi != cword_idx) {
+            if (cword_idx != 0xffffffffu && (tid & 31) == 0) cplane[cword_idx] = cword;
+            cword_idx = wi;
+            cword = 0;
+          }
+          if (b) cword |= 1u << (gpos & 31);
         }
-        if (b) cword |= 1u << (gpos & 31);
       }
     }
-    if (cword_idx != 0xffffffffu && (tid & 31) == 0) cplane[cword_idx] = cword;
+    if (masks && cword_idx != 0xffffffffu && (tid & 31) == 0) cplane[cword_idx] = cword;
     float* orgb = out_rgb ? out_rgb : V.out_rgb;
     float* oT = out_rgb ? out_T : V.out_T;
     const size_t hw = (size_t)V.width * V.height;
@@ -312,6 +321,10 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
   __shared__ u32 s_max;
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
+  if (p.tbl->flags & GS_FLAG_FORWARD_ONLY) {   // no composited-pair bits were recorded
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(hdr, GS_ERR_INVALID_ARG);
+    return;
+  }
   const FrameTable* tbl = p.tbl;
   if (!vals) vals = (tbl->npasses_needed & 1) ? p.vals1 : p.vals0;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -506,7 +519,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
   if (tid == 0) release_tile_counter(&hdr->tile_counter_bwd, &hdr->bwd_exits);
 }
 
-template <int K, bool FMAP>
+template <int K, bool FMAP, bool MASKS>
 static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, const u32* vals, float* rgb, float* T,
                                 const Launch& L) {
   constexpr int PPT = GS_PPT_FWD, NT = BLOCK / PPT;
@@ -514,10 +527,10 @@ static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, const u3
   const size_t smem = (size_t)NT * SRec<K>::F * sizeof(float);
   if (!grid) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_render_fwd<K, PPT, FMAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_render_fwd<K, PPT, FMAP, MASKS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<K, PPT, FMAP>, NT, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<K, PPT, FMAP, MASKS>, NT, smem) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     grid = per_sm * L.sm_count;
@@ -525,7 +538,7 @@ static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, const u3
   int g = grid;
   if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
   if (g < 1) g = 1;
-  k_render_fwd<K, PPT, FMAP><<<g, NT, smem, L.stream>>>(p, vals, rgb, T);
+  k_render_fwd<K, PPT, FMAP, MASKS><<<g, NT, smem, L.stream>>>(p, vals, rgb, T);
   return cudaGetLastError();
 }
 
@@ -555,29 +568,31 @@ static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const u3
 }
 
 
-template <bool FMAP>
+template <bool FMAP, bool MASKS>
 static cudaError_t launch_fwd_k(const FrameTable& tbl, const WsPtrs& p, float* out, float* out_T, const Launch& L) {
   const u32* vals = nullptr;   // chosen on the device: the sort's pass count depends on the depth range
   switch (tbl.K) {
-    case 0: return launch_fwd_t<0, FMAP>(tbl, p, vals, out, out_T, L);
-    case 1: return launch_fwd_t<1, FMAP>(tbl, p, vals, out, out_T, L);
-    case 2: return launch_fwd_t<2, FMAP>(tbl, p, vals, out, out_T, L);
-    case 3: return launch_fwd_t<3, FMAP>(tbl, p, vals, out, out_T, L);
-    case 4: return launch_fwd_t<4, FMAP>(tbl, p, vals, out, out_T, L);
-    case 5: return launch_fwd_t<5, FMAP>(tbl, p, vals, out, out_T, L);
-    case 6: return launch_fwd_t<6, FMAP>(tbl, p, vals, out, out_T, L);
-    case 7: return launch_fwd_t<7, FMAP>(tbl, p, vals, out, out_T, L);
-    case 8: return launch_fwd_t<8, FMAP>(tbl, p, vals, out, out_T, L);
+    case 0: return launch_fwd_t<0, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
+    case 1: return launch_fwd_t<1, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
+    case 2: return launch_fwd_t<2, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
+    case 3: return launch_fwd_t<3, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
+    case 4: return launch_fwd_t<4, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
+    case 5: return launch_fwd_t<5, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
+    case 6: return launch_fwd_t<6, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
+    case 7: return launch_fwd_t<7, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
+    case 8: return launch_fwd_t<8, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L) {
-  return launch_fwd_k<false>(tbl, p, out_rgb, out_T, L);
+cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L,
+                              bool masks) {
+  return masks ? launch_fwd_k<false, true>(tbl, p, out_rgb, out_T, L)
+               : launch_fwd_k<false, false>(tbl, p, out_rgb, out_T, L);
 }
 
 cudaError_t launch_render_freq_map(const FrameTable& tbl, const WsPtrs& p, float* out_map, const Launch& L) {
-  return launch_fwd_k<true>(tbl, p, out_map, nullptr, L);
+  return launch_fwd_k<true, false>(tbl, p, out_map, nullptr, L);
 }
 
 cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL, const Launch& L) {

@@ -253,7 +253,7 @@ class PlainRenderer:
         from . import binding as B
         from . import raster
         self.B, self.torch, self.raster = B, torch, raster
-        self.cfg = cfg or B.make_config()
+        self.cfg = cfg or B.make_config(flags=B.GS_FLAG_FORWARD_ONLY)   # rendering only
         self.dev = torch.device(device)
         self.scene_t = [raster.to_device(s, self.dev, B.GS_F32) for s in scenes]
         self.meta = [(s["means"].shape[0], s["weights"].shape[1], int(round(s["sh"].shape[1] ** 0.5)) - 1)

@@ -154,6 +154,20 @@ def test_config1_gradients_vs_oracle_analytic():
     assert not bad, f"gradient rel-L2 above {GRAD_TOL}: {bad} (all: {errs})"
 
 
+def test_forward_only_frames_render_the_same_and_refuse_a_backward():
+    from paper_2508_05343_b300 import binding as B
+    prims, cam = scenes.config_scene(0), scenes.config_cameras(0)[0]
+    oc, gc = cfg_pair()
+    _, _, img, _ = gpu_render(prims, cam, gc)
+    fo = B.make_config(eps2d=oc["eps2d"], alpha_max=oc["alpha_max"], alpha_min=oc["alpha_min"], T_min=oc["T_min"],
+                       bg=oc["bg"], flags=B.GS_FLAG_FORWARD_ONLY)
+    r, _, img_fo, _ = gpu_render(prims, cam, fo)
+    assert torch.equal(img, img_fo)
+    B.gabsplat_render_bwd_2d(r.frame, torch.zeros_like(img))
+    st, _ = r.status()
+    assert st == B.GS_ERR_INVALID_ARG
+
+
 def _variant_scene():
     spec = scenes.SceneSpec(n=1500, K=3, sh_degree=2, layout="uniform", box=1.0, log_scale=(-3.0, 0.5))
     p = scenes.make_scene(spec, 61)
