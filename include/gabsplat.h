@@ -98,13 +98,8 @@ typedef struct {
  * GS_FLAG_Z_ATTENUATION: the variant that keeps the z-integration constant C2 of supplement A.2,
  * so the 2D filter bank is (1 - sum w_i) + sum w_i C2_i cos(2 pi f2D_i . d) with
  * C2_i = exp(-2 pi^2 f_proj,z,i^2 / S_22), S the inverse of the ray-space covariance J W Sigma
- * W^T J^T (undilated).
- * GS_FLAG_FORWARD_ONLY: the frame will not be differentiated.  gabsplat_render_fwd then skips
- * recording, per warp of 64 pixels, which pairs its pixels composited (the bits the backward pass
- * walks); gabsplat_render_bwd_2d on such a frame sets GS_ERR_INVALID_ARG in the device status.
- * Other bits are rejected. */
+ * W^T J^T (undilated).  Other bits are rejected. */
 #define GS_FLAG_Z_ATTENUATION 1u
-#define GS_FLAG_FORWARD_ONLY 2u
 typedef struct {
   float eps2d, alpha_max, alpha_min, T_min;
   float bg[3];
@@ -203,6 +198,13 @@ gs_status gabsplat_bin_sort(const gs_frame* frame, gs_stream stream);
  * out_rgb [3][H][W] (device, required) and out_T [H][W] (device, may be NULL).  Keeps the final
  * transmittance and the last contributor per pixel in the workspace for the backward pass. */
 gs_status gabsplat_render_fwd(const gs_frame* frame, float* out_rgb, float* out_T, gs_stream stream);
+
+/* Stage 3 for frames that will not be differentiated (rendering only): the same images and
+ * per-pixel state as gabsplat_render_fwd, without recording, per warp of 64 pixels, which pairs
+ * its pixels composited (the bits the backward pass walks), which makes it faster.
+ * gabsplat_render_bwd_2d after it (with no gabsplat_render_fwd of the same frame) sets
+ * GS_ERR_INVALID_ARG in the device status. */
+gs_status gabsplat_render_fwd_only(const gs_frame* frame, float* out_rgb, float* out_T, gs_stream stream);
 
 /* Frequency maps (the visualisation of Sec. 4: the weighted Gabor frequencies of the primitives
  * blended into the image): the compositing of stage 3 with each primitive's colour replaced by

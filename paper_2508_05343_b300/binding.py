@@ -18,7 +18,6 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_
 GS_F32, GS_BF16 = 0, 1
 GS_LOSS_L1, GS_LOSS_L2 = 0, 1
 GS_FLAG_Z_ATTENUATION = 1
-GS_FLAG_FORWARD_ONLY = 2
 GS_TILE, GS_MAX_K, GS_MAX_SH_DEGREE, GS_MAX_VIEWS = 16, 8, 3, 16
 
 
@@ -83,6 +82,7 @@ SIGNATURES = {
     "gabsplat_bin_sort": (C.c_int, [P_(gs_frame), C.c_void_p]),
     "gabsplat_render_fwd": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p, C.c_void_p]),
     "gabsplat_render_freq_map": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p]),
+    "gabsplat_render_fwd_only": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p, C.c_void_p]),
     "gabsplat_densify_accumulate": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gabsplat_densify_scratch_bytes": (C.c_size_t, [C.c_int]),
     "gabsplat_densify": (C.c_int, [P_(gs_prims), C.c_void_p, C.c_void_p, C.c_void_p, P_(gs_densify_config),
@@ -170,6 +170,11 @@ def gabsplat_bin_sort(frame, stream=None):
 
 def gabsplat_render_fwd(frame, out_rgb, out_T=None, stream=None):
     _check("gabsplat_render_fwd", lib.gabsplat_render_fwd(C.byref(frame), _ptr(out_rgb), _ptr(out_T), _stream(stream)))
+
+
+def gabsplat_render_fwd_only(frame, out_rgb, out_T=None, stream=None):
+    _check("gabsplat_render_fwd_only", lib.gabsplat_render_fwd_only(C.byref(frame), _ptr(out_rgb), _ptr(out_T),
+                                                                    _stream(stream)))
 
 
 def gabsplat_render_freq_map(frame, out_map, stream=None):

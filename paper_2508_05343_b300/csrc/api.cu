@@ -182,7 +182,7 @@ gs_status gabsplat_preprocess(const gs_frame* frame, const gs_prims* pr, const g
   if (reinterpret_cast<uintptr_t>(pr->quats) & 15) return GS_ERR_INVALID_ARG;
   if (!(cam->fx > 0.f) || !(cam->fy > 0.f) || !(cam->znear > 0.f) || !(cam->zfar > cam->znear))
     return GS_ERR_INVALID_ARG;
-  if ((cfg->flags & ~(unsigned)(GS_FLAG_Z_ATTENUATION | GS_FLAG_FORWARD_ONLY)) != 0 || !(cfg->eps2d >= 0.f) || !(cfg->alpha_max > 0.f) || !(cfg->alpha_max < 1.f) ||
+  if ((cfg->flags & ~(unsigned)GS_FLAG_Z_ATTENUATION) != 0 || !(cfg->eps2d >= 0.f) || !(cfg->alpha_max > 0.f) || !(cfg->alpha_max < 1.f) ||
       !(cfg->alpha_min > 0.f) || !(cfg->T_min > 0.f))
     return GS_ERR_INVALID_ARG;
   t.storage = pr->storage;
@@ -230,6 +230,15 @@ gs_status gabsplat_render_fwd(const gs_frame* frame, float* out_rgb, float* out_
   if (s != GS_OK) return s;
   if (!out_rgb) return GS_ERR_INVALID_ARG;
   return from_cuda(launch_render_fwd(t, make_ptrs(L, frame->ws), out_rgb, out_T, make_launch(stream), true));
+}
+
+gs_status gabsplat_render_fwd_only(const gs_frame* frame, float* out_rgb, float* out_T, gs_stream stream) {
+  FrameTable t;
+  WsLayout L;
+  const gs_status s = frame_meta(frame, t, L);
+  if (s != GS_OK) return s;
+  if (!out_rgb) return GS_ERR_INVALID_ARG;
+  return from_cuda(launch_render_fwd(t, make_ptrs(L, frame->ws), out_rgb, out_T, make_launch(stream), false));
 }
 
 gs_status gabsplat_render_freq_map(const gs_frame* frame, float* out_map, gs_stream stream) {

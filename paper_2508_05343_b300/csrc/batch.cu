@@ -42,7 +42,7 @@ WsLayout batch_layout(const gs_batch_frame* f) {
 gs_status build_batch_table(const gs_batch_frame* f, const gs_view* views, int nviews, const gs_config* cfg,
                             FrameTable& t) {
   if (nviews < 0 || nviews > f->max_views || (nviews > 0 && !views) || !cfg) return GS_ERR_INVALID_ARG;
-  if ((cfg->flags & ~(unsigned)(GS_FLAG_Z_ATTENUATION | GS_FLAG_FORWARD_ONLY)) != 0 || !(cfg->eps2d >= 0.f) || !(cfg->alpha_max > 0.f) || !(cfg->alpha_max < 1.f) ||
+  if ((cfg->flags & ~(unsigned)GS_FLAG_Z_ATTENUATION) != 0 || !(cfg->eps2d >= 0.f) || !(cfg->alpha_max > 0.f) || !(cfg->alpha_max < 1.f) ||
       !(cfg->alpha_min > 0.f) || !(cfg->T_min > 0.f))
     return GS_ERR_INVALID_ARG;
   memset(&t, 0, sizeof(t));

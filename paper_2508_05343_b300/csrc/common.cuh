@@ -88,7 +88,8 @@ struct WsHeader {
   u32 sorted_buf;           // 0: sorted pairs in keys0/vals0, 1: in keys1/vals1
   u32 n_active;             // primitives that touch at least one tile (entries of the active list)
   u32 fwd_exits, bwd_exits; // CTAs of the current compositing launch that have finished
-  u32 pad[11];
+  u32 masks_epoch;          // epoch of the last forward that recorded the composited-pair bits
+  u32 pad[10];
 };
 
 // Offsets of every region of a workspace (host-computed; all 256-byte aligned).

@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
   __shared__ u32 s_tile;
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
+  if (MASKS && blockIdx.x == 0 && threadIdx.x == 0) hdr->masks_epoch = hdr->epoch;   // bits of this frame
   const FrameTable* tbl = p.tbl;
   if (!vals) vals = (tbl->npasses_needed & 1) ? p.vals1 : p.vals0;
   const int tid = threadIdx.x;
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
     // backward pass to skip the pairs no pixel of the warp composited
     u32* cplane = p.cmask + (size_t)(tid >> 5) * p.cmask_plane;
     u32 cword = 0, cword_idx = 0xffffffffu;
-    const bool masks = MASKS && !(tbl->flags & GS_FLAG_FORWARD_ONLY);   // uniform over the launch
+    constexpr bool masks = MASKS;
     for (u32 start = rg.x; start < rg.y; start += NT) {
       if (__syncthreads_count(tdone) == NT) break;
       const u32 idx = start + tid;
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
   __shared__ u32 s_max;
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
-  if (p.tbl->flags & GS_FLAG_FORWARD_ONLY) {   // no composited-pair bits were recorded
+  if (hdr->masks_epoch != hdr->epoch) {   // no forward of this frame recorded the composited-pair bits
     if (blockIdx.x == 0 && threadIdx.x == 0) set_status(hdr, GS_ERR_INVALID_ARG);
     return;
   }

@@ -48,9 +48,10 @@ class Rasterizer:
 
     # ---- stages -------------------------------------------------------------------------
     def forward(self, prims_t: dict, camera: dict, cfg: B.gs_config, storage=B.GS_F32, out_rgb=None, out_T=None,
-                auto_capacity=True):
+                auto_capacity=True, forward_only=False):
         """preprocess -> bin_sort -> render_fwd.  With auto_capacity the pair count is read back once
-        (a host synchronisation) and the workspace regrown if it overflowed."""
+        (a host synchronisation) and the workspace regrown if it overflowed.  forward_only renders
+        without the state a backward pass needs (gabsplat_render_fwd_only)."""
         self._prims = B.make_prims(prims_t, storage)
         self.storage = storage
         self.frame.storage = storage        # the frame carries the storage type to every stage
@@ -62,7 +63,7 @@ class Rasterizer:
         for _ in range(2):
             B.gabsplat_preprocess(self.frame, self._prims, self._cam, cfg)
             B.gabsplat_bin_sort(self.frame)
-            B.gabsplat_render_fwd(self.frame, out_rgb, out_T)
+            (B.gabsplat_render_fwd_only if forward_only else B.gabsplat_render_fwd)(self.frame, out_rgb, out_T)
             if not auto_capacity:
                 break
             st, pairs = B.gabsplat_device_status(self.frame)

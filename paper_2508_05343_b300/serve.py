@@ -253,7 +253,7 @@ class PlainRenderer:
         from . import binding as B
         from . import raster
         self.B, self.torch, self.raster = B, torch, raster
-        self.cfg = cfg or B.make_config(flags=B.GS_FLAG_FORWARD_ONLY)   # rendering only
+        self.cfg = cfg or B.make_config()
         self.dev = torch.device(device)
         self.scene_t = [raster.to_device(s, self.dev, B.GS_F32) for s in scenes]
         self.meta = [(s["means"].shape[0], s["weights"].shape[1], int(round(s["sh"].shape[1] ** 0.5)) - 1)
@@ -288,7 +288,7 @@ class PlainRenderer:
             rast = self._rast(r.scene, r.width, r.height)
             out = torch.empty(3, r.height, r.width, device=self.dev)
             rast.forward(self.scene_t[r.scene], S.orbit_camera(r.width, r.height, r.azimuth, r.elevation), self.cfg,
-                         out_rgb=out, auto_capacity=True)          # reads the status: one request at a time
+                         out_rgb=out, auto_capacity=True, forward_only=True)   # reads the status each request
             done_t[r.rid] = time.perf_counter() - t0
             if keep_images:
                 images[r.rid] = out

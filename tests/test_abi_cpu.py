@@ -81,7 +81,7 @@ def test_invalid_arguments_rejected_on_host(B):
     assert lib.gabsplat_preprocess(C.byref(f), C.byref(pr), C.byref(cam), C.byref(cfg), None) == B.GS_ERR_INVALID_ARG
     cam.fx = cam.fy = 50.0
     cam.znear, cam.zfar = 0.2, 100.0
-    cfg.flags = 4                           # unknown flag (bits 0-1 are defined)
+    cfg.flags = 2                           # unknown flag (bit 0 is the z-attenuation variant)
     assert lib.gabsplat_preprocess(C.byref(f), C.byref(pr), C.byref(cam), C.byref(cfg), None) == B.GS_ERR_INVALID_ARG
     img = C.c_void_p(0x100000)
     assert lib.gabsplat_loss(img, img, 0, 0, img, img, img, None) == B.GS_ERR_INVALID_ARG

@@ -154,14 +154,18 @@ def test_config1_gradients_vs_oracle_analytic():
     assert not bad, f"gradient rel-L2 above {GRAD_TOL}: {bad} (all: {errs})"
 
 
-def test_forward_only_frames_render_the_same_and_refuse_a_backward():
+def test_forward_only_render_matches_and_refuses_a_backward():
+    """gabsplat_render_fwd_only gives the image of gabsplat_render_fwd; a backward of a frame whose
+    only forward was forward-only reports an invalid argument instead of reading stale state."""
     from paper_2508_05343_b300 import binding as B
+    from paper_2508_05343_b300 import raster
     prims, cam = scenes.config_scene(0), scenes.config_cameras(0)[0]
     oc, gc = cfg_pair()
     _, _, img, _ = gpu_render(prims, cam, gc)
-    fo = B.make_config(eps2d=oc["eps2d"], alpha_max=oc["alpha_max"], alpha_min=oc["alpha_min"], T_min=oc["T_min"],
-                       bg=oc["bg"], flags=B.GS_FLAG_FORWARD_ONLY)
-    r, _, img_fo, _ = gpu_render(prims, cam, fo)
+    n, K = prims["means"].shape[0], prims["weights"].shape[1]
+    r = raster.Rasterizer(n, K, 0, cam["width"], cam["height"])
+    img_fo = r.forward(raster.to_device(prims), cam, gc, forward_only=True)
+    torch.cuda.synchronize()
     assert torch.equal(img, img_fo)
     B.gabsplat_render_bwd_2d(r.frame, torch.zeros_like(img))
     st, _ = r.status()
