@@ -475,12 +475,7 @@ def run_ours(args):
         achieved, peak, unit = amount / sec / 1e9, hbm_peak, "GB/s"
     else:
         achieved, peak, unit = amount / sec / 1e12, alu_peak, "TFLOP/s"
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tf):
-        rec = json.load(open(tf)).get(top)
-        if rec and rec.get("source_sha") == _kernel_source_sha():
-            traffic = rec.get("dram_bytes_per_launch")
+    traffic = _measured_traffic(top, W, H, n)
     roofline = {"kernel": top, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": unit,
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if bound == "hbm" else
@@ -592,14 +587,34 @@ def _pci_id(props):
         return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
 
 
-def _kernel_source_sha():
+KERNEL_SOURCES = {"preprocess": "preprocess.cu", "bin_sort": "sort.cu", "render_fwd": "render.cu",
+                  "loss": "loss.cu", "render_bwd": "render.cu", "preprocess_bwd": "preprocess.cu"}
+
+
+def kernel_source_sha(stage):
+    """Hash of the sources that define a stage's kernels: its .cu file, common.cuh and the header."""
     import hashlib
     h = hashlib.sha1()
-    d = os.path.join(ROOT, "paper_2508_05343_b300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in (os.path.join(ROOT, "paper_2508_05343_b300", "csrc", KERNEL_SOURCES[stage]),
+              os.path.join(ROOT, "paper_2508_05343_b300", "csrc", "common.cuh"),
+              os.path.join(ROOT, "include", "gabsplat.h")):
+        h.update(open(f, "rb").read())
     return h.hexdigest()[:12]
+
+
+def _measured_traffic(stage, W, H, n):
+    """DRAM bytes per launch of a stage's kernel from the ncu summary in profiles/ (lines
+    `stage source_sha width height n bytes`), if it was taken on these kernel sources and this
+    workload; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_train_iter.txt")
+    if not os.path.exists(path):
+        return None
+    sha = kernel_source_sha(stage)
+    for line in open(path):
+        f = line.split()
+        if len(f) == 6 and f[0] == stage and f[1] == sha and (int(f[2]), int(f[3]), int(f[4])) == (W, H, n):
+            return int(f[5])
+    return None
 
 
 def main():
