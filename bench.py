@@ -611,6 +611,8 @@ def _measured_traffic(stage, W, H, n):
         return None
     sha = kernel_source_sha(stage)
     for line in open(path):
+        if line.startswith("#"):
+            continue
         f = line.split()
         if len(f) == 6 and f[0] == stage and f[1] == sha and (int(f[2]), int(f[3]), int(f[4])) == (W, H, n):
             return int(f[5])
