@@ -356,13 +356,13 @@ def run_ours(args):
         setattr(g_s, k, t.data_ptr() if t.numel() else None)
     vv = rast.views()
     tbits = max(0, math.ceil(math.log2(max(1, vv["tiles_x"] * vv["tiles_y"]))))
-    npasses = math.ceil((32 + tbits) / 8)                    # launched
+    tpasses = math.ceil(tbits / 8)                           # tile-sort passes (launched = needed)
     zb = lambda z: int(np.float32(z).view(np.uint32))
     dbits = max(1, (zb(cams[0]["zfar"]) - zb(cams[0]["znear"])).bit_length())
-    npasses_needed = min(npasses, math.ceil((dbits + tbits) / 8))   # passes that do work
-    # my kernels per step: setup, bin + scan + emit + records, histogram + passes + ranges, render_fwd,
-    # loss (2), render_bwd, zero-fill + preprocess_bwd
-    launches_per_step = 1 + 4 + (1 + npasses + 1) + 1 + 2 + 1 + 2
+    dpasses = min(4, math.ceil(dbits / 8))                   # depth-sort passes that do work (4 launched)
+    # my kernels per step: setup; bin, active scan, 4 depth passes, rank scan, emit, records; tile
+    # histogram + tile passes + ranges; render_fwd; loss (2); render_bwd; zero-fill + preprocess_bwd
+    launches_per_step = 1 + 9 + (1 + tpasses + 1) + 1 + 2 + 1 + 2
     stage_names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd"]
 
     def pose_of(s):
@@ -459,9 +459,13 @@ def run_ours(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
     work = {
-        # all primitives: mean/scale/quat read, counts written; active ones: attributes read, record written
-        "preprocess": ("hbm", n * (40 + 8) + n_act * (4 + param_b + rec_b) + P * 12),
-        "bin_sort": ("hbm", P * (8 + npasses_needed * 24 + 8)),
+        # all primitives: mean/scale/quat read, counts written and scanned; active ones: depth key
+        # written, compacted (16) and depth-sorted (16 per pass), rank scan (key, count, order,
+        # offset: 20), order and offset read by emission and records (12), attributes read and
+        # record written; one 8-byte pair written per kept tile
+        "preprocess": ("hbm", n * (40 + 8) + n_act * (8 + 16 + 16 * dpasses + 20 + 12 + param_b + rec_b) + P * 8),
+        # tile histogram read, each tile pass reads and writes 8-byte pairs, ranges read
+        "bin_sort": ("hbm", P * (8 + tpasses * 16 + 8)),
         "render_fwd": ("alu", n_eval * ops_walk + n_reach * ops_reach + n_comp * ops_comp),
         "loss": ("hbm", img.numel() * 12) if args.loss == "l1" else ("alu", img.numel() * SSIM_FLOPS_PER_VALUE),
         "render_bwd": ("alu", n_contrib * ops_walk + n_comp * ops_bwd),

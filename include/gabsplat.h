@@ -107,7 +107,7 @@ typedef struct {
 } gs_config;
 
 /* Sizes of one frame and the caller-owned device workspace that holds its state between the
- * calls (projected records, key/value pairs, tile ranges, per-pixel transmittance and last
+ * calls (projected records, (tile, depth rank) pairs, tile ranges, per-pixel transmittance and last
  * contributor).  One frame = one view of one scene.  The same frame description and
  * workspace must be passed to every stage of that frame; the stages of two frames that share
  * a workspace must not overlap on the device. */
@@ -134,16 +134,22 @@ typedef struct {
 } gs_prim_grads;
 
 /* Device pointers into a workspace, for inspection and tests (valid after the stage that
- * writes them).  records: [n][record_floats] projected 2D primitives laid out as
+ * writes them).  Primitives that reach at least one tile are "active"; they are numbered by depth
+ * rank r = 0 .. n_active - 1 (camera depth ascending, ties by primitive index), and order[r] is the
+ * primitive of rank r.  records: [n_active][record_floats], row r for the primitive of rank r, the
+ * projected 2D primitive laid out as
  *   {mu_x, mu_y, conic_a, conic_b, conic_c, opacity, 1 - sum w, depth, r, g, b, 0,
  *    f2D_0x, f2D_0y, ..., f2D_(K-1)y, w_0 .. w_(K-1), 0 padding to a multiple of 4}
  * where the 2D Gaussian is exp(-(a dx^2 + c dy^2)/2 - b dx dy).
- * touched/offsets [n] uint32; keys [pairs] uint64 = tile << 32 | float bits of depth;
- * values [pairs] uint32 primitive index; ranges [tiles][2] uint32 [start, end);
+ * touched [n] uint32 kept tiles per primitive (by primitive index); offsets [n_active] uint32 first
+ * pair position of each rank; keys [pairs] uint64 = tile << 32 | depth rank (sorted: by tile, then
+ * rank, so each tile's pairs are in depth order; unsorted: emission order); ranges [tiles][2] uint32
+ * [start, end);
  * T_final [H][W] float32; n_contrib [H][W] uint32 (1-based position in the tile's list of
  * the last composited pair); n_eval [H][W] uint32 pairs the forward pass evaluated at the pixel
  * (its tile's list length, or up to the pair that ended compositing); n_reach [H][W] uint32 of those,
- * pairs whose envelope passed o G >= alpha_min; n_comp [H][W] uint32 pairs composited; grad2d [n][grad2d_floats] float32
+ * pairs whose envelope passed o G >= alpha_min; n_comp [H][W] uint32 pairs composited; grad2d
+ * [n_active][grad2d_floats] float32 by depth rank
  *   {d mu_x, d mu_y, d a, d b, d c, d opacity, d r, d g, d b, d f2D (2K), d (cosine weight) (K),
  *    d (1 - sum w), 0 pad}: the filter bank (1 - sum w) + sum w'_i cos(.) is differentiated in its
  *    two weight terms separately (w' = w, or w C2 in the z-attenuation variant, whose records hold
@@ -152,10 +158,10 @@ typedef struct {
   float* records;
   unsigned* touched;
   unsigned* offsets;
+  unsigned* order;
+  unsigned n_active;
   unsigned long long* keys_sorted;
-  unsigned* values_sorted;
   unsigned long long* keys_unsorted;
-  unsigned* values_unsorted;
   unsigned* ranges;
   float* T_final;
   unsigned* n_contrib;
@@ -185,12 +191,14 @@ gs_status gabsplat_workspace_init(const gs_frame* frame, gs_stream stream);
 gs_status gabsplat_preprocess(const gs_frame* frame, const gs_prims* prims, const gs_camera* cam,
                               const gs_config* cfg, gs_stream stream);
 
-/* Stage 2, tile binning and depth sort (Sec. 3.1, "sorted by depth"; Sec. 3.3.3): exclusive
- * scan of the touched-tile counts, emission of one (tile << 32 | depth bits, primitive) pair per
- * touched tile, a stable least-significant-digit radix sort of the pairs, and per-tile
- * [start, end) ranges.  The pair count stays on the device.  GS_ERR_CAPACITY (device status)
- * if it exceeds frame->pair_capacity; gabsplat_device_status() then reports the needed count.
- * (The scan and the emission run inside the preprocess launch; this call sorts and ranges.) */
+/* Stage 2, tile binning and depth sort (Sec. 3.1, "sorted by depth"; Sec. 3.3.3).  Inside the
+ * preprocess call: the active primitives are sorted by camera depth (a stable radix sort of their
+ * depth keys, so equal depths keep primitive order), the kept-tile counts are scanned in that
+ * order, and one (tile << 32 | depth rank) pair is emitted per kept tile, in rank order.  This
+ * call sorts the pairs by tile with a stable least-significant-digit radix sort of the tile bits,
+ * which leaves each tile's pairs in (depth, primitive) order, and writes per-tile [start, end)
+ * ranges.  The pair count stays on the device.  GS_ERR_CAPACITY (device status) if it exceeds
+ * frame->pair_capacity; gabsplat_device_status() then reports the needed count. */
 gs_status gabsplat_bin_sort(const gs_frame* frame, gs_stream stream);
 
 /* Stage 3, front-to-back alpha compositing of the 2D Gabor primitives (Sec. 3.3.2 Eq. 9 and

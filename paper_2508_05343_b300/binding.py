@@ -58,8 +58,8 @@ class gs_prim_arrays(C.Structure):
 
 class gs_ws_views(C.Structure):
     _fields_ = [("records", C.c_void_p), ("touched", C.c_void_p), ("offsets", C.c_void_p),
-                ("keys_sorted", C.c_void_p), ("values_sorted", C.c_void_p), ("keys_unsorted", C.c_void_p),
-                ("values_unsorted", C.c_void_p), ("ranges", C.c_void_p), ("T_final", C.c_void_p),
+                ("order", C.c_void_p), ("n_active", C.c_uint), ("keys_sorted", C.c_void_p),
+                ("keys_unsorted", C.c_void_p), ("ranges", C.c_void_p), ("T_final", C.c_void_p),
                 ("n_contrib", C.c_void_p), ("n_eval", C.c_void_p), ("n_reach", C.c_void_p), ("n_comp", C.c_void_p), ("grad2d", C.c_void_p), ("record_floats", C.c_int),
                 ("grad2d_floats", C.c_int), ("tiles_x", C.c_int), ("tiles_y", C.c_int)]
 

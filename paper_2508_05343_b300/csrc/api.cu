@@ -25,18 +25,22 @@ WsLayout make_layout(u32 n_prims, int K, u32 n_tiles, u64 n_pixels, u64 capacity
   L.rec_f = rec_floats(K);
   L.g2d_f = g2d_floats(K);
   L.n_chunks = (n_prims + CHUNK - 1) / CHUNK;
-  L.n_parts = (u32)((capacity + SORT_TILE - 1) / SORT_TILE);
+  const u64 sort_items = capacity > n_prims ? capacity : n_prims;   // pairs, or active primitives
+  L.n_parts = (u32)((sort_items + SORT_TILE - 1) / SORT_TILE);
   L.header = take(sizeof(WsHeader));
   L.table = take(sizeof(FrameTable));
   L.records = take((size_t)n_prims * L.rec_f * sizeof(float));
   L.touched = take((size_t)n_prims * 4);
   L.offsets = take((size_t)n_prims * 4);
+  L.order = take((size_t)n_prims * 4);
   L.active = take((size_t)n_prims * 4);
+  L.rank_of = take((size_t)n_prims * 4);
+  L.dkeys0 = take((size_t)n_prims * 8);
+  L.dkeys1 = take((size_t)n_prims * 8);
   L.scan_status = take((size_t)(L.n_chunks ? L.n_chunks : 1) * 8);
+  L.rank_status = take((size_t)(L.n_chunks ? L.n_chunks : 1) * 8);
   L.keys0 = take((size_t)capacity * 8);
   L.keys1 = take((size_t)capacity * 8);
-  L.vals0 = take((size_t)capacity * 4);
-  L.vals1 = take((size_t)capacity * 4);
   L.hist = take((size_t)MAX_PASSES * RADIX * 4);
   L.sort_status = take((size_t)(L.n_parts ? L.n_parts : 1) * RADIX * 8);
   L.ranges = take((size_t)n_tiles * 8);
@@ -59,12 +63,15 @@ WsPtrs make_ptrs(const WsLayout& L, void* ws) {
   p.records = reinterpret_cast<float*>(b + L.records);
   p.touched = reinterpret_cast<u32*>(b + L.touched);
   p.offsets = reinterpret_cast<u32*>(b + L.offsets);
+  p.order = reinterpret_cast<u32*>(b + L.order);
   p.active = reinterpret_cast<u32*>(b + L.active);
+  p.rank_of = reinterpret_cast<u32*>(b + L.rank_of);
+  p.dkeys0 = reinterpret_cast<u64*>(b + L.dkeys0);
+  p.dkeys1 = reinterpret_cast<u64*>(b + L.dkeys1);
   p.scan_status = reinterpret_cast<u64*>(b + L.scan_status);
+  p.rank_status = reinterpret_cast<u64*>(b + L.rank_status);
   p.keys0 = reinterpret_cast<u64*>(b + L.keys0);
   p.keys1 = reinterpret_cast<u64*>(b + L.keys1);
-  p.vals0 = reinterpret_cast<u32*>(b + L.vals0);
-  p.vals1 = reinterpret_cast<u32*>(b + L.vals1);
   p.hist = reinterpret_cast<u32*>(b + L.hist);
   p.sort_status = reinterpret_cast<u64*>(b + L.sort_status);
   p.ranges = reinterpret_cast<uint2*>(b + L.ranges);
@@ -96,10 +103,11 @@ int tile_bits(u32 ntiles) {
   while (b < 32 && ((u64)1 << b) < (u64)ntiles) ++b;
   return b;
 }
-int sort_passes(u32 ntiles) { return (32 + tile_bits(ntiles) + RADIX_BITS - 1) / RADIX_BITS; }
+int tile_passes(u32 ntiles) { return (tile_bits(ntiles) + RADIX_BITS - 1) / RADIX_BITS; }
 
 // Depth keys of culled-in primitives lie in (bits(znear), bits(zfar)]: positive floats order like their
-// bit patterns, so subtracting bits(znear) leaves a value below 2^depth_bits.
+// bit patterns, so subtracting bits(znear) leaves a value below 2^depth_bits, and the depth sort needs
+// ceil(depth_bits / 8) digit passes.  The tile sort needs ceil(tile bits / 8) (none for one tile).
 void set_depth_window(FrameTable& t, float znear_min, float zfar_max) {
   u32 lo, hi;
   memcpy(&lo, &znear_min, 4);
@@ -108,8 +116,10 @@ void set_depth_window(FrameTable& t, float znear_min, float zfar_max) {
   while (db < 32 && ((u64)(hi - lo) >> db) != 0) ++db;
   t.depth_base = lo;
   t.depth_bits = db;
-  t.npasses_needed = (db + tile_bits(t.total_tiles) + RADIX_BITS - 1) / RADIX_BITS;
-  if (t.npasses_needed > t.npasses) t.npasses_needed = t.npasses;
+  t.dpasses_needed = (db + RADIX_BITS - 1) / RADIX_BITS;
+  if (t.dpasses_needed > DPASSES) t.dpasses_needed = DPASSES;
+  t.tpasses_needed = tile_passes(t.total_tiles);
+  if (t.tpasses_needed > t.tpasses) t.tpasses_needed = t.tpasses;
 }
 
 static bool frame_sizes_ok(int n, int K, int sh_degree, int width, int height, u64 cap) {
@@ -132,7 +142,7 @@ static gs_status frame_meta(const gs_frame* f, FrameTable& t, WsLayout& L) {
   t.total_prims = (u32)f->n;
   t.total_tiles = (u32)(tx * ty);
   t.total_pixels = (u64)f->width * f->height;
-  t.npasses = sort_passes(t.total_tiles);
+  t.tpasses = tile_passes(t.total_tiles);
   t.launch_prims = t.total_prims;
   t.launch_tiles = t.total_tiles;
   t.v[0].n = f->n;
@@ -356,10 +366,10 @@ gs_status gabsplat_workspace_views(const gs_frame* frame, gs_ws_views* out) {
   out->records = p.records;
   out->touched = p.touched;
   out->offsets = p.offsets;
+  out->order = p.order;
+  out->n_active = h.n_active;
   out->keys_sorted = odd ? p.keys1 : p.keys0;
-  out->values_sorted = odd ? p.vals1 : p.vals0;
   out->keys_unsorted = p.keys0;     // valid between gabsplat_preprocess and gabsplat_bin_sort
-  out->values_unsorted = p.vals0;
   out->ranges = reinterpret_cast<unsigned*>(p.ranges);
   out->T_final = p.T_final;
   out->n_contrib = p.n_contrib;

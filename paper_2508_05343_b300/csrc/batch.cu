@@ -56,7 +56,7 @@ gs_status build_batch_table(const gs_batch_frame* f, const gs_view* views, int n
   t.T_min = cfg->T_min;
   t.flags = cfg->flags;
   for (int i = 0; i < 3; ++i) t.bg[i] = cfg->bg[i];
-  t.npasses = sort_passes((u32)f->max_tiles);   // fixed per workspace, so graph replays agree
+  t.tpasses = tile_passes((u32)f->max_tiles);   // fixed per workspace, so graph replays agree
   t.launch_prims = (u32)f->max_prims;
   t.launch_tiles = (u32)f->max_tiles;
   u64 prims = 0, tiles = 0, pixels = 0;

@@ -26,7 +26,8 @@ constexpr int SORT_ITEMS = GS_SORT_ITEMS;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // keys per onesweep partition
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
-constexpr int MAX_PASSES = 8;
+constexpr int DPASSES = 4;     // depth-sort passes launched (depth keys have at most 32 bits)
+constexpr int MAX_PASSES = 8;  // digit-pass slots: 0..3 depth sort, 4..7 tile sort
 constexpr int CMASK_PLANES = 8;   // warps of a compositing CTA (one pixel per thread at most 8 warps)
 
 // Number of floats of a projected 2D record and of a per-primitive 2D gradient row.
@@ -66,10 +67,11 @@ struct FrameTable {
   float eps2d, alpha_max, alpha_min, T_min;
   float bg[3];
   u32 flags;                        // gs_config.flags (GS_FLAG_*)
-  int npasses;                      // digit passes launched (worst case for the workspace; host)
-  int npasses_needed;               // passes that do work: ceil((depth_bits + tile bits) / 8)
+  int tpasses;                      // tile-sort digit passes launched (fixed per workspace; host)
+  int tpasses_needed;               // tile-sort passes that do work: ceil(tile bits of this frame / 8)
+  int dpasses_needed;               // depth-sort passes that do work: ceil(depth_bits / 8)
   u32 depth_base;                   // float bits of the nearest depth (znear): depth keys minus this fit
-  int depth_bits;                   //   in depth_bits bits, so the sort digits come from (tile, depth - base)
+  int depth_bits;                   //   in depth_bits bits
   u32 launch_prims, launch_tiles;   // host-side launch sizing (capacity of the workspace); not read on the device
   ViewDesc v[GS_MAX_VIEWS];
 };
@@ -79,23 +81,25 @@ struct WsHeader {
   int status;               // gs_status of the current frame (0 = ok)
   u32 epoch;                // bumped by the setup kernel once per frame; tags look-back words
   u64 pairs;                // (tile, primitive) pairs emitted by the frame (may exceed capacity)
-  u32 chunk_counter;        // preprocess chunk allocator
+  u32 chunk_counter;        // chunk allocator of the active-list scan
   u32 tile_counter_fwd;     // render_fwd tile allocator
   u32 tile_counter_bwd;     // render_bwd tile allocator
   u32 nonfinite;            // primitives culled because a projected value was not finite
   u32 sort_counter[MAX_PASSES];
   u32 timeout_site;         // which bounded wait gave up (diagnostics)
-  u32 sorted_buf;           // 0: sorted pairs in keys0/vals0, 1: in keys1/vals1
-  u32 n_active;             // primitives that touch at least one tile (entries of the active list)
+  u32 sorted_buf;           // 0: sorted pairs in keys0, 1: in keys1
+  u32 n_active;             // primitives that touch at least one tile (depth ranks 0 .. n_active - 1)
   u32 fwd_exits, bwd_exits; // CTAs of the current compositing launch that have finished
   u32 masks_epoch;          // epoch of the last forward that recorded the composited-pair bits
-  u32 pad[10];
+  u32 rank_chunk_counter;   // chunk allocator of the rank-order scan
+  u32 pad[9];
 };
 
 // Offsets of every region of a workspace (host-computed; all 256-byte aligned).
 struct WsLayout {
-  size_t header, table, records, touched, offsets, active, scan_status, keys0, keys1, vals0, vals1, hist,
-      sort_status, ranges, cmask, T_final, n_contrib, n_eval, n_reach, n_comp, grad2d, total;
+  size_t header, table, records, touched, offsets, order, active, rank_of, dkeys0, dkeys1, scan_status, rank_status,
+      keys0, keys1,
+      hist, sort_status, ranges, cmask, T_final, n_contrib, n_eval, n_reach, n_comp, grad2d, total;
   u32 n_prims, n_tiles, n_chunks, n_parts;
   u64 n_pixels, capacity;
   int K, rec_f, g2d_f;
@@ -105,15 +109,19 @@ struct WsLayout {
 struct WsPtrs {
   WsHeader* hdr;
   const FrameTable* tbl;
-  float* records;
-  u32* touched;
-  u32* offsets;
-  u32* active;        // [n_prims] indices of primitives that touch a tile (any order)
-  u64* scan_status;
-  u64* keys0;
+  float* records;     // [n_prims][rec_f] by depth rank (row r: primitive order[r])
+  u32* touched;       // [n_prims] kept tiles per primitive
+  u32* offsets;       // [n_prims] by depth rank: first pair position of the primitive of that rank
+  u32* order;         // [n_prims] by depth rank: primitive index (the depth-sorted active list)
+  u32* active;        // [n_prims] the active primitives in index order (emission, records and the
+                      //   gradient chain run over this list: coalesced attribute access, mixed sizes)
+  u32* rank_of;       // [n_prims] by primitive index: depth rank of an active primitive
+  u64* dkeys0;        // [n_prims] depth-sort keys (depth bits - depth_base) << 32 | primitive; dkeys1 also
+  u64* dkeys1;        //   holds each active primitive's key at its primitive index before the scan
+  u64* scan_status;   // [n_chunks] look-back words of the active-list scan
+  u64* rank_status;   // [n_chunks] look-back words of the rank-order scan
+  u64* keys0;         // [capacity] pairs tile << 32 | depth rank (emission order, then sort ping-pong)
   u64* keys1;
-  u32* vals0;
-  u32* vals1;
   u32* hist;          // [MAX_PASSES][RADIX]
   u64* sort_status;   // [n_parts][RADIX]
   uint2* ranges;      // [n_tiles]
@@ -124,23 +132,17 @@ struct WsPtrs {
   u32* n_eval;        // [n_pixels] pairs the forward pass evaluated per pixel
   u32* n_reach;       // [n_pixels] of those, pairs that passed the footprint test (o G >= alpha_min)
   u32* n_comp;        // [n_pixels] pairs composited
-  float* grad2d;      // [n_prims][g2d_f]
+  float* grad2d;      // [n_prims][g2d_f] by depth rank
   u64 capacity;
   u32 n_chunks, n_parts;
   u32 cmask_plane;     // words per plane: capacity / 32 + tiles + 2 (each tile owns whole words)
 };
 
 WsLayout make_layout(u32 n_prims, int K, u32 n_tiles, u64 n_pixels, u64 capacity);
-int sort_passes(u32 ntiles);
+int tile_passes(u32 ntiles);
 int tile_bits(u32 ntiles);
 void set_depth_window(FrameTable& t, float znear_min, float zfar_max);
 
-// Sort digit source: the 64-bit key (tile << 32 | float bits of depth) re-packed as
-// (tile << depth_bits | depth bits - depth_base), which orders exactly like the key for depths in
-// (znear, zfar] and has 32 - depth_bits fewer significant bits.
-__device__ __forceinline__ u64 sort_value(u64 key, u32 base, int dbits) {
-  return ((key >> 32) << dbits) | (u64)((u32)key - base);
-}
 WsPtrs make_ptrs(const WsLayout& L, void* ws);
 
 // ------------------------------------------------------------------------------------------
@@ -172,6 +174,51 @@ __device__ __forceinline__ u64 global_timer_ns() {
 // Every spin-wait gives up after this long (or this many polls) and sets GS_ERR_TIMEOUT.
 constexpr u64 SPIN_LIMIT_NS = 1000000000ull;   // 1 s
 constexpr u32 SPIN_LIMIT_POLLS = 1u << 24;
+
+__device__ __forceinline__ void set_status(WsHeader* hdr, int s);
+
+#ifndef GS_LB_WINDOW
+#define GS_LB_WINDOW 4
+#endif
+constexpr int LB_WINDOW = GS_LB_WINDOW;   // look-back words read per step
+
+// Decoupled look-back walk of partition `part` (one thread): adds the published values of
+// partitions part - 1, part - 2, ... (word of partition j at status[j * stride]) back to the nearest
+// inclusive prefix and returns that exclusive prefix.  LB_WINDOW predecessors are read per step as
+// independent loads (one memory latency); consumption stops at the first word not yet published
+// for this tag, which is polled again.  Partition 0 always publishes a prefix.  Bounded: after the
+// spin limit it sets GS_ERR_TIMEOUT (site `site`) and returns what it has.
+__device__ __forceinline__ u64 lookback_walk(const u64* status, u64 stride, u32 part, u32 tag, WsHeader* hdr,
+                                             u32 site) {
+  const u32 tag22 = tag & 0x3FFFFFu;
+  u64 excl = 0;
+  u32 pi = part;   // partitions pi - 1, pi - 2, ... are still to be added
+  u32 polls = 0;
+  const u64 t0 = global_timer_ns();
+  for (;;) {
+    u64 w[LB_WINDOW];
+#pragma unroll
+    for (int j = 0; j < LB_WINDOW; ++j) w[j] = (u32)j < pi ? ld_relaxed(status + (u64)(pi - 1 - j) * stride) : 0ull;
+    u32 used = 0;
+#pragma unroll
+    for (int j = 0; j < LB_WINDOW; ++j) {
+      if (used != (u32)j || (u32)j >= pi) break;   // an earlier word stopped the walk
+      if (lb_flag(w[j]) == 0 || lb_tag(w[j]) != tag22) break;
+      excl += lb_value(w[j]);
+      if (lb_flag(w[j]) == LB_FLAG_PREFIX) return excl;
+      ++used;
+    }
+    pi -= used;
+    if (used == 0) {
+      if (++polls > SPIN_LIMIT_POLLS || ((polls & 1023u) == 0 && global_timer_ns() - t0 > SPIN_LIMIT_NS)) {
+        hdr->timeout_site = site;
+        set_status(hdr, GS_ERR_TIMEOUT);
+        return excl;
+      }
+      __nanosleep(20);
+    }
+  }
+}
 
 __device__ __forceinline__ void set_status(WsHeader* hdr, int s) { atomicCAS(&hdr->status, 0, s); }
 __device__ __forceinline__ int read_status(const WsHeader* hdr) {
@@ -304,6 +351,7 @@ int device_sm_count();
 
 cudaError_t launch_setup(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
 cudaError_t launch_preprocess(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
+cudaError_t launch_depth_sort(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
 cudaError_t launch_bin_sort(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
 // masks: record the composited-pair bits the backward pass reads (off for forward-only rendering)
 cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L,

@@ -32,11 +32,12 @@ __global__ void k_setup(FrameTable tbl, WsPtrs p) {
     h->epoch = h->epoch + 1;
     h->pairs = 0;
     h->chunk_counter = 0;
+    h->rank_chunk_counter = 0;
     h->tile_counter_fwd = 0;
     h->tile_counter_bwd = 0;
     h->nonfinite = 0;
     h->timeout_site = 0;
-    h->sorted_buf = (u32)(tbl.npasses_needed & 1);
+    h->sorted_buf = (u32)(tbl.tpasses_needed & 1);
     h->n_active = 0;
     h->fwd_exits = 0;
     h->bwd_exits = 0;
@@ -297,10 +298,11 @@ __device__ __forceinline__ u32 bin_one(const FrameTable* tbl, u32 gi, const WsPt
   return (u32)wx * (u32)(b.y1 - b.y0 + 1);   // tiles of the 3-sigma square (culled per tile later)
 }
 
-// The 2D record of one primitive that touches at least one tile: conic from the float64
-// determinant, colour, splatted frequencies.  Recomputes the binning quantities (bit-identical).
+// The 2D record of one primitive that touches at least one tile (row `row`, its depth rank): conic
+// from the float64 determinant, colour, splatted frequencies.  Recomputes the binning quantities
+// (bit-identical).
 template <int K, int STORAGE>
-__device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, const WsPtrs& p) {
+__device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, u32 row, const WsPtrs& p) {
   const int v = view_of_prim(tbl, gi);
   const ViewDesc& V = tbl->v[v];
   const u32 k = gi - V.prim_base;
@@ -382,7 +384,7 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, const 
     for (int i = 12 + 3 * K; i < rec_floats(K); ++i) rec[i] = 0.f;
   }
   rec[6] = 1.f - wsum;
-  float4* dst = reinterpret_cast<float4*>(p.records + (size_t)gi * rec_floats(K));
+  float4* dst = reinterpret_cast<float4*>(p.records + (size_t)row * rec_floats(K));
 #pragma unroll
   for (int i = 0; i < rec_floats(K) / 4; ++i) dst[i] = make_float4(rec[4 * i], rec[4 * i + 1], rec[4 * i + 2], rec[4 * i + 3]);
 }
@@ -419,10 +421,13 @@ __device__ __forceinline__ void flat_tile(u32 j, u32 my_excl, int x0, int y0, in
   f.tx = ox0 + (int)(local - ry * (u32)owx);
 }
 
-// Binning in three launches: (1) bin every primitive and count the tiles of its 3-sigma square
-// that a pixel can reach (warp-cooperative, no CTA barriers), appending primitives with at least one
-// tile to the active list; (2) exclusive scan of the counts (single pass, decoupled look-back over
-// 4096-element chunks); (3) emission of the kept pairs, warp-cooperative over the active list.
+// Binning: (1) bin every primitive and count the tiles of its 3-sigma square that a pixel can reach
+// (warp-cooperative, no CTA barriers); a primitive with at least one such tile is active and gets a
+// depth key; (2) scan of the active flags (single pass, decoupled look-back over 4096-primitive
+// chunks) that lists the active primitives' depth keys in primitive order; (3) depth sort of that
+// list (sort.cu), whose positions are the depth ranks; (4) scan of the kept-tile counts in rank
+// order, giving each rank its first pair position; (5) emission of the kept pairs in rank order,
+// warp-cooperative.
 
 // Per-owner counts of kept tiles over a warp's flat tile list; returns this lane's count.
 __device__ __forceinline__ u32 count_kept(u32 wsq_total, u32 my_sq_excl, int x0, int y0, int wx, const Reach& rr,
@@ -477,27 +482,71 @@ __global__ void __launch_bounds__(BLOCK) k_bin(WsPtrs p) {
     u32 wsq_total;
     const u32 my_sq_excl = warp_excl_scan(sq, lane, wsq_total);
     const u32 cnt = count_kept(wsq_total, my_sq_excl, x0, y0, wx, rr, s_cnt[warp], lane);
-    if (gi < total) p.touched[gi] = cnt;
-    const u32 ballot = __ballot_sync(0xffffffffu, cnt > 0);
-    u32 abase = 0;
-    if (lane == 0 && ballot) abase = atomicAdd(&hdr->n_active, (u32)__popc(ballot));
-    abase = __shfl_sync(0xffffffffu, abase, 0);
-    if (cnt > 0) p.active[abase + __popc(ballot & ((1u << lane) - 1u))] = gi;
+    if (gi < total) {
+      p.touched[gi] = cnt;
+      // depth in (znear, zfar]: its float bits minus bits(znear) lie in [1, 2^depth_bits)
+      if (cnt > 0) p.dkeys1[gi] = ((u64)(dbits - tbl->depth_base) << 32) | gi;
+    }
   }
 }
 
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_CHUNK = BLOCK * SCAN_ITEMS;   // counts per look-back partition
 
-__global__ void __launch_bounds__(BLOCK) k_scan_touched(WsPtrs p) {
+// Decoupled look-back of one chunk (one thread): publishes the chunk's aggregate, adds the
+// predecessors' values back to the nearest published inclusive prefix, publishes its own inclusive
+// prefix and returns the exclusive one.  Bounded: after the spin limit it sets GS_ERR_TIMEOUT (site
+// `site`) and publishes what it has, so its successors do not wait.
+__device__ u64 chunk_lookback(u64* status, u32 chunk, u32 tag, u64 agg, WsHeader* hdr, u32 site) {
+  u64* st = status + chunk;
+  if (chunk == 0) {
+    st_relaxed(st, lb_pack(LB_FLAG_PREFIX, tag, agg));
+    return 0;
+  }
+  st_relaxed(st, lb_pack(LB_FLAG_AGG, tag, agg));
+  const u64 excl = lookback_walk(status, 1, chunk, tag, hdr, site);
+  st_relaxed(st, lb_pack(LB_FLAG_PREFIX, tag, excl + agg));
+  return excl;
+}
+
+// Exclusive scan over the CTA of one value per thread (thread t owns SCAN_ITEMS consecutive items);
+// thread 0 runs the chunk's look-back.  Returns the thread's global exclusive prefix; the chunk's
+// exclusive prefix and total are left in s_excl / s_tot.
+__device__ __forceinline__ u64 chunk_scan(u32 sum, u32* s_warp, u64& s_excl, u64& s_tot, u64* status, u32 chunk,
+                                          u32 tag, WsHeader* hdr, u32 site) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  u32 wtot;
+  const u32 wex = warp_excl_scan(sum, lane, wtot);
+  if (lane == 31) s_warp[warp] = wex + sum;
+  __syncthreads();
+  if (warp == 0) {
+    const u32 wv = lane < BLOCK / 32 ? s_warp[lane] : 0u;
+    u32 wt;
+    const u32 wx = warp_excl_scan(wv, lane, wt);
+    if (lane < BLOCK / 32) s_warp[lane] = wx;
+    if (lane == 0) {
+      s_excl = chunk_lookback(status, chunk, tag, wt, hdr, site);
+      s_tot = wt;
+    }
+  }
+  __syncthreads();
+  return s_excl + s_warp[warp] + wex;
+}
+
+// (2) Active list: the primitives with at least one kept tile and their depth keys, in primitive
+// order, and the digit counts of the depth sort.  Publishes n_active.
+__global__ void __launch_bounds__(BLOCK) k_scan_active(WsPtrs p) {
   __shared__ u32 s_chunk;
   __shared__ u32 s_warp[BLOCK / 32];
-  __shared__ u64 s_excl;
+  __shared__ u64 s_excl, s_tot;
+  __shared__ u32 s_h[DPASSES][RADIX];
   const FrameTable* tbl = p.tbl;
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < DPASSES * RADIX; i += BLOCK) (&s_h[0][0])[i] = 0;
   const u32 total = tbl->total_prims;
+  const int need = tbl->dpasses_needed;
   const u32 tag = hdr->epoch;
   for (;;) {
     if (tid == 0) s_chunk = atomicAdd(&hdr->chunk_counter, 1u);
@@ -505,73 +554,82 @@ __global__ void __launch_bounds__(BLOCK) k_scan_touched(WsPtrs p) {
     const u32 chunk = s_chunk;
     const u64 base = (u64)chunk * SCAN_CHUNK;
     if (base >= total) break;
-    // thread t owns SCAN_ITEMS consecutive counts
-    u32 v[SCAN_ITEMS], sum = 0;
     const u64 my0 = base + (u64)tid * SCAN_ITEMS;
+    u32 flags = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i)
+      if (my0 + i < total && p.touched[my0 + i] > 0) flags |= 1u << i;
+    u64 run = chunk_scan((u32)__popc(flags), s_warp, s_excl, s_tot, p.scan_status, chunk, tag, hdr, 1);
+    if (tid == 0 && base + SCAN_CHUNK >= total) hdr->n_active = (u32)(s_excl + s_tot);
+    while (flags) {
+      const int i = __ffs(flags) - 1;
+      flags &= flags - 1;
+      const u64 key = p.dkeys1[my0 + i];
+      p.active[run] = (u32)(my0 + i);
+      p.dkeys0[run++] = key;
+      for (int ps = 0; ps < need; ++ps) atomicAdd(&s_h[ps][(u32)(key >> (32 + RADIX_BITS * ps)) & (RADIX - 1)], 1u);
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  for (int i = tid; i < need * RADIX; i += BLOCK) {
+    const u32 c = (&s_h[0][0])[i];
+    if (c) atomicAdd(p.hist + i, c);
+  }
+}
+
+// (4) Rank order: order[r] = the primitive of depth rank r, rank_of[order[r]] = r, offsets[r] = its
+// first pair position (exclusive scan of the kept-tile counts in rank order).  Publishes the pair
+// count and checks the pair capacity.
+__global__ void __launch_bounds__(BLOCK) k_scan_ranked(WsPtrs p) {
+  __shared__ u32 s_chunk;
+  __shared__ u32 s_warp[BLOCK / 32];
+  __shared__ u64 s_excl, s_tot;
+  const FrameTable* tbl = p.tbl;
+  WsHeader* hdr = p.hdr;
+  if (read_status(hdr) != 0) return;
+  const int tid = threadIdx.x;
+  const u32 total = hdr->n_active;
+  const u64* __restrict__ sorted = (tbl->dpasses_needed & 1) ? p.dkeys1 : p.dkeys0;
+  const u32 tag = hdr->epoch;
+  for (;;) {
+    if (tid == 0) s_chunk = atomicAdd(&hdr->rank_chunk_counter, 1u);
+    __syncthreads();
+    const u32 chunk = s_chunk;
+    const u64 base = (u64)chunk * SCAN_CHUNK;
+    if (base >= total) break;
+    const u64 my0 = base + (u64)tid * SCAN_ITEMS;
+    u32 v[SCAN_ITEMS], sum = 0;
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i) {
-      v[i] = (my0 + i < total) ? p.touched[my0 + i] : 0u;
+      v[i] = 0;
+      if (my0 + i < total) {
+        const u32 gi = (u32)sorted[my0 + i];
+        p.order[my0 + i] = gi;
+        p.rank_of[gi] = (u32)(my0 + i);
+        v[i] = p.touched[gi];
+      }
       sum += v[i];
     }
-    u32 wtot;
-    const u32 wex = warp_excl_scan(sum, lane, wtot);
-    if (lane == 31) s_warp[warp] = wex + sum;
-    __syncthreads();
-    if (warp == 0) {
-      const u32 wv = lane < BLOCK / 32 ? s_warp[lane] : 0u;
-      u32 wt;
-      const u32 wx = warp_excl_scan(wv, lane, wt);
-      if (lane < BLOCK / 32) s_warp[lane] = wx;
-      if (lane == 0) {
-        const u32 agg = wt;
-        u64* st = p.scan_status + chunk;
-        u64 excl = 0;
-        if (chunk == 0) {
-          st_relaxed(st, lb_pack(LB_FLAG_PREFIX, tag, agg));
-        } else {
-          st_relaxed(st, lb_pack(LB_FLAG_AGG, tag, agg));
-          u32 pidx = chunk - 1;
-          u32 polls = 0;
-          const u64 t0 = global_timer_ns();
-          for (;;) {
-            const u64 w = ld_relaxed(p.scan_status + pidx);
-            if (lb_flag(w) != 0 && lb_tag(w) == (tag & 0x3FFFFFu)) {
-              excl += lb_value(w);
-              if (lb_flag(w) == LB_FLAG_PREFIX) break;
-              --pidx;  // chunk 0 always publishes a prefix
-              continue;
-            }
-            if (++polls > SPIN_LIMIT_POLLS || ((polls & 1023u) == 0 && global_timer_ns() - t0 > SPIN_LIMIT_NS)) {
-              hdr->timeout_site = 1;
-              set_status(hdr, GS_ERR_TIMEOUT);
-              break;
-            }
-            __nanosleep(32);
-          }
-          st_relaxed(st, lb_pack(LB_FLAG_PREFIX, tag, excl + agg));
-        }
-        s_excl = excl;
-        if (base + SCAN_CHUNK >= total) {   // last chunk: publish the pair count
-          const u64 P = excl + agg;
-          hdr->pairs = P;
-          if (P > p.capacity) set_status(hdr, GS_ERR_CAPACITY);
-        }
-      }
+    u64 run = chunk_scan(sum, s_warp, s_excl, s_tot, p.rank_status, chunk, tag, hdr, 2);
+    if (tid == 0 && base + SCAN_CHUNK >= total) {   // last chunk: publish the pair count
+      const u64 P = s_excl + s_tot;
+      hdr->pairs = P;
+      if (P > p.capacity) set_status(hdr, GS_ERR_CAPACITY);
     }
-    __syncthreads();
-    u32 run = (u32)s_excl + s_warp[warp] + wex;
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i) {
-      if (my0 + i < total) p.offsets[my0 + i] = run;
+      if (my0 + i < total) p.offsets[my0 + i] = (u32)run;
       run += v[i];
     }
     __syncthreads();
   }
 }
 
-// Emission over the active list: 32 primitives per warp, each lane re-bins its own (bit-identical),
-// the warp walks the owners' squares and writes each kept tile at offset(owner) + its rank among
-// the owner's kept tiles (row-major), i.e. in the order of the specification.
+// (5) Emission over the active list (index order, so a warp's 32 primitives mix near and far ones
+// and its tile walks stay balanced): each lane re-bins its own primitive (bit-identical), the warp
+// walks the owners' squares and writes tile << 32 | rank for each kept tile at offsets[rank] + its
+// index among the owner's kept tiles (row-major).
 __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
   __shared__ u32 s_run[BLOCK / 32][32];
   const FrameTable* tbl = p.tbl;
@@ -584,13 +642,14 @@ __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
   for (u32 grp = blockIdx.x * (BLOCK / 32) + warp; (u64)grp * 32 < nact; grp += nwarps) {
     const u32 ia = grp * 32 + lane;
     const u32 gi = ia < nact ? p.active[ia] : 0u;
+    const u32 rank = ia < nact ? p.rank_of[gi] : 0u;
     int x0 = 0, y0 = 0, wx = 1, tiles_x = 1;
     u32 dbits = 0, tile_base = 0, sq = 0;
     bool nonfinite = false;
     Reach rr;
     rr.mux = rr.muy = rr.A = rr.C = rr.kx = rr.ky = rr.B2 = rr.thr = 0.f;
     if (ia < nact) sq = bin_one(tbl, gi, p, x0, y0, wx, dbits, tile_base, tiles_x, nonfinite, rr);
-    const u32 off = ia < nact ? p.offsets[gi] : 0u;
+    const u32 off = ia < nact ? p.offsets[rank] : 0u;
     u32 wsq_total;
     const u32 my_sq_excl = warp_excl_scan(sq, lane, wsq_total);
     s_run[warp][lane] = 0;
@@ -603,17 +662,13 @@ __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
       const u32 ballot = __ballot_sync(0xffffffffu, kept);
       const u32 peers = __match_any_sync(0xffffffffu, j < wsq_total ? ft.owner : 32 + lane);
       const u32 ooff = __shfl_sync(0xffffffffu, off, ft.owner);
-      const u32 odb = __shfl_sync(0xffffffffu, dbits, ft.owner);
-      const u32 ogi = __shfl_sync(0xffffffffu, gi, ft.owner);
+      const u32 orank = __shfl_sync(0xffffffffu, rank, ft.owner);
       const u32 otb = __shfl_sync(0xffffffffu, tile_base, ft.owner);
       const int otx = __shfl_sync(0xffffffffu, tiles_x, ft.owner);
       const u32 run = j < wsq_total ? s_run[warp][ft.owner] : 0u;
       if (kept) {
         const u64 pos = (u64)ooff + run + __popc(ballot & peers & lt);
-        if (pos < p.capacity) {
-          p.keys0[pos] = ((u64)(otb + (u32)ft.ty * (u32)otx + (u32)ft.tx) << 32) | odb;
-          p.vals0[pos] = ogi;
-        }
+        if (pos < p.capacity) p.keys0[pos] = ((u64)(otb + (u32)ft.ty * (u32)otx + (u32)ft.tx) << 32) | orank;
       }
       __syncwarp();
       if (j < wsq_total && lane == __ffs(peers) - 1) s_run[warp][ft.owner] = run + __popc(ballot & peers);
@@ -622,12 +677,15 @@ __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
   }
 }
 
-// 2D records of the active primitives (full warps: culled primitives are not in the list).
+// 2D records of the active primitives (full warps over the active list), each at its depth rank.
 template <int K, int STORAGE>
 __global__ void __launch_bounds__(BLOCK) k_records(WsPtrs p) {
   if (read_status(p.hdr) != 0) return;
   const u32 n = p.hdr->n_active;
-  for (u32 i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) record_one<K, STORAGE>(p.tbl, p.active[i], p);
+  for (u32 i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+    const u32 gi = p.active[i];
+    record_one<K, STORAGE>(p.tbl, gi, p.rank_of[gi], p);
+  }
 }
 
 // Zero every attribute gradient (culled primitives keep zeros; active ones are overwritten).
@@ -668,11 +726,12 @@ __global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grad
   const u32 n_act = p.hdr->n_active;
   for (u32 ia = blockIdx.x * BLOCK + threadIdx.x; ia < n_act; ia += gridDim.x * BLOCK) {
     const u32 gi = p.active[ia];
+    const u32 row = p.rank_of[gi];   // grad2d rows are depth ranks
     const int k = (int)(gi - V.prim_base);
     const bool active = true;
     float g2[g2d_floats(K)];
     if (active) {
-      const float4* src = reinterpret_cast<const float4*>(p.grad2d + (size_t)gi * g2d_floats(K));
+      const float4* src = reinterpret_cast<const float4*>(p.grad2d + (size_t)row * g2d_floats(K));
 #pragma unroll
       for (int i = 0; i < g2d_floats(K) / 4; ++i) {
         const float4 t = src[i];
@@ -957,16 +1016,20 @@ cudaError_t launch_setup(const FrameTable& tbl, const WsPtrs& p, const Launch& L
 
 template <int K, int ST>
 static cudaError_t launch_pre_t(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
-  static int bgrid = 0, sgrid = 0, egrid = 0, rgrid = 0;
+  static int bgrid = 0, sgrid = 0, qgrid = 0, egrid = 0, rgrid = 0;
   if (!bgrid) bgrid = persistent_grid(k_bin, BLOCK, 0, L.sm_count);
-  if (!sgrid) sgrid = persistent_grid(k_scan_touched, BLOCK, 0, L.sm_count);
+  if (!sgrid) sgrid = persistent_grid(k_scan_active, BLOCK, 0, L.sm_count);
+  if (!qgrid) qgrid = persistent_grid(k_scan_ranked, BLOCK, 0, L.sm_count);
   if (!egrid) egrid = persistent_grid(k_emit, BLOCK, 0, L.sm_count);
   if (!rgrid) rgrid = persistent_grid(k_records<K, ST>, BLOCK, 0, L.sm_count);
   const int need = (int)((tbl.launch_prims + BLOCK - 1) / BLOCK);
   const int schunks = (int)((tbl.launch_prims + SCAN_CHUNK - 1) / SCAN_CHUNK);
   auto clampg = [](int g, int cap) { return g < 1 ? 1 : (g > cap ? cap : g); };
   k_bin<<<clampg(need, bgrid), BLOCK, 0, L.stream>>>(p);
-  k_scan_touched<<<clampg(schunks, sgrid), BLOCK, 0, L.stream>>>(p);
+  k_scan_active<<<clampg(schunks, sgrid), BLOCK, 0, L.stream>>>(p);
+  cudaError_t e = launch_depth_sort(tbl, p, L);
+  if (e != cudaSuccess) return e;
+  k_scan_ranked<<<clampg(schunks, qgrid), BLOCK, 0, L.stream>>>(p);
   k_emit<<<clampg(need, egrid), BLOCK, 0, L.stream>>>(p);
   k_records<K, ST><<<clampg(need, rgrid), BLOCK, 0, L.stream>>>(p);
   return cudaGetLastError();

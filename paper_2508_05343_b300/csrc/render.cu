@@ -130,7 +130,7 @@ __device__ __forceinline__ int2 thread_pixel(int tx, int ty, int tid) {
 // MASKS: record per warp which pairs its pixels composited (for the backward pass); forward-only
 // uses (serving, frequency maps) skip it and keep the per-thread early exit.
 template <int K, int PPT, bool FMAP, bool MASKS>
-__global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32* vals, float* out_rgb,
+__global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, float* out_rgb,
                                                             float* out_T) {
   constexpr int NT = BLOCK / PPT;
   constexpr int F4 = SRec<K>::F4;
@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
   if (read_status(hdr) != 0) return;
   if (MASKS && blockIdx.x == 0 && threadIdx.x == 0) hdr->masks_epoch = hdr->epoch;   // bits of this frame
   const FrameTable* tbl = p.tbl;
-  if (!vals) vals = (tbl->npasses_needed & 1) ? p.vals1 : p.vals0;
+  // sorted pairs tile << 32 | depth rank; the rank is the record (and grad2d) row
+  const u64* __restrict__ pairs = (tbl->tpasses_needed & 1) ? p.keys1 : p.keys0;
   const int tid = threadIdx.x;
   const u32 ntiles = tbl->total_tiles;
   const float amax = tbl->alpha_max, amin = tbl->alpha_min, Tmin = tbl->T_min;
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, const u32*
       if (__syncthreads_count(tdone) == NT) break;
       const u32 idx = start + tid;
       if (idx < rg.y) {
-        const float* rec = p.records + (size_t)vals[idx] * rec_floats(K);
+        const float* rec = p.records + (size_t)(u32)pairs[idx] * rec_floats(K);
         stage_record<K>(rec, s_rec + tid * F4, amin);
         if (FMAP) s_rec[tid * F4 + 2] = frequency_features<K>(rec);
       }
@@ -302,7 +303,7 @@ __device__ __forceinline__ void flush_pair_grads(const float* a, float* dst) {
 }
 
 template <int K, int PPT>
-__global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32* vals,
+__global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p,
                                                             const float* __restrict__ dL_drgb) {
   constexpr int NT = BLOCK / PPT;
   constexpr int F4 = SRec<K>::F4;
@@ -327,7 +328,8 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
     return;
   }
   const FrameTable* tbl = p.tbl;
-  if (!vals) vals = (tbl->npasses_needed & 1) ? p.vals1 : p.vals0;
+  // sorted pairs tile << 32 | depth rank; the rank is the record (and grad2d) row
+  const u64* __restrict__ pairs = (tbl->tpasses_needed & 1) ? p.keys1 : p.keys0;
   const int tid = threadIdx.x, lane = tid & 31;
   const u32 ntiles = tbl->total_tiles;
   const float amax = tbl->alpha_max, amin = tbl->alpha_min;
@@ -386,7 +388,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
       const u32 bstart = bend - rg.x > (u32)NT ? bend - NT : rg.x;
       const u32 cnt = bend - bstart;
       if ((u32)tid < cnt) {
-        const u32 id = vals[bstart + tid];
+        const u32 id = (u32)pairs[bstart + tid];
         s_id[tid] = id;
         stage_record<K>(p.records + (size_t)id * rec_floats(K), s_rec + tid * F4, amin);
       }
@@ -521,7 +523,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p, const u32*
 }
 
 template <int K, bool FMAP, bool MASKS>
-static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, const u32* vals, float* rgb, float* T,
+static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, float* rgb, float* T,
                                 const Launch& L) {
   constexpr int PPT = GS_PPT_FWD, NT = BLOCK / PPT;
   static int grid = 0;
@@ -539,12 +541,12 @@ static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, const u3
   int g = grid;
   if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
   if (g < 1) g = 1;
-  k_render_fwd<K, PPT, FMAP, MASKS><<<g, NT, smem, L.stream>>>(p, vals, rgb, T);
+  k_render_fwd<K, PPT, FMAP, MASKS><<<g, NT, smem, L.stream>>>(p, rgb, T);
   return cudaGetLastError();
 }
 
 template <int K>
-static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const u32* vals, const float* dL,
+static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const float* dL,
                                 const Launch& L) {
   constexpr int PPT = GS_PPT_BWD, NT = BLOCK / PPT;
   static int grid = 0;
@@ -564,24 +566,23 @@ static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const u3
   int g = grid;
   if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
   if (g < 1) g = 1;
-  k_render_bwd<K, PPT><<<g, NT, smem, L.stream>>>(p, vals, dL);
+  k_render_bwd<K, PPT><<<g, NT, smem, L.stream>>>(p, dL);
   return cudaGetLastError();
 }
 
 
 template <bool FMAP, bool MASKS>
 static cudaError_t launch_fwd_k(const FrameTable& tbl, const WsPtrs& p, float* out, float* out_T, const Launch& L) {
-  const u32* vals = nullptr;   // chosen on the device: the sort's pass count depends on the depth range
   switch (tbl.K) {
-    case 0: return launch_fwd_t<0, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
-    case 1: return launch_fwd_t<1, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
-    case 2: return launch_fwd_t<2, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
-    case 3: return launch_fwd_t<3, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
-    case 4: return launch_fwd_t<4, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
-    case 5: return launch_fwd_t<5, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
-    case 6: return launch_fwd_t<6, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
-    case 7: return launch_fwd_t<7, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
-    case 8: return launch_fwd_t<8, FMAP, MASKS>(tbl, p, vals, out, out_T, L);
+    case 0: return launch_fwd_t<0, FMAP, MASKS>(tbl, p, out, out_T, L);
+    case 1: return launch_fwd_t<1, FMAP, MASKS>(tbl, p, out, out_T, L);
+    case 2: return launch_fwd_t<2, FMAP, MASKS>(tbl, p, out, out_T, L);
+    case 3: return launch_fwd_t<3, FMAP, MASKS>(tbl, p, out, out_T, L);
+    case 4: return launch_fwd_t<4, FMAP, MASKS>(tbl, p, out, out_T, L);
+    case 5: return launch_fwd_t<5, FMAP, MASKS>(tbl, p, out, out_T, L);
+    case 6: return launch_fwd_t<6, FMAP, MASKS>(tbl, p, out, out_T, L);
+    case 7: return launch_fwd_t<7, FMAP, MASKS>(tbl, p, out, out_T, L);
+    case 8: return launch_fwd_t<8, FMAP, MASKS>(tbl, p, out, out_T, L);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -597,17 +598,16 @@ cudaError_t launch_render_freq_map(const FrameTable& tbl, const WsPtrs& p, float
 }
 
 cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL, const Launch& L) {
-  const u32* vals = nullptr;   // chosen on the device: the sort's pass count depends on the depth range
   switch (tbl.K) {
-    case 0: return launch_bwd_t<0>(tbl, p, vals, dL, L);
-    case 1: return launch_bwd_t<1>(tbl, p, vals, dL, L);
-    case 2: return launch_bwd_t<2>(tbl, p, vals, dL, L);
-    case 3: return launch_bwd_t<3>(tbl, p, vals, dL, L);
-    case 4: return launch_bwd_t<4>(tbl, p, vals, dL, L);
-    case 5: return launch_bwd_t<5>(tbl, p, vals, dL, L);
-    case 6: return launch_bwd_t<6>(tbl, p, vals, dL, L);
-    case 7: return launch_bwd_t<7>(tbl, p, vals, dL, L);
-    case 8: return launch_bwd_t<8>(tbl, p, vals, dL, L);
+    case 0: return launch_bwd_t<0>(tbl, p, dL, L);
+    case 1: return launch_bwd_t<1>(tbl, p, dL, L);
+    case 2: return launch_bwd_t<2>(tbl, p, dL, L);
+    case 3: return launch_bwd_t<3>(tbl, p, dL, L);
+    case 4: return launch_bwd_t<4>(tbl, p, dL, L);
+    case 5: return launch_bwd_t<5>(tbl, p, dL, L);
+    case 6: return launch_bwd_t<6>(tbl, p, dL, L);
+    case 7: return launch_bwd_t<7>(tbl, p, dL, L);
+    case 8: return launch_bwd_t<8>(tbl, p, dL, L);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -120,17 +120,18 @@ class Rasterizer:
             nb = count * torch.empty(0, dtype=dtype).element_size()
             return self.ws[off:off + nb].view(dtype)
 
+        na = v.n_active   # rows of records / grad2d / offsets / order are depth ranks 0 .. na - 1
         return dict(
-            records=sl(v.records, self.n * v.record_floats, torch.float32).view(self.n, v.record_floats),
-            touched=sl(v.touched, self.n, torch.int32), offsets=sl(v.offsets, self.n, torch.int32),
-            keys_sorted=sl(v.keys_sorted, P, torch.int64), values_sorted=sl(v.values_sorted, P, torch.int32),
+            records=sl(v.records, na * v.record_floats, torch.float32).view(na, v.record_floats),
+            touched=sl(v.touched, self.n, torch.int32), offsets=sl(v.offsets, na, torch.int32),
+            order=sl(v.order, na, torch.int32), n_active=na, keys_sorted=sl(v.keys_sorted, P, torch.int64),
             ranges=sl(v.ranges, 2 * ntiles, torch.int32).view(ntiles, 2),
             T_final=sl(v.T_final, npix, torch.float32).view(self.height, self.width),
             n_contrib=sl(v.n_contrib, npix, torch.int32).view(self.height, self.width),
             n_eval=sl(v.n_eval, npix, torch.int32).view(self.height, self.width),
             n_reach=sl(v.n_reach, npix, torch.int32).view(self.height, self.width),
             n_comp=sl(v.n_comp, npix, torch.int32).view(self.height, self.width),
-            grad2d=sl(v.grad2d, self.n * v.grad2d_floats, torch.float32).view(self.n, v.grad2d_floats),
+            grad2d=sl(v.grad2d, na * v.grad2d_floats, torch.float32).view(na, v.grad2d_floats),
             pairs=pairs, tiles_x=v.tiles_x, tiles_y=v.tiles_y,
             record_floats=v.record_floats, grad2d_floats=v.grad2d_floats)
 

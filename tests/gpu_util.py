@@ -66,3 +66,12 @@ def gpu_grads(r, dL):
     g = r.backward(torch.as_tensor(dL, dtype=torch.float32, device="cuda").contiguous())
     torch.cuda.synchronize()
     return {k: v.float().cpu().numpy() for k, v in g.items()}
+
+
+def by_prim(v, key, n):
+    """Rows of a rank-indexed workspace view (records, grad2d) at their primitives' indices
+    (zeros for primitives that reach no tile)."""
+    rows = v[key].cpu().numpy().astype(np.float64)
+    out = np.zeros((n, rows.shape[1]))
+    out[v["order"].cpu().numpy().astype(np.int64)] = rows
+    return out

@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Bars: tile lists / sort keys / ranges / touched counts bit-exact; images within 2e-4 max-abs per
+Bars: tile lists / depth ranks / sorted pairs / ranges / touched counts bit-exact; images within 2e-4 max-abs per
 channel (pixels where float32 and float64 may branch differently at alpha_min or T_min get the
 extra allowance of one skipped pair and are counted); gradients within 1e-3 relative L2 per
 attribute group of the oracle's analytic gradients and of its central finite differences.
@@ -12,20 +12,30 @@ import torch
 from oracle import gabsplat_oracle as O
 from paper_2508_05343_b300 import scenes
 from tests.conftest import cuda_available
-from tests.gpu_util import (AMBIG_EXTRA, ATTRS, GRAD_TOL, IMG_TOL, assert_image_parity, bf16_prims, cfg_pair,
-                            compare_images, gpu_grads, gpu_render, rel_l2)
+from tests.gpu_util import (AMBIG_EXTRA, ATTRS, GRAD_TOL, IMG_TOL, assert_image_parity, bf16_prims, by_prim,
+                            cfg_pair, compare_images, gpu_grads, gpu_render, rel_l2)
 
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_available(), reason="needs a CUDA device")]
 
 
 def check_binning(r, spec):
+    """Bins against the oracle's binning: kept-tile counts; the depth ranks (active primitives by
+    float32 camera depth, ties by index); each rank's first pair position; and the sorted pairs,
+    whose tiles and primitives must be the oracle's (tile, depth, primitive) sort exactly."""
     v = r.views()
     assert v["pairs"] == spec["P"]
-    np.testing.assert_array_equal(v["touched"].cpu().numpy().astype(np.int64), spec["touched"])
-    valid = spec["touched"] > 0
-    np.testing.assert_array_equal(v["offsets"].cpu().numpy().astype(np.int64)[valid], spec["offsets"][valid])
-    np.testing.assert_array_equal(v["keys_sorted"].cpu().numpy().view(np.uint64), spec["sorted_keys"])
-    np.testing.assert_array_equal(v["values_sorted"].cpu().numpy().view(np.uint32), spec["sorted_vals"])
+    touched = spec["touched"]
+    np.testing.assert_array_equal(v["touched"].cpu().numpy().astype(np.int64), touched)
+    act = np.nonzero(touched > 0)[0]
+    dbits = np.asarray(spec["depth"], np.float32).view(np.uint32)[act]
+    order_ref = act[np.argsort(dbits, kind="stable")]
+    order = v["order"].cpu().numpy().astype(np.int64)
+    np.testing.assert_array_equal(order, order_ref)
+    cnt = touched[order_ref]
+    np.testing.assert_array_equal(v["offsets"].cpu().numpy().astype(np.int64), np.cumsum(cnt) - cnt)
+    keys = v["keys_sorted"].cpu().numpy().view(np.uint64)
+    np.testing.assert_array_equal(keys >> np.uint64(32), spec["sorted_keys"] >> np.uint64(32))
+    np.testing.assert_array_equal(order[(keys & np.uint64(0xFFFFFFFF)).astype(np.int64)], spec["sorted_vals"])
     # tile ranges: identical [start, end) for every non-empty tile; empty tiles empty on both sides
     rg = v["ranges"].cpu().numpy().view(np.uint32).astype(np.int64)
     ref = spec["ranges"].astype(np.int64)
@@ -40,7 +50,7 @@ def check_records(v, out, prims):
     """Projected records vs the float64 projection (primitives that reach at least one tile)."""
     spec, proj = out["spec"], out["proj"]
     valid = spec["valid"] & (spec["touched"] > 0)
-    rec = v["records"].cpu().numpy().astype(np.float64)[valid]
+    rec = by_prim(v, "records", len(valid))[valid]
     K = prims["weights"].shape[1]
     np.testing.assert_allclose(rec[:, 0:2], proj["mu2d"].numpy()[valid], rtol=1e-5, atol=1e-3)
     conic = proj["conic"].numpy()[valid]
@@ -140,7 +150,7 @@ def test_config1_gradients_vs_oracle_analytic():
     g = gpu_grads(r, dL)
     errs = {k: rel_l2(g[k], ref[k]) for k in ATTRS}
     # 2D (per-record) gradients too: mu2d, conic, opacity, rgb, f2d, weights
-    g2 = r.views()["grad2d"].cpu().numpy().astype(np.float64)
+    g2 = by_prim(r.views(), "grad2d", prims["means"].shape[0])
     K = prims["weights"].shape[1]
     r2 = ref["grad2d"]
     errs["2d.mu"] = rel_l2(g2[:, 0:2], r2["mu2d"])
@@ -190,7 +200,7 @@ def test_z_attenuation_variant_image_records_and_gradients():
     assert_image_parity(img.cpu().numpy(), out)
     K = prims["weights"].shape[1]
     valid = out["spec"]["valid"] & (out["spec"]["touched"] > 0)
-    rec = v["records"].cpu().numpy().astype(np.float64)[valid]
+    rec = by_prim(v, "records", len(valid))[valid]
     cw = out["proj"]["cos_weights"].numpy()[valid]
     np.testing.assert_allclose(rec[:, 12 + 2 * K:12 + 3 * K], cw, rtol=1e-4, atol=1e-6)
     np.testing.assert_allclose(rec[:, 6], 1.0 - prims["weights"][valid].astype(np.float64).sum(1), atol=1e-6)
@@ -330,8 +340,8 @@ def test_bounded_lookback_wait_reports_timeout():
     r, pt, _, _ = gpu_render(prims, cam, gc)
     assert r.views()["pairs"] > 2 * 4096
     B.gabsplat_preprocess(r.frame, B.make_prims(pt), B.make_camera(cam), gc)
-    SORT_COUNTER0 = 32     # byte offset of sort_counter[0] in the workspace header
-    r.ws[SORT_COUNTER0:SORT_COUNTER0 + 4].view(torch.int32).fill_(1)
+    TILE_SORT_COUNTER0 = 48     # byte offset of the first tile pass's partition counter in the header
+    r.ws[TILE_SORT_COUNTER0:TILE_SORT_COUNTER0 + 4].view(torch.int32).fill_(1)
     B.gabsplat_bin_sort(r.frame)
     st, _ = r.status()
     assert st == B.GS_ERR_TIMEOUT
