@@ -26,7 +26,7 @@ WsLayout make_layout(u32 n_prims, int K, u32 n_tiles, u64 n_pixels, u64 capacity
   L.g2d_f = g2d_floats(K);
   L.n_chunks = (n_prims + CHUNK - 1) / CHUNK;
   const u64 sort_items = capacity > n_prims ? capacity : n_prims;   // pairs, or active primitives
-  L.n_parts = (u32)((sort_items + SORT_TILE - 1) / SORT_TILE);
+  L.n_parts = (u32)((sort_items + SORT_TILE - 1) / SORT_TILE);          // partitions of either sort, at most
   L.header = take(sizeof(WsHeader));
   L.table = take(sizeof(FrameTable));
   L.records = take((size_t)n_prims * L.rec_f * sizeof(float));

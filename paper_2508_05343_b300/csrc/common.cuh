@@ -21,9 +21,16 @@ constexpr int CHUNK = BLOCK;          // primitives per preprocess chunk (one pe
 #ifndef GS_SORT_ITEMS
 #define GS_SORT_ITEMS 16
 #endif
+#ifndef GS_DSORT_ITEMS
+#define GS_DSORT_ITEMS 4
+#endif
+#ifndef GS_SORT_MIN_CTAS
+#define GS_SORT_MIN_CTAS 3
+#endif
 constexpr int SORT_THREADS = GS_SORT_THREADS;   // >= 256: the first 256 threads own one digit each
-constexpr int SORT_ITEMS = GS_SORT_ITEMS;
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // keys per onesweep partition
+constexpr int SORT_ITEMS = GS_SORT_ITEMS;       // keys per thread of a tile-sort partition
+constexpr int DSORT_ITEMS = GS_DSORT_ITEMS;     // keys per thread of a depth-sort partition
+constexpr int SORT_TILE = SORT_THREADS * (SORT_ITEMS < DSORT_ITEMS ? SORT_ITEMS : DSORT_ITEMS);   // smallest partition
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int DPASSES = 4;     // depth-sort passes launched (depth keys have at most 32 bits)

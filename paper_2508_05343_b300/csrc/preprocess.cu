@@ -559,15 +559,19 @@ __global__ void __launch_bounds__(BLOCK) k_scan_active(WsPtrs p) {
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i)
       if (my0 + i < total && p.touched[my0 + i] > 0) flags |= 1u << i;
+    u64 key[SCAN_ITEMS];   // loaded before any store, so the loads overlap
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) key[i] = (flags >> i) & 1u ? p.dkeys1[my0 + i] : 0ull;
     u64 run = chunk_scan((u32)__popc(flags), s_warp, s_excl, s_tot, p.scan_status, chunk, tag, hdr, 1);
     if (tid == 0 && base + SCAN_CHUNK >= total) hdr->n_active = (u32)(s_excl + s_tot);
-    while (flags) {
-      const int i = __ffs(flags) - 1;
-      flags &= flags - 1;
-      const u64 key = p.dkeys1[my0 + i];
-      p.active[run] = (u32)(my0 + i);
-      p.dkeys0[run++] = key;
-      for (int ps = 0; ps < need; ++ps) atomicAdd(&s_h[ps][(u32)(key >> (32 + RADIX_BITS * ps)) & (RADIX - 1)], 1u);
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      if ((flags >> i) & 1u) {
+        p.active[run] = (u32)(my0 + i);
+        p.dkeys0[run++] = key[i];
+        for (int ps = 0; ps < need; ++ps)
+          atomicAdd(&s_h[ps][(u32)(key[i] >> (32 + RADIX_BITS * ps)) & (RADIX - 1)], 1u);
+      }
     }
     __syncthreads();
   }
@@ -599,17 +603,19 @@ __global__ void __launch_bounds__(BLOCK) k_scan_ranked(WsPtrs p) {
     const u64 base = (u64)chunk * SCAN_CHUNK;
     if (base >= total) break;
     const u64 my0 = base + (u64)tid * SCAN_ITEMS;
-    u32 v[SCAN_ITEMS], sum = 0;
+    // all loads first (keys, then the counts they index), then the stores: the loads overlap
+    u32 gi[SCAN_ITEMS], v[SCAN_ITEMS], sum = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) gi[i] = my0 + i < total ? (u32)sorted[my0 + i] : 0xFFFFFFFFu;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) v[i] = gi[i] != 0xFFFFFFFFu ? p.touched[gi[i]] : 0u;
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i) {
-      v[i] = 0;
-      if (my0 + i < total) {
-        const u32 gi = (u32)sorted[my0 + i];
-        p.order[my0 + i] = gi;
-        p.rank_of[gi] = (u32)(my0 + i);
-        v[i] = p.touched[gi];
-      }
       sum += v[i];
+      if (gi[i] != 0xFFFFFFFFu) {
+        p.order[my0 + i] = gi[i];
+        p.rank_of[gi[i]] = (u32)(my0 + i);
+      }
     }
     u64 run = chunk_scan(sum, s_warp, s_excl, s_tot, p.rank_status, chunk, tag, hdr, 2);
     if (tid == 0 && base + SCAN_CHUNK >= total) {   // last chunk: publish the pair count

@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(256) k_digit_hist(WsPtrs p) {
 
 static_assert(SORT_THREADS >= RADIX && SORT_THREADS % 32 == 0, "one digit per thread of the first RADIX threads");
 
+template <int ITEMS>
 struct SortSmem {
   u32 warp_cnt[SORT_THREADS / 32][RADIX];
   u32 local_excl[RADIX];
@@ -46,7 +47,7 @@ struct SortSmem {
   u32 hist_excl[RADIX];
   u32 scratch[SORT_THREADS / 32];
   u32 part;
-  u64 keys[SORT_TILE];
+  u64 keys[SORT_THREADS * ITEMS];
 };
 
 // Exclusive scan of one value per thread over the CTA (two barriers); threads >= RADIX pass 0.
@@ -68,12 +69,15 @@ __device__ __forceinline__ u32 block_excl_scan(u32 v, u32* scratch /*SORT_THREAD
   return wbase + incl - v;
 }
 
-// One digit pass over bits [32 + 8 pass, 40 + 8 pass) of the keys.  slot < DPASSES: depth sort of
-// the n_active primitive keys (pass = slot); otherwise tile sort of the pairs (pass = slot - DPASSES).
-__global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* __restrict__ kin,
-                                                           u64* __restrict__ kout, int slot) {
+// One digit pass over bits [32 + 8 pass, 40 + 8 pass) of the keys, in partitions of
+// SORT_THREADS * ITEMS keys.  slot < DPASSES: depth sort of the n_active primitive keys
+// (pass = slot); otherwise tile sort of the pairs (pass = slot - DPASSES).
+template <int ITEMS>
+__global__ void __launch_bounds__(SORT_THREADS, GS_SORT_MIN_CTAS) k_onesweep(WsPtrs p, const u64* __restrict__ kin,
+                                                                           u64* __restrict__ kout, int slot) {
+  constexpr int PART = SORT_THREADS * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
+  SortSmem<ITEMS>& S = *reinterpret_cast<SortSmem<ITEMS>*>(smem_raw);
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
   const bool tiles = slot >= DPASSES;
@@ -99,19 +103,19 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* 
     for (int i = tid; i < (SORT_THREADS / 32) * RADIX; i += SORT_THREADS) (&S.warp_cnt[0][0])[i] = 0;
     __syncthreads();
     const u32 part = S.part;
-    const u64 base = (u64)part * SORT_TILE;
+    const u64 base = (u64)part * PART;
     if (base >= P) break;
-    u64 key[SORT_ITEMS];
-    u32 rank[SORT_ITEMS];
-    const u64 wbase = base + (u64)warp * 32 * SORT_ITEMS;
+    u64 key[ITEMS];
+    u32 rank[ITEMS];
+    const u64 wbase = base + (u64)warp * 32 * ITEMS;
 #pragma unroll
-    for (int i = 0; i < SORT_ITEMS; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
       const u64 idx = wbase + (u64)i * 32 + lane;
       const bool valid = idx < P;
       key[i] = valid ? kin[idx] : ~0ull;
     }
 #pragma unroll
-    for (int i = 0; i < SORT_ITEMS; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
       const u64 idx = wbase + (u64)i * 32 + lane;
       const bool valid = idx < P;
       const u32 d = (u32)(key[i] >> shift) & (RADIX - 1);
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* 
     __syncthreads();
     // local scatter into shared memory (stable: warp order, round order, lane order)
 #pragma unroll
-    for (int i = 0; i < SORT_ITEMS; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
       const u64 idx = wbase + (u64)i * 32 + lane;
       if (idx < P) {
         const u32 d = (u32)(key[i] >> shift) & (RADIX - 1);
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* 
       }
     }
     __syncthreads();
-    const u32 nvalid = (u32)((P - base) < (u64)SORT_TILE ? (P - base) : (u64)SORT_TILE);
+    const u32 nvalid = (u32)((P - base) < (u64)PART ? (P - base) : (u64)PART);
     for (u32 j = tid; j < nvalid; j += SORT_THREADS) {
       const u64 k = S.keys[j];
       const u32 d = (u32)(k >> shift) & (RADIX - 1);
@@ -173,31 +177,47 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(WsPtrs p, const u64* 
   }
 }
 
-__global__ void k_tile_ranges(WsPtrs p) {
+// Per-tile [start, end) of the sorted pairs: a pair starts (ends) its tile's range when its
+// predecessor (successor) has another tile.  Neighbours come from the adjacent lanes; only the
+// warp's edge lanes load them.
+__global__ void __launch_bounds__(256) k_tile_ranges(WsPtrs p) {
   if (read_status(p.hdr) != 0) return;
   const u64* __restrict__ keys = (p.tbl->tpasses_needed & 1) ? p.keys1 : p.keys0;
   const u64 Pall = p.hdr->pairs;
   const u64 P = Pall < p.capacity ? Pall : p.capacity;
   const u32 ntiles = p.tbl->total_tiles;
-  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (u64)gridDim.x * blockDim.x) {
-    const u32 t = (u32)(keys[i] >> 32);
+  const int lane = threadIdx.x & 31;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  // warp-uniform trip count: every lane takes part in the shuffles
+  for (u64 w0 = ((u64)blockIdx.x * blockDim.x + threadIdx.x) & ~31ull; w0 < P; w0 += stride) {
+    const u64 i = w0 + lane;
+    const bool in = i < P;
+    const u32 t = in ? (u32)(keys[i] >> 32) : 0xFFFFFFFFu;
+    u32 prev = __shfl_up_sync(0xffffffffu, t, 1);
+    u32 next = __shfl_down_sync(0xffffffffu, t, 1);
+    if (lane == 0) prev = i > 0 && in ? (u32)(keys[i - 1] >> 32) : 0xFFFFFFFFu;
+    if (lane == 31 || i + 1 >= P) next = i + 1 < P ? (u32)(keys[i + 1] >> 32) : 0xFFFFFFFFu;
+    if (!in) continue;
     if (t >= ntiles) {   // cannot happen for keys this frame emitted; guards the table write
       set_status(p.hdr, GS_ERR_INVALID_ARG);
       continue;
     }
-    if (i == 0 || (u32)(keys[i - 1] >> 32) != t) p.ranges[t].x = (u32)i;
-    if (i + 1 == P || (u32)(keys[i + 1] >> 32) != t) p.ranges[t].y = (u32)(i + 1);
+    if (i == 0 || prev != t) p.ranges[t].x = (u32)i;
+    if (i + 1 == P || next != t) p.ranges[t].y = (u32)(i + 1);
   }
 }
 
+template <int ITEMS>
 static int sort_grid(const Launch& L) {
   static int grid = 0;
   if (!grid) {
-    const size_t smem = sizeof(SortSmem);
-    if (cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    const size_t smem = sizeof(SortSmem<ITEMS>);
+    if (cudaFuncSetAttribute(k_onesweep<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
       return -1;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep, SORT_THREADS, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<ITEMS>, SORT_THREADS, smem) !=
+            cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     grid = per_sm * L.sm_count;
@@ -207,15 +227,17 @@ static int sort_grid(const Launch& L) {
 
 // Passes [first, first + count) of one sort, ping-ponging between b0 and b1 (input in b0); a pass
 // with no work leaves its input in place, so the result is in b1 iff the number of working passes is
-// odd.  `items` bounds the partitions a pass can have.
+// odd.  `items` bounds the keys a pass can have.
+template <int ITEMS>
 static cudaError_t run_passes(const WsPtrs& p, u64* b0, u64* b1, int first, int count, u64 items, const Launch& L) {
-  const int sg = sort_grid(L);
+  const int sg = sort_grid<ITEMS>(L);
   if (sg < 0) return cudaErrorInvalidValue;
-  u64 parts = (items + SORT_TILE - 1) / SORT_TILE;
+  constexpr int PART = SORT_THREADS * ITEMS;
+  const u64 parts = (items + PART - 1) / PART;
   int grid = (u64)sg < parts ? sg : (int)parts;
   if (grid < 1) grid = 1;
   for (int ps = 0; ps < count; ++ps) {
-    k_onesweep<<<grid, SORT_THREADS, sizeof(SortSmem), L.stream>>>(p, b0, b1, first + ps);
+    k_onesweep<ITEMS><<<grid, SORT_THREADS, sizeof(SortSmem<ITEMS>), L.stream>>>(p, b0, b1, first + ps);
     u64* t = b0;
     b0 = b1;
     b1 = t;
@@ -224,13 +246,13 @@ static cudaError_t run_passes(const WsPtrs& p, u64* b0, u64* b1, int first, int 
 }
 
 cudaError_t launch_depth_sort(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
-  return run_passes(p, p.dkeys0, p.dkeys1, 0, DPASSES, tbl.launch_prims, L);
+  return run_passes<DSORT_ITEMS>(p, p.dkeys0, p.dkeys1, 0, DPASSES, tbl.launch_prims, L);
 }
 
 cudaError_t launch_bin_sort(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
   if (tbl.tpasses > 0) {
     k_digit_hist<<<L.sm_count * 4, 256, 0, L.stream>>>(p);
-    const cudaError_t e = run_passes(p, p.keys0, p.keys1, DPASSES, tbl.tpasses, p.capacity, L);
+    const cudaError_t e = run_passes<SORT_ITEMS>(p, p.keys0, p.keys1, DPASSES, tbl.tpasses, p.capacity, L);
     if (e != cudaSuccess) return e;
   }
   k_tile_ranges<<<L.sm_count * 8, 256, 0, L.stream>>>(p);
