@@ -382,6 +382,14 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, u32 ro
     }
 #pragma unroll
     for (int i = 12 + 3 * K; i < rec_floats(K); ++i) rec[i] = 0.f;
+    // rec[11]: 1 if |f2D_i . d| <= FAST_PHASE_CYCLES for every component at every pixel centre of
+    // the primitive's tile rectangle (the compositing kernels then skip the phase reduction)
+    const float ax = fmaxf(fabsf(FA((float)(TILE * b.x0), 0.5f) - b.mux), fabsf(FA((float)(TILE * b.x1), TILE - 0.5f) - b.mux));
+    const float ay = fmaxf(fabsf(FA((float)(TILE * b.y0), 0.5f) - b.muy), fabsf(FA((float)(TILE * b.y1), TILE - 0.5f) - b.muy));
+    float bound = 0.f;
+#pragma unroll
+    for (int i = 0; i < K; ++i) bound = fmaxf(bound, fabsf(rec[12 + 2 * i]) * ax + fabsf(rec[12 + 2 * i + 1]) * ay);
+    rec[11] = bound <= FAST_PHASE_CYCLES ? 1.f : 0.f;
   }
   rec[6] = 1.f - wsum;
   float4* dst = reinterpret_cast<float4*>(p.records + (size_t)row * rec_floats(K));

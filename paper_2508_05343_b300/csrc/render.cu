@@ -3,23 +3,30 @@
 // tiles from an atomic counter.  The tile's depth-sorted pairs are staged into shared memory in
 // batches of 256 records; the evaluation of alpha is a single inlined function with explicit
 // fused-multiply-add intrinsics so the backward kernel reproduces the forward's decisions exactly.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace gs {
 
 constexpr float LOG2E = 1.4426950408889634f;
 constexpr float TWO_PI = 6.283185307179586f;
+constexpr float INV_TWO_PI = 0.15915494309189535f;
 
-// Shared-memory record (floats): {mu_x, mu_y, A', B'}, {C', thr, o, 1 - sum w}, {r, g, b, -},
-// {f2D_0x, f2D_0y, ...}, {w_0 ...}; A' = -a/2 log2 e, B' = -b log2 e, C' = -c/2 log2 e so that
-// G = 2^(A' dx^2 + B' dx dy + C' dy^2); thr = log2(alpha_min / o): o G < alpha_min <=> power < thr,
-// and since the filter bank is <= 1 (weights >= 0) such pairs have alpha < alpha_min: skipped early.
+// Shared-memory record (floats): {mu_x, mu_y, A', B'}, {C', thr, o, 1 - sum w}, {r, g, b, fast},
+// {2 pi f2D_0x, 2 pi f2D_0y, ...}, {w_0 ...}; A' = -a/2 log2 e, B' = -b log2 e, C' = -c/2 log2 e so
+// that G = 2^(A' dx^2 + B' dx dy + C' dy^2); thr = log2(alpha_min / o): o G < alpha_min <=>
+// power < thr, and since the filter bank is <= 1 (weights >= 0) such pairs have alpha < alpha_min:
+// skipped early.  fast (set by the record kernel) = 1 when every |f2D_i . d| over the primitive's
+// tile rectangle is within FAST_PHASE_CYCLES, so the phase needs no range reduction; the forward
+// and the backward read the same flag, so both evaluate the bank the same way.
 template <int K>
 struct SRec {
   static constexpr int F = rec_floats(K);
   static constexpr int F4 = F / 4;
 };
 
+// The f2D values are scaled by 2 pi one float4 at a time, so little is live while the pixel state is.
 template <int K>
 __device__ __forceinline__ void stage_record(const float* __restrict__ rec, float4* dst, float alpha_min) {
   const float4* src = reinterpret_cast<const float4*>(rec);
@@ -29,7 +36,16 @@ __device__ __forceinline__ void stage_record(const float* __restrict__ rec, floa
   dst[1] = make_float4(-0.5f * LOG2E * h1.x, o > 0.f ? log2f(alpha_min / o) : 3.0e38f, o, h1.z);
   dst[2] = h2;
 #pragma unroll
-  for (int i = 3; i < SRec<K>::F4; ++i) dst[i] = __ldg(src + i);
+  for (int i = 0; i < SRec<K>::F4 - 3; ++i) {
+    float4 t = __ldg(src + 3 + i);
+    // floats 0 .. 2K - 1 after the colour are f2D (scaled); the weights follow (for odd K in the
+    // same float4 as the last component)
+    if (4 * i + 0 < 2 * K) t.x = __fmul_rn(TWO_PI, t.x);
+    if (4 * i + 1 < 2 * K) t.y = __fmul_rn(TWO_PI, t.y);
+    if (4 * i + 2 < 2 * K) t.z = __fmul_rn(TWO_PI, t.z);
+    if (4 * i + 3 < 2 * K) t.w = __fmul_rn(TWO_PI, t.w);
+    dst[3 + i] = t;
+  }
 }
 
 // Frequency features of one record: sum_i w_i |f2D_i|, sum_i w_i |f2D_i,x|, sum_i w_i |f2D_i,y|.
@@ -63,21 +79,22 @@ __device__ __forceinline__ float gauss_power(const float4& h0, const float4& h1,
   return __fmaf_rn(dx, __fmaf_rn(h0.z, dx, __fmul_rn(h0.w, dy)), __fmul_rn(__fmul_rn(h1.x, dy), dy));
 }
 
-// Phase (cycles) reduced to [-1/2, 1/2]: cos(2 pi x) = cos(2 pi (x - rint(x))).
-__device__ __forceinline__ float reduced_phase(float fx, float fy, float dx, float dy) {
-  const float ph = __fmaf_rn(fx, dx, __fmul_rn(fy, dy));
-  return __fsub_rn(ph, rintf(ph));
+// Phase 2 pi f2D . d (radians) from the staged (2 pi f2D_x, 2 pi f2D_y).  FAST: as it is;
+// otherwise reduced to [-pi, pi] through cycles, cos(2 pi t) = cos(2 pi (t - rint(t))).
+template <bool FAST>
+__device__ __forceinline__ float phase_angle(float Fx, float Fy, float dx, float dy) {
+  const float th = __fmaf_rn(Fx, dx, __fmul_rn(Fy, dy));
+  if (FAST) return th;
+  const float t = __fmul_rn(th, INV_TWO_PI);
+  return __fmul_rn(TWO_PI, __fsub_rn(t, rintf(t)));
 }
 
 // Filter bank (1 - sum w) + sum w_i cos(2 pi f2D_i . d)  (Sec. 3.3.2, Eq. 9)
-template <int K>
+template <int K, bool FAST>
 __device__ __forceinline__ float filter_bank(const float* r, float w0, float dx, float dy) {
   float bank = w0;
 #pragma unroll
-  for (int i = 0; i < K; ++i) {
-    const float x = reduced_phase(r[2 * i], r[2 * i + 1], dx, dy);
-    bank = __fmaf_rn(r[2 * K + i], __cosf(__fmul_rn(TWO_PI, x)), bank);
-  }
+  for (int i = 0; i < K; ++i) bank = __fmaf_rn(r[2 * K + i], __cosf(phase_angle<FAST>(r[2 * i], r[2 * i + 1], dx, dy)), bank);
   return bank;
 }
 
@@ -102,6 +119,25 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 // 5% less time in the backward than 16x4 at 1.5M primitives, 1600x1064).
 #ifndef GS_WARP_SQUARE
 #define GS_WARP_SQUARE 1
+#endif
+
+// Resident CTAs per SM the compositing kernels are compiled for (0: the compiler's choice; forcing
+// 8 forward CTAs, 64 registers, measured slower than the compiler's 72).
+#ifndef GS_FWD_MIN_CTAS
+#define GS_FWD_MIN_CTAS 0
+#endif
+#ifndef GS_BWD_MIN_CTAS
+#define GS_BWD_MIN_CTAS 0
+#endif
+#if GS_FWD_MIN_CTAS
+#define GS_FWD_BOUNDS __launch_bounds__(BLOCK / PPT, GS_FWD_MIN_CTAS)
+#else
+#define GS_FWD_BOUNDS __launch_bounds__(BLOCK / PPT)
+#endif
+#if GS_BWD_MIN_CTAS
+#define GS_BWD_BOUNDS __launch_bounds__(BLOCK / PPT, GS_BWD_MIN_CTAS)
+#else
+#define GS_BWD_BOUNDS __launch_bounds__(BLOCK / PPT)
 #endif
 
 // Called by thread 0 of every CTA after it has left its tile loop: the last CTA of the launch
@@ -130,7 +166,7 @@ __device__ __forceinline__ int2 thread_pixel(int tx, int ty, int tid) {
 // MASKS: record per warp which pairs its pixels composited (for the backward pass); forward-only
 // uses (serving, frequency maps) skip it and keep the per-thread early exit.
 template <int K, int PPT, bool FMAP, bool MASKS>
-__global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, float* out_rgb,
+__global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
                                                             float* out_T) {
   constexpr int NT = BLOCK / PPT;
   constexpr int F4 = SRec<K>::F4;
@@ -192,6 +228,7 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, float* out
         }
         const float4* r = s_rec + j * F4;
         const float4 h0 = r[0], h1 = r[1];
+        const bool fast = reinterpret_cast<const float*>(r)[11] != 0.f;   // the same for every lane
         const float dx = __fsub_rn(fpx, h0.x);
         bool comp = false;
         tdone = true;
@@ -203,7 +240,8 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_fwd(WsPtrs p, float* out
             if (pw >= h1.y) {
               ++reached[q];
               const float G = ex2_approx(pw);
-              const float bank = filter_bank<K>(reinterpret_cast<const float*>(r + 3), h1.w, dx, dy);
+              const float* fr = reinterpret_cast<const float*>(r + 3);
+              const float bank = fast ? filter_bank<K, true>(fr, h1.w, dx, dy) : filter_bank<K, false>(fr, h1.w, dx, dy);
               const float alpha = fminf(amax, __fmul_rn(__fmul_rn(h1.z, G), bank));
               if (alpha >= amin) {
                 const float test = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
@@ -283,8 +321,8 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[32], int lane) {
 }
 
 // One pair's accumulated 2D gradients, converted from the log2-domain conic (A' = -a/2 log2 e,
-// B' = -b log2 e, C' = -c/2 log2 e) to (a, b, c), added to its grad2d row with one vector atomic
-// per 4 values (zero groups skipped).
+// B' = -b log2 e, C' = -c/2 log2 e) to (a, b, c) and from the staged 2 pi f2D to f2D, added to its
+// grad2d row with one vector atomic per 4 values (zero groups skipped).
 template <int K>
 __device__ __forceinline__ void flush_pair_grads(const float* a, float* dst) {
   constexpr int NV = 10 + 3 * K, NG = g2d_floats(K);
@@ -296,6 +334,8 @@ __device__ __forceinline__ void flush_pair_grads(const float* a, float* dst) {
   row[3] *= cB;
   row[4] *= cA;
 #pragma unroll
+  for (int i = 9; i < 9 + 2 * K; ++i) row[i] *= TWO_PI;
+#pragma unroll
   for (int i = 0; i < NG / 4; ++i) {
     const float4 qv = make_float4(row[4 * i], row[4 * i + 1], row[4 * i + 2], row[4 * i + 3]);
     if (qv.x != 0.f || qv.y != 0.f || qv.z != 0.f || qv.w != 0.f) atomicAdd(reinterpret_cast<float4*>(dst) + i, qv);
@@ -303,7 +343,7 @@ __device__ __forceinline__ void flush_pair_grads(const float* a, float* dst) {
 }
 
 template <int K, int PPT>
-__global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p,
+__global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p,
                                                             const float* __restrict__ dL_drgb) {
   constexpr int NT = BLOCK / PPT;
   constexpr int F4 = SRec<K>::F4;
@@ -411,12 +451,15 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p,
         const u32 pos = w0 + (u32)bit - rg.x;     // 0-based position in the tile list
         const float4* r = s_rec + j * F4;
         const float4 h0 = r[0], h1 = r[1];
-        const float* fw = reinterpret_cast<const float*>(r + 3);
+        const bool fast = reinterpret_cast<const float*>(r)[11] != 0.f;   // the same for every lane
+        const float* fw = reinterpret_cast<const float*>(r + 3);   // 2 pi f2D, then the weights
         float gv[NVP];
 #pragma unroll
         for (int i = 0; i < NVP; ++i) gv[i] = 0.f;
         bool contrib = false;
         const float dx = __fsub_rn(fpx, h0.x);
+        // the per-pixel work, instantiated for records with and without phase reduction
+        auto pixels = [&](auto fast_tag) {
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
           if (pos >= last[q]) continue;
@@ -428,12 +471,12 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p,
           float bank = h1.w;
 #pragma unroll
           for (int i = 0; i < K; ++i) {
-            const float x = reduced_phase(fw[2 * i], fw[2 * i + 1], dx, dy);
-            const float ang = __fmul_rn(TWO_PI, x);
+            const float ang = phase_angle<decltype(fast_tag)::value>(fw[2 * i], fw[2 * i + 1], dx, dy);
             cs[i] = __cosf(ang);
             sn[i] = __sinf(ang);
-            bank = __fmaf_rn(fw[2 * K + i], cs[i], bank);
           }
+#pragma unroll
+          for (int i = 0; i < K; ++i) bank = __fmaf_rn(fw[2 * K + i], cs[i], bank);
           const float araw = __fmul_rn(__fmul_rn(h1.z, G), bank);
           const float alpha = fminf(amax, araw);
           if (alpha < amin) continue;
@@ -463,21 +506,25 @@ __global__ void __launch_bounds__(BLOCK / PPT) k_render_bwd(WsPtrs p,
           gv[4] += ey * dy;                                // w.r.t. C'
           float gdx = 2.f * h0.z * ex + h0.w * ey;
           float gdy = h0.w * ex + 2.f * h1.x * ey;
-          const float mph = -TWO_PI * dLdbank;
 #pragma unroll
           for (int i = 0; i < K; ++i) {
             const float wi = fw[2 * K + i];
             gv[9 + 2 * K + i] += dLdbank * cs[i];                  // d (cosine weight i)
-            const float gph = mph * wi * sn[i];                     // d phase (cycles)
-            gv[9 + 2 * i] += gph * dx;
-            gv[9 + 2 * i + 1] += gph * dy;
-            gdx += gph * fw[2 * i];
-            gdy += gph * fw[2 * i + 1];
+            const float gth = -dLdbank * wi * sn[i];                // d phase (radians)
+            gv[9 + 2 * i] += gth * dx;                              // w.r.t. 2 pi f2D (scaled at flush)
+            gv[9 + 2 * i + 1] += gth * dy;
+            gdx += gth * fw[2 * i];
+            gdy += gth * fw[2 * i + 1];
           }
           gv[9 + 3 * K] += dLdbank;                        // d (1 - sum w)
           gv[0] -= gdx;                                    // d mu = - d (pixel - mu)
           gv[1] -= gdy;
         }
+        };
+        if (fast)
+          pixels(std::true_type{});
+        else
+          pixels(std::false_type{});
         if (__ballot_sync(0xffffffffu, contrib)) {
 #if GS_BWD_SMEM_REDUCE
           // transpose through shared memory: lane l stores value v at row v, column l; lane v
