@@ -44,6 +44,7 @@ WsLayout make_layout(u32 n_prims, int K, u32 n_tiles, u64 n_pixels, u64 capacity
   L.hist = take((size_t)MAX_PASSES * RADIX * 4);
   L.sort_status = take((size_t)(L.n_parts ? L.n_parts : 1) * RADIX * 8);
   L.ranges = take((size_t)n_tiles * 8);
+  L.tile_order = take((size_t)n_tiles * 4);
   L.cmask = take((size_t)CMASK_PLANES * (capacity / 32 + n_tiles + 2) * 4);
   L.T_final = take((size_t)n_pixels * 4);
   L.n_contrib = take((size_t)n_pixels * 4);
@@ -75,6 +76,7 @@ WsPtrs make_ptrs(const WsLayout& L, void* ws) {
   p.hist = reinterpret_cast<u32*>(b + L.hist);
   p.sort_status = reinterpret_cast<u64*>(b + L.sort_status);
   p.ranges = reinterpret_cast<uint2*>(b + L.ranges);
+  p.tile_order = reinterpret_cast<u32*>(b + L.tile_order);
   p.cmask = reinterpret_cast<u32*>(b + L.cmask);
   p.cmask_plane = (u32)(L.capacity / 32 + L.n_tiles + 2);
   p.T_final = reinterpret_cast<float*>(b + L.T_final);

@@ -111,7 +111,7 @@ struct WsHeader {
 struct WsLayout {
   size_t header, table, records, touched, offsets, order, active, rank_of, dkeys0, dkeys1, scan_status, rank_status,
       keys0, keys1,
-      hist, sort_status, ranges, cmask, T_final, n_contrib, n_eval, n_reach, n_comp, grad2d, total;
+      hist, sort_status, ranges, tile_order, cmask, T_final, n_contrib, n_eval, n_reach, n_comp, grad2d, total;
   u32 n_prims, n_tiles, n_chunks, n_parts;
   u64 n_pixels, capacity;
   int K, rec_f, g2d_f;
@@ -137,6 +137,7 @@ struct WsPtrs {
   u32* hist;          // [MAX_PASSES][RADIX]
   u64* sort_status;   // [n_parts][RADIX]
   uint2* ranges;      // [n_tiles]
+  u32* tile_order;    // [n_tiles] tiles by descending pair count (the compositing kernels' schedule)
   u32* cmask;         // [CMASK_PLANES][cmask_plane] per compositing warp slot: bit (pos & 31) of word
                       // (pos >> 5) + tile set if a pixel of that warp composited the pair at sorted position pos
   float* T_final;     // [n_pixels]

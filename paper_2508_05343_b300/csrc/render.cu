@@ -1,6 +1,6 @@
 // Per-tile compositing of the 2D Gabor primitives (Sec. 3.3.2 Eq. 9, Sec. 3.3.3 Eq. 10) and its
-// reverse-order adjoint.  One CTA of 256 threads owns a 16x16 tile (one pixel per thread) and pulls
-// tiles from an atomic counter.  The tile's depth-sorted pairs are staged into shared memory in
+// reverse-order adjoint.  One CTA owns a 16x16 tile and pulls tiles from an atomic counter, longest
+// pair lists first.  The tile's depth-sorted pairs are staged into shared memory in
 // batches of 256 records; the evaluation of alpha is a single inlined function with explicit
 // fused-multiply-add intrinsics so the backward kernel reproduces the forward's decisions exactly.
 #include <type_traits>
@@ -182,7 +182,10 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
   const u32 ntiles = tbl->total_tiles;
   const float amax = tbl->alpha_max, amin = tbl->alpha_min, Tmin = tbl->T_min;
   for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&hdr->tile_counter_fwd, 1u);
+    if (tid == 0) {   // tiles in the order of tile_order: longest pair lists first
+      const u32 slot = atomicAdd(&hdr->tile_counter_fwd, 1u);
+      s_tile = slot < ntiles ? p.tile_order[slot] : 0xFFFFFFFFu;
+    }
     __syncthreads();
     const u32 tile = s_tile;
     if (tile >= ntiles) break;
@@ -374,8 +377,9 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p,
   const u32 ntiles = tbl->total_tiles;
   const float amax = tbl->alpha_max, amin = tbl->alpha_min;
   for (;;) {
-    if (tid == 0) {
-      s_tile = atomicAdd(&hdr->tile_counter_bwd, 1u);
+    if (tid == 0) {   // tiles in the order of tile_order: longest pair lists first
+      const u32 slot = atomicAdd(&hdr->tile_counter_bwd, 1u);
+      s_tile = slot < ntiles ? p.tile_order[slot] : 0xFFFFFFFFu;
       s_max = 0;
     }
     __syncthreads();

@@ -207,6 +207,41 @@ __global__ void __launch_bounds__(256) k_tile_ranges(WsPtrs p) {
   }
 }
 
+// The compositing kernels' schedule: tiles by descending pair count, bucketed (count / 4, capped),
+// so persistent CTAs start the longest lists first and the launch ends on short ones.  One CTA.
+constexpr int ORDER_THREADS = 1024, ORDER_BUCKETS = 1024, ORDER_SHIFT = 2;
+__global__ void __launch_bounds__(ORDER_THREADS) k_tile_order(WsPtrs p) {
+  __shared__ u32 s_off[ORDER_BUCKETS];
+  __shared__ u32 s_warp[ORDER_THREADS / 32];
+  if (read_status(p.hdr) != 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const u32 ntiles = p.tbl->total_tiles;
+  auto bucket = [](uint2 rg) {   // descending length -> ascending bucket
+    const u32 b = (rg.y - rg.x) >> ORDER_SHIFT;
+    return (u32)(ORDER_BUCKETS - 1) - (b < (u32)(ORDER_BUCKETS - 1) ? b : (u32)(ORDER_BUCKETS - 1));
+  };
+  s_off[tid] = 0;   // ORDER_THREADS == ORDER_BUCKETS
+  __syncthreads();
+  for (u32 t = tid; t < ntiles; t += ORDER_THREADS) atomicAdd(&s_off[bucket(p.ranges[t])], 1u);
+  __syncthreads();
+  // exclusive scan of the bucket counts, one per thread
+  const u32 v = s_off[tid];
+  u32 incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 x = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += x;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  u32 wbase = 0;
+  for (int w = 0; w < warp; ++w) wbase += s_warp[w];
+  s_off[tid] = wbase + incl - v;
+  __syncthreads();
+  for (u32 t = tid; t < ntiles; t += ORDER_THREADS) p.tile_order[atomicAdd(&s_off[bucket(p.ranges[t])], 1u)] = t;
+}
+static_assert(ORDER_THREADS == ORDER_BUCKETS, "one bucket per thread");
+
 template <int ITEMS>
 static int sort_grid(const Launch& L) {
   static int grid = 0;
@@ -256,6 +291,7 @@ cudaError_t launch_bin_sort(const FrameTable& tbl, const WsPtrs& p, const Launch
     if (e != cudaSuccess) return e;
   }
   k_tile_ranges<<<L.sm_count * 8, 256, 0, L.stream>>>(p);
+  k_tile_order<<<1, ORDER_THREADS, 0, L.stream>>>(p);
   return cudaGetLastError();
 }
 
