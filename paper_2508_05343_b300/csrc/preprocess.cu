@@ -691,9 +691,18 @@ __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
   }
 }
 
+// Resident CTAs per SM that the record and gradient-chain kernels are compiled for.  Both are
+// latency-bound over scattered attribute rows, so occupancy matters more than a few spilled registers.
+#ifndef GS_RECORDS_MIN_CTAS
+#define GS_RECORDS_MIN_CTAS 1
+#endif
+#ifndef GS_PBWD_MIN_CTAS
+#define GS_PBWD_MIN_CTAS 2
+#endif
+
 // 2D records of the active primitives (full warps over the active list), each at its depth rank.
 template <int K, int STORAGE>
-__global__ void __launch_bounds__(BLOCK) k_records(WsPtrs p) {
+__global__ void __launch_bounds__(BLOCK, GS_RECORDS_MIN_CTAS) k_records(WsPtrs p) {
   if (read_status(p.hdr) != 0) return;
   const u32 n = p.hdr->n_active;
   for (u32 i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
@@ -731,7 +740,7 @@ __global__ void k_zero_grads(gs_prim_grads G, int n, int K, int nsh) {
 // forward above; clamps pass zero gradient).
 // ------------------------------------------------------------------------------------------
 template <int K, int STORAGE>
-__global__ void __launch_bounds__(BLOCK) k_preprocess_bwd(WsPtrs p, gs_prim_grads G) {
+__global__ void __launch_bounds__(BLOCK, GS_PBWD_MIN_CTAS) k_preprocess_bwd(WsPtrs p, gs_prim_grads G) {
   const FrameTable* tbl = p.tbl;
   if (read_status(p.hdr) != 0) return;
   const ViewDesc& V = tbl->v[0];

@@ -46,12 +46,26 @@ def check_binning(r, spec):
     return v
 
 
+def fast_phase_bound(out, K):
+    """Largest |f2D_i . d| (cycles) over the pixel centres of each primitive's tile rectangle, from
+    the float64 projection: the record flag (slot 11) is 1 where this is at most 2 cycles."""
+    spec, f2d = out["spec"], out["proj"]["f2d"].numpy().reshape(-1, K, 2)
+    mu, rect = spec["mu2d"], spec["rect"]
+    ax = np.maximum(np.abs(16 * rect[:, 0] + 0.5 - mu[:, 0]), np.abs(16 * rect[:, 1] + 15.5 - mu[:, 0]))
+    ay = np.maximum(np.abs(16 * rect[:, 2] + 0.5 - mu[:, 1]), np.abs(16 * rect[:, 3] + 15.5 - mu[:, 1]))
+    return (np.abs(f2d[:, :, 0]) * ax[:, None] + np.abs(f2d[:, :, 1]) * ay[:, None]).max(1)
+
+
 def check_records(v, out, prims):
     """Projected records vs the float64 projection (primitives that reach at least one tile)."""
     spec, proj = out["spec"], out["proj"]
     valid = spec["valid"] & (spec["touched"] > 0)
     rec = by_prim(v, "records", len(valid))[valid]
     K = prims["weights"].shape[1]
+    if K:   # the unreduced-phase flag, away from the 2-cycle edge where float32 may round either way
+        bound = fast_phase_bound(out, K)[valid]
+        clear = np.abs(bound - 2.0) > 1e-3
+        np.testing.assert_array_equal(rec[clear, 11], (bound[clear] <= 2.0).astype(np.float64))
     np.testing.assert_allclose(rec[:, 0:2], proj["mu2d"].numpy()[valid], rtol=1e-5, atol=1e-3)
     conic = proj["conic"].numpy()[valid]
     scale = np.abs(conic).max(1, keepdims=True)
@@ -90,6 +104,8 @@ def test_config1_forward_bitexact_bins_and_image():
     r, _, img, _ = gpu_render(prims, cam, gc)
     v = check_binning(r, out["spec"])
     check_records(v, out, prims)
+    flags = v["records"].cpu().numpy()[:, 11]
+    assert (flags == 1.0).any() and (flags == 0.0).any()   # both bank evaluations are exercised
     assert_image_parity(img.cpu().numpy(), out)
 
 
