@@ -360,10 +360,10 @@ def run_ours(args):
     zb = lambda z: int(np.float32(z).view(np.uint32))
     dbits = max(1, (zb(cams[0]["zfar"]) - zb(cams[0]["znear"])).bit_length())
     dpasses = min(4, math.ceil(dbits / 8))                   # depth-sort passes that do work (4 launched)
-    # my kernels per step: setup; bin, active scan, 4 depth passes, rank scan, emit, records; tile
-    # histogram + tile passes + ranges + tile schedule; render_fwd; loss (2); render_bwd; zero-fill +
-    # preprocess_bwd
-    launches_per_step = 1 + 9 + (1 + tpasses + 2) + 1 + 2 + 1 + 2
+    # my kernels per step: setup; bin, active count + scan, 4 depth passes, rank count + scan, emit,
+    # records; tile histogram + tile passes + ranges + tile schedule; render_fwd; loss (2);
+    # render_bwd; zero-fill + preprocess_bwd
+    launches_per_step = 1 + 11 + (1 + tpasses + 2) + 1 + 2 + 1 + 2
     stage_names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd"]
 
     def pose_of(s):

@@ -93,7 +93,6 @@ struct WsHeader {
   int status;               // gs_status of the current frame (0 = ok)
   u32 epoch;                // bumped by the setup kernel once per frame; tags look-back words
   u64 pairs;                // (tile, primitive) pairs emitted by the frame (may exceed capacity)
-  u32 chunk_counter;        // chunk allocator of the active-list scan
   u32 tile_counter_fwd;     // render_fwd tile allocator
   u32 tile_counter_bwd;     // render_bwd tile allocator
   u32 nonfinite;            // primitives culled because a projected value was not finite
@@ -103,8 +102,7 @@ struct WsHeader {
   u32 n_active;             // primitives that touch at least one tile (depth ranks 0 .. n_active - 1)
   u32 fwd_exits, bwd_exits; // CTAs of the current compositing launch that have finished
   u32 masks_epoch;          // epoch of the last forward that recorded the composited-pair bits
-  u32 rank_chunk_counter;   // chunk allocator of the rank-order scan
-  u32 pad[9];
+  u32 pad[11];
 };
 
 // Offsets of every region of a workspace (host-computed; all 256-byte aligned).
@@ -130,8 +128,8 @@ struct WsPtrs {
   u32* rank_of;       // [n_prims] by primitive index: depth rank of an active primitive
   u64* dkeys0;        // [n_prims] depth-sort keys (depth bits - depth_base) << 32 | primitive; dkeys1 also
   u64* dkeys1;        //   holds each active primitive's key at its primitive index before the scan
-  u64* scan_status;   // [n_chunks] look-back words of the active-list scan
-  u64* rank_status;   // [n_chunks] look-back words of the rank-order scan
+  u64* scan_status;   // [n_chunks] per-chunk sums of the active-list scan
+  u64* rank_status;   // [n_chunks] per-chunk sums of the rank-order scan
   u64* keys0;         // [capacity] pairs tile << 32 | depth rank (emission order, then sort ping-pong)
   u64* keys1;
   u32* hist;          // [MAX_PASSES][RADIX]

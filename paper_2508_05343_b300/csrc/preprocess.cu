@@ -31,8 +31,6 @@ __global__ void k_setup(FrameTable tbl, WsPtrs p) {
     h->status = 0;
     h->epoch = h->epoch + 1;
     h->pairs = 0;
-    h->chunk_counter = 0;
-    h->rank_chunk_counter = 0;
     h->tile_counter_fwd = 0;
     h->tile_counter_bwd = 0;
     h->nonfinite = 0;
@@ -431,11 +429,10 @@ __device__ __forceinline__ void flat_tile(u32 j, u32 my_excl, int x0, int y0, in
 
 // Binning: (1) bin every primitive and count the tiles of its 3-sigma square that a pixel can reach
 // (warp-cooperative, no CTA barriers); a primitive with at least one such tile is active and gets a
-// depth key; (2) scan of the active flags (single pass, decoupled look-back over 4096-primitive
-// chunks) that lists the active primitives' depth keys in primitive order; (3) depth sort of that
-// list (sort.cu), whose positions are the depth ranks; (4) scan of the kept-tile counts in rank
-// order, giving each rank its first pair position; (5) emission of the kept pairs in rank order,
-// warp-cooperative.
+// depth key; (2) scan of the active flags that lists the active primitives' depth keys in primitive
+// order; (3) depth sort of that list (sort.cu), whose positions are the depth ranks; (4) scan of the
+// kept-tile counts in rank order, giving each rank its first pair position; (5) emission of the
+// kept pairs, warp-cooperative.
 
 // Per-owner counts of kept tiles over a warp's flat tile list; returns this lane's count.
 __device__ __forceinline__ u32 count_kept(u32 wsq_total, u32 my_sq_excl, int x0, int y0, int wx, const Reach& rr,
@@ -501,28 +498,33 @@ __global__ void __launch_bounds__(BLOCK) k_bin(WsPtrs p) {
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_CHUNK = BLOCK * SCAN_ITEMS;   // counts per look-back partition
 
-// Decoupled look-back of one chunk (one thread): publishes the chunk's aggregate, adds the
-// predecessors' values back to the nearest published inclusive prefix, publishes its own inclusive
-// prefix and returns the exclusive one.  Bounded: after the spin limit it sets GS_ERR_TIMEOUT (site
-// `site`) and publishes what it has, so its successors do not wait.
-__device__ u64 chunk_lookback(u64* status, u32 chunk, u32 tag, u64 agg, WsHeader* hdr, u32 site) {
-  u64* st = status + chunk;
-  if (chunk == 0) {
-    st_relaxed(st, lb_pack(LB_FLAG_PREFIX, tag, agg));
-    return 0;
-  }
-  st_relaxed(st, lb_pack(LB_FLAG_AGG, tag, agg));
-  const u64 excl = lookback_walk(status, 1, chunk, tag, hdr, site);
-  st_relaxed(st, lb_pack(LB_FLAG_PREFIX, tag, excl + agg));
-  return excl;
+// The two scans below run as reduce-then-scan: one launch writes each 4096-element chunk's sum, the
+// next adds up its chunk's predecessors directly and scans the chunk.  With about as many chunks as
+// resident CTAs, a single-pass look-back would walk back through almost every chunk before it.
+
+// Sum over the CTA of one value per thread (every thread gets the sum).
+__device__ __forceinline__ u64 block_sum(u64 v, u64* s_red /*BLOCK / 32*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  u64 t = 0;
+#pragma unroll
+  for (int w = 0; w < BLOCK / 32; ++w) t += s_red[w];
+  __syncthreads();
+  return t;
 }
 
-// Exclusive scan over the CTA of one value per thread (thread t owns SCAN_ITEMS consecutive items);
-// thread 0 runs the chunk's look-back.  Returns the thread's global exclusive prefix; the chunk's
-// exclusive prefix and total are left in s_excl / s_tot.
-__device__ __forceinline__ u64 chunk_scan(u32 sum, u32* s_warp, u64& s_excl, u64& s_tot, u64* status, u32 chunk,
-                                          u32 tag, WsHeader* hdr, u32 site) {
+// Exclusive scan over the CTA of one value per thread (thread t owns SCAN_ITEMS consecutive items),
+// offset by the sum of the partials of the chunks before `chunk`.  Returns the thread's exclusive
+// prefix; the chunk's total is left in s_tot.
+__device__ __forceinline__ u64 chunk_scan(u32 sum, const u64* partial, u32 chunk, u32* s_warp, u64* s_red,
+                                          u64& s_tot) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  u64 before = 0;
+  for (u32 c = tid; c < chunk; c += BLOCK) before += partial[c];
+  before = block_sum(before, s_red);
   u32 wtot;
   const u32 wex = warp_excl_scan(sum, lane, wtot);
   if (lane == 31) s_warp[warp] = wex + sum;
@@ -532,56 +534,62 @@ __device__ __forceinline__ u64 chunk_scan(u32 sum, u32* s_warp, u64& s_excl, u64
     u32 wt;
     const u32 wx = warp_excl_scan(wv, lane, wt);
     if (lane < BLOCK / 32) s_warp[lane] = wx;
-    if (lane == 0) {
-      s_excl = chunk_lookback(status, chunk, tag, wt, hdr, site);
-      s_tot = wt;
-    }
+    if (lane == 0) s_tot = wt;
   }
   __syncthreads();
-  return s_excl + s_warp[warp] + wex;
+  return before + s_warp[warp] + wex;
 }
 
-// (2) Active list: the primitives with at least one kept tile and their depth keys, in primitive
+// (2a) Active primitives per chunk of 4096 (partials of the active-list scan).
+__global__ void __launch_bounds__(BLOCK) k_count_active(WsPtrs p) {
+  __shared__ u64 s_red[BLOCK / 32];
+  if (read_status(p.hdr) != 0) return;
+  const u32 total = p.tbl->total_prims;
+  const u64 base = (u64)blockIdx.x * SCAN_CHUNK;
+  if (base >= total) return;
+  const u64 my0 = base + (u64)threadIdx.x * SCAN_ITEMS;
+  u32 c = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) c += (my0 + i < total && p.touched[my0 + i] > 0) ? 1u : 0u;
+  const u64 t = block_sum(c, s_red);
+  if (threadIdx.x == 0) p.scan_status[blockIdx.x] = t;
+}
+
+// (2b) Active list: the primitives with at least one kept tile and their depth keys, in primitive
 // order, and the digit counts of the depth sort.  Publishes n_active.
 __global__ void __launch_bounds__(BLOCK) k_scan_active(WsPtrs p) {
-  __shared__ u32 s_chunk;
   __shared__ u32 s_warp[BLOCK / 32];
-  __shared__ u64 s_excl, s_tot;
+  __shared__ u64 s_red[BLOCK / 32];
+  __shared__ u64 s_tot;
   __shared__ u32 s_h[DPASSES][RADIX];
   const FrameTable* tbl = p.tbl;
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
   const int tid = threadIdx.x;
-  for (int i = tid; i < DPASSES * RADIX; i += BLOCK) (&s_h[0][0])[i] = 0;
   const u32 total = tbl->total_prims;
+  const u32 chunk = blockIdx.x;
+  const u64 base = (u64)chunk * SCAN_CHUNK;
+  if (base >= total) return;
   const int need = tbl->dpasses_needed;
-  const u32 tag = hdr->epoch;
-  for (;;) {
-    if (tid == 0) s_chunk = atomicAdd(&hdr->chunk_counter, 1u);
-    __syncthreads();
-    const u32 chunk = s_chunk;
-    const u64 base = (u64)chunk * SCAN_CHUNK;
-    if (base >= total) break;
-    const u64 my0 = base + (u64)tid * SCAN_ITEMS;
-    u32 flags = 0;
+  for (int i = tid; i < DPASSES * RADIX; i += BLOCK) (&s_h[0][0])[i] = 0;
+  const u64 my0 = base + (u64)tid * SCAN_ITEMS;
+  u32 flags = 0;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i)
-      if (my0 + i < total && p.touched[my0 + i] > 0) flags |= 1u << i;
-    u64 key[SCAN_ITEMS];   // loaded before any store, so the loads overlap
+  for (int i = 0; i < SCAN_ITEMS; ++i)
+    if (my0 + i < total && p.touched[my0 + i] > 0) flags |= 1u << i;
+  u64 key[SCAN_ITEMS];   // loaded before any store, so the loads overlap
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) key[i] = (flags >> i) & 1u ? p.dkeys1[my0 + i] : 0ull;
-    u64 run = chunk_scan((u32)__popc(flags), s_warp, s_excl, s_tot, p.scan_status, chunk, tag, hdr, 1);
-    if (tid == 0 && base + SCAN_CHUNK >= total) hdr->n_active = (u32)(s_excl + s_tot);
+  for (int i = 0; i < SCAN_ITEMS; ++i) key[i] = (flags >> i) & 1u ? p.dkeys1[my0 + i] : 0ull;
+  u64 run = chunk_scan((u32)__popc(flags), p.scan_status, chunk, s_warp, s_red, s_tot);
+  if (tid == 0 && base + SCAN_CHUNK >= total) hdr->n_active = (u32)(run + s_tot);   // thread 0's prefix is the chunk's
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-      if ((flags >> i) & 1u) {
-        p.active[run] = (u32)(my0 + i);
-        p.dkeys0[run++] = key[i];
-        for (int ps = 0; ps < need; ++ps)
-          atomicAdd(&s_h[ps][(u32)(key[i] >> (32 + RADIX_BITS * ps)) & (RADIX - 1)], 1u);
-      }
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    if ((flags >> i) & 1u) {
+      p.active[run] = (u32)(my0 + i);
+      p.dkeys0[run++] = key[i];
+      for (int ps = 0; ps < need; ++ps)
+        atomicAdd(&s_h[ps][(u32)(key[i] >> (32 + RADIX_BITS * ps)) & (RADIX - 1)], 1u);
     }
-    __syncthreads();
   }
   __syncthreads();
   for (int i = tid; i < need * RADIX; i += BLOCK) {
@@ -590,53 +598,65 @@ __global__ void __launch_bounds__(BLOCK) k_scan_active(WsPtrs p) {
   }
 }
 
-// (4) Rank order: order[r] = the primitive of depth rank r, rank_of[order[r]] = r, offsets[r] = its
+// (4a) Kept tiles per chunk of 4096 depth ranks (partials of the rank-order scan).
+__global__ void __launch_bounds__(BLOCK) k_count_ranked(WsPtrs p) {
+  __shared__ u64 s_red[BLOCK / 32];
+  if (read_status(p.hdr) != 0) return;
+  const u32 total = p.hdr->n_active;
+  const u64 base = (u64)blockIdx.x * SCAN_CHUNK;
+  if (base >= total) return;
+  const u64* __restrict__ sorted = (p.tbl->dpasses_needed & 1) ? p.dkeys1 : p.dkeys0;
+  const u64 my0 = base + (u64)threadIdx.x * SCAN_ITEMS;
+  u32 gi[SCAN_ITEMS], c = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) gi[i] = my0 + i < total ? (u32)sorted[my0 + i] : 0xFFFFFFFFu;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) c += gi[i] != 0xFFFFFFFFu ? p.touched[gi[i]] : 0u;
+  const u64 t = block_sum(c, s_red);
+  if (threadIdx.x == 0) p.rank_status[blockIdx.x] = t;
+}
+
+// (4b) Rank order: order[r] = the primitive of depth rank r, rank_of[order[r]] = r, offsets[r] = its
 // first pair position (exclusive scan of the kept-tile counts in rank order).  Publishes the pair
 // count and checks the pair capacity.
 __global__ void __launch_bounds__(BLOCK) k_scan_ranked(WsPtrs p) {
-  __shared__ u32 s_chunk;
   __shared__ u32 s_warp[BLOCK / 32];
-  __shared__ u64 s_excl, s_tot;
+  __shared__ u64 s_red[BLOCK / 32];
+  __shared__ u64 s_tot;
   const FrameTable* tbl = p.tbl;
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
   const int tid = threadIdx.x;
   const u32 total = hdr->n_active;
+  const u32 chunk = blockIdx.x;
+  const u64 base = (u64)chunk * SCAN_CHUNK;
+  if (base >= total) return;
   const u64* __restrict__ sorted = (tbl->dpasses_needed & 1) ? p.dkeys1 : p.dkeys0;
-  const u32 tag = hdr->epoch;
-  for (;;) {
-    if (tid == 0) s_chunk = atomicAdd(&hdr->rank_chunk_counter, 1u);
-    __syncthreads();
-    const u32 chunk = s_chunk;
-    const u64 base = (u64)chunk * SCAN_CHUNK;
-    if (base >= total) break;
-    const u64 my0 = base + (u64)tid * SCAN_ITEMS;
-    // all loads first (keys, then the counts they index), then the stores: the loads overlap
-    u32 gi[SCAN_ITEMS], v[SCAN_ITEMS], sum = 0;
+  const u64 my0 = base + (u64)tid * SCAN_ITEMS;
+  // all loads first (keys, then the counts they index), then the stores: the loads overlap
+  u32 gi[SCAN_ITEMS], v[SCAN_ITEMS], sum = 0;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) gi[i] = my0 + i < total ? (u32)sorted[my0 + i] : 0xFFFFFFFFu;
+  for (int i = 0; i < SCAN_ITEMS; ++i) gi[i] = my0 + i < total ? (u32)sorted[my0 + i] : 0xFFFFFFFFu;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) v[i] = gi[i] != 0xFFFFFFFFu ? p.touched[gi[i]] : 0u;
+  for (int i = 0; i < SCAN_ITEMS; ++i) v[i] = gi[i] != 0xFFFFFFFFu ? p.touched[gi[i]] : 0u;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-      sum += v[i];
-      if (gi[i] != 0xFFFFFFFFu) {
-        p.order[my0 + i] = gi[i];
-        p.rank_of[gi[i]] = (u32)(my0 + i);
-      }
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    sum += v[i];
+    if (gi[i] != 0xFFFFFFFFu) {
+      p.order[my0 + i] = gi[i];
+      p.rank_of[gi[i]] = (u32)(my0 + i);
     }
-    u64 run = chunk_scan(sum, s_warp, s_excl, s_tot, p.rank_status, chunk, tag, hdr, 2);
-    if (tid == 0 && base + SCAN_CHUNK >= total) {   // last chunk: publish the pair count
-      const u64 P = s_excl + s_tot;
-      hdr->pairs = P;
-      if (P > p.capacity) set_status(hdr, GS_ERR_CAPACITY);
-    }
+  }
+  u64 run = chunk_scan(sum, p.rank_status, chunk, s_warp, s_red, s_tot);
+  if (tid == 0 && base + SCAN_CHUNK >= total) {   // last chunk: publish the pair count
+    const u64 P = run + s_tot;                      // thread 0's prefix is the chunk's
+    hdr->pairs = P;
+    if (P > p.capacity) set_status(hdr, GS_ERR_CAPACITY);
+  }
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-      if (my0 + i < total) p.offsets[my0 + i] = (u32)run;
-      run += v[i];
-    }
-    __syncthreads();
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    if (my0 + i < total) p.offsets[my0 + i] = (u32)run;
+    run += v[i];
   }
 }
 
@@ -1039,20 +1059,21 @@ cudaError_t launch_setup(const FrameTable& tbl, const WsPtrs& p, const Launch& L
 
 template <int K, int ST>
 static cudaError_t launch_pre_t(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
-  static int bgrid = 0, sgrid = 0, qgrid = 0, egrid = 0, rgrid = 0;
+  static int bgrid = 0, egrid = 0, rgrid = 0;
   if (!bgrid) bgrid = persistent_grid(k_bin, BLOCK, 0, L.sm_count);
-  if (!sgrid) sgrid = persistent_grid(k_scan_active, BLOCK, 0, L.sm_count);
-  if (!qgrid) qgrid = persistent_grid(k_scan_ranked, BLOCK, 0, L.sm_count);
   if (!egrid) egrid = persistent_grid(k_emit, BLOCK, 0, L.sm_count);
   if (!rgrid) rgrid = persistent_grid(k_records<K, ST>, BLOCK, 0, L.sm_count);
   const int need = (int)((tbl.launch_prims + BLOCK - 1) / BLOCK);
   const int schunks = (int)((tbl.launch_prims + SCAN_CHUNK - 1) / SCAN_CHUNK);
   auto clampg = [](int g, int cap) { return g < 1 ? 1 : (g > cap ? cap : g); };
   k_bin<<<clampg(need, bgrid), BLOCK, 0, L.stream>>>(p);
-  k_scan_active<<<clampg(schunks, sgrid), BLOCK, 0, L.stream>>>(p);
+  const int sg = schunks < 1 ? 1 : schunks;   // one CTA per chunk (CTAs past the data return)
+  k_count_active<<<sg, BLOCK, 0, L.stream>>>(p);
+  k_scan_active<<<sg, BLOCK, 0, L.stream>>>(p);
   cudaError_t e = launch_depth_sort(tbl, p, L);
   if (e != cudaSuccess) return e;
-  k_scan_ranked<<<clampg(schunks, qgrid), BLOCK, 0, L.stream>>>(p);
+  k_count_ranked<<<sg, BLOCK, 0, L.stream>>>(p);
+  k_scan_ranked<<<sg, BLOCK, 0, L.stream>>>(p);
   k_emit<<<clampg(need, egrid), BLOCK, 0, L.stream>>>(p);
   k_records<K, ST><<<clampg(need, rgrid), BLOCK, 0, L.stream>>>(p);
   return cudaGetLastError();

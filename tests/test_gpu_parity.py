@@ -356,7 +356,7 @@ def test_bounded_lookback_wait_reports_timeout():
     r, pt, _, _ = gpu_render(prims, cam, gc)
     assert r.views()["pairs"] > 2 * 4096
     B.gabsplat_preprocess(r.frame, B.make_prims(pt), B.make_camera(cam), gc)
-    TILE_SORT_COUNTER0 = 48     # byte offset of the first tile pass's partition counter in the header
+    TILE_SORT_COUNTER0 = 44     # byte offset of the first tile pass's partition counter in the header
     r.ws[TILE_SORT_COUNTER0:TILE_SORT_COUNTER0 + 4].view(torch.int32).fill_(1)
     B.gabsplat_bin_sort(r.frame)
     st, _ = r.status()
