@@ -37,19 +37,40 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_loss_partial(const float* __re
   const double invN = 1.0 / (double)count;
   const float invNf = (float)invN;                   // = (float)(+-1.0 * invN): the same dL bits
   float s = 0.f, c = 0.f;
-  const long long stride = (long long)gridDim.x * LOSS_THREADS;
-  for (long long i = (long long)blockIdx.x * LOSS_THREADS + threadIdx.x; i < count; i += stride) {
-    const float d = __fsub_rn(img[i], tgt[i]);
+  // one value: |d| (L1) or d^2 (L2, with the product's rounding error) into the compensated sum
+  auto one = [&](float x, float y) -> float {
+    const float d = __fsub_rn(x, y);
     if (kind == GS_LOSS_L1) {
       add_compensated(s, c, fabsf(d));
-      dL[i] = d > 0.f ? invNf : (d < 0.f ? -invNf : 0.f);
-    } else {
-      const float p = __fmul_rn(d, d);
-      add_compensated(s, c, p);
-      c = __fadd_rn(c, __fmaf_rn(d, d, -p));
-      dL[i] = (float)(2.0 * (double)d * invN);
+      return d > 0.f ? invNf : (d < 0.f ? -invNf : 0.f);
     }
+    const float p = __fmul_rn(d, d);
+    add_compensated(s, c, p);
+    c = __fadd_rn(c, __fmaf_rn(d, d, -p));
+    return (float)(2.0 * (double)d * invN);
+  };
+  const long long stride = (long long)gridDim.x * LOSS_THREADS;
+  const long long i0 = (long long)blockIdx.x * LOSS_THREADS + threadIdx.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(img) | reinterpret_cast<uintptr_t>(tgt) |
+                     reinterpret_cast<uintptr_t>(dL)) & 15) == 0;
+  long long done = 0;
+  if (vec) {   // 16-byte loads and stores over the whole float4s
+    const long long n4 = count / 4;
+    const float4* a4 = reinterpret_cast<const float4*>(img);
+    const float4* b4 = reinterpret_cast<const float4*>(tgt);
+    float4* g4 = reinterpret_cast<float4*>(dL);
+    for (long long i = i0; i < n4; i += stride) {
+      const float4 a = __ldg(a4 + i), b = __ldg(b4 + i);
+      float4 g;
+      g.x = one(a.x, b.x);
+      g.y = one(a.y, b.y);
+      g.z = one(a.z, b.z);
+      g.w = one(a.w, b.w);
+      g4[i] = g;
+    }
+    done = 4 * n4;
   }
+  for (long long i = done + i0; i < count; i += stride) dL[i] = one(img[i], tgt[i]);
   const double t = cta_sum<LOSS_THREADS>((double)s + (double)c, s_warp);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
