@@ -79,22 +79,43 @@ __device__ __forceinline__ float gauss_power(const float4& h0, const float4& h1,
   return __fmaf_rn(dx, __fmaf_rn(h0.z, dx, __fmul_rn(h0.w, dy)), __fmul_rn(__fmul_rn(h1.x, dy), dy));
 }
 
-// Phase 2 pi f2D . d (radians) from the staged (2 pi f2D_x, 2 pi f2D_y).  FAST: as it is;
-// otherwise reduced to [-pi, pi] through cycles, cos(2 pi t) = cos(2 pi (t - rint(t))).
+// Envelope exponents of a thread's PPT pixels (rows y .. y + PPT - 1 of one column, offsets dx and
+// dy[q] from the mean): row q + 1 follows row q by the recurrence pw(dy + 1) = pw(dy) + B' dx +
+// C' (2 dy + 1).  The forward and the backward both use it, so they take the same decisions.
+template <int PPT>
+__device__ __forceinline__ void pixel_powers(const float4& h0, const float4& h1, float dx, float dy0, float* dy,
+                                             float* pw) {
+  dy[0] = dy0;
+  pw[0] = gauss_power(h0, h1, dx, dy0);
+  const float bdx = __fmul_rn(h0.w, dx);
+#pragma unroll
+  for (int q = 1; q < PPT; ++q) {
+    dy[q] = __fadd_rn(dy[q - 1], 1.f);
+    pw[q] = __fadd_rn(pw[q - 1], __fmaf_rn(h1.x, __fmaf_rn(2.f, dy[q - 1], 1.f), bdx));
+  }
+}
+
+// Phase 2 pi f2D . d (radians) of a thread's first pixel from the staged (2 pi f2D_x, 2 pi f2D_y);
+// each further row adds 2 pi f2D_y.
+__device__ __forceinline__ float raw_phase(float Fx, float Fy, float dx, float dy) {
+  return __fmaf_rn(Fx, dx, __fmul_rn(Fy, dy));
+}
+
+// FAST: the phase as it is; otherwise reduced to [-pi, pi] through cycles,
+// cos(2 pi t) = cos(2 pi (t - rint(t))).
 template <bool FAST>
-__device__ __forceinline__ float phase_angle(float Fx, float Fy, float dx, float dy) {
-  const float th = __fmaf_rn(Fx, dx, __fmul_rn(Fy, dy));
+__device__ __forceinline__ float reduced_angle(float th) {
   if (FAST) return th;
   const float t = __fmul_rn(th, INV_TWO_PI);
   return __fmul_rn(TWO_PI, __fsub_rn(t, rintf(t)));
 }
 
-// Filter bank (1 - sum w) + sum w_i cos(2 pi f2D_i . d)  (Sec. 3.3.2, Eq. 9)
+// Filter bank (1 - sum w) + sum w_i cos(2 pi f2D_i . d)  (Sec. 3.3.2, Eq. 9) from the phases.
 template <int K, bool FAST>
-__device__ __forceinline__ float filter_bank(const float* r, float w0, float dx, float dy) {
+__device__ __forceinline__ float filter_bank(const float* th, const float* w, float w0) {
   float bank = w0;
 #pragma unroll
-  for (int i = 0; i < K; ++i) bank = __fmaf_rn(r[2 * K + i], __cosf(phase_angle<FAST>(r[2 * i], r[2 * i + 1], dx, dy)), bank);
+  for (int i = 0; i < K; ++i) bank = __fmaf_rn(w[i], __cosf(reduced_angle<FAST>(th[i])), bank);
   return bank;
 }
 
@@ -196,7 +217,7 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
     const int2 pxy = thread_pixel<PPT>(tx, ty, tid);
     const int px = pxy.x, py0 = pxy.y;
     const uint2 rg = p.ranges[tile];
-    const float fpx = (float)px + 0.5f;
+    const float fpx = (float)px + 0.5f, fpy0 = (float)py0 + 0.5f;
     float T[PPT], C0[PPT], C1[PPT], C2[PPT];
     u32 last[PPT], evaluated[PPT], reached[PPT], composited[PPT];
     bool done[PPT];
@@ -233,18 +254,29 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
         const float4 h0 = r[0], h1 = r[1];
         const bool fast = reinterpret_cast<const float*>(r)[11] != 0.f;   // the same for every lane
         const float dx = __fsub_rn(fpx, h0.x);
-        bool comp = false;
-        tdone = true;
+        float dyq[PPT], pwq[PPT];
+        pixel_powers<PPT>(h0, h1, dx, __fsub_rn(fpy0, h0.y), dyq, pwq);
+        bool reach[PPT], any = false;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
-          if (!done[q]) {
-            const float dy = __fsub_rn((float)(py0 + q) + 0.5f, h0.y);
-            const float pw = gauss_power(h0, h1, dx, dy);
-            if (pw >= h1.y) {
+          reach[q] = !done[q] && pwq[q] >= h1.y;
+          any = any || reach[q];
+        }
+        bool comp = false;
+        if (any) {
+          const float* fr = reinterpret_cast<const float*>(r + 3);
+          float th[K > 0 ? K : 1];
+#pragma unroll
+          for (int i = 0; i < K; ++i) th[i] = raw_phase(fr[2 * i], fr[2 * i + 1], dx, dyq[0]);
+#pragma unroll
+          for (int q = 0; q < PPT; ++q) {
+            if (q > 0)
+#pragma unroll
+              for (int i = 0; i < K; ++i) th[i] = __fadd_rn(th[i], fr[2 * i + 1]);
+            if (reach[q]) {
               ++reached[q];
-              const float G = ex2_approx(pw);
-              const float* fr = reinterpret_cast<const float*>(r + 3);
-              const float bank = fast ? filter_bank<K, true>(fr, h1.w, dx, dy) : filter_bank<K, false>(fr, h1.w, dx, dy);
+              const float G = ex2_approx(pwq[q]);
+              const float bank = fast ? filter_bank<K, true>(th, fr + 2 * K, h1.w) : filter_bank<K, false>(th, fr + 2 * K, h1.w);
               const float alpha = fminf(amax, __fmul_rn(__fmul_rn(h1.z, G), bank));
               if (alpha >= amin) {
                 const float test = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
@@ -265,8 +297,10 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
               }
             }
           }
-          tdone = tdone && done[q];
         }
+        tdone = true;
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) tdone = tdone && done[q];
         if (masks) {
           const u32 b = __ballot_sync(0xffffffffu, comp);
           const u32 gpos = start + (u32)j;
@@ -392,7 +426,7 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p,
     const int2 pxy = thread_pixel<PPT>(tx, ty, tid);
     const int px = pxy.x, py0 = pxy.y;
     const uint2 rg = p.ranges[tile];
-    const float fpx = (float)px + 0.5f;
+    const float fpx = (float)px + 0.5f, fpy0 = (float)py0 + 0.5f;
     const float* gsrc = dL_drgb ? dL_drgb : V.dL_drgb;
     const size_t hw = (size_t)V.width * V.height;
     float T[PPT], Tfin[PPT], g0[PPT], g1[PPT], g2[PPT], bgdot[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
@@ -464,18 +498,26 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p,
         const float dx = __fsub_rn(fpx, h0.x);
         // the per-pixel work, instantiated for records with and without phase reduction
         auto pixels = [&](auto fast_tag) {
+        float dyq[PPT], pwq[PPT];
+        pixel_powers<PPT>(h0, h1, dx, __fsub_rn(fpy0, h0.y), dyq, pwq);
+        float th[K > 0 ? K : 1];   // raw phases of the current row (the forward's recurrence)
+#pragma unroll
+        for (int i = 0; i < K; ++i) th[i] = raw_phase(fw[2 * i], fw[2 * i + 1], dx, dyq[0]);
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
+          if (q > 0)
+#pragma unroll
+            for (int i = 0; i < K; ++i) th[i] = __fadd_rn(th[i], fw[2 * i + 1]);
           if (pos >= last[q]) continue;
-          const float dy = __fsub_rn((float)(py0 + q) + 0.5f, h0.y);
-          const float pw = gauss_power(h0, h1, dx, dy);
+          const float dy = dyq[q];
+          const float pw = pwq[q];
           if (pw < h1.y) continue;
           const float G = ex2_approx(pw);
           float cs[K > 0 ? K : 1], sn[K > 0 ? K : 1];
           float bank = h1.w;
 #pragma unroll
           for (int i = 0; i < K; ++i) {
-            const float ang = phase_angle<decltype(fast_tag)::value>(fw[2 * i], fw[2 * i + 1], dx, dy);
+            const float ang = reduced_angle<decltype(fast_tag)::value>(th[i]);
             cs[i] = __cosf(ang);
             sn[i] = __sinf(ang);
           }
