@@ -395,36 +395,49 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, u32 ro
   for (int i = 0; i < rec_floats(K) / 4; ++i) dst[i] = make_float4(rec[4 * i], rec[4 * i + 1], rec[4 * i + 2], rec[4 * i + 3]);
 }
 
-// Entry j of a warp's flat list of 3-sigma-square tiles (owner lanes in order, tiles row-major):
-// the owner lane (largest lane whose exclusive start <= j), the tile and the owner's reach
-// parameters.  Every lane takes part in the shuffles.
+// A warp's owners (one per lane) for the flat walk over their 3-sigma squares, staged in shared
+// memory once per group of 32 primitives so each walk step reads its owner's fields with vector
+// loads.  m = floor((2^32 - 1) / wx): local / wx is umulhi(local, m), or one more (one correction
+// step; exact for every local < 2^32).
+struct __align__(16) Owner {
+  float mux, muy, A, C, kx, ky, B2, thr;   // Reach
+  u32 excl, xy0, wx, m;                    // xy0 = x0 | y0 << 16 (tile coordinates < 2^16)
+  u32 off, rank, tile_base, tiles_x;       // emission: first pair position, depth rank, view tiling
+};
+__device__ __forceinline__ void stage_owner(Owner& o, u32 excl, int x0, int y0, int wx, const Reach& r, u32 off,
+                                            u32 rank, u32 tile_base, int tiles_x) {
+  o.mux = r.mux; o.muy = r.muy; o.A = r.A; o.C = r.C; o.kx = r.kx; o.ky = r.ky; o.B2 = r.B2; o.thr = r.thr;
+  o.excl = excl; o.xy0 = (u32)x0 | ((u32)y0 << 16); o.wx = (u32)wx; o.m = 0xFFFFFFFFu / (u32)wx;
+  o.off = off; o.rank = rank; o.tile_base = tile_base; o.tiles_x = (u32)tiles_x;
+}
+
+// Entry j of the warp's flat list of 3-sigma-square tiles (owner lanes in order, tiles row-major):
+// the owner lane (largest lane whose exclusive start <= j), its tile and reach parameters.  Every
+// lane takes part in the shuffles.
 struct FlatTile {
   int owner, tx, ty;
   Reach r;
 };
-__device__ __forceinline__ void flat_tile(u32 j, u32 my_excl, int x0, int y0, int wx, const Reach& rr, FlatTile& f) {
+__device__ __forceinline__ void flat_tile(u32 j, u32 my_excl, const Owner* own, FlatTile& f) {
   int lo = 0;
 #pragma unroll
   for (int step = 16; step > 0; step >>= 1) {
     const int cand = lo + step;
     if (__shfl_sync(0xffffffffu, my_excl, cand) <= j) lo = cand;
   }
-  const u32 o_excl = __shfl_sync(0xffffffffu, my_excl, lo);
-  const int ox0 = __shfl_sync(0xffffffffu, x0, lo), oy0 = __shfl_sync(0xffffffffu, y0, lo);
-  const int owx = __shfl_sync(0xffffffffu, wx, lo);
-  f.r.mux = __shfl_sync(0xffffffffu, rr.mux, lo);
-  f.r.muy = __shfl_sync(0xffffffffu, rr.muy, lo);
-  f.r.A = __shfl_sync(0xffffffffu, rr.A, lo);
-  f.r.C = __shfl_sync(0xffffffffu, rr.C, lo);
-  f.r.kx = __shfl_sync(0xffffffffu, rr.kx, lo);
-  f.r.ky = __shfl_sync(0xffffffffu, rr.ky, lo);
-  f.r.B2 = __shfl_sync(0xffffffffu, rr.B2, lo);
-  f.r.thr = __shfl_sync(0xffffffffu, rr.thr, lo);
-  const u32 local = j - o_excl;
-  const u32 ry = local / (u32)owx;
+  const Owner& o = own[lo];
+  f.r.mux = o.mux; f.r.muy = o.muy; f.r.A = o.A; f.r.C = o.C;
+  f.r.kx = o.kx; f.r.ky = o.ky; f.r.B2 = o.B2; f.r.thr = o.thr;
+  const u32 local = j - o.excl;
+  u32 ry = __umulhi(local, o.m);
+  u32 rx = local - ry * o.wx;
+  if (rx >= o.wx) {
+    ++ry;
+    rx -= o.wx;
+  }
   f.owner = lo;
-  f.ty = oy0 + (int)ry;
-  f.tx = ox0 + (int)(local - ry * (u32)owx);
+  f.ty = (int)((o.xy0 >> 16) + ry);
+  f.tx = (int)((o.xy0 & 0xFFFFu) + rx);
 }
 
 // Binning: (1) bin every primitive and count the tiles of its 3-sigma square that a pixel can reach
@@ -436,13 +449,14 @@ __device__ __forceinline__ void flat_tile(u32 j, u32 my_excl, int x0, int y0, in
 
 // Per-owner counts of kept tiles over a warp's flat tile list; returns this lane's count.
 __device__ __forceinline__ u32 count_kept(u32 wsq_total, u32 my_sq_excl, int x0, int y0, int wx, const Reach& rr,
-                                          u32* s_cnt, int lane) {
+                                          u32* s_cnt, Owner* own, int lane) {
   s_cnt[lane] = 0;
+  stage_owner(own[lane], my_sq_excl, x0, y0, wx, rr, 0u, 0u, 0u, 1);
   __syncwarp();
   for (u32 base = 0; base < wsq_total; base += 32) {
     const u32 j = base + lane;
     FlatTile ft;
-    flat_tile(j, my_sq_excl, x0, y0, wx, rr, ft);
+    flat_tile(j, my_sq_excl, own, ft);
     const bool kept = j < wsq_total && tile_reached(ft.r, ft.tx, ft.ty);
     const u32 ballot = __ballot_sync(0xffffffffu, kept);
     const u32 peers = __match_any_sync(0xffffffffu, j < wsq_total ? ft.owner : 32 + lane);
@@ -465,6 +479,7 @@ __device__ __forceinline__ u32 warp_excl_scan(u32 v, int lane, u32& total) {
 
 __global__ void __launch_bounds__(BLOCK) k_bin(WsPtrs p) {
   __shared__ u32 s_cnt[BLOCK / 32][32];
+  __shared__ Owner s_own[BLOCK / 32][32];
   const FrameTable* tbl = p.tbl;
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
@@ -486,7 +501,8 @@ __global__ void __launch_bounds__(BLOCK) k_bin(WsPtrs p) {
     }
     u32 wsq_total;
     const u32 my_sq_excl = warp_excl_scan(sq, lane, wsq_total);
-    const u32 cnt = count_kept(wsq_total, my_sq_excl, x0, y0, wx, rr, s_cnt[warp], lane);
+    const u32 cnt = count_kept(wsq_total, my_sq_excl, x0, y0, wx, rr, s_cnt[warp], s_own[warp], lane);
+    __syncwarp();   // the owner table is restaged by the next group
     if (gi < total) {
       p.touched[gi] = cnt;
       // depth in (znear, zfar]: its float bits minus bits(znear) lie in [1, 2^depth_bits)
@@ -666,6 +682,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan_ranked(WsPtrs p) {
 // index among the owner's kept tiles (row-major).
 __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
   __shared__ u32 s_run[BLOCK / 32][32];
+  __shared__ Owner s_own[BLOCK / 32][32];
   const FrameTable* tbl = p.tbl;
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
@@ -687,22 +704,20 @@ __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
     u32 wsq_total;
     const u32 my_sq_excl = warp_excl_scan(sq, lane, wsq_total);
     s_run[warp][lane] = 0;
+    stage_owner(s_own[warp][lane], my_sq_excl, x0, y0, wx, rr, off, rank, tile_base, tiles_x);
     __syncwarp();
     for (u32 base = 0; base < wsq_total; base += 32) {
       const u32 j = base + lane;
       FlatTile ft;
-      flat_tile(j, my_sq_excl, x0, y0, wx, rr, ft);
+      flat_tile(j, my_sq_excl, s_own[warp], ft);
       const bool kept = j < wsq_total && tile_reached(ft.r, ft.tx, ft.ty);
       const u32 ballot = __ballot_sync(0xffffffffu, kept);
       const u32 peers = __match_any_sync(0xffffffffu, j < wsq_total ? ft.owner : 32 + lane);
-      const u32 ooff = __shfl_sync(0xffffffffu, off, ft.owner);
-      const u32 orank = __shfl_sync(0xffffffffu, rank, ft.owner);
-      const u32 otb = __shfl_sync(0xffffffffu, tile_base, ft.owner);
-      const int otx = __shfl_sync(0xffffffffu, tiles_x, ft.owner);
       const u32 run = j < wsq_total ? s_run[warp][ft.owner] : 0u;
       if (kept) {
-        const u64 pos = (u64)ooff + run + __popc(ballot & peers & lt);
-        if (pos < p.capacity) p.keys0[pos] = ((u64)(otb + (u32)ft.ty * (u32)otx + (u32)ft.tx) << 32) | orank;
+        const Owner& o = s_own[warp][ft.owner];
+        const u64 pos = (u64)o.off + run + __popc(ballot & peers & lt);
+        if (pos < p.capacity) p.keys0[pos] = ((u64)(o.tile_base + (u32)ft.ty * o.tiles_x + (u32)ft.tx) << 32) | o.rank;
       }
       __syncwarp();
       if (j < wsq_total && lane == __ffs(peers) - 1) s_run[warp][ft.owner] = run + __popc(ballot & peers);
