@@ -180,6 +180,29 @@ def test_config1_gradients_vs_oracle_analytic():
     assert not bad, f"gradient rel-L2 above {GRAD_TOL}: {bad} (all: {errs})"
 
 
+def test_backward_writes_every_gradient_row():
+    """Gradients are overwritten, not accumulated: with every output pre-filled with NaN, primitives
+    that reach no tile get exact zeros and every other row is finite (one kernel writes both)."""
+    from paper_2508_05343_b300 import raster
+    prims, cam = scenes.config_scene(1), scenes.config_cameras(1)[0]
+    _, gc = cfg_pair()
+    r, _, _, _ = gpu_render(prims, cam, gc)
+    touched = r.views()["touched"].cpu().numpy()
+    n = prims["means"].shape[0]
+    assert 0 < (touched > 0).sum() < n
+    grads = {k: torch.full(r._keep[k].shape, float("nan"), dtype=torch.float32, device="cuda") for k in raster.ATTRS}
+    grads["means2d"] = torch.full((n, 2), float("nan"), device="cuda")
+    dL = torch.as_tensor(np.random.default_rng(5).standard_normal((3, cam["height"], cam["width"])) * 1e-3,
+                         dtype=torch.float32, device="cuda")
+    g = r.backward(dL, grads)
+    torch.cuda.synchronize()
+    for k, v in g.items():
+        a = v.float().cpu().numpy().reshape(n, -1)
+        assert np.isfinite(a).all(), k
+        assert (a[touched == 0] == 0.0).all(), k
+        assert np.abs(a[touched > 0]).sum() > 0.0, k
+
+
 def test_forward_only_render_matches_and_refuses_a_backward():
     """gabsplat_render_fwd_only gives the image of gabsplat_render_fwd; a backward of a frame whose
     only forward was forward-only reports an invalid argument instead of reading stale state."""
