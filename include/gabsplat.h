@@ -181,8 +181,8 @@ size_t gabsplat_workspace_size(int n, int K, int sh_degree, int width, int heigh
                                unsigned long long pair_capacity);
 
 /* Zero-fills the workspace (asynchronously on `stream`).  Required once after the workspace is
- * allocated (or allocate it zero-filled): the single-pass scans tag their look-back words with a
- * per-frame epoch, and a zeroed word is never mistaken for a published one. */
+ * allocated (or allocate it zero-filled): the radix sort's passes tag their look-back words with
+ * a per-frame epoch, and a zeroed word is never mistaken for a published one. */
 gs_status gabsplat_workspace_init(const gs_frame* frame, gs_stream stream);
 
 /* Stage 1, per-primitive projection (Sec. 3.1 Eq. 2, Sec. 3.3.1 Eq. 7, Sec. 3.3.2 Eq. 8):

@@ -37,8 +37,8 @@ WsLayout make_layout(u32 n_prims, int K, u32 n_tiles, u64 n_pixels, u64 capacity
   L.rank_of = take((size_t)n_prims * 4);
   L.dkeys0 = take((size_t)n_prims * 8);
   L.dkeys1 = take((size_t)n_prims * 8);
-  L.scan_status = take((size_t)(L.n_chunks ? L.n_chunks : 1) * 8);
-  L.rank_status = take((size_t)(L.n_chunks ? L.n_chunks : 1) * 8);
+  L.scan_partials = take((size_t)(L.n_chunks ? L.n_chunks : 1) * 8);
+  L.rank_partials = take((size_t)(L.n_chunks ? L.n_chunks : 1) * 8);
   L.keys0 = take((size_t)capacity * 8);
   L.keys1 = take((size_t)capacity * 8);
   L.hist = take((size_t)MAX_PASSES * RADIX * 4);
@@ -69,8 +69,8 @@ WsPtrs make_ptrs(const WsLayout& L, void* ws) {
   p.rank_of = reinterpret_cast<u32*>(b + L.rank_of);
   p.dkeys0 = reinterpret_cast<u64*>(b + L.dkeys0);
   p.dkeys1 = reinterpret_cast<u64*>(b + L.dkeys1);
-  p.scan_status = reinterpret_cast<u64*>(b + L.scan_status);
-  p.rank_status = reinterpret_cast<u64*>(b + L.rank_status);
+  p.scan_partials = reinterpret_cast<u64*>(b + L.scan_partials);
+  p.rank_partials = reinterpret_cast<u64*>(b + L.rank_partials);
   p.keys0 = reinterpret_cast<u64*>(b + L.keys0);
   p.keys1 = reinterpret_cast<u64*>(b + L.keys1);
   p.hist = reinterpret_cast<u32*>(b + L.hist);

@@ -107,7 +107,7 @@ struct WsHeader {
 
 // Offsets of every region of a workspace (host-computed; all 256-byte aligned).
 struct WsLayout {
-  size_t header, table, records, touched, offsets, order, active, rank_of, dkeys0, dkeys1, scan_status, rank_status,
+  size_t header, table, records, touched, offsets, order, active, rank_of, dkeys0, dkeys1, scan_partials, rank_partials,
       keys0, keys1,
       hist, sort_status, ranges, tile_order, cmask, T_final, n_contrib, n_eval, n_reach, n_comp, grad2d, total;
   u32 n_prims, n_tiles, n_chunks, n_parts;
@@ -128,8 +128,8 @@ struct WsPtrs {
   u32* rank_of;       // [n_prims] by primitive index: depth rank of an active primitive
   u64* dkeys0;        // [n_prims] depth-sort keys (depth bits - depth_base) << 32 | primitive; dkeys1 also
   u64* dkeys1;        //   holds each active primitive's key at its primitive index before the scan
-  u64* scan_status;   // [n_chunks] per-chunk sums of the active-list scan
-  u64* rank_status;   // [n_chunks] per-chunk sums of the rank-order scan
+  u64* scan_partials;   // [n_chunks] per-chunk sums of the active-list scan
+  u64* rank_partials;   // [n_chunks] per-chunk sums of the rank-order scan
   u64* keys0;         // [capacity] pairs tile << 32 | depth rank (emission order, then sort ping-pong)
   u64* keys1;
   u32* hist;          // [MAX_PASSES][RADIX]

@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(BLOCK) k_count_active(WsPtrs p) {
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) c += (my0 + i < total && p.touched[my0 + i] > 0) ? 1u : 0u;
   const u64 t = block_sum(c, s_red);
-  if (threadIdx.x == 0) p.scan_status[blockIdx.x] = t;
+  if (threadIdx.x == 0) p.scan_partials[blockIdx.x] = t;
 }
 
 // (2b) Active list: the primitives with at least one kept tile and their depth keys, in primitive
@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan_active(WsPtrs p) {
   u64 key[SCAN_ITEMS];   // loaded before any store, so the loads overlap
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) key[i] = (flags >> i) & 1u ? p.dkeys1[my0 + i] : 0ull;
-  u64 run = chunk_scan((u32)__popc(flags), p.scan_status, chunk, s_warp, s_red, s_tot);
+  u64 run = chunk_scan((u32)__popc(flags), p.scan_partials, chunk, s_warp, s_red, s_tot);
   if (tid == 0 && base + SCAN_CHUNK >= total) hdr->n_active = (u32)(run + s_tot);   // thread 0's prefix is the chunk's
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(BLOCK) k_count_ranked(WsPtrs p) {
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) c += gi[i] != 0xFFFFFFFFu ? p.touched[gi[i]] : 0u;
   const u64 t = block_sum(c, s_red);
-  if (threadIdx.x == 0) p.rank_status[blockIdx.x] = t;
+  if (threadIdx.x == 0) p.rank_partials[blockIdx.x] = t;
 }
 
 // (4b) Rank order: order[r] = the primitive of depth rank r, rank_of[order[r]] = r, offsets[r] = its
@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan_ranked(WsPtrs p) {
       p.rank_of[gi[i]] = (u32)(my0 + i);
     }
   }
-  u64 run = chunk_scan(sum, p.rank_status, chunk, s_warp, s_red, s_tot);
+  u64 run = chunk_scan(sum, p.rank_partials, chunk, s_warp, s_red, s_tot);
   if (tid == 0 && base + SCAN_CHUNK >= total) {   // last chunk: publish the pair count
     const u64 P = run + s_tot;                      // thread 0's prefix is the chunk's
     hdr->pairs = P;
