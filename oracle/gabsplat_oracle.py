@@ -196,46 +196,64 @@ def _tile_reachable(prims_np, prim_of, tile_x, tile_y, mux, muy, ca, cb, cc, det
     """Which (primitive, tile) pairs of the 3-sigma squares can give some pixel alpha >= alpha_min.
 
     alpha = o G(x) bank(x) <= o G(x) because the filter bank is at most 1, so a pixel needs
-    q(x) = (x - mu)^T Sigma2D^-1 (x - mu) <= 2 ln(o / alpha_min).  A tile is kept if the minimum of q
-    over the box spanned by its pixel centres is at most an upper bound of that threshold; dropping
-    the other tiles removes only pairs that every pixel skips, so the image is unchanged.  All in
-    float32, single correctly rounded operations in the written order:
-      conic = (c, -b, a) / float32(det);  x = o / alpha_min = m 2^e (frexp, m in [0.5, 1));
+    q(x) = (x - mu)^T Sigma2D^-1 (x - mu) <= 2 ln(o / alpha_min).  The set {q <= thr} is an ellipse,
+    and the pixel centres of a row of tiles lie in a horizontal strip, so the centres of that row
+    which the ellipse can reach lie in one x-interval: between the ellipse's leftmost and rightmost
+    points within the strip.  A tile is kept if its pixel-centre x-range meets that interval (in exact
+    arithmetic this is the same as its box of pixel centres meeting the ellipse); dropping the other
+    tiles removes only pairs that every pixel skips, so the image is unchanged.  thr bounds the
+    threshold from above and the interval is widened slightly, so float32 rounding keeps the rule
+    conservative.  All in float32, single correctly rounded operations in the written order:
+      conic A = c / det32, B = -b / det32, C = a / det32;  x = o / alpha_min = m 2^e (frexp);
       m2 = 2 m, t = (e - 1) LN2_UP + (m2 - 1) / sqrt(m2)  (>= ln x since ln m2 <= (m2 - 1)/sqrt m2);
-      thr = (2 t) (1 + 2^-10) + 2^-6  (margin for float32 evaluation);  o < alpha_min reaches nothing;
-      per primitive kx = (-B) / C, ky = (-B) / A, B2 = 2 B;
-      box: xl = (16 tx + 0.5) - mu_x, xh = (16 tx + 15.5) - mu_x (same for y); q_min = 0 if the box
-      holds the mean, else the least of the four edge minima, edge x = e: s = clip(kx e, yl, yh),
-      q = ((A e) e + (B2 e) s) + (C s) s; edge y = e: s = clip(ky e, xl, xh), q = ((C e) e + (B2 e) s) + (A s) s.
+      thr = (2 t) (1 + 2^-10) + 2^-6;  o < alpha_min reaches nothing;
+      per primitive: D = A C - B B;  ye = sqrt((thr A) / D), xe = sqrt((thr C) / D) (the half extents),
+      ys = ((-B) xe) / C (the y of the rightmost point; the leftmost is at -ys),
+      ye' = ye (1 + 2^-10) + 2^-8;  unless D, A, C > 0 and D, ys, ye' are finite, every tile of the
+      square is kept;
+      per row: yl = (16 ty + 0.5) - mu_y, yh = (16 ty + 15.5) - mu_y, lo = max(yl, -ye'),
+      hi = min(yh, ye'), an empty row if lo > hi;
+      x+-(y) = ((-B) y +- sqrt(max((A thr) - (D y) y, 0))) / A:  xr = x+(clip(ys, lo, hi)),
+      xl = x-(clip(-ys, lo, hi)), widened to xr' = (xr + |xr| 2^-10) + 2^-8, xl' = (xl - |xl| 2^-10) - 2^-8;
+      kept tiles tx in [ceil(((xl' + mu_x) - 15.5) / 16), floor(((xr' + mu_x) - 0.5) / 16)].
     """
     f32 = np.float32
     with np.errstate(all="ignore"):
         op = np.asarray(prims_np["opacity"], f32)
         amin = f32(cfg["alpha_min"])
         det32 = det.astype(f32)
-        A, B, Cc = (cc / det32)[prim_of], (-cb / det32)[prim_of], (ca / det32)[prim_of]
+        A, B, C = cc / det32, -cb / det32, ca / det32
         xq = op / amin
         mq, eq = np.frexp(xq)
         m2 = mq * f32(2)
         t = (eq - 1).astype(f32) * LN2_UP + (m2 - f32(1)) / np.sqrt(m2)
-        thr = ((f32(2) * t) * f32(1 + 2 ** -10) + f32(2 ** -6))[prim_of]
+        thr = (f32(2) * t) * f32(1 + 2 ** -10) + f32(2 ** -6)
+        D = A * C - B * B
+        ye = np.sqrt((thr * A) / D)
+        xe = np.sqrt((thr * C) / D)
+        ys = ((-B) * xe) / C
+        yew = ye * f32(1 + 2 ** -10) + f32(2 ** -8)
+        ok = (D > f32(0)) & (A > f32(0)) & (C > f32(0)) & np.isfinite(D) & np.isfinite(ys) & np.isfinite(yew)
+        A, B, C, D, thr, ys, yew, ok, mx, my = (v[prim_of] for v in (A, B, C, D, thr, ys, yew, ok, mux, muy))
         reach = (op >= amin)[prim_of]
-        mx, my = mux[prim_of], muy[prim_of]
-        bx, by = (tile_x * 16).astype(f32), (tile_y * 16).astype(f32)
-        xl, xh = (bx + f32(0.5)) - mx, (bx + f32(15.5)) - mx
-        yl, yh = (by + f32(0.5)) - my, (by + f32(15.5)) - my
+        by = (tile_y * 16).astype(f32)
+        lo = np.maximum((by + f32(0.5)) - my, -yew)
+        hi = np.minimum((by + f32(15.5)) - my, yew)
 
-        kx, ky, B2 = (-B) / Cc, (-B) / A, f32(2) * B
+        def x_at(y, sign):
+            root = np.sqrt(np.maximum(A * thr - (D * y) * y, f32(0)))
+            return ((-B) * y + root) / A if sign > 0 else ((-B) * y - root) / A
 
-        def edge(a_, c_, k_, e, lo, hi):
-            s = np.minimum(np.maximum(k_ * e, lo), hi)
-            return ((a_ * e) * e + (B2 * e) * s) + (c_ * s) * s
-
-        qmin = np.minimum(np.minimum(edge(A, Cc, kx, xl, yl, yh), edge(A, Cc, kx, xh, yl, yh)),
-                          np.minimum(edge(Cc, A, ky, yl, xl, xh), edge(Cc, A, ky, yh, xl, xh)))
-        inside = (xl <= 0) & (xh >= 0) & (yl <= 0) & (yh >= 0)
-        qmin = np.where(inside, f32(0), qmin)
-    return reach & (qmin <= thr)
+        xr = x_at(np.minimum(np.maximum(ys, lo), hi), +1)
+        xl = x_at(np.minimum(np.maximum(-ys, lo), hi), -1)
+        xr = (xr + np.abs(xr) * f32(2 ** -10)) + f32(2 ** -8)
+        xl = (xl - np.abs(xl) * f32(2 ** -10)) - f32(2 ** -8)
+        t_lo = np.ceil((((xl + mx) - f32(15.5)) * f32(0.0625)))
+        t_hi = np.floor((((xr + mx) - f32(0.5)) * f32(0.0625)))
+        row_ok = lo <= hi
+        tx = tile_x.astype(f32)
+        in_row = row_ok & (tx >= t_lo) & (tx <= t_hi)
+    return reach & np.where(ok, in_row, True)
 
 
 def bin_spec(prims_np: dict, cam, cfg, cull: bool = True) -> dict:

@@ -224,12 +224,18 @@ __device__ __forceinline__ void bin_spec(const ViewDesc& V, float eps2d, float m
 
 // Tiles a pixel can reach (binning specification): alpha = o G bank <= o G, so a pixel needs the
 // squared Mahalanobis distance q <= 2 ln(o / alpha_min).  thr is a float32 upper bound of that
-// (frexp and ln m <= (m - 1)/sqrt(m), plus a margin for float32 evaluation); a tile of the 3-sigma
-// square is kept when the minimum of q over the box of its pixel centres is <= thr.  Dropped tiles
-// hold only pairs that every pixel skips, so no pixel changes.  Single correctly rounded float32
-// operations in the order the oracle's specification states.
+// (frexp and ln m <= (m - 1)/sqrt(m), plus a margin for float32 evaluation).  {q <= thr} is an
+// ellipse and the pixel centres of a row of tiles lie in a horizontal strip, so the centres of the
+// row it can reach lie in one x-interval, between its leftmost and rightmost points within the
+// strip; a tile is kept when its pixel-centre x-range meets that interval (widened slightly).
+// Dropped tiles hold only pairs that every pixel skips, so no pixel changes.  Single correctly
+// rounded float32 operations in the order the oracle's specification states.
 struct Reach {
-  float mux, muy, A, C, kx, ky, B2, thr;
+  float mux, muy;   // projected mean
+  float A, B, D;    // conic (A, B, C) and D = A C - B^2
+  float thr;        // threshold on q
+  float ys;         // y of the ellipse's rightmost point (the leftmost is at -ys)
+  float yew;        // y half-extent, widened; < 0: keep every tile of the square's rows
 };
 constexpr float LN2_UP = 0.693147182464599609375f;   // the float32 just above ln 2
 constexpr float PI_SQ = 9.869604401089358f;          // pi^2
@@ -243,33 +249,51 @@ __device__ __forceinline__ bool reach_params(const BinSpec& b, float eps2d, floa
   const float m = frexpf(FDV(o, amin), &e);
   const float m2 = FM(m, 2.f);
   const float t = FA(FM((float)(e - 1), LN2_UP), FDV(FS(m2, 1.f), __fsqrt_rn(m2)));
-  r.thr = FA(FM(FM(2.f, t), 1.0009765625f), 0.015625f);
-  r.A = A;
-  r.C = C;
-  r.kx = FDV(-B, C);
-  r.ky = FDV(-B, A);
-  r.B2 = FM(2.f, B);
+  const float thr = FA(FM(FM(2.f, t), 1.0009765625f), 0.015625f);
+  const float D = FS(FM(A, C), FM(B, B));
+  const float ye = __fsqrt_rn(FDV(FM(thr, A), D));
+  const float xe = __fsqrt_rn(FDV(FM(thr, C), D));
+  const float ys = FDV(FM(-B, xe), C);
+  const float yew = FA(FM(ye, 1.0009765625f), 0.00390625f);
+  const bool ok = D > 0.f && A > 0.f && C > 0.f && isfinite(D) && isfinite(ys) && isfinite(yew);
   r.mux = b.mux;
   r.muy = b.muy;
+  r.A = A;
+  r.B = B;
+  r.D = D;
+  r.thr = thr;
+  r.ys = ys;
+  r.yew = ok ? yew : -1.f;
   return true;
 }
 
-__device__ __forceinline__ float reach_edge(float a, float c, float k, float b2, float e, float lo, float hi) {
-  const float s = fminf(fmaxf(FM(k, e), lo), hi);
-  return FA(FA(FM(FM(a, e), e), FM(FM(b2, e), s)), FM(FM(c, s), s));
+// x of the ellipse's boundary at height y: ((-B) y +- sqrt(max(A thr - (D y) y, 0))) / A.
+__device__ __forceinline__ float boundary_x(const Reach& r, float y, bool right) {
+  const float root = __fsqrt_rn(fmaxf(FS(FM(r.A, r.thr), FM(FM(r.D, y), y)), 0.f));
+  const float by = FM(-r.B, y);
+  return FDV(right ? FA(by, root) : FS(by, root), r.A);
 }
 
-__device__ __forceinline__ bool tile_reached(const Reach& r, int tx, int ty) {
-  const float bx = (float)(16 * tx), by = (float)(16 * ty);
-  const float xl = FS(FA(bx, 0.5f), r.mux), xh = FS(FA(bx, 15.5f), r.mux);
-  const float yl = FS(FA(by, 0.5f), r.muy), yh = FS(FA(by, 15.5f), r.muy);
-  if (xl <= 0.f && xh >= 0.f && yl <= 0.f && yh >= 0.f) return true;
-  const float q = fminf(fminf(reach_edge(r.A, r.C, r.kx, r.B2, xl, yl, yh), reach_edge(r.A, r.C, r.kx, r.B2, xh, yl, yh)),
-                        fminf(reach_edge(r.C, r.A, r.ky, r.B2, yl, xl, xh), reach_edge(r.C, r.A, r.ky, r.B2, yh, xl, xh)));
-  return q <= r.thr;
+// Kept tiles of row ty of a square whose columns are [x0, x1]: returns their count and sets first.
+__device__ __forceinline__ int row_tiles(const Reach& r, int ty, int x0, int x1, int& first) {
+  first = x0;
+  if (r.yew < 0.f) return x1 - x0 + 1;
+  const float by = (float)(TILE * ty);
+  const float lo = fmaxf(FS(FA(by, 0.5f), r.muy), -r.yew);
+  const float hi = fminf(FS(FA(by, TILE - 0.5f), r.muy), r.yew);
+  if (!(lo <= hi)) return 0;
+  float xr = boundary_x(r, fminf(fmaxf(r.ys, lo), hi), true);
+  float xl = boundary_x(r, fminf(fmaxf(-r.ys, lo), hi), false);
+  xr = FA(FA(xr, FM(fabsf(xr), 0.0009765625f)), 0.00390625f);
+  xl = FS(FS(xl, FM(fabsf(xl), 0.0009765625f)), 0.00390625f);
+  const float a = fmaxf(ceilf(FM(FS(FA(xl, r.mux), 15.5f), 0.0625f)), (float)x0);
+  const float b = fminf(floorf(FM(FS(FA(xr, r.mux), 0.5f), 0.0625f)), (float)x1);
+  if (!(a <= b)) return 0;
+  first = (int)a;
+  return (int)(b - a) + 1;
 }
 
-// Bin one primitive (the float32 binning specification).  Returns the touched-tile count.
+// Bin one primitive (the float32 binning specification).  Returns the rows of its 3-sigma square.
 __device__ __forceinline__ u32 bin_one(const FrameTable* tbl, u32 gi, const WsPtrs& p, int& x0, int& y0, int& wx,
                                        u32& dbits, u32& tile_base, int& tiles_x, bool& nonfinite, Reach& r) {
   const int v = view_of_prim(tbl, gi);
@@ -293,7 +317,7 @@ __device__ __forceinline__ u32 bin_one(const FrameTable* tbl, u32 gi, const WsPt
   y0 = b.y0;
   wx = b.x1 - b.x0 + 1;
   dbits = __float_as_uint(b.tz);
-  return (u32)wx * (u32)(b.y1 - b.y0 + 1);   // tiles of the 3-sigma square (culled per tile later)
+  return (u32)(b.y1 - b.y0 + 1);   // rows of the 3-sigma square (each culled to an interval later)
 }
 
 // The 2D record of one primitive that touches at least one tile (row `row`, its depth rank): conic
@@ -395,49 +419,43 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, u32 ro
   for (int i = 0; i < rec_floats(K) / 4; ++i) dst[i] = make_float4(rec[4 * i], rec[4 * i + 1], rec[4 * i + 2], rec[4 * i + 3]);
 }
 
-// A warp's owners (one per lane) for the flat walk over their 3-sigma squares, staged in shared
-// memory once per group of 32 primitives so each walk step reads its owner's fields with vector
-// loads.  m = floor((2^32 - 1) / wx): local / wx is umulhi(local, m), or one more (one correction
-// step; exact for every local < 2^32).
+// A warp's owners (one per lane) for the flat walk over the rows of their 3-sigma squares, staged in
+// shared memory once per group of 32 primitives so each walk step reads its owner's fields with
+// vector loads.
 struct __align__(16) Owner {
-  float mux, muy, A, C, kx, ky, B2, thr;   // Reach
-  u32 excl, xy0, wx, m;                    // xy0 = x0 | y0 << 16 (tile coordinates < 2^16)
-  u32 off, rank, tile_base, tiles_x;       // emission: first pair position, depth rank, view tiling
+  Reach r;
+  u32 excl, xy0, wx, pad;              // xy0 = x0 | y0 << 16 (tile coordinates < 2^16)
+  u32 off, rank, tile_base, tiles_x;   // emission: first pair position, depth rank, view tiling
 };
 __device__ __forceinline__ void stage_owner(Owner& o, u32 excl, int x0, int y0, int wx, const Reach& r, u32 off,
                                             u32 rank, u32 tile_base, int tiles_x) {
-  o.mux = r.mux; o.muy = r.muy; o.A = r.A; o.C = r.C; o.kx = r.kx; o.ky = r.ky; o.B2 = r.B2; o.thr = r.thr;
-  o.excl = excl; o.xy0 = (u32)x0 | ((u32)y0 << 16); o.wx = (u32)wx; o.m = 0xFFFFFFFFu / (u32)wx;
+  o.r = r;
+  o.excl = excl; o.xy0 = (u32)x0 | ((u32)y0 << 16); o.wx = (u32)wx; o.pad = 0;
   o.off = off; o.rank = rank; o.tile_base = tile_base; o.tiles_x = (u32)tiles_x;
 }
 
-// Entry j of the warp's flat list of 3-sigma-square tiles (owner lanes in order, tiles row-major):
-// the owner lane (largest lane whose exclusive start <= j), its tile and reach parameters.  Every
-// lane takes part in the shuffles.
-struct FlatTile {
-  int owner, tx, ty;
-  Reach r;
+// Entry j of the warp's flat list of square rows (owner lanes in order, rows top to bottom): the
+// owner lane (largest lane whose exclusive start <= j), and the number and first column of the
+// row's kept tiles.  Every lane takes part in the shuffles.
+struct FlatRow {
+  int owner, ty, first, count;
 };
-__device__ __forceinline__ void flat_tile(u32 j, u32 my_excl, const Owner* own, FlatTile& f) {
+__device__ __forceinline__ void flat_row(u32 j, u32 total, u32 my_excl, const Owner* own, FlatRow& f) {
   int lo = 0;
 #pragma unroll
   for (int step = 16; step > 0; step >>= 1) {
     const int cand = lo + step;
     if (__shfl_sync(0xffffffffu, my_excl, cand) <= j) lo = cand;
   }
-  const Owner& o = own[lo];
-  f.r.mux = o.mux; f.r.muy = o.muy; f.r.A = o.A; f.r.C = o.C;
-  f.r.kx = o.kx; f.r.ky = o.ky; f.r.B2 = o.B2; f.r.thr = o.thr;
-  const u32 local = j - o.excl;
-  u32 ry = __umulhi(local, o.m);
-  u32 rx = local - ry * o.wx;
-  if (rx >= o.wx) {
-    ++ry;
-    rx -= o.wx;
-  }
   f.owner = lo;
-  f.ty = (int)((o.xy0 >> 16) + ry);
-  f.tx = (int)((o.xy0 & 0xFFFFu) + rx);
+  f.count = 0;
+  f.first = 0;
+  f.ty = 0;
+  if (j >= total) return;
+  const Owner& o = own[lo];
+  const int x0 = (int)(o.xy0 & 0xFFFFu);
+  f.ty = (int)(o.xy0 >> 16) + (int)(j - o.excl);
+  f.count = row_tiles(o.r, f.ty, x0, x0 + (int)o.wx - 1, f.first);
 }
 
 // Binning: (1) bin every primitive and count the tiles of its 3-sigma square that a pixel can reach
@@ -447,22 +465,18 @@ __device__ __forceinline__ void flat_tile(u32 j, u32 my_excl, const Owner* own, 
 // kept-tile counts in rank order, giving each rank its first pair position; (5) emission of the
 // kept pairs, warp-cooperative.
 
-// Per-owner counts of kept tiles over a warp's flat tile list; returns this lane's count.
-__device__ __forceinline__ u32 count_kept(u32 wsq_total, u32 my_sq_excl, int x0, int y0, int wx, const Reach& rr,
+// Per-owner counts of kept tiles over the warp's flat list of square rows; returns this lane's count.
+__device__ __forceinline__ u32 count_kept(u32 rows_total, u32 my_row_excl, int x0, int y0, int wx, const Reach& rr,
                                           u32* s_cnt, Owner* own, int lane) {
   s_cnt[lane] = 0;
-  stage_owner(own[lane], my_sq_excl, x0, y0, wx, rr, 0u, 0u, 0u, 1);
+  stage_owner(own[lane], my_row_excl, x0, y0, wx, rr, 0u, 0u, 0u, 1);
   __syncwarp();
-  for (u32 base = 0; base < wsq_total; base += 32) {
-    const u32 j = base + lane;
-    FlatTile ft;
-    flat_tile(j, my_sq_excl, own, ft);
-    const bool kept = j < wsq_total && tile_reached(ft.r, ft.tx, ft.ty);
-    const u32 ballot = __ballot_sync(0xffffffffu, kept);
-    const u32 peers = __match_any_sync(0xffffffffu, j < wsq_total ? ft.owner : 32 + lane);
-    if (j < wsq_total && lane == __ffs(peers) - 1) s_cnt[ft.owner] += __popc(ballot & peers);
-    __syncwarp();
+  for (u32 base = 0; base < rows_total; base += 32) {
+    FlatRow fr;
+    flat_row(base + lane, rows_total, my_row_excl, own, fr);
+    if (fr.count > 0) atomicAdd(&s_cnt[fr.owner], (u32)fr.count);
   }
+  __syncwarp();
   return s_cnt[lane];
 }
 
@@ -493,7 +507,7 @@ __global__ void __launch_bounds__(BLOCK) k_bin(WsPtrs p) {
     u32 dbits = 0, tile_base = 0, sq = 0;
     bool nonfinite = false;
     Reach rr;
-    rr.mux = rr.muy = rr.A = rr.C = rr.kx = rr.ky = rr.B2 = rr.thr = 0.f;
+    rr.mux = rr.muy = rr.A = rr.B = rr.D = rr.thr = rr.ys = rr.yew = 0.f;
     if (gi < total) sq = bin_one(tbl, gi, p, x0, y0, wx, dbits, tile_base, tiles_x, nonfinite, rr);
     if (__any_sync(0xffffffffu, nonfinite) && lane == 0) {
       atomicAdd(&hdr->nonfinite, 1u);
@@ -677,9 +691,10 @@ __global__ void __launch_bounds__(BLOCK) k_scan_ranked(WsPtrs p) {
 }
 
 // (5) Emission over the active list (index order, so a warp's 32 primitives mix near and far ones
-// and its tile walks stay balanced): each lane re-bins its own primitive (bit-identical), the warp
-// walks the owners' squares and writes tile << 32 | rank for each kept tile at offsets[rank] + its
-// index among the owner's kept tiles (row-major).
+// and its walk stays balanced): each lane re-bins its own primitive (bit-identical), the warp walks
+// the flat list of the owners' square rows 32 at a time, gets each row's kept tiles as an interval,
+// and then writes tile << 32 | rank for the kept tiles of those 32 rows, 32 at a time, at
+// offsets[rank] + the tile's index among the owner's kept tiles (row-major).
 __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
   __shared__ u32 s_run[BLOCK / 32][32];
   __shared__ Owner s_own[BLOCK / 32][32];
@@ -688,39 +703,54 @@ __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
   if (read_status(hdr) != 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 nact = hdr->n_active;
-  const u32 lt = (1u << lane) - 1u;
   const u32 nwarps = gridDim.x * (BLOCK / 32);
   for (u32 grp = blockIdx.x * (BLOCK / 32) + warp; (u64)grp * 32 < nact; grp += nwarps) {
     const u32 ia = grp * 32 + lane;
     const u32 gi = ia < nact ? p.active[ia] : 0u;
     const u32 rank = ia < nact ? p.rank_of[gi] : 0u;
     int x0 = 0, y0 = 0, wx = 1, tiles_x = 1;
-    u32 dbits = 0, tile_base = 0, sq = 0;
+    u32 dbits = 0, tile_base = 0, rows = 0;
     bool nonfinite = false;
     Reach rr;
-    rr.mux = rr.muy = rr.A = rr.C = rr.kx = rr.ky = rr.B2 = rr.thr = 0.f;
-    if (ia < nact) sq = bin_one(tbl, gi, p, x0, y0, wx, dbits, tile_base, tiles_x, nonfinite, rr);
+    rr.mux = rr.muy = rr.A = rr.B = rr.D = rr.thr = rr.ys = rr.yew = 0.f;
+    if (ia < nact) rows = bin_one(tbl, gi, p, x0, y0, wx, dbits, tile_base, tiles_x, nonfinite, rr);
     const u32 off = ia < nact ? p.offsets[rank] : 0u;
-    u32 wsq_total;
-    const u32 my_sq_excl = warp_excl_scan(sq, lane, wsq_total);
+    u32 rows_total;
+    const u32 my_row_excl = warp_excl_scan(rows, lane, rows_total);
     s_run[warp][lane] = 0;
-    stage_owner(s_own[warp][lane], my_sq_excl, x0, y0, wx, rr, off, rank, tile_base, tiles_x);
+    stage_owner(s_own[warp][lane], my_row_excl, x0, y0, wx, rr, off, rank, tile_base, tiles_x);
     __syncwarp();
-    for (u32 base = 0; base < wsq_total; base += 32) {
-      const u32 j = base + lane;
-      FlatTile ft;
-      flat_tile(j, my_sq_excl, s_own[warp], ft);
-      const bool kept = j < wsq_total && tile_reached(ft.r, ft.tx, ft.ty);
-      const u32 ballot = __ballot_sync(0xffffffffu, kept);
-      const u32 peers = __match_any_sync(0xffffffffu, j < wsq_total ? ft.owner : 32 + lane);
-      const u32 run = j < wsq_total ? s_run[warp][ft.owner] : 0u;
-      if (kept) {
-        const Owner& o = s_own[warp][ft.owner];
-        const u64 pos = (u64)o.off + run + __popc(ballot & peers & lt);
-        if (pos < p.capacity) p.keys0[pos] = ((u64)(o.tile_base + (u32)ft.ty * o.tiles_x + (u32)ft.tx) << 32) | o.rank;
-      }
+    for (u32 base = 0; base < rows_total; base += 32) {
+      FlatRow fr;
+      flat_row(base + lane, rows_total, my_row_excl, s_own[warp], fr);
+      // this row's first pair position: the owner's kept tiles in earlier rows (earlier steps, and
+      // earlier lanes of this step)
+      u32 tot;
+      const u32 ex = warp_excl_scan((u32)fr.count, lane, tot);
+      const u32 peers = __match_any_sync(0xffffffffu, base + lane < rows_total ? fr.owner : 32 + lane);
+      const int lead = __ffs(peers) - 1;
+      const u32 pos0 = s_own[warp][fr.owner].off + s_run[warp][fr.owner] + ex - __shfl_sync(0xffffffffu, ex, lead);
       __syncwarp();
-      if (j < wsq_total && lane == __ffs(peers) - 1) s_run[warp][ft.owner] = run + __popc(ballot & peers);
+      if (fr.count > 0) atomicAdd(&s_run[warp][fr.owner], (u32)fr.count);
+      // the kept tiles of these 32 rows, one per lane
+      for (u32 e0 = 0; e0 < tot; e0 += 32) {
+        const u32 e = e0 + lane;
+        int src = 0;   // the row lane holding entry e: the largest lane whose exclusive start <= e
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int cand = src + step;
+          if (__shfl_sync(0xffffffffu, ex, cand) <= e) src = cand;
+        }
+        const u32 k = e - __shfl_sync(0xffffffffu, ex, src);
+        const int ty = __shfl_sync(0xffffffffu, fr.ty, src);
+        const int first = __shfl_sync(0xffffffffu, fr.first, src);
+        const int owner = __shfl_sync(0xffffffffu, fr.owner, src);
+        const u32 pos = __shfl_sync(0xffffffffu, pos0, src) + k;
+        if (e < tot && pos < p.capacity) {
+          const Owner& o = s_own[warp][owner];
+          p.keys0[pos] = ((u64)(o.tile_base + (u32)ty * o.tiles_x + (u32)(first + (int)k)) << 32) | o.rank;
+        }
+      }
       __syncwarp();
     }
   }

@@ -254,7 +254,9 @@ def test_z_attenuation_variant_image_records_and_gradients():
 
 def test_config1_gradients_vs_oracle_finite_differences():
     """Directional derivatives of the oracle (central differences in float64) along seeded random
-    directions that move a few primitives, against the GPU's analytic gradient."""
+    directions that move a few primitives, against the GPU's analytic gradient.  The image is not
+    smooth where a pixel's compositing decision (alpha >= alpha_min, T >= T_min) changes between the
+    two perturbed renders; a draw with such a pixel under the loss is replaced by the next one."""
     prims, cam = scenes.config_scene(1), scenes.config_cameras(1)[0]
     oc, gc = cfg_pair()
     out = O.render(prims, cam, oc)
@@ -267,7 +269,9 @@ def test_config1_gradients_vs_oracle_finite_differences():
     cand = np.nonzero((spec["touched"] > 0) & (spec["touched"] <= 6))[0]
     scale = dict(means=0.01, scales=0.005, quats=0.3, opacity=0.05, sh=0.1, freqs=0.5, weights=0.05)
     p64 = {k: (np.asarray(v, np.float64) if isinstance(v, np.ndarray) else v) for k, v in prims.items()}
-    for trial in range(3):
+    live = np.abs(dL).sum(0) > 0
+    checked = 0
+    for draw in range(12):
         ids = rng.choice(cand, 6, replace=False)
         tiles = set()
         for k in ids:
@@ -279,14 +283,21 @@ def test_config1_gradients_vs_oracle_finite_differences():
             u[k][ids] = rng.standard_normal(u[k][ids].shape) * scale[k]
         analytic = sum(float((g[k].astype(np.float64) * u[k]).sum()) for k in ATTRS)
 
-        def L(h):
+        def render(h):
             q = {k: (p64[k] + h * u[k] if k in ATTRS else p64[k]) for k in p64}
-            o = O.render(q, cam, oc, tiles=tiles)
-            return float((o["image"].numpy() * dL).sum())
+            return O.render(q, cam, oc, tiles=tiles)
 
         h = 1e-4
-        fd = (L(h) - L(-h)) / (2 * h)
-        assert abs(analytic - fd) <= GRAD_TOL * abs(fd) + 1e-9, (trial, analytic, fd)
+        op, om = render(h), render(-h)
+        flips = (op["n_comp"].numpy() != om["n_comp"].numpy()) | (op["n_contrib"].numpy() != om["n_contrib"].numpy())
+        if (flips & live).any():
+            continue
+        fd = (float((op["image"].numpy() * dL).sum()) - float((om["image"].numpy() * dL).sum())) / (2 * h)
+        assert abs(analytic - fd) <= GRAD_TOL * abs(fd) + 1e-9, (draw, analytic, fd)
+        checked += 1
+        if checked == 3:
+            break
+    assert checked == 3
 
 
 @pytest.mark.parametrize("K,storage,w,h", [(0, 0, 100, 70), (1, 0, 100, 70), (3, 0, 53, 97), (8, 0, 100, 70),
