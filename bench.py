@@ -2,8 +2,8 @@
 """Benchmark of the 3D Gabor splatting rasterizer (fwd+bwd ms/iter at 1.5M primitives, 1600x1064).
 
 One step = one training iteration of the rasterizer on one view: gabsplat_preprocess ->
-gabsplat_bin_sort -> gabsplat_render_fwd -> L1 loss -> gabsplat_render_bwd (2D adjoint, then
-the attribute chain rule), on the 1.5M-primitive, K=4, SH-degree-3 synthetic scene cycling through
+gabsplat_bin_sort -> gabsplat_render_fwd -> L1 loss -> the two halves of gabsplat_render_bwd (2D
+adjoint with the gradient zero-fill folded in, then the attribute chain rule), on the 1.5M-primitive, K=4, SH-degree-3 synthetic scene cycling through
 its 16 orbit poses.  Primitives (450 MB in float32) are larger than L2, so no flush is needed.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--storage bf16]
@@ -362,8 +362,8 @@ def run_ours(args):
     dpasses = min(4, math.ceil(dbits / 8))                   # depth-sort passes that do work (4 launched)
     # my kernels per step: setup; bin, active count + scan, 4 depth passes, rank count + scan, emit,
     # records; tile histogram + tile passes + ranges + tile schedule; render_fwd; loss (2);
-    # render_bwd; zero-fill + preprocess_bwd
-    launches_per_step = 1 + 11 + (1 + tpasses + 2) + 1 + 2 + 1 + 2
+    # grad2d clear + render_bwd (with the attribute-gradient zero-fill); preprocess_bwd
+    launches_per_step = 1 + 11 + (1 + tpasses + 2) + 1 + 2 + 2 + 1
     stage_names = ["preprocess", "bin_sort", "render_fwd", "loss", "render_bwd", "preprocess_bwd"]
 
     def pose_of(s):
@@ -384,9 +384,9 @@ def run_ours(args):
         else:
             B.gabsplat_loss_l1_dssim(img, tj, 0.2, loss_val, dL, scratch)
         if evs: evs[4].record()
-        B.gabsplat_render_bwd_2d(frame, dL)
+        B.gabsplat_render_bwd_2d_zero(frame, dL, g_s)
         if evs: evs[5].record()
-        B.gabsplat_preprocess_bwd(frame, g_s)
+        B.gabsplat_preprocess_bwd_prezeroed(frame, g_s)
         if evs: evs[6].record()
 
     def barrier():
@@ -500,8 +500,9 @@ def run_ours(args):
         "render_fwd": ("alu", n_eval * ops_eval),
         "loss": ("hbm", img.numel() * 12) if args.loss == "l1" else ("flop", img.numel() * SSIM_FLOPS_PER_VALUE),
         "render_bwd": ("alu", n_contrib * 3 * ops_eval),
-        # gradients of every primitive written (zeros for culled ones), active ones read their inputs
-        "preprocess_bwd": ("hbm", n * grad_b + n_act * (4 + param_b + g2d_b + grad_b)),
+        # active primitives read their inputs and grad2d row and write their gradients (the other
+        # rows were zero-filled inside render_bwd)
+        "preprocess_bwd": ("hbm", n_act * (4 + param_b + g2d_b + grad_b)),
     }
     top = max(stage_ms, key=stage_ms.get)
     bound, amount = work[top]

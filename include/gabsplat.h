@@ -236,10 +236,21 @@ gs_status gabsplat_render_bwd(const gs_frame* frame, const float* dL_drgb, const
                               gs_stream stream);
 
 /* The two halves of gabsplat_render_bwd, callable separately (e.g. to time them):
- * gabsplat_render_bwd_2d accumulates the per-primitive 2D gradients (workspace grad2d) from
- * dL/d(rgb); gabsplat_preprocess_bwd chains them to the attributes in gs_prim_grads. */
+ * gabsplat_render_bwd_2d clears grad2d (workspace), then accumulates the per-primitive 2D gradients
+ * from dL/d(rgb); gabsplat_preprocess_bwd zero-fills every array of gs_prim_grads, then chains
+ * grad2d to the attributes of the primitives that reach a tile. */
 gs_status gabsplat_render_bwd_2d(const gs_frame* frame, const float* dL_drgb, gs_stream stream);
 gs_status gabsplat_preprocess_bwd(const gs_frame* frame, const gs_prim_grads* grads, gs_stream stream);
+
+/* The halves that gabsplat_render_bwd itself runs.  gabsplat_render_bwd_2d_zero does what
+ * gabsplat_render_bwd_2d does and, inside the same kernel, zero-fills every array of grads (the
+ * compositing walk is bound by instruction issue, the fill by HBM writes, so the fill costs little
+ * time).  gabsplat_preprocess_bwd_prezeroed then writes only the rows of primitives that reach a
+ * tile: the other rows must already be zero, i.e. grads must be the arrays just given to
+ * gabsplat_render_bwd_2d_zero for this frame.  grads is required (GS_ERR_INVALID_ARG if NULL). */
+gs_status gabsplat_render_bwd_2d_zero(const gs_frame* frame, const float* dL_drgb, const gs_prim_grads* grads,
+                                      gs_stream stream);
+gs_status gabsplat_preprocess_bwd_prezeroed(const gs_frame* frame, const gs_prim_grads* grads, gs_stream stream);
 
 /* Photometric loss of Sec. 3.4.1 (its L1 part; L2 for gradient checks): mean over `count` values
  * of |image - target| or (image - target)^2.  Writes the loss (float64, device, 1 value) and

@@ -92,6 +92,8 @@ SIGNATURES = {
     "gabsplat_render_bwd": (C.c_int, [P_(gs_frame), C.c_void_p, P_(gs_prim_grads), C.c_void_p]),
     "gabsplat_render_bwd_2d": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p]),
     "gabsplat_preprocess_bwd": (C.c_int, [P_(gs_frame), P_(gs_prim_grads), C.c_void_p]),
+    "gabsplat_render_bwd_2d_zero": (C.c_int, [P_(gs_frame), C.c_void_p, P_(gs_prim_grads), C.c_void_p]),
+    "gabsplat_preprocess_bwd_prezeroed": (C.c_int, [P_(gs_frame), P_(gs_prim_grads), C.c_void_p]),
     "gabsplat_loss_scratch_bytes": (C.c_size_t, [C.c_longlong]),
     "gabsplat_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),
@@ -192,6 +194,16 @@ def gabsplat_render_bwd_2d(frame, dL_drgb, stream=None):
 
 def gabsplat_preprocess_bwd(frame, grads, stream=None):
     _check("gabsplat_preprocess_bwd", lib.gabsplat_preprocess_bwd(C.byref(frame), C.byref(grads), _stream(stream)))
+
+
+def gabsplat_render_bwd_2d_zero(frame, dL_drgb, grads, stream=None):
+    _check("gabsplat_render_bwd_2d_zero", lib.gabsplat_render_bwd_2d_zero(C.byref(frame), _ptr(dL_drgb),
+                                                                          C.byref(grads), _stream(stream)))
+
+
+def gabsplat_preprocess_bwd_prezeroed(frame, grads, stream=None):
+    _check("gabsplat_preprocess_bwd_prezeroed",
+           lib.gabsplat_preprocess_bwd_prezeroed(C.byref(frame), C.byref(grads), _stream(stream)))
 
 
 def gabsplat_loss_scratch_bytes(count):

@@ -262,34 +262,53 @@ gs_status gabsplat_render_freq_map(const gs_frame* frame, float* out_map, gs_str
   return from_cuda(launch_render_freq_map(t, make_ptrs(L, frame->ws), out_map, make_launch(stream)));
 }
 
-gs_status gabsplat_render_bwd_2d(const gs_frame* frame, const float* dL_drgb, gs_stream stream) {
+// The 2D adjoint (grad2d rows cleared first); with grads, the kernel also zero-fills them.
+static gs_status render_bwd_2d(const gs_frame* frame, const float* dL_drgb, const gs_prim_grads* grads,
+                               gs_stream stream) {
   FrameTable t;
   WsLayout L;
   const gs_status s = frame_meta(frame, t, L);
   if (s != GS_OK) return s;
   if (!dL_drgb) return GS_ERR_INVALID_ARG;
   const WsPtrs p = make_ptrs(L, frame->ws);
-  const Launch lc = make_launch(stream);
-  cudaError_t e = cudaMemsetAsync(p.grad2d, 0, (size_t)frame->n * L.g2d_f * sizeof(float), lc.stream);
-  if (e == cudaSuccess) e = launch_render_bwd(t, p, dL_drgb, lc);
-  return from_cuda(e);
+  if (!grads) return from_cuda(launch_render_bwd(t, p, dL_drgb, nullptr, make_launch(stream)));
+  const ZeroJob z = make_zero_job(*grads, t.v[0].n, t.K, (t.sh_degree + 1) * (t.sh_degree + 1), t.total_tiles);
+  return from_cuda(launch_render_bwd(t, p, dL_drgb, &z, make_launch(stream)));
 }
 
-gs_status gabsplat_preprocess_bwd(const gs_frame* frame, const gs_prim_grads* grads, gs_stream stream) {
+static gs_status preprocess_bwd(const gs_frame* frame, const gs_prim_grads* grads, bool prezeroed,
+                                gs_stream stream) {
   FrameTable t;
   WsLayout L;
   const gs_status s = frame_meta(frame, t, L);
   if (s != GS_OK) return s;
   if (!grads) return GS_ERR_INVALID_ARG;
-  return from_cuda(launch_preprocess_bwd(t, make_ptrs(L, frame->ws), *grads, make_launch(stream)));
+  return from_cuda(launch_preprocess_bwd(t, make_ptrs(L, frame->ws), *grads, prezeroed, make_launch(stream)));
+}
+
+gs_status gabsplat_render_bwd_2d(const gs_frame* frame, const float* dL_drgb, gs_stream stream) {
+  return render_bwd_2d(frame, dL_drgb, nullptr, stream);
+}
+
+gs_status gabsplat_preprocess_bwd(const gs_frame* frame, const gs_prim_grads* grads, gs_stream stream) {
+  return preprocess_bwd(frame, grads, false, stream);
+}
+
+gs_status gabsplat_render_bwd_2d_zero(const gs_frame* frame, const float* dL_drgb, const gs_prim_grads* grads,
+                                      gs_stream stream) {
+  if (!grads) return GS_ERR_INVALID_ARG;
+  return render_bwd_2d(frame, dL_drgb, grads, stream);
+}
+
+gs_status gabsplat_preprocess_bwd_prezeroed(const gs_frame* frame, const gs_prim_grads* grads, gs_stream stream) {
+  return preprocess_bwd(frame, grads, true, stream);
 }
 
 gs_status gabsplat_render_bwd(const gs_frame* frame, const float* dL_drgb, const gs_prim_grads* grads,
                               gs_stream stream) {
-  if (!grads) return GS_ERR_INVALID_ARG;
-  const gs_status s = gabsplat_render_bwd_2d(frame, dL_drgb, stream);
+  const gs_status s = gabsplat_render_bwd_2d_zero(frame, dL_drgb, grads, stream);
   if (s != GS_OK) return s;
-  return gabsplat_preprocess_bwd(frame, grads, stream);
+  return gabsplat_preprocess_bwd_prezeroed(frame, grads, stream);
 }
 
 size_t gabsplat_loss_scratch_bytes(long long count) {

@@ -102,7 +102,8 @@ struct WsHeader {
   u32 n_active;             // primitives that touch at least one tile (depth ranks 0 .. n_active - 1)
   u32 fwd_exits, bwd_exits; // CTAs of the current compositing launch that have finished
   u32 masks_epoch;          // epoch of the last forward that recorded the composited-pair bits
-  u32 pad[11];
+  u32 zero_counter;         // chunks of the attribute-gradient zero-fill handed out by render_bwd
+  u32 pad[10];
 };
 
 // Offsets of every region of a workspace (host-computed; all 256-byte aligned).
@@ -368,8 +369,33 @@ cudaError_t launch_bin_sort(const FrameTable& tbl, const WsPtrs& p, const Launch
 cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L,
                               bool masks);
 cudaError_t launch_render_freq_map(const FrameTable& tbl, const WsPtrs& p, float* out_map, const Launch& L);
-cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL_drgb, const Launch& L);
-cudaError_t launch_preprocess_bwd(const FrameTable& tbl, const WsPtrs& p, const gs_prim_grads& g, const Launch& L);
+// Zero-fill of the attribute gradients carried out by the compositing backward: that kernel is
+// bound by instruction issue and the fill by HBM writes, so the fill runs in its shadow.  The
+// arrays are cut into chunks of ZERO_CHUNK floats; a CTA takes `quota` chunks after each tile and
+// the rest once the tile queue is empty.
+#ifndef GS_ZERO_SPREAD_PCT
+#define GS_ZERO_SPREAD_PCT 50   // the fill is handed out by the time this share of the tiles is taken
+#endif
+constexpr int ZERO_ARRAYS = 8;
+constexpr u32 ZERO_CHUNK = 4096;
+struct ZeroJob {
+  float* a[ZERO_ARRAYS];
+  u64 n[ZERO_ARRAYS];          // floats of each array (0 for a NULL pointer)
+  u32 base[ZERO_ARRAYS + 1];   // first chunk of each array; base[ZERO_ARRAYS] = total chunks
+  u32 quota;                   // chunks per tile; 0: no fill
+};
+// The zero-fill of every array of g (n primitives, K Gabor components, nsh SH coefficients per
+// channel), spread so that it is handed out by the time GS_ZERO_SPREAD_PCT % of the ntiles tiles
+// are taken.
+ZeroJob make_zero_job(const gs_prim_grads& g, int n, int K, int nsh, u32 ntiles);
+
+// z: NULL, or a zero-fill for the kernel to carry out.
+cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL_drgb, const ZeroJob* z,
+                              const Launch& L);
+// prezeroed: the gradients of primitives that reach no tile are already zero (a ZeroJob of the
+// same arrays ran in this frame's render_bwd), so only the active primitives' rows are written.
+cudaError_t launch_preprocess_bwd(const FrameTable& tbl, const WsPtrs& p, const gs_prim_grads& g, bool prezeroed,
+                                  const Launch& L);
 cudaError_t launch_loss(const float* img, const float* tgt, long long count, int kind, double* loss_out, float* dL,
                         double* partials, int nblocks, cudaStream_t s);
 size_t l1_dssim_partials(int C, int H, int W);

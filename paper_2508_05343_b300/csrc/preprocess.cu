@@ -39,6 +39,7 @@ __global__ void k_setup(FrameTable tbl, WsPtrs p) {
     h->n_active = 0;
     h->fwd_exits = 0;
     h->bwd_exits = 0;
+    h->zero_counter = 0;
     for (int i = 0; i < MAX_PASSES; ++i) h->sort_counter[i] = 0;
   }
 }
@@ -800,6 +801,23 @@ __global__ void k_zero_grads(gs_prim_grads G, int n, int K, int nsh) {
   zero_fill(G.means2d, 2 * (size_t)n, tid, nt);
 }
 
+ZeroJob make_zero_job(const gs_prim_grads& g, int n, int K, int nsh, u32 ntiles) {
+  ZeroJob z{};
+  float* const a[ZERO_ARRAYS] = {g.means, g.scales, g.quats, g.opacity, g.sh, g.freqs, g.weights, g.means2d};
+  const u64 per[ZERO_ARRAYS] = {3, 3, 4, 1, 3 * (u64)nsh, 3 * (u64)K, (u64)K, 2};
+  u64 chunks = 0;
+  for (int i = 0; i < ZERO_ARRAYS; ++i) {
+    z.a[i] = a[i];
+    z.n[i] = a[i] && n > 0 ? per[i] * (u64)n : 0;
+    z.base[i] = (u32)chunks;
+    chunks += (z.n[i] + ZERO_CHUNK - 1) / ZERO_CHUNK;
+  }
+  z.base[ZERO_ARRAYS] = (u32)chunks;
+  const u64 spread = (u64)ntiles * GS_ZERO_SPREAD_PCT / 100 > 0 ? (u64)ntiles * GS_ZERO_SPREAD_PCT / 100 : 1;
+  z.quota = chunks ? (u32)((chunks + spread - 1) / spread) : 0;
+  return z;
+}
+
 // ------------------------------------------------------------------------------------------
 // Backward: 2D record gradients -> primitive attribute gradients (exact chain rule of the
 // forward above; clamps pass zero gradient).
@@ -1125,12 +1143,13 @@ static cudaError_t launch_pre_t(const FrameTable& tbl, const WsPtrs& p, const La
 }
 
 template <int K, int ST>
-static cudaError_t launch_pre_bwd_t(const FrameTable& tbl, const WsPtrs& p, const gs_prim_grads& g, const Launch& L) {
+static cudaError_t launch_pre_bwd_t(const FrameTable& tbl, const WsPtrs& p, const gs_prim_grads& g, bool prezeroed,
+                                    const Launch& L) {
   static int grid = 0;
   if (!grid) grid = persistent_grid(k_preprocess_bwd<K, ST>, BLOCK, 0, L.sm_count);
   const int n = tbl.v[0].n;
   const int nsh = (tbl.sh_degree + 1) * (tbl.sh_degree + 1);
-  k_zero_grads<<<L.sm_count * 4, 256, 0, L.stream>>>(g, n, K, nsh);
+  if (!prezeroed) k_zero_grads<<<L.sm_count * 4, 256, 0, L.stream>>>(g, n, K, nsh);
   int blocks = (n + BLOCK - 1) / BLOCK;
   if (blocks > grid) blocks = grid;
   if (blocks < 1) blocks = 1;
@@ -1156,8 +1175,9 @@ cudaError_t launch_preprocess(const FrameTable& tbl, const WsPtrs& p, const Laun
   GS_DISPATCH_K(tbl.K, tbl.storage, launch_pre_t, tbl, p, L)
 }
 
-cudaError_t launch_preprocess_bwd(const FrameTable& tbl, const WsPtrs& p, const gs_prim_grads& g, const Launch& L) {
-  GS_DISPATCH_K(tbl.K, tbl.storage, launch_pre_bwd_t, tbl, p, g, L)
+cudaError_t launch_preprocess_bwd(const FrameTable& tbl, const WsPtrs& p, const gs_prim_grads& g, bool prezeroed,
+                                  const Launch& L) {
+  GS_DISPATCH_K(tbl.K, tbl.storage, launch_pre_bwd_t, tbl, p, g, prezeroed, L)
 }
 
 }  // namespace gs

@@ -163,10 +163,11 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 
 // Called by thread 0 of every CTA after it has left its tile loop: the last CTA of the launch
 // resets the tile allocator, so each compositing launch of a frame starts from tile 0.
-__device__ __forceinline__ void release_tile_counter(u32* counter, u32* exits) {
+__device__ __forceinline__ void release_tile_counter(u32* counter, u32* exits, u32* counter2 = nullptr) {
   __threadfence();
   if (atomicAdd(exits, 1u) == gridDim.x - 1) {
     *counter = 0;
+    if (counter2) *counter2 = 0;
     *exits = 0;
   }
 }
@@ -379,9 +380,31 @@ __device__ __forceinline__ void flush_pair_grads(const float* a, float* dst) {
   }
 }
 
+// Chunks [c0, c0 + count) of a zero-fill, by the whole CTA: 16-byte streaming stores where the
+// array is 16-byte aligned (chunks are multiples of 4 floats), scalar stores otherwise.
+__device__ __noinline__ void zero_chunks(const ZeroJob& z, u32 c0, u32 count) {
+  const u32 total = z.base[ZERO_ARRAYS];
+  const u32 c1 = c0 < total - min(total, count) ? c0 + count : total;
+  for (u32 c = c0; c < c1; ++c) {
+    int i = 0;
+    while (c >= z.base[i + 1]) ++i;   // c < total: ends at an array that owns chunk c
+    const u64 off = (u64)(c - z.base[i]) * ZERO_CHUNK;
+    const u32 len = (u32)min((u64)ZERO_CHUNK, z.n[i] - off);
+    float* a = z.a[i] + off;
+    u32 done = 0;
+    if ((reinterpret_cast<uintptr_t>(z.a[i]) & 15u) == 0) {
+      const u32 n4 = len >> 2;
+      for (u32 j = threadIdx.x; j < n4; j += blockDim.x)
+        __stcs(reinterpret_cast<float4*>(a) + j, make_float4(0.f, 0.f, 0.f, 0.f));
+      done = 4 * n4;
+    }
+    for (u32 j = done + threadIdx.x; j < len; j += blockDim.x) a[j] = 0.f;
+  }
+}
+
 template <int K, int PPT>
-__global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p,
-                                                            const float* __restrict__ dL_drgb) {
+__global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ dL_drgb,
+                                           const __grid_constant__ ZeroJob z) {
   constexpr int NT = BLOCK / PPT;
   constexpr int F4 = SRec<K>::F4;
   constexpr int NV = 10 + 3 * K;         // gradient values per pair
@@ -398,6 +421,7 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p,
 #endif
   __shared__ u32 s_tile;
   __shared__ u32 s_max;
+  __shared__ u32 s_zc;
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
   if (hdr->masks_epoch != hdr->epoch) {   // no forward of this frame recorded the composited-pair bits
@@ -611,8 +635,24 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p,
       bend = bstart;
     }
     __syncthreads();
+    if (z.quota) {   // this tile's share of the zero-fill, issued behind its walk
+      if (tid == 0) s_zc = atomicAdd(&hdr->zero_counter, z.quota);
+      __syncthreads();
+      zero_chunks(z, s_zc, z.quota);
+    }
   }
-  if (tid == 0) release_tile_counter(&hdr->tile_counter_bwd, &hdr->bwd_exits);
+  // the tile queue is empty: the chunks still unclaimed
+  if (z.quota) {
+    for (;;) {
+      __syncthreads();   // every thread has read s_tile / s_zc of the previous round
+      if (tid == 0) s_zc = atomicAdd(&hdr->zero_counter, z.quota);
+      __syncthreads();
+      const u32 c0 = s_zc;
+      if (c0 >= z.base[ZERO_ARRAYS]) break;   // CTA-uniform
+      zero_chunks(z, c0, z.quota);
+    }
+  }
+  if (tid == 0) release_tile_counter(&hdr->tile_counter_bwd, &hdr->bwd_exits, &hdr->zero_counter);
 }
 
 template <int K, bool FMAP, bool MASKS>
@@ -638,8 +678,19 @@ static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, float* r
   return cudaGetLastError();
 }
 
+// Clears the 2D gradient rows of the n_active ranked primitives before the backward accumulates.
 template <int K>
-static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const float* dL,
+__global__ void __launch_bounds__(256) k_zero_grad2d(WsPtrs p) {
+  if (read_status(p.hdr) != 0) return;
+  static_assert(g2d_floats(K) % 4 == 0, "grad2d rows are whole float4s");
+  const size_t n4 = (size_t)p.hdr->n_active * (g2d_floats(K) / 4);
+  float4* g = reinterpret_cast<float4*>(p.grad2d);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+    g[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <int K>
+static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const float* dL, const ZeroJob* z,
                                 const Launch& L) {
   constexpr int PPT = GS_PPT_BWD, NT = BLOCK / PPT;
   static int grid = 0;
@@ -659,7 +710,9 @@ static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const fl
   int g = grid;
   if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
   if (g < 1) g = 1;
-  k_render_bwd<K, PPT><<<g, NT, smem, L.stream>>>(p, dL);
+  ZeroJob none{};
+  k_zero_grad2d<K><<<L.sm_count * 2, 256, 0, L.stream>>>(p);
+  k_render_bwd<K, PPT><<<g, NT, smem, L.stream>>>(p, dL, z ? *z : none);
   return cudaGetLastError();
 }
 
@@ -690,17 +743,18 @@ cudaError_t launch_render_freq_map(const FrameTable& tbl, const WsPtrs& p, float
   return launch_fwd_k<true, false>(tbl, p, out_map, nullptr, L);
 }
 
-cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL, const Launch& L) {
+cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL, const ZeroJob* z,
+                              const Launch& L) {
   switch (tbl.K) {
-    case 0: return launch_bwd_t<0>(tbl, p, dL, L);
-    case 1: return launch_bwd_t<1>(tbl, p, dL, L);
-    case 2: return launch_bwd_t<2>(tbl, p, dL, L);
-    case 3: return launch_bwd_t<3>(tbl, p, dL, L);
-    case 4: return launch_bwd_t<4>(tbl, p, dL, L);
-    case 5: return launch_bwd_t<5>(tbl, p, dL, L);
-    case 6: return launch_bwd_t<6>(tbl, p, dL, L);
-    case 7: return launch_bwd_t<7>(tbl, p, dL, L);
-    case 8: return launch_bwd_t<8>(tbl, p, dL, L);
+    case 0: return launch_bwd_t<0>(tbl, p, dL, z, L);
+    case 1: return launch_bwd_t<1>(tbl, p, dL, z, L);
+    case 2: return launch_bwd_t<2>(tbl, p, dL, z, L);
+    case 3: return launch_bwd_t<3>(tbl, p, dL, z, L);
+    case 4: return launch_bwd_t<4>(tbl, p, dL, z, L);
+    case 5: return launch_bwd_t<5>(tbl, p, dL, z, L);
+    case 6: return launch_bwd_t<6>(tbl, p, dL, z, L);
+    case 7: return launch_bwd_t<7>(tbl, p, dL, z, L);
+    case 8: return launch_bwd_t<8>(tbl, p, dL, z, L);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -61,6 +61,8 @@ def test_invalid_arguments_rejected_on_host(B):
     assert lib.gabsplat_bin_sort(C.byref(f), None) == B.GS_ERR_INVALID_ARG
     assert lib.gabsplat_render_fwd(C.byref(f), None, None, None) == B.GS_ERR_INVALID_ARG
     assert lib.gabsplat_render_bwd(None, None, None, None) == B.GS_ERR_INVALID_ARG
+    assert lib.gabsplat_render_bwd_2d_zero(C.byref(f), None, None, None) == B.GS_ERR_INVALID_ARG
+    assert lib.gabsplat_preprocess_bwd_prezeroed(None, None, None) == B.GS_ERR_INVALID_ARG
     f.ws = 0x1000 + 8                       # misaligned (never dereferenced)
     assert lib.gabsplat_bin_sort(C.byref(f), None) == B.GS_ERR_WORKSPACE
     f.ws, f.ws_bytes = 0x100000, 16         # too small (never dereferenced)
