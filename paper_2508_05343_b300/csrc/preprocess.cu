@@ -822,6 +822,15 @@ ZeroJob make_zero_job(const gs_prim_grads& g, int n, int K, int nsh, u32 ntiles)
 // Backward: 2D record gradients -> primitive attribute gradients (exact chain rule of the
 // forward above; clamps pass zero gradient).
 // ------------------------------------------------------------------------------------------
+
+// a d - b c within a few units in the last place, also under cancellation: Kahan's algorithm
+// with a fused multiply-add recovering the rounding error of b c.
+__device__ __forceinline__ float det2_kahan(float a, float d, float b, float c) {
+  const float w = b * c;
+  const float e = fmaf(-b, c, w);   // w - b c, exactly
+  const float f = fmaf(a, d, -w);
+  return f + e;
+}
 template <int K, int STORAGE>
 __global__ void __launch_bounds__(BLOCK, GS_PBWD_MIN_CTAS) k_preprocess_bwd(WsPtrs p, gs_prim_grads G) {
   const FrameTable* tbl = p.tbl;
@@ -870,7 +879,8 @@ __global__ void __launch_bounds__(BLOCK, GS_PBWD_MIN_CTAS) k_preprocess_bwd(WsPt
     const float ty = W[3] * mx + W[4] * my + W[5] * mz + V.t[1];
     const float tz = W[6] * mx + W[7] * my + W[8] * mz + V.t[2];
     const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
-    const float qw = q4.x / qn, qx = q4.y / qn, qy = q4.z / qn, qz = q4.w / qn;
+    const float iqn = 1.f / qn;
+    const float qw = q4.x * iqn, qx = q4.y * iqn, qy = q4.z * iqn, qz = q4.w * iqn;
     float R[9];
     R[0] = 1.f - 2.f * (qy * qy + qz * qz); R[1] = 2.f * (qx * qy - qw * qz); R[2] = 2.f * (qx * qz + qw * qy);
     R[3] = 2.f * (qx * qy + qw * qz); R[4] = 1.f - 2.f * (qx * qx + qz * qz); R[5] = 2.f * (qy * qz - qw * qx);
@@ -881,6 +891,7 @@ __global__ void __launch_bounds__(BLOCK, GS_PBWD_MIN_CTAS) k_preprocess_bwd(WsPt
     float Sg[9];
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) Sg[3 * i + j] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
+    const float ifx = 1.f / V.fx, ify = 1.f / V.fy;
     const float limx = 1.3f * (0.5f * (float)V.width / V.fx), limy = 1.3f * (0.5f * (float)V.height / V.fy);
     const float rux = tx / tz, ruy = ty / tz;
     const bool clx = (rux < -limx) || (rux > limx), cly = (ruy < -limy) || (ruy > limy);
@@ -903,10 +914,11 @@ __global__ void __launch_bounds__(BLOCK, GS_PBWD_MIN_CTAS) k_preprocess_bwd(WsPt
     const float A11 = U1[0] * T1[0] + U1[1] * T1[1] + U1[2] * T1[2];
     const float bv0 = T0[0] * Sw[0] + T0[1] * Sw[1] + T0[2] * Sw[2];
     const float bv1 = T1[0] * Sw[0] + T1[1] * Sw[1] + T1[2] * Sw[2];
-    // dilated 2D covariance inverse (conic), float64 determinant
-    const double ea = (double)(A00 + eps), eb = (double)A01, ec = (double)(A11 + eps);
-    const double idet = 1.0 / (ea * ec - eb * eb);
-    const float Qa = (float)(ec * idet), Qb = (float)(-eb * idet), Qc = (float)(ea * idet);
+    // dilated 2D covariance inverse (conic); the determinants here feed gradients only, so float32
+    // with Kahan's compensated 2x2 determinant stands in for the forward's float64 one
+    const float ea = A00 + eps, eb = A01, ec = A11 + eps;
+    const float idet = 1.f / det2_kahan(ea, ec, eb, eb);
+    const float Qa = ec * idet, Qb = -eb * idet, Qc = ea * idet;
     // ---- conic -> 2D covariance: dSigma2D = -Q G Q with G = [[ga, gb/2], [gb/2, gc]] ----
     const float ga = g2[2], gbh = 0.5f * g2[3], gc = g2[4];
     const float QG00 = Qa * ga + Qb * gbh, QG01 = Qa * gbh + Qb * gc;
@@ -917,16 +929,16 @@ __global__ void __launch_bounds__(BLOCK, GS_PBWD_MIN_CTAS) k_preprocess_bwd(WsPt
     float gtx = 0.f, gty = 0.f, gtz = 0.f, gux = 0.f, guy = 0.f;
     float gb0 = 0.f, gb1 = 0.f, gcz = 0.f;   // gcz: dL/d(w3^T Sigma w3), the variant only
     if (K > 0) {
-      const double detA = (double)A00 * (double)A11 - (double)A01 * (double)A01;
+      const float detA = det2_kahan(A00, A11, A01, A01);
       float iA00 = 0.f, iA01 = 0.f, iA11 = 0.f, r0 = 0.f, r1 = 0.f;
-      if (detA > 0.0) {
-        const float id = (float)(1.0 / detA);
+      if (detA > 0.f) {
+        const float id = 1.f / detA;
         iA00 = A11 * id; iA01 = -A01 * id; iA11 = A00 * id;
-        r0 = (float)((double)A11 * bv0 - (double)A01 * bv1) * id;
-        r1 = (float)((double)A00 * bv1 - (double)A01 * bv0) * id;
+        r0 = det2_kahan(A11, bv0, A01, bv1) * id;
+        r1 = det2_kahan(A00, bv1, A01, bv0) * id;
       }
       float gr0 = 0.f, gr1 = 0.f;
-      const float tzfx = tz / V.fx, tzfy = tz / V.fy;
+      const float tzfx = tz * ifx, tzfy = tz * ify;
       // the bank's weight terms: G_i = dL/d(cosine weight i), G0 = dL/d(1 - sum w); in the
       // z-attenuation variant the cosine weight is w_i C2_i, C2_i = exp(-2 pi^2 fpz_i^2 sz) with
       // sz = c - b^T A^-1 b (clamped at 0), else C2_i = 1
@@ -961,7 +973,7 @@ __global__ void __launch_bounds__(BLOCK, GS_PBWD_MIN_CTAS) k_preprocess_bwd(WsPt
         const float gg0 = gfx * tzfx + gpz * ux;
         const float gg1 = gfy * tzfy + gpz * uy;
         const float ggz = gpz;
-        gtz += gfx * g0 / V.fx + gfy * g1 / V.fy;
+        gtz += gfx * g0 * ifx + gfy * g1 * ify;
         gux += gpz * g0;
         guy += gpz * g1;
         gfr[3 * i] = W[0] * gg0 + W[3] * gg1 + W[6] * ggz;
@@ -1037,10 +1049,10 @@ __global__ void __launch_bounds__(BLOCK, GS_PBWD_MIN_CTAS) k_preprocess_bwd(WsPt
     const float gqz = 2.f * (-2.f * qz * gR[0] - qw * gR[1] + qx * gR[2] + qw * gR[3] - 2.f * qz * gR[4] + qy * gR[5] +
                              qx * gR[6] + qy * gR[7]);
     const float dotq = qw * gqw + qx * gqx + qy * gqy + qz * gqz;
-    gquat[0] = (gqw - qw * dotq) / qn;
-    gquat[1] = (gqx - qx * dotq) / qn;
-    gquat[2] = (gqy - qy * dotq) / qn;
-    gquat[3] = (gqz - qz * dotq) / qn;
+    gquat[0] = (gqw - qw * dotq) * iqn;
+    gquat[1] = (gqx - qx * dotq) * iqn;
+    gquat[2] = (gqy - qy * dotq) * iqn;
+    gquat[3] = (gqz - qz * dotq) * iqn;
     // ---- SH colour ----
     {
       float dx = mx - V.campos[0], dy = my - V.campos[1], dz = mz - V.campos[2];
