@@ -321,6 +321,15 @@ __device__ __forceinline__ u32 bin_one(const FrameTable* tbl, u32 gi, const WsPt
   return (u32)(b.y1 - b.y0 + 1);   // rows of the 3-sigma square (each culled to an interval later)
 }
 
+// a d - b c within a few units in the last place, also under cancellation: Kahan's algorithm
+// with a fused multiply-add recovering the rounding error of b c.
+__device__ __forceinline__ float det2_kahan(float a, float d, float b, float c) {
+  const float w = b * c;
+  const float e = fmaf(-b, c, w);   // w - b c, exactly
+  const float f = fmaf(a, d, -w);
+  return f + e;
+}
+
 // The 2D record of one primitive that touches at least one tile (row `row`, its depth rank): conic
 // from the float64 determinant, colour, splatted frequencies.  Recomputes the binning quantities
 // (bit-identical).
@@ -336,10 +345,9 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, u32 ro
   const float4 q = __ldg(reinterpret_cast<const float4*>(V.quats) + k);
   BinSpec b;
   bin_spec(V, tbl->eps2d, mx, my, mz, s0, s1, s2, q, b);
-  // ---- 2D record: conic from the float64 determinant, colour, splatted frequencies ----
-  const double inv_det = 1.0 / b.det;
-  const double da = (double)FA(b.A00, tbl->eps2d), db = (double)b.A01, dc = (double)FA(b.A11, tbl->eps2d);
-  const float ca = (float)(dc * inv_det), cb = (float)(-db * inv_det), cc = (float)(da * inv_det);
+  // ---- 2D record: conic from the (float64, rounded) determinant, colour, splatted frequencies ----
+  const float det32 = __double2float_rn(b.det);
+  const float ca = FDV(FA(b.A11, tbl->eps2d), det32), cb = FDV(-b.A01, det32), cc = FDV(FA(b.A00, tbl->eps2d), det32);
   const float op = __ldg(V.opacity + k);
 
   // colour: SH at the viewing direction, shifted by 0.5 and clamped at 0
@@ -373,14 +381,12 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, u32 ro
     const float Sw2 = b.Sig[2] * W[6] + b.Sig[4] * W[7] + b.Sig[5] * W[8];
     const float bv0 = b.T0[0] * Sw0 + b.T0[1] * Sw1 + b.T0[2] * Sw2;
     const float bv1 = b.T1[0] * Sw0 + b.T1[1] * Sw1 + b.T1[2] * Sw2;
-    const double detA = (double)b.A00 * (double)b.A11 - (double)b.A01 * (double)b.A01;
+    const float detA = det2_kahan(b.A00, b.A11, b.A01, b.A01);
     float r0 = 0.f, r1 = 0.f;
-    if (detA > 0.0) {
-      const double n0 = (double)b.A11 * (double)bv0 - (double)b.A01 * (double)bv1;
-      const double n1 = (double)b.A00 * (double)bv1 - (double)b.A01 * (double)bv0;
-      const float idet = (float)(1.0 / detA);
-      r0 = (float)n0 * idet;
-      r1 = (float)n1 * idet;
+    if (detA > 0.f) {
+      const float idet = 1.f / detA;
+      r0 = det2_kahan(b.A11, bv0, b.A01, bv1) * idet;
+      r1 = det2_kahan(b.A00, bv1, b.A01, bv0) * idet;
     }
     const float tzfx = b.tz / V.fx, tzfy = b.tz / V.fy;
     // z-attenuation variant: 1/S_22 = c - b^T A^-1 b (the Schur complement of the ray-space
@@ -760,7 +766,7 @@ __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
 // Resident CTAs per SM that the record and gradient-chain kernels are compiled for.  Both are
 // latency-bound over scattered attribute rows, so occupancy matters more than a few spilled registers.
 #ifndef GS_RECORDS_MIN_CTAS
-#define GS_RECORDS_MIN_CTAS 1
+#define GS_RECORDS_MIN_CTAS 2
 #endif
 #ifndef GS_PBWD_MIN_CTAS
 #define GS_PBWD_MIN_CTAS 2
@@ -823,14 +829,6 @@ ZeroJob make_zero_job(const gs_prim_grads& g, int n, int K, int nsh, u32 ntiles)
 // forward above; clamps pass zero gradient).
 // ------------------------------------------------------------------------------------------
 
-// a d - b c within a few units in the last place, also under cancellation: Kahan's algorithm
-// with a fused multiply-add recovering the rounding error of b c.
-__device__ __forceinline__ float det2_kahan(float a, float d, float b, float c) {
-  const float w = b * c;
-  const float e = fmaf(-b, c, w);   // w - b c, exactly
-  const float f = fmaf(a, d, -w);
-  return f + e;
-}
 template <int K, int STORAGE>
 __global__ void __launch_bounds__(BLOCK, GS_PBWD_MIN_CTAS) k_preprocess_bwd(WsPtrs p, gs_prim_grads G) {
   const FrameTable* tbl = p.tbl;
