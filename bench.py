@@ -81,10 +81,19 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={pci_bus_id}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        # nvidia-smi takes a moment to start: wait (at most 5 s) for its first sample, so the
+        # samples cover the whole timed region that follows
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < 5.0 and self.proc.poll() is None:
+            self.fh.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
+        self.t_ready = time.time()
 
     def stop(self):
         if self.proc is None:
