@@ -226,6 +226,30 @@ def test_backward_writes_every_gradient_row(offset):
         assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b), k
 
 
+def test_backward_with_some_gradient_outputs_null():
+    """Any gs_prim_grads pointer may be NULL: the zero-fill inside the compositing backward and the
+    chain rule skip those arrays and write the others as a full backward does."""
+    from paper_2508_05343_b300 import raster
+    prims, cam = scenes.config_scene(1), scenes.config_cameras(1)[0]
+    _, gc = cfg_pair()
+    r, _, _, _ = gpu_render(prims, cam, gc)
+    n = prims["means"].shape[0]
+    dL = torch.as_tensor(np.random.default_rng(6).standard_normal((3, cam["height"], cam["width"])) * 1e-3,
+                         dtype=torch.float32, device="cuda")
+    full = {k: v.clone() for k, v in r.backward(dL).items()}
+    some = {"means": torch.full((n, 3), float("nan"), device="cuda"),
+            "sh": torch.full(tuple(r._keep["sh"].shape), float("nan"), device="cuda"),
+            "means2d": torch.full((n, 2), float("nan"), device="cuda")}
+    g = r.backward(dL, some)
+    torch.cuda.synchronize()
+    assert set(g) == {"means", "sh", "means2d"}
+    for k, v in g.items():
+        a = v.float().cpu().numpy().reshape(n, -1)
+        b = full[k].float().cpu().numpy().reshape(n, -1)
+        assert np.isfinite(a).all(), k
+        assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b), k
+
+
 def test_forward_only_render_matches_and_refuses_a_backward():
     """gabsplat_render_fwd_only gives the image of gabsplat_render_fwd; a backward of a frame whose
     only forward was forward-only reports an invalid argument instead of reading stale state."""
