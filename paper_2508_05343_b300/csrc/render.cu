@@ -162,7 +162,8 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 #endif
 
 // Called by thread 0 of every CTA after it has left its tile loop: the last CTA of the launch
-// resets the tile allocator, so each compositing launch of a frame starts from tile 0.
+// resets the tile allocator (and counter2, the backward's zero-fill chunk counter, if given), so
+// each compositing launch of a frame starts from tile 0.
 __device__ __forceinline__ void release_tile_counter(u32* counter, u32* exits, u32* counter2 = nullptr) {
   __threadfence();
   if (atomicAdd(exits, 1u) == gridDim.x - 1) {
