@@ -454,25 +454,26 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ d
     const float fpx = (float)px + 0.5f, fpy0 = (float)py0 + 0.5f;
     const float* gsrc = dL_drgb ? dL_drgb : V.dL_drgb;
     const size_t hw = (size_t)V.width * V.height;
-    float T[PPT], Tfin[PPT], g0[PPT], g1[PPT], g2[PPT], bgdot[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
+    // tbg: T_final (bg . dL/dC), the background's share of dL/dalpha (scaled by 1 / (1 - alpha))
+    float T[PPT], g0[PPT], g1[PPT], g2[PPT], tbg[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
     u32 last[PPT];
     u32 wlast = 0;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-      T[q] = Tfin[q] = 1.f;
+      T[q] = 1.f;
       g0[q] = g1[q] = g2[q] = 0.f;
       acc0[q] = acc1[q] = acc2[q] = 0.f;
       last[q] = 0;
       const int py = py0 + q;
       if (px < V.width && py < V.height) {
         const size_t pix = (size_t)py * V.width + px;
-        T[q] = Tfin[q] = p.T_final[V.pix_base + pix];
+        T[q] = p.T_final[V.pix_base + pix];
         last[q] = p.n_contrib[V.pix_base + pix];
         g0[q] = gsrc[pix];
         g1[q] = gsrc[hw + pix];
         g2[q] = gsrc[2 * hw + pix];
       }
-      bgdot[q] = tbl->bg[0] * g0[q] + tbl->bg[1] * g1[q] + tbl->bg[2] * g2[q];
+      tbg[q] = T[q] * (tbl->bg[0] * g0[q] + tbl->bg[1] * g1[q] + tbl->bg[2] * g2[q]);
       wlast = max(wlast, last[q]);
     }
     // the last composited pair over the warp / CTA bounds the reverse walk
@@ -521,6 +522,7 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ d
         for (int i = 0; i < NVP; ++i) gv[i] = 0.f;
         bool contrib = false;
         const float dx = __fsub_rn(fpx, h0.x);
+        const float oln2 = h1.z * 0.6931471805599453f;   // opacity ln 2
         // the per-pixel work, instantiated for records with and without phase reduction
         auto pixels = [&](auto fast_tag) {
         float dyq[PPT], pwq[PPT];
@@ -561,16 +563,17 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ d
           gv[7] += wgt * g1[q];
           gv[8] += wgt * g2[q];
           float dLda = T[q] * ((c.x - acc0[q]) * g0[q] + (c.y - acc1[q]) * g1[q] + (c.z - acc2[q]) * g2[q]) -
-                       Tfin[q] * bgdot[q] * ioma;
+                       tbg[q] * ioma;
           acc0[q] = alpha * c.x + oma * acc0[q];
           acc1[q] = alpha * c.y + oma * acc1[q];
           acc2[q] = alpha * c.z + oma * acc2[q];
           if (araw > amax) dLda = 0.f;                     // clamped: no gradient through alpha
-          const float o = h1.z;
-          const float dLdbank = dLda * o * G;
-          gv[5] += dLda * G * bank;                        // d opacity
+          const float dLdG = dLda * G;
+          const float dLdbank = dLdG * h1.z;
+          const float dLdo = dLdG * bank;
+          gv[5] += dLdo;                                   // d opacity
           // log2-domain power p2: G = 2^p2, dG/dp2 = G ln 2, so dL/dp2 = dLda o bank G ln 2
-          const float dLdp2 = dLdbank * bank * 0.6931471805599453f;
+          const float dLdp2 = dLdo * oln2;
           const float ex = dLdp2 * dx, ey = dLdp2 * dy;
           gv[2] += ex * dx;                                // w.r.t. A' (converted at flush)
           gv[3] += ex * dy;                                // w.r.t. B'
