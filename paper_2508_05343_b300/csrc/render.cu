@@ -265,7 +265,8 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
           any = any || reach[q];
         }
         bool comp = false;
-        if (any) {
+        // the per-pixel work, instantiated for records with and without phase reduction
+        auto pixels = [&](auto fast_tag) {
           const float* fr = reinterpret_cast<const float*>(r + 3);
           float th[K > 0 ? K : 1];
 #pragma unroll
@@ -278,7 +279,7 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
             if (reach[q]) {
               ++reached[q];
               const float G = ex2_approx(pwq[q]);
-              const float bank = fast ? filter_bank<K, true>(th, fr + 2 * K, h1.w) : filter_bank<K, false>(th, fr + 2 * K, h1.w);
+              const float bank = filter_bank<K, decltype(fast_tag)::value>(th, fr + 2 * K, h1.w);
               const float alpha = fminf(amax, __fmul_rn(__fmul_rn(h1.z, G), bank));
               if (alpha >= amin) {
                 const float test = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
@@ -299,6 +300,12 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
               }
             }
           }
+        };
+        if (any) {
+          if (fast)
+            pixels(std::true_type{});
+          else
+            pixels(std::false_type{});
         }
         tdone = true;
 #pragma unroll
