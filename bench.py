@@ -481,10 +481,10 @@ def run_ours(args):
     rec_b = (12 + 4 * ((3 * K + 3) // 4)) * 4
     g2d_b = 4 * ((9 + 3 * K + 3) // 4) * 4
     grad_b = 4 * (3 + 3 + 4 + 1 + (deg + 1) ** 2 * 3 + 3 * K + K + 2)
-    # Algorithmic FP32 work of the blending kernels, per unit as the survey's measurement section
-    # fixes it: every evaluated pixel-pair costs 14 + 4K FP32 operations in the forward (offset and
-    # quadratic form, exp argument, the K-term filter bank after cycle-domain reduction, alpha,
-    # blend; an FMA is one operation) and three times that in the backward, whose evaluated
+    # Algorithmic FP32 work of the blending kernels, per unit of work: every evaluated pixel-pair
+    # costs 14 + 4K FP32 operations in the forward (offset and quadratic form, exp argument, the
+    # K-term filter bank after cycle-domain reduction, alpha, blend; an FMA is one operation) and
+    # three times that in the backward, whose evaluated
     # pixel-pairs are those up to each pixel's last contributor.  The peak is the FP32 issue rate,
     # 148 SMs x 128 lanes x the median SM clock: one operation per lane per cycle.  A finer count,
     # which charges the filter bank only to pixel-pairs passing o G >= alpha_min and the adjoints
