@@ -110,6 +110,19 @@ __device__ __forceinline__ float reduced_angle(float th) {
   return __fmul_rn(TWO_PI, __fsub_rn(t, rintf(t)));
 }
 
+// Two pixels' values in one register pair.  The packed FP32 instructions of sm_100 and later
+// (__ffma2_rn, __fmul2_rn, __fadd2_rn) work on both halves with one issue and round each half
+// exactly as the scalar instruction does, so packed and scalar evaluation give the same bits.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// reduced_angle on both halves: t - rint(t) = t + rint(-t) is exact, so this equals the scalar form.
+template <bool FAST>
+__device__ __forceinline__ float2 reduced_angle2(float2 th) {
+  if (FAST) return th;
+  const float2 t = __fmul2_rn(th, f2(INV_TWO_PI));
+  return __fmul2_rn(f2(TWO_PI), __fadd2_rn(t, make_float2(rintf(-t.x), rintf(-t.y))));
+}
+
 // Filter bank (1 - sum w) + sum w_i cos(2 pi f2D_i . d)  (Sec. 3.3.2, Eq. 9) from the phases.
 template <int K, bool FAST>
 __device__ __forceinline__ float filter_bank(const float* th, const float* w, float w0) {
@@ -142,13 +155,14 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 #define GS_WARP_SQUARE 1
 #endif
 
-// Resident CTAs per SM the compositing kernels are compiled for (0: the compiler's choice; forcing
-// 8 forward CTAs, 64 registers, measured slower than the compiler's 72).
+// Resident CTAs per SM the compositing kernels are compiled for (0: the compiler's choice).  The
+// backward's two-pixel packed adjoint takes 127 registers (4 CTAs per SM) on its own; held to 96
+// for 5 CTAs per SM it spills 16 bytes and runs 5% faster.
 #ifndef GS_FWD_MIN_CTAS
 #define GS_FWD_MIN_CTAS 0
 #endif
 #ifndef GS_BWD_MIN_CTAS
-#define GS_BWD_MIN_CTAS 0
+#define GS_BWD_MIN_CTAS 5
 #endif
 #if GS_FWD_MIN_CTAS
 #define GS_FWD_BOUNDS __launch_bounds__(BLOCK / PPT, GS_FWD_MIN_CTAS)
@@ -268,34 +282,76 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
         // the per-pixel work, instantiated for records with and without phase reduction
         auto pixels = [&](auto fast_tag) {
           const float* fr = reinterpret_cast<const float*>(r + 3);
-          float th[K > 0 ? K : 1];
+          if constexpr (PPT == 2) {
+            // both pixels at once in packed FP32 (bit-identical to the per-pixel form below); the
+            // envelope, bank and alpha of a pixel that is not reached are computed and discarded
+            float2 thp[K > 0 ? K : 1];
 #pragma unroll
-          for (int i = 0; i < K; ++i) th[i] = raw_phase(fr[2 * i], fr[2 * i + 1], dx, dyq[0]);
+            for (int i = 0; i < K; ++i) {
+              const float t0 = raw_phase(fr[2 * i], fr[2 * i + 1], dx, dyq[0]);
+              thp[i] = make_float2(t0, __fadd_rn(t0, fr[2 * i + 1]));
+            }
+            const float2 G = make_float2(ex2_approx(pwq[0]), ex2_approx(pwq[1]));
+            float2 bank = f2(h1.w);
 #pragma unroll
-          for (int q = 0; q < PPT; ++q) {
-            if (q > 0)
+            for (int i = 0; i < K; ++i) {
+              const float2 a = reduced_angle2<decltype(fast_tag)::value>(thp[i]);
+              bank = __ffma2_rn(f2(fr[2 * K + i]), make_float2(__cosf(a.x), __cosf(a.y)), bank);
+            }
+            float2 al = __fmul2_rn(__fmul2_rn(f2(h1.z), G), bank);
+            al.x = fminf(amax, al.x);
+            al.y = fminf(amax, al.y);
+            const float2 Tp = make_float2(T[0], T[1]);
+            const float2 test = __fmul2_rn(Tp, __ffma2_rn(al, f2(-1.f), f2(1.f)));   // T (1 - alpha)
+            float2 wgt = __fmul2_rn(al, Tp);
+            const bool pass0 = reach[0] && al.x >= amin, pass1 = reach[1] && al.y >= amin;
+            const bool stop0 = pass0 && test.x < Tmin, stop1 = pass1 && test.y < Tmin;
+            const bool comp0 = pass0 && !stop0, comp1 = pass1 && !stop1;
+            const u32 here = start + (u32)j + 1u - rg.x;
+            reached[0] += reach[0] ? 1u : 0u;
+            reached[1] += reach[1] ? 1u : 0u;
+            if (stop0) { done[0] = true; evaluated[0] = here; }
+            if (stop1) { done[1] = true; evaluated[1] = here; }
+            if (comp0) { T[0] = test.x; last[0] = here; ++composited[0]; } else { wgt.x = 0.f; }
+            if (comp1) { T[1] = test.y; last[1] = here; ++composited[1]; } else { wgt.y = 0.f; }
+            const float4 c = r[2];   // a zero weight leaves the (non-negative) sums unchanged
+            const float2 s0 = __ffma2_rn(f2(c.x), wgt, make_float2(C0[0], C0[1]));
+            const float2 s1 = __ffma2_rn(f2(c.y), wgt, make_float2(C1[0], C1[1]));
+            const float2 s2 = __ffma2_rn(f2(c.z), wgt, make_float2(C2[0], C2[1]));
+            C0[0] = s0.x; C0[1] = s0.y;
+            C1[0] = s1.x; C1[1] = s1.y;
+            C2[0] = s2.x; C2[1] = s2.y;
+            comp = comp0 || comp1;
+          } else {
+            float th[K > 0 ? K : 1];
 #pragma unroll
-              for (int i = 0; i < K; ++i) th[i] = __fadd_rn(th[i], fr[2 * i + 1]);
-            if (reach[q]) {
-              ++reached[q];
-              const float G = ex2_approx(pwq[q]);
-              const float bank = filter_bank<K, decltype(fast_tag)::value>(th, fr + 2 * K, h1.w);
-              const float alpha = fminf(amax, __fmul_rn(__fmul_rn(h1.z, G), bank));
-              if (alpha >= amin) {
-                const float test = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
-                if (test < Tmin) {
-                  done[q] = true;
-                  evaluated[q] = start + (u32)j + 1u - rg.x;
-                } else {
-                  const float4 c = r[2];
-                  const float wgt = alpha * T[q];
-                  C0[q] = __fmaf_rn(c.x, wgt, C0[q]);
-                  C1[q] = __fmaf_rn(c.y, wgt, C1[q]);
-                  C2[q] = __fmaf_rn(c.z, wgt, C2[q]);
-                  T[q] = test;
-                  last[q] = start + (u32)j + 1u - rg.x;
-                  ++composited[q];
-                  comp = true;
+            for (int i = 0; i < K; ++i) th[i] = raw_phase(fr[2 * i], fr[2 * i + 1], dx, dyq[0]);
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+              if (q > 0)
+#pragma unroll
+                for (int i = 0; i < K; ++i) th[i] = __fadd_rn(th[i], fr[2 * i + 1]);
+              if (reach[q]) {
+                ++reached[q];
+                const float G = ex2_approx(pwq[q]);
+                const float bank = filter_bank<K, decltype(fast_tag)::value>(th, fr + 2 * K, h1.w);
+                const float alpha = fminf(amax, __fmul_rn(__fmul_rn(h1.z, G), bank));
+                if (alpha >= amin) {
+                  const float test = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
+                  if (test < Tmin) {
+                    done[q] = true;
+                    evaluated[q] = start + (u32)j + 1u - rg.x;
+                  } else {
+                    const float4 c = r[2];
+                    const float wgt = alpha * T[q];
+                    C0[q] = __fmaf_rn(c.x, wgt, C0[q]);
+                    C1[q] = __fmaf_rn(c.y, wgt, C1[q]);
+                    C2[q] = __fmaf_rn(c.z, wgt, C2[q]);
+                    T[q] = test;
+                    last[q] = start + (u32)j + 1u - rg.x;
+                    ++composited[q];
+                    comp = true;
+                  }
                 }
               }
             }
@@ -534,72 +590,163 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ d
         auto pixels = [&](auto fast_tag) {
         float dyq[PPT], pwq[PPT];
         pixel_powers<PPT>(h0, h1, dx, __fsub_rn(fpy0, h0.y), dyq, pwq);
-        float th[K > 0 ? K : 1];   // raw phases of the current row (the forward's recurrence)
-#pragma unroll
-        for (int i = 0; i < K; ++i) th[i] = raw_phase(fw[2 * i], fw[2 * i + 1], dx, dyq[0]);
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-          if (q > 0)
-#pragma unroll
-            for (int i = 0; i < K; ++i) th[i] = __fadd_rn(th[i], fw[2 * i + 1]);
-          if (pos >= last[q]) continue;
-          const float dy = dyq[q];
-          const float pw = pwq[q];
-          if (pw < h1.y) continue;
-          const float G = ex2_approx(pw);
-          float cs[K > 0 ? K : 1], sn[K > 0 ? K : 1];
-          float bank = h1.w;
+        if constexpr (PPT == 2) {
+          // Both pixels at once.  Envelope, bank and alpha in packed FP32, bit-identical to the
+          // forward's decisions.  A pixel that does not take part gets alpha 0 (its transmittance
+          // and colour sums stay as they are) and dL/dalpha 0 (it adds nothing), and the two
+          // pixels' adjoints are summed before they meet the shared factors: dx is common, and
+          // sums against dy use each pixel's own offset.
+          const bool live0 = pos < last[0] && pwq[0] >= h1.y;
+          const bool live1 = pos < last[1] && pwq[1] >= h1.y;
+          if (!(live0 || live1)) return;
+          float2 thp[K > 0 ? K : 1];
 #pragma unroll
           for (int i = 0; i < K; ++i) {
-            const float ang = reduced_angle<decltype(fast_tag)::value>(th[i]);
-            cs[i] = __cosf(ang);
-            sn[i] = __sinf(ang);
+            const float t0 = raw_phase(fw[2 * i], fw[2 * i + 1], dx, dyq[0]);
+            thp[i] = make_float2(t0, __fadd_rn(t0, fw[2 * i + 1]));
           }
+          const float2 G = make_float2(ex2_approx(pwq[0]), ex2_approx(pwq[1]));
+          float2 cs[K > 0 ? K : 1], sn[K > 0 ? K : 1];
+          float2 bank = f2(h1.w);
 #pragma unroll
-          for (int i = 0; i < K; ++i) bank = __fmaf_rn(fw[2 * K + i], cs[i], bank);
-          const float araw = __fmul_rn(__fmul_rn(h1.z, G), bank);
-          const float alpha = fminf(amax, araw);
-          if (alpha < amin) continue;
+          for (int i = 0; i < K; ++i) {
+            const float2 a = reduced_angle2<decltype(fast_tag)::value>(thp[i]);
+            cs[i] = make_float2(__cosf(a.x), __cosf(a.y));
+            sn[i] = make_float2(__sinf(a.x), __sinf(a.y));
+            bank = __ffma2_rn(f2(fw[2 * K + i]), cs[i], bank);
+          }
+          const float2 araw = __fmul2_rn(__fmul2_rn(f2(h1.z), G), bank);
+          const float ax = fminf(amax, araw.x), ay = fminf(amax, araw.y);
+          const bool pass0 = live0 && ax >= amin, pass1 = live1 && ay >= amin;
+          if (!(pass0 || pass1)) return;
           contrib = true;
-          const float oma = 1.f - alpha;
-          const float ioma = rcp_approx(oma);
-          T[q] = T[q] * ioma;                              // transmittance before this pair
+          const float2 alpha = make_float2(pass0 ? ax : 0.f, pass1 ? ay : 0.f);
+          const float2 oma = __ffma2_rn(alpha, f2(-1.f), f2(1.f));
+          const float2 ioma = make_float2(rcp_approx(oma.x), rcp_approx(oma.y));
+          const float2 Tn = __fmul2_rn(make_float2(T[0], T[1]), ioma);   // transmittance before this pair
+          if (pass0) T[0] = Tn.x;
+          if (pass1) T[1] = Tn.y;
           const float4 c = r[2];
-          const float wgt = alpha * T[q];
-          gv[6] += wgt * g0[q];
-          gv[7] += wgt * g1[q];
-          gv[8] += wgt * g2[q];
-          float dLda = T[q] * ((c.x - acc0[q]) * g0[q] + (c.y - acc1[q]) * g1[q] + (c.z - acc2[q]) * g2[q]) -
-                       tbg[q] * ioma;
-          acc0[q] = alpha * c.x + oma * acc0[q];
-          acc1[q] = alpha * c.y + oma * acc1[q];
-          acc2[q] = alpha * c.z + oma * acc2[q];
-          if (araw > amax) dLda = 0.f;                     // clamped: no gradient through alpha
-          const float dLdG = dLda * G;
-          const float dLdbank = dLdG * h1.z;
-          const float dLdo = dLdG * bank;
-          gv[5] += dLdo;                                   // d opacity
+          const float2 wgt = __fmul2_rn(alpha, Tn);
+          const float2 G0 = make_float2(g0[0], g0[1]), G1 = make_float2(g1[0], g1[1]), G2 = make_float2(g2[0], g2[1]);
+          float2 A0 = make_float2(acc0[0], acc0[1]), A1 = make_float2(acc1[0], acc1[1]),
+                 A2 = make_float2(acc2[0], acc2[1]);
+          // (c - acc) . dL/dC, then dL/dalpha = T (c - acc) . dL/dC - tbg / (1 - alpha)
+          float2 dcg = __fmul2_rn(__ffma2_rn(A2, f2(-1.f), f2(c.z)), G2);
+          dcg = __ffma2_rn(__ffma2_rn(A1, f2(-1.f), f2(c.y)), G1, dcg);
+          dcg = __ffma2_rn(__ffma2_rn(A0, f2(-1.f), f2(c.x)), G0, dcg);
+          float2 dLda = __ffma2_rn(__fmul2_rn(make_float2(tbg[0], tbg[1]), ioma), f2(-1.f), __fmul2_rn(Tn, dcg));
+          A0 = __ffma2_rn(oma, A0, __fmul2_rn(alpha, f2(c.x)));
+          A1 = __ffma2_rn(oma, A1, __fmul2_rn(alpha, f2(c.y)));
+          A2 = __ffma2_rn(oma, A2, __fmul2_rn(alpha, f2(c.z)));
+          acc0[0] = A0.x; acc0[1] = A0.y;
+          acc1[0] = A1.x; acc1[1] = A1.y;
+          acc2[0] = A2.x; acc2[1] = A2.y;
+          // no gradient through a clamped alpha, none from a pixel that does not take part
+          if (!pass0 || araw.x > amax) dLda.x = 0.f;
+          if (!pass1 || araw.y > amax) dLda.y = 0.f;
+          gv[6] = fmaf(wgt.y, g0[1], wgt.x * g0[0]);
+          gv[7] = fmaf(wgt.y, g1[1], wgt.x * g1[0]);
+          gv[8] = fmaf(wgt.y, g2[1], wgt.x * g2[0]);
+          const float2 dLdG = __fmul2_rn(dLda, G);
+          const float2 dLdbank = __fmul2_rn(dLdG, f2(h1.z));
+          const float2 dLdo = __fmul2_rn(dLdG, bank);
           // log2-domain power p2: G = 2^p2, dG/dp2 = G ln 2, so dL/dp2 = dLda o bank G ln 2
-          const float dLdp2 = dLdo * oln2;
-          const float ex = dLdp2 * dx, ey = dLdp2 * dy;
-          gv[2] += ex * dx;                                // w.r.t. A' (converted at flush)
-          gv[3] += ex * dy;                                // w.r.t. B'
-          gv[4] += ey * dy;                                // w.r.t. C'
-          float gdx = 2.f * h0.z * ex + h0.w * ey;
-          float gdy = h0.w * ex + 2.f * h1.x * ey;
+          const float2 dLdp2 = __fmul2_rn(dLdo, f2(oln2));
+          const float2 edy = __fmul2_rn(dLdp2, make_float2(dyq[0], dyq[1]));
+          const float P = dLdp2.x + dLdp2.y;               // sum of dL/dp2
+          const float Y = edy.x + edy.y;                   // sum of dL/dp2 dy
+          const float Ex = P * dx;                         // sum of dL/dp2 dx
+          gv[5] = dLdo.x + dLdo.y;                         // d opacity
+          gv[2] = Ex * dx;                                 // w.r.t. A' (converted at flush)
+          gv[3] = Y * dx;                                  // w.r.t. B'
+          gv[4] = fmaf(edy.y, dyq[1], edy.x * dyq[0]);     // w.r.t. C'
+          float gdx = 2.f * h0.z * Ex + h0.w * Y;
+          float gdy = h0.w * Ex + 2.f * h1.x * Y;
 #pragma unroll
           for (int i = 0; i < K; ++i) {
             const float wi = fw[2 * K + i];
-            gv[9 + 2 * K + i] += dLdbank * cs[i];                  // d (cosine weight i)
-            const float gth = -dLdbank * wi * sn[i];                // d phase (radians)
-            gv[9 + 2 * i] += gth * dx;                              // w.r.t. 2 pi f2D (scaled at flush)
-            gv[9 + 2 * i + 1] += gth * dy;
+            const float2 kc = __fmul2_rn(dLdbank, cs[i]);
+            const float2 ks = __fmul2_rn(dLdbank, sn[i]);
+            gv[9 + 2 * K + i] = kc.x + kc.y;                         // d (cosine weight i)
+            const float gth = -wi * (ks.x + ks.y);                   // d phase (radians), both pixels
+            const float gthdy = -wi * fmaf(ks.y, dyq[1], ks.x * dyq[0]);
+            gv[9 + 2 * i] = gth * dx;                                // w.r.t. 2 pi f2D (scaled at flush)
+            gv[9 + 2 * i + 1] = gthdy;
             gdx += gth * fw[2 * i];
             gdy += gth * fw[2 * i + 1];
           }
-          gv[9 + 3 * K] += dLdbank;                        // d (1 - sum w)
-          gv[0] -= gdx;                                    // d mu = - d (pixel - mu)
-          gv[1] -= gdy;
+          gv[9 + 3 * K] = dLdbank.x + dLdbank.y;           // d (1 - sum w)
+          gv[0] = -gdx;                                    // d mu = - d (pixel - mu)
+          gv[1] = -gdy;
+        } else {
+          float th[K > 0 ? K : 1];   // raw phases of the current row (the forward's recurrence)
+#pragma unroll
+          for (int i = 0; i < K; ++i) th[i] = raw_phase(fw[2 * i], fw[2 * i + 1], dx, dyq[0]);
+#pragma unroll
+          for (int q = 0; q < PPT; ++q) {
+            if (q > 0)
+#pragma unroll
+              for (int i = 0; i < K; ++i) th[i] = __fadd_rn(th[i], fw[2 * i + 1]);
+            if (pos >= last[q]) continue;
+            const float dy = dyq[q];
+            const float pw = pwq[q];
+            if (pw < h1.y) continue;
+            const float G = ex2_approx(pw);
+            float cs[K > 0 ? K : 1], sn[K > 0 ? K : 1];
+            float bank = h1.w;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+              const float ang = reduced_angle<decltype(fast_tag)::value>(th[i]);
+              cs[i] = __cosf(ang);
+              sn[i] = __sinf(ang);
+            }
+#pragma unroll
+            for (int i = 0; i < K; ++i) bank = __fmaf_rn(fw[2 * K + i], cs[i], bank);
+            const float araw = __fmul_rn(__fmul_rn(h1.z, G), bank);
+            const float alpha = fminf(amax, araw);
+            if (alpha < amin) continue;
+            contrib = true;
+            const float oma = 1.f - alpha;
+            const float ioma = rcp_approx(oma);
+            T[q] = T[q] * ioma;                              // transmittance before this pair
+            const float4 c = r[2];
+            const float wgt = alpha * T[q];
+            gv[6] += wgt * g0[q];
+            gv[7] += wgt * g1[q];
+            gv[8] += wgt * g2[q];
+            float dLda = T[q] * ((c.x - acc0[q]) * g0[q] + (c.y - acc1[q]) * g1[q] + (c.z - acc2[q]) * g2[q]) -
+                         tbg[q] * ioma;
+            acc0[q] = alpha * c.x + oma * acc0[q];
+            acc1[q] = alpha * c.y + oma * acc1[q];
+            acc2[q] = alpha * c.z + oma * acc2[q];
+            if (araw > amax) dLda = 0.f;                     // clamped: no gradient through alpha
+            const float dLdG = dLda * G;
+            const float dLdbank = dLdG * h1.z;
+            const float dLdo = dLdG * bank;
+            gv[5] += dLdo;                                   // d opacity
+            // log2-domain power p2: G = 2^p2, dG/dp2 = G ln 2, so dL/dp2 = dLda o bank G ln 2
+            const float dLdp2 = dLdo * oln2;
+            const float ex = dLdp2 * dx, ey = dLdp2 * dy;
+            gv[2] += ex * dx;                                // w.r.t. A' (converted at flush)
+            gv[3] += ex * dy;                                // w.r.t. B'
+            gv[4] += ey * dy;                                // w.r.t. C'
+            float gdx = 2.f * h0.z * ex + h0.w * ey;
+            float gdy = h0.w * ex + 2.f * h1.x * ey;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+              const float wi = fw[2 * K + i];
+              gv[9 + 2 * K + i] += dLdbank * cs[i];                  // d (cosine weight i)
+              const float gth = -dLdbank * wi * sn[i];                // d phase (radians)
+              gv[9 + 2 * i] += gth * dx;                              // w.r.t. 2 pi f2D (scaled at flush)
+              gv[9 + 2 * i + 1] += gth * dy;
+              gdx += gth * fw[2 * i];
+              gdy += gth * fw[2 * i + 1];
+            }
+            gv[9 + 3 * K] += dLdbank;                        // d (1 - sum w)
+            gv[0] -= gdx;                                    // d mu = - d (pixel - mu)
+            gv[1] -= gdy;
+          }
         }
         };
         if (fast)
