@@ -74,18 +74,33 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Two pixels' values in one register pair.  The packed FP32 instructions of sm_100 and later
+// (__ffma2_rn, __fmul2_rn, __fadd2_rn) work on both halves with one issue and round each half
+// exactly as the scalar instruction does, so packed and scalar evaluation give the same bits.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
 // Exponent (log2 domain) of the 2D Gaussian at offset (dx, dy).
 __device__ __forceinline__ float gauss_power(const float4& h0, const float4& h1, float dx, float dy) {
   return __fmaf_rn(dx, __fmaf_rn(h0.z, dx, __fmul_rn(h0.w, dy)), __fmul_rn(__fmul_rn(h1.x, dy), dy));
 }
 
 // Envelope exponents of a thread's PPT pixels (rows y .. y + PPT - 1 of one column, offsets dx and
-// dy[q] from the mean): row q + 1 follows row q by the recurrence pw(dy + 1) = pw(dy) + B' dx +
-// C' (2 dy + 1).  The forward and the backward both use it, so they take the same decisions.
+// dy[q] from the mean).  Two rows are evaluated directly, both in one packed instruction stream;
+// more rows follow row q by the recurrence pw(dy + 1) = pw(dy) + B' dx + C' (2 dy + 1).  The
+// forward and the backward both use it, so they take the same decisions.
 template <int PPT>
 __device__ __forceinline__ void pixel_powers(const float4& h0, const float4& h1, float dx, float dy0, float* dy,
                                              float* pw) {
   dy[0] = dy0;
+  if constexpr (PPT == 2) {
+    dy[1] = __fadd_rn(dy0, 1.f);
+    const float2 d = make_float2(dy[0], dy[1]);
+    const float2 e = __ffma2_rn(f2(dx), __ffma2_rn(f2(h0.z), f2(dx), __fmul2_rn(f2(h0.w), d)),
+                                __fmul2_rn(__fmul2_rn(f2(h1.x), d), d));   // gauss_power of each row
+    pw[0] = e.x;
+    pw[1] = e.y;
+    return;
+  }
   pw[0] = gauss_power(h0, h1, dx, dy0);
   const float bdx = __fmul_rn(h0.w, dx);
 #pragma unroll
@@ -109,11 +124,6 @@ __device__ __forceinline__ float reduced_angle(float th) {
   const float t = __fmul_rn(th, INV_TWO_PI);
   return __fmul_rn(TWO_PI, __fsub_rn(t, rintf(t)));
 }
-
-// Two pixels' values in one register pair.  The packed FP32 instructions of sm_100 and later
-// (__ffma2_rn, __fmul2_rn, __fadd2_rn) work on both halves with one issue and round each half
-// exactly as the scalar instruction does, so packed and scalar evaluation give the same bits.
-__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
 // reduced_angle on both halves: t - rint(t) = t + rint(-t) is exact, so this equals the scalar form.
 template <bool FAST>
@@ -765,13 +775,15 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ d
             const int v = 32 * g + lane;
             if (v < NV) {
               const float4* row = reinterpret_cast<const float4*>(s_red + v * RS);
-              float4 a = row[0];
+              const float4 a = row[0];
+              float2 lo = make_float2(a.x, a.y), hi = make_float2(a.z, a.w);   // packed column sums
 #pragma unroll
               for (int c = 1; c < 8; ++c) {
                 const float4 t = row[c];
-                a.x += t.x; a.y += t.y; a.z += t.z; a.w += t.w;
+                lo = __fadd2_rn(lo, make_float2(t.x, t.y));
+                hi = __fadd2_rn(hi, make_float2(t.z, t.w));
               }
-              atomicAdd(&s_acc[j * NS + v], (a.x + a.y) + (a.z + a.w));
+              atomicAdd(&s_acc[j * NS + v], (lo.x + lo.y) + (hi.x + hi.y));
             }
           }
           __syncwarp();
