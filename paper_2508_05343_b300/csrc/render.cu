@@ -110,10 +110,16 @@ __device__ __forceinline__ void pixel_powers(const float4& h0, const float4& h1,
   }
 }
 
-// Phase 2 pi f2D . d (radians) of a thread's first pixel from the staged (2 pi f2D_x, 2 pi f2D_y);
-// each further row adds 2 pi f2D_y.
+// Phase 2 pi f2D . d (radians) of a thread's first pixel from the staged (2 pi f2D_x, 2 pi f2D_y).
+// With more than two rows per thread each further row adds 2 pi f2D_y; two rows are evaluated
+// directly (row_phases2).
 __device__ __forceinline__ float raw_phase(float Fx, float Fy, float dx, float dy) {
   return __fmaf_rn(Fx, dx, __fmul_rn(Fy, dy));
+}
+
+// Phases of both rows of a thread's column, each as raw_phase gives it for its own offset.
+__device__ __forceinline__ float2 row_phases2(float Fx, float Fy, float dx, const float* dy) {
+  return __ffma2_rn(f2(Fx), f2(dx), __fmul2_rn(f2(Fy), make_float2(dy[0], dy[1])));
 }
 
 // FAST: the phase as it is; otherwise reduced to [-pi, pi] through cycles,
@@ -297,10 +303,7 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
             // envelope, bank and alpha of a pixel that is not reached are computed and discarded
             float2 thp[K > 0 ? K : 1];
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-              const float t0 = raw_phase(fr[2 * i], fr[2 * i + 1], dx, dyq[0]);
-              thp[i] = make_float2(t0, __fadd_rn(t0, fr[2 * i + 1]));
-            }
+            for (int i = 0; i < K; ++i) thp[i] = row_phases2(fr[2 * i], fr[2 * i + 1], dx, dyq);
             const float2 G = make_float2(ex2_approx(pwq[0]), ex2_approx(pwq[1]));
             float2 bank = f2(h1.w);
 #pragma unroll
@@ -611,10 +614,7 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ d
           if (!(live0 || live1)) return;
           float2 thp[K > 0 ? K : 1];
 #pragma unroll
-          for (int i = 0; i < K; ++i) {
-            const float t0 = raw_phase(fw[2 * i], fw[2 * i + 1], dx, dyq[0]);
-            thp[i] = make_float2(t0, __fadd_rn(t0, fw[2 * i + 1]));
-          }
+          for (int i = 0; i < K; ++i) thp[i] = row_phases2(fw[2 * i], fw[2 * i + 1], dx, dyq);
           const float2 G = make_float2(ex2_approx(pwq[0]), ex2_approx(pwq[1]));
           float2 cs[K > 0 ? K : 1], sn[K > 0 ? K : 1];
           float2 bank = f2(h1.w);
