@@ -171,14 +171,20 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 #define GS_WARP_SQUARE 1
 #endif
 
-// Resident CTAs per SM the compositing kernels are compiled for (0: the compiler's choice).  The
-// backward's two-pixel packed adjoint takes 127 registers (4 CTAs per SM) on its own; held to 96
-// for 5 CTAs per SM it spills 16 bytes and runs 5% faster.
+// Resident CTAs per SM the compositing kernels are compiled for (0: the compiler's choice).  At
+// K = 4 the backward's two-pixel packed adjoint takes 127 registers (4 CTAs per SM) on its own;
+// held to 96 for 5 CTAs per SM it spills 16 bytes and runs 5% faster.  The packed adjoint holds
+// both pixels' cosines and sines, so above GS_BWD_PACKED_MAX_K components it would spill heavily
+// under that cap (404 bytes at K = 8, 1.8x slower): those K keep the per-pixel adjoint at 4 CTAs
+// per SM (left to itself the compiler takes 159 registers at K = 8, 3 CTAs per SM).
 #ifndef GS_FWD_MIN_CTAS
 #define GS_FWD_MIN_CTAS 0
 #endif
 #ifndef GS_BWD_MIN_CTAS
 #define GS_BWD_MIN_CTAS 5
+#endif
+#ifndef GS_BWD_PACKED_MAX_K
+#define GS_BWD_PACKED_MAX_K 4
 #endif
 #if GS_FWD_MIN_CTAS
 #define GS_FWD_BOUNDS __launch_bounds__(BLOCK / PPT, GS_FWD_MIN_CTAS)
@@ -186,7 +192,7 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 #define GS_FWD_BOUNDS __launch_bounds__(BLOCK / PPT)
 #endif
 #if GS_BWD_MIN_CTAS
-#define GS_BWD_BOUNDS __launch_bounds__(BLOCK / PPT, GS_BWD_MIN_CTAS)
+#define GS_BWD_BOUNDS __launch_bounds__(BLOCK / PPT, K <= GS_BWD_PACKED_MAX_K ? GS_BWD_MIN_CTAS : 4)
 #else
 #define GS_BWD_BOUNDS __launch_bounds__(BLOCK / PPT)
 #endif
@@ -603,7 +609,7 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ d
         auto pixels = [&](auto fast_tag) {
         float dyq[PPT], pwq[PPT];
         pixel_powers<PPT>(h0, h1, dx, __fsub_rn(fpy0, h0.y), dyq, pwq);
-        if constexpr (PPT == 2) {
+        if constexpr (PPT == 2 && K <= GS_BWD_PACKED_MAX_K) {
           // Both pixels at once.  Envelope, bank and alpha in packed FP32, bit-identical to the
           // forward's decisions.  A pixel that does not take part gets alpha 0 (its transmittance
           // and colour sums stay as they are) and dL/dalpha 0 (it adds nothing), and the two
@@ -690,14 +696,23 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ d
           gv[0] = -gdx;                                    // d mu = - d (pixel - mu)
           gv[1] = -gdy;
         } else {
-          float th[K > 0 ? K : 1];   // raw phases of the current row (the forward's recurrence)
+          // raw phases of the current row, taken as the forward takes them (two rows: row_phases2)
+          float th[K > 0 ? K : 1], th1[K > 0 ? K : 1];
 #pragma unroll
-          for (int i = 0; i < K; ++i) th[i] = raw_phase(fw[2 * i], fw[2 * i + 1], dx, dyq[0]);
+          for (int i = 0; i < K; ++i) {
+            if constexpr (PPT == 2) {
+              const float2 t = row_phases2(fw[2 * i], fw[2 * i + 1], dx, dyq);
+              th[i] = t.x;
+              th1[i] = t.y;
+            } else {
+              th[i] = raw_phase(fw[2 * i], fw[2 * i + 1], dx, dyq[0]);
+            }
+          }
 #pragma unroll
           for (int q = 0; q < PPT; ++q) {
             if (q > 0)
 #pragma unroll
-              for (int i = 0; i < K; ++i) th[i] = __fadd_rn(th[i], fw[2 * i + 1]);
+              for (int i = 0; i < K; ++i) th[i] = PPT == 2 ? th1[i] : __fadd_rn(th[i], fw[2 * i + 1]);
             if (pos >= last[q]) continue;
             const float dy = dyq[q];
             const float pw = pwq[q];
