@@ -368,11 +368,165 @@ def bin_spec(prims_np: dict, cam, cfg, cull: bool = True) -> dict:
                 tiles_x=tiles_x, tiles_y=tiles_y)
 
 
+def _box_min_q(a, b, c, x0, x1, y0, y1):
+    """Smallest q(x, y) = a x^2 + 2 b x y + c y^2 over the box [x0, x1] x [y0, y1] (positive definite
+    q, coordinates relative to the mean): 0 if the box holds the mean, else the least of the four
+    edge minima, each the 1D quadratic's vertex clipped to its edge."""
+    inside = (x0 <= 0) & (0 <= x1) & (y0 <= 0) & (0 <= y1)
+    best = np.full(np.shape(a), np.inf)
+    for x in (x0, x1):
+        y = np.clip(-b * x / c, y0, y1)
+        best = np.minimum(best, a * x * x + 2 * b * x * y + c * y * y)
+    for y in (y0, y1):
+        x = np.clip(-b * y / a, x0, x1)
+        best = np.minimum(best, a * x * x + 2 * b * x * y + c * y * y)
+    return np.where(inside, 0.0, best)
+
+
+def bin_fp64(prims_np: dict, cam, cfg) -> dict:
+    """The binning in float64 throughout, with no float32 step: depth, projected mean and dilated 2D
+    covariance from project() (Sec. 3.1), the largest eigenvalue and the 3-sigma radius
+    ceil(3 sqrt(lambda_max)), the tile rectangle floor((mu -+ r) / 16), and the reach rule of
+    _tile_reachable in exact form: a tile is kept when the ellipse q <= 2 ln(o / alpha_min) meets
+    the box of its pixel centres.  It is the reference that the float32 binning specification of
+    bin_spec() is measured against (binning_differences); its pair set defines no image."""
+    with torch.no_grad():
+        proj = project(_to_f64(prims_np), cam, cfg)
+    mu = proj["mu2d"].numpy()
+    cov = proj["cov2d"].numpy()
+    ca, cb, cc = cov[:, 0, 0], cov[:, 0, 1], cov[:, 1, 1]
+    depth = proj["depth"].numpy()
+    op = np.asarray(prims_np["opacity"], np.float64)
+    n = mu.shape[0]
+    tiles_x = (int(cam["width"]) + TILE - 1) // TILE
+    tiles_y = (int(cam["height"]) + TILE - 1) // TILE
+    with np.errstate(invalid="ignore", over="ignore", divide="ignore"):
+        det = ca * cc - cb * cb
+        mid = 0.5 * (ca + cc)
+        lam = mid + np.sqrt(np.maximum(mid * mid - det, 0.0))
+        rad = np.ceil(3.0 * np.sqrt(np.maximum(lam, 0.0)))
+        finite = np.isfinite(mu).all(1) & np.isfinite(det) & np.isfinite(rad)
+        valid = (depth > cam["znear"]) & (depth <= cam["zfar"]) & (det > 0) & finite
+        x0 = np.floor((mu[:, 0] - rad) / TILE)
+        x1 = np.floor((mu[:, 0] + rad) / TILE)
+        y0 = np.floor((mu[:, 1] - rad) / TILE)
+        y1 = np.floor((mu[:, 1] + rad) / TILE)
+    valid &= (x1 >= 0) & (x0 <= tiles_x - 1) & (y1 >= 0) & (y0 <= tiles_y - 1)
+    x0 = np.where(valid, np.clip(x0, 0, tiles_x - 1), 0).astype(np.int64)
+    x1 = np.where(valid, np.clip(x1, 0, tiles_x - 1), -1).astype(np.int64)
+    y0 = np.where(valid, np.clip(y0, 0, tiles_y - 1), 0).astype(np.int64)
+    y1 = np.where(valid, np.clip(y1, 0, tiles_y - 1), -1).astype(np.int64)
+    cnt = np.where(valid, (x1 - x0 + 1) * (y1 - y0 + 1), 0)
+    prim_of = np.repeat(np.arange(n), cnt)
+    local = np.arange(int(cnt.sum())) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+    wx = (x1 - x0 + 1)[prim_of]
+    ty = y0[prim_of] + local // wx
+    tx = x0[prim_of] + local % wx
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ia, ib, ic = cc / det, -cb / det, ca / det                  # the conic Sigma2D^-1
+        thr = 2.0 * np.log(np.maximum(op, 1e-300) / cfg["alpha_min"])
+        m = prim_of
+        qmin = _box_min_q(ia[m], ib[m], ic[m], 16.0 * tx + 0.5 - mu[m, 0], 16.0 * tx + 15.5 - mu[m, 0],
+                          16.0 * ty + 0.5 - mu[m, 1], 16.0 * ty + 15.5 - mu[m, 1])
+    keep = (op[m] >= cfg["alpha_min"]) & (qmin <= thr[m])
+    return dict(valid=valid, radius=rad, rect=np.stack([x0, x1, y0, y1], -1), prim_of=prim_of[keep],
+                tile=(ty * tiles_x + tx)[keep], qmin=qmin[keep], thr=thr, tiles_x=tiles_x)
+
+
+def binning_differences(prims_np: dict, cam, cfg, spec=None) -> dict:
+    """How the float32 binning specification (bin_spec) differs from the pure float64 binning
+    (bin_fp64): primitives whose validity or rectangle differs, and (primitive, tile) pairs listed
+    by only one of them.  spec_only pairs are reported with the float64 margin of their tile
+    (min q over the tile minus the threshold; > 0 means no pixel of the tile reaches alpha_min, so
+    the pair leaves the image unchanged); fp64_only pairs are ones the float32 rule drops."""
+    spec = bin_spec(prims_np, cam, cfg) if spec is None else spec
+    ref = bin_fp64(prims_np, cam, cfg)
+    tiles_x = spec["tiles_x"]
+    rect_s = np.where(spec["valid"][:, None], spec["rect"], -1)
+    rect_d = np.where(ref["valid"][:, None], ref["rect"], -1)
+    rect_diff = int(np.any(rect_s != rect_d, axis=1).sum())
+    key_s = spec["vals"].astype(np.int64) * (tiles_x * spec["tiles_y"]) + (spec["keys"] >> np.uint64(32)).astype(np.int64)
+    key_d = ref["prim_of"].astype(np.int64) * (tiles_x * spec["tiles_y"]) + ref["tile"]
+    only_s = np.setdiff1d(key_s, key_d)
+    only_d = np.setdiff1d(key_d, key_s)
+    # float64 margin of the spec-only pairs: min q over their tile minus the reach threshold
+    ntile = tiles_x * spec["tiles_y"]
+    ps, ts = only_s // ntile, only_s % ntile
+    with torch.no_grad():
+        proj = project(_to_f64({k: np.asarray(prims_np[k])[ps] for k in
+                                ("means", "scales", "quats", "opacity", "sh", "freqs", "weights")}), cam, cfg)
+    mu, cov = proj["mu2d"].numpy(), proj["cov2d"].numpy()
+    det = cov[:, 0, 0] * cov[:, 1, 1] - cov[:, 0, 1] ** 2
+    tx, ty = ts % tiles_x, ts // tiles_x
+    with np.errstate(invalid="ignore", divide="ignore"):
+        qmin = _box_min_q(cov[:, 1, 1] / det, -cov[:, 0, 1] / det, cov[:, 0, 0] / det,
+                          16.0 * tx + 0.5 - mu[:, 0], 16.0 * tx + 15.5 - mu[:, 0],
+                          16.0 * ty + 0.5 - mu[:, 1], 16.0 * ty + 15.5 - mu[:, 1])
+    margin = qmin - ref["thr"][ps]
+    r = rect_d[ps]
+    in_rect = (tx >= r[:, 0]) & (tx <= r[:, 1]) & (ty >= r[:, 2]) & (ty <= r[:, 3])
+    return dict(P_spec=int(key_s.size), P_fp64=int(key_d.size), rect_diff=rect_diff,
+                spec_only=int(only_s.size), fp64_only=int(only_d.size),
+                spec_only_unreachable=int((in_rect & (margin > 0)).sum()),
+                spec_only_outside_fp64_rect=int((~in_rect).sum()),
+                spec_only_margin=margin, spec_only_in_fp64_rect=in_rect, fp64_only_pairs=only_d)
+
+
 # ----------------------------------------------------------------------------------------------
 # Compositing (Eq. 10 with the 2D Gabor primitive of Eq. 9)
 # ----------------------------------------------------------------------------------------------
-AMBIG_ALPHA = 1e-5     # |alpha - threshold| below this: float32 and float64 may branch differently
-AMBIG_T = 1e-8         # |T (1 - alpha) - T_min| below this: likewise
+# Threshold decisions that float32 may take differently (survey reading c16).  The GPU evaluates
+# alpha in float32 from the float32 projection that the binning specification rounds (projected
+# mean and 2D covariance), so its alpha differs from this float64 alpha by (1) the effect of that
+# rounding, which is computed here exactly by evaluating alpha a second time from the rounded
+# projection, and (2) the rounding of the evaluation itself, bounded below from the size of the
+# terms.  A decision is ambiguous when alpha_min (or alpha_max, or T_min) lies between the float64
+# value and the float32 window; such a pixel is flagged, and its result "the other way" is
+# computed by flipping that decision (flip_allowance).
+U32 = 2.0 ** -24          # float32 unit roundoff
+COS_ERR = 2e-6            # absolute error of the single-precision cosine at |angle| <= 4 pi
+F2D_ROUNDINGS = 8         # roundings charged to each float32 entry behind f2D (see f2d_rounding_bound)
+EVAL_SAFETY = 2.0         # factor over the first-order bounds below
+
+
+def f2d_rounding_bound(prims_np: dict, cam, cfg, ids=None):
+    """First-order bound on how far a float32 evaluation of Eq. 7-8 can move f2D (and, in the
+    z-attenuation variant, the cosine weights w C2): [m,K,2] and [m,K] for primitives ids.
+
+    Forming the ray-space covariance Sigma'' = M R S^2 R^T M^T (M = JW) and f_proj = M^-T f in
+    float32 perturbs each entry by a few roundings of its terms' magnitudes, |M||R| S^2 |R|^T |M|^T
+    and |M^-T||f|.  The bound is F2D_ROUNDINGS u times the sum, over those entries, of |d f2D /
+    d entry| times that magnitude (torch.autograd through splat_frequency).  For elongated
+    primitives, whose Sigma'' is ill-conditioned, it is far larger than u |f2D|.  Eight roundings
+    per entry: an entry of a product of three 3x3 factors is a sum of nine products, each formed
+    from three roundings, added in a chain."""
+    p = _to_f64({k: np.asarray(prims_np[k])[ids] if ids is not None else prims_np[k]
+                 for k in ("means", "scales", "quats", "opacity", "sh", "freqs", "weights")})
+    K = p["weights"].shape[1]
+    m = p["means"].shape[0]
+    if K == 0 or m == 0:
+        return torch.zeros(m, K, 2, dtype=F64), torch.zeros(m, K, dtype=F64)
+    W, tc = camera_tensors(cam)
+    t = p["means"] @ W.T + tc
+    M = jacobian(t, cam) @ W
+    R = rotation_from_quaternion(p["quats"])
+    S2 = p["scales"] ** 2
+    MR, MRa = M @ R, M.abs() @ R.abs()
+    sig = ((MR * S2[:, None, :]) @ MR.transpose(-1, -2)).requires_grad_(True)
+    sig_mag = (MRa * S2[:, None, :]) @ MRa.transpose(-1, -2)
+    MinvT = torch.linalg.inv(M).transpose(-1, -2)
+    fp = torch.einsum("nij,nkj->nki", MinvT, p["freqs"]).requires_grad_(True)
+    fp_mag = torch.einsum("nij,nkj->nki", MinvT.abs(), p["freqs"].abs())
+    f2d = splat_frequency(fp, sig)
+    cw = p["weights"] * z_attenuation(fp, sig) if cfg.get("z_atten") else None
+    bf = torch.zeros(m, K, 2, dtype=F64)
+    bw = torch.zeros(m, K, dtype=F64)
+    for k in range(K):
+        outs = [(f2d[:, k, 0], bf[:, k, 0]), (f2d[:, k, 1], bf[:, k, 1])] + ([(cw[:, k], bw[:, k])] if cw is not None else [])
+        for y, dst in outs:
+            gs, gf = torch.autograd.grad(y.sum(), [sig, fp], retain_graph=True)
+            dst.copy_((gs.abs() * sig_mag).sum((1, 2)) + (gf.abs() * fp_mag).sum((1, 2)))
+    return F2D_ROUNDINGS * U32 * bf, F2D_ROUNDINGS * U32 * bw
 
 
 def gabor_alpha(px, py, rec, cfg):
@@ -391,39 +545,116 @@ def gabor_alpha(px, py, rec, cfg):
     return rec["opacity"][None, :] * G * bank
 
 
-def composite(px, py, rec, cfg):
+def alpha_window(px, py, rec, cfg, alpha_raw, rounded=None):
+    """[lo, hi] holding both this float64 alpha_raw and every float32 evaluation of it.
+
+    rounded: the float32 projected means and conics that the binning specification produces for the
+    same pairs (float64 tensors).  The float32 evaluation then lies within e of the alpha of that
+    rounded projection, with e the first-order rounding bound of: the envelope exponent
+    (8 u per term of 1/2 d^T Q d, and 2^-19 for the exponential); each bank component
+    (COS_ERR + the phase error of a float32 f2D, 2 pi (|df2D_x| |dx| + |df2D_y| |dy|) with df2D from
+    f2d_rounding_bound, + 4 u |phase| for rounding the phase; the cosine weight's own error in the
+    z-attenuation variant); and the products (4 u)."""
+    with torch.no_grad():
+        src = rec if rounded is None else dict(rec, mu2d=rounded["mu2d"], conic=rounded["conic"])
+        alt = alpha_raw if rounded is None else gabor_alpha(px, py, src, cfg)
+        dx = px[:, None] - src["mu2d"][None, :, 0]
+        dy = py[:, None] - src["mu2d"][None, :, 1]
+        a, b, c = src["conic"][:, 0], src["conic"][:, 1], src["conic"][:, 2]
+        terms = 0.5 * (a.abs() * dx * dx + c.abs() * dy * dy) + (b * dx * dy).abs()
+        G = torch.exp(-(0.5 * (a * dx * dx + c * dy * dy) + b * dx * dy))
+        e = alt.abs() * (8 * U32 * terms + 2.0 ** -19 + 4 * U32)
+        w = rec["cos_weights"]
+        if w.shape[1] > 0:
+            f = rec["f2d"]
+            ph = 2.0 * math.pi * ((dx[..., None] * f[None, :, :, 0]).abs() + (dy[..., None] * f[None, :, :, 1]).abs())
+            err = COS_ERR + 4 * U32 * ph
+            if rounded is not None and "f2d_err" in rounded:
+                fe = rounded["f2d_err"]
+                err = err + 2.0 * math.pi * (dx.abs()[..., None] * fe[None, :, :, 0] + dy.abs()[..., None] * fe[None, :, :, 1])
+            e_bank = (w.abs()[None] * err).sum(-1) + 4 * U32 * (1 + w.abs().sum(-1))[None]
+            if rounded is not None and "cw_err" in rounded:
+                e_bank = e_bank + rounded["cw_err"].sum(-1)[None]
+            e = e + rec["opacity"][None, :] * G * e_bank
+        e = EVAL_SAFETY * e
+        lo = torch.minimum(alpha_raw, alt - e)
+        hi = torch.maximum(alpha_raw, alt + e)
+    return lo, hi
+
+
+def composite(px, py, rec, cfg, rounded=None):
     """Front-to-back compositing of L depth-ordered pairs at P pixels (Eq. 10).
 
     Returns colour [P,3], final transmittance [P], the 1-based list position of the last
-    composited pair [P] (0 if none), ambiguity flags for forward / backward comparisons and the
-    number of composited pairs [P].
+    composited pair [P] (0 if none), ambiguity flags for forward / backward comparisons, the
+    number of composited pairs [P], and the allowance [P,3] of each flagged pixel: the sum over
+    its ambiguous decisions of |result with that decision flipped - result|, background included.
     """
     L = rec["mu2d"].shape[0]
     alpha_raw = gabor_alpha(px, py, rec, cfg)
     alpha = torch.clamp_max(alpha_raw, cfg["alpha_max"])
+    amin, amax, Tmin = cfg["alpha_min"], cfg["alpha_max"], cfg["T_min"]
     with torch.no_grad():
-        keep = alpha >= cfg["alpha_min"]
+        keep = alpha >= amin
     a_eff = torch.where(keep, alpha, torch.zeros_like(alpha))
     T_after = torch.cumprod(1.0 - a_eff, dim=1)
     idx = torch.arange(L)
     with torch.no_grad():
-        stop = keep & (T_after < cfg["T_min"])
+        stop = keep & (T_after < Tmin)
         s = torch.where(stop.any(1), stop.int().argmax(1), torch.full((px.shape[0],), L, dtype=torch.long))
         include = keep & (idx[None, :] < s[:, None])
         evaluated = idx[None, :] <= s[:, None]
         last = torch.where(include, idx[None, :] + 1, torch.zeros_like(idx)[None, :]).amax(1)
-        near_min = (alpha - cfg["alpha_min"]).abs() < AMBIG_ALPHA
-        near_T = keep & ((T_after - cfg["T_min"]).abs() < AMBIG_T)
-        near_max = (alpha_raw - cfg["alpha_max"]).abs() < AMBIG_ALPHA
-        amb_f = ((near_min | near_T) & evaluated).any(1)
+        ar = alpha_raw.detach()
+        lo, hi = alpha_window(px, py, {k: v.detach() for k, v in rec.items()}, cfg, ar, rounded)
+        near_min = (torch.clamp_max(lo, amax) < amin) & (amin <= torch.clamp_max(hi, amax))
+        near_max = (lo < amax) & (amax <= hi)
+        # relative error of the float32 transmittance after each pair: the alpha windows of the
+        # composited pairs so far (relative to 1 - alpha) plus two roundings per pair
+        rel = torch.where(keep, (hi - lo) / (1.0 - a_eff.detach()) + 2 * U32, torch.zeros_like(ar))
+        near_T = keep & ((T_after.detach() - Tmin).abs() <= 1.5 * T_after.detach() * torch.cumsum(rel, 1))
+        flip_min = near_min & evaluated
+        flip_T = near_T & evaluated
+        amb_f = (flip_min | flip_T).any(1)
         amb_b = amb_f | (near_max & evaluated).any(1)
+        allow = torch.zeros(px.shape[0], 3, dtype=F64)
+        for p in torch.nonzero(amb_f)[:, 0].tolist():
+            allow[p] = flip_allowance(ar[p], rec["rgb"].detach(), cfg,
+                                      torch.nonzero(flip_min[p])[:, 0].tolist(), torch.nonzero(flip_T[p])[:, 0].tolist())
     ones = torch.ones(px.shape[0], 1, dtype=F64)
     T_before = torch.cat([ones, T_after[:, :-1]], 1)
     weight = torch.where(include, a_eff * T_before, torch.zeros_like(a_eff))
     C = weight @ rec["rgb"]
     T_ext = torch.cat([T_before, T_after[:, -1:]], 1) if L > 0 else ones
     T_final = torch.gather(T_ext, 1, s[:, None])[:, 0]
-    return C, T_final, last, amb_f, amb_b, include.sum(1)
+    return C, T_final, last, amb_f, amb_b, include.sum(1), allow
+
+
+def composite_pixel(alpha_raw, rgb, cfg, flip_keep=(), flip_stop=()):
+    """One pixel composited pair by pair (Eq. 10), with the alpha_min decision of the pairs in
+    flip_keep and the T_min decision of those in flip_stop inverted.  Returns C + T bg [3]."""
+    T, C = 1.0, torch.zeros(3, dtype=F64)
+    for j in range(alpha_raw.shape[0]):
+        a = min(float(alpha_raw[j]), cfg["alpha_max"])
+        if (a >= cfg["alpha_min"]) == (j in flip_keep):
+            continue
+        test = T * (1.0 - a)
+        if (test < cfg["T_min"]) != (j in flip_stop):
+            break
+        C = C + rgb[j] * (a * T)
+        T = test
+    return C + T * torch.tensor(cfg["bg"], dtype=F64)
+
+
+def flip_allowance(alpha_raw, rgb, cfg, flips_min, flips_T):
+    """Sum over the ambiguous decisions of a pixel of |result with that decision flipped - result|."""
+    base = composite_pixel(alpha_raw, rgb, cfg)
+    out = torch.zeros(3, dtype=F64)
+    for j in flips_min:
+        out += (composite_pixel(alpha_raw, rgb, cfg, flip_keep=(j,)) - base).abs()
+    for j in flips_T:
+        out += (composite_pixel(alpha_raw, rgb, cfg, flip_stop=(j,)) - base).abs()
+    return out
 
 
 def _tile_pixels(tx, ty, width, height):
@@ -443,8 +674,9 @@ def _to_f64(prims, requires_grad=False):
     return out
 
 
-def _render_tiles(proj, spec, cam, cfg, dL_dC=None, tiles=None, max_elems=1 << 22):
-    """Composite every tile (or the listed tile ids); optionally back-propagate dL/dC per tile."""
+def _render_tiles(proj, spec, cam, cfg, dL_dC=None, tiles=None, max_elems=1 << 22, prims=None):
+    """Composite every tile (or the listed tile ids); optionally back-propagate dL/dC per tile.
+    prims (the numpy inputs) lets the ambiguity windows include the float32 f2D bound."""
     width, height = cam["width"], cam["height"]
     tiles_x = spec["tiles_x"]
     bg = torch.tensor(cfg["bg"], dtype=F64)
@@ -454,7 +686,23 @@ def _render_tiles(proj, spec, cam, cfg, dL_dC=None, tiles=None, max_elems=1 << 2
     comp = torch.zeros(height, width, dtype=torch.long)
     amb_f = torch.zeros(height, width, dtype=torch.bool)
     amb_b = torch.zeros(height, width, dtype=torch.bool)
+    allow = torch.zeros(3, height, width, dtype=F64)
     K = proj["weights"].shape[1]
+    # the float32 projection of the binning specification (what a float32 evaluation consumes)
+    cov32 = spec["cov2d"].astype(np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        det32 = cov32[:, 0] * cov32[:, 2] - cov32[:, 1] * cov32[:, 1]
+        conic32 = np.stack([cov32[:, 2] / det32, -cov32[:, 1] / det32, cov32[:, 0] / det32], -1)
+    rounded_all = dict(mu2d=torch.from_numpy(spec["mu2d"].astype(np.float64)), conic=torch.from_numpy(conic32))
+    if prims is not None and K > 0:
+        # f2D bound for the primitives of the rendered tiles only
+        tl = range(spec["tiles_x"] * spec["tiles_y"]) if tiles is None else tiles
+        sel = [spec["sorted_vals"][int(spec["ranges"][t, 0]):int(spec["ranges"][t, 1])] for t in tl]
+        used = np.unique(np.concatenate(sel)).astype(np.int64) if sel else np.zeros(0, np.int64)
+        fe, we = f2d_rounding_bound(prims, cam, cfg, used)
+        n_all = proj["mu2d"].shape[0]
+        rounded_all["f2d_err"] = torch.zeros(n_all, K, 2, dtype=F64).index_copy_(0, torch.from_numpy(used), fe)
+        rounded_all["cw_err"] = torch.zeros(n_all, K, dtype=F64).index_copy_(0, torch.from_numpy(used), we)
     tile_list = range(spec["tiles_x"] * spec["tiles_y"]) if tiles is None else tiles
     for tid in tile_list:
         s0, s1 = int(spec["ranges"][tid, 0]), int(spec["ranges"][tid, 1])
@@ -468,7 +716,8 @@ def _render_tiles(proj, spec, cam, cfg, dL_dC=None, tiles=None, max_elems=1 << 2
         for c0 in range(0, gxp.shape[0], chunk):
             sl = slice(c0, c0 + chunk)
             rec = {k: proj[k].index_select(0, ids) for k in REC_KEYS}   # fresh graph per pixel chunk
-            C, T, lst, af, ab, nc = composite(gxp[sl], gyp[sl], rec, cfg)
+            rounded = {k: v.index_select(0, ids) for k, v in rounded_all.items()}
+            C, T, lst, af, ab, nc, al = composite(gxp[sl], gyp[sl], rec, cfg, rounded)
             out = C + T[:, None] * bg[None, :]
             if dL_dC is not None:
                 g = dL_dC[:, gyi[sl], gxi[sl]].T
@@ -479,15 +728,18 @@ def _render_tiles(proj, spec, cam, cfg, dL_dC=None, tiles=None, max_elems=1 << 2
             comp[gyi[sl], gxi[sl]] = nc
             amb_f[gyi[sl], gxi[sl]] = af
             amb_b[gyi[sl], gxi[sl]] = ab
-    return dict(image=img, T=Tf, n_contrib=last, n_comp=comp, ambiguous=amb_f, ambiguous_bwd=amb_b)
+            allow[:, gyi[sl], gxi[sl]] = al.T
+    return dict(image=img, T=Tf, n_contrib=last, n_comp=comp, ambiguous=amb_f, ambiguous_bwd=amb_b,
+                allowance=allow)
 
 
-def render(prims: dict, cam, cfg, tiles=None, third_row="z", cull=True) -> dict:
-    """Forward render in float64.  prims: numpy arrays (means, scales, quats, opacity, sh, freqs, weights)."""
-    spec = bin_spec(prims, cam, cfg, cull=cull)
+def render(prims: dict, cam, cfg, tiles=None, third_row="z", cull=True, spec=None) -> dict:
+    """Forward render in float64.  prims: numpy arrays (means, scales, quats, opacity, sh, freqs, weights).
+    spec: bin_spec(prims, cam, cfg, cull) when the caller already has it."""
+    spec = bin_spec(prims, cam, cfg, cull=cull) if spec is None else spec
     with torch.no_grad():
         proj = project(_to_f64(prims), cam, cfg, third_row)
-    out = _render_tiles(proj, spec, cam, cfg, tiles=tiles)
+    out = _render_tiles(proj, spec, cam, cfg, tiles=tiles, prims=prims)
     out["spec"] = spec
     out["proj"] = {k: v.detach() for k, v in proj.items()}
     return out
@@ -510,8 +762,9 @@ def render_frequency_map(prims: dict, cam, cfg) -> dict:
     with torch.no_grad():
         proj = project(_to_f64(prims), cam, cfg)
     proj = dict(proj, rgb=frequency_features(proj))
-    out = _render_tiles(proj, spec, cam, dict(cfg, bg=(0.0, 0.0, 0.0)))
+    out = _render_tiles(proj, spec, cam, dict(cfg, bg=(0.0, 0.0, 0.0)), prims=prims)
     out["map"] = out.pop("image")
+    out["spec"] = spec
     return out
 
 
@@ -526,7 +779,7 @@ def render_backward(prims: dict, cam, cfg, dL_dC) -> dict:
     proj = project(leaves, cam, cfg)
     rec = {k: proj[k].detach().clone().requires_grad_(True) for k in REC_KEYS}
     g = torch.as_tensor(np.asarray(dL_dC, np.float64), dtype=F64)
-    out = _render_tiles(rec, spec, cam, cfg, dL_dC=g)
+    out = _render_tiles(rec, spec, cam, cfg, dL_dC=g, prims=prims)
     g2d = {k: (rec[k].grad if rec[k].grad is not None else torch.zeros_like(rec[k])) for k in REC_KEYS}
     outs = [proj[k] for k in REC_KEYS if proj[k].requires_grad]
     gouts = [g2d[k] for k in REC_KEYS if proj[k].requires_grad]
