@@ -7,7 +7,8 @@ from oracle import gabsplat_oracle as O
 
 IMG_TOL = 2e-4      # max-abs per channel, float32 image vs float64 oracle
 GRAD_TOL = 1e-3     # relative L2 per attribute group
-AMBIG_EXTRA = 1e-2  # extra allowance at pixels where float32/float64 may take a different threshold branch
+MAX_FLAGGED = 1e-3  # flagged pixels (a threshold decision float32 may take the other way) per image pixel
+FLAGS_PER_PAIR = 2e-5   # ... or per listed pixel-pair, whichever allows more (see assert_image_parity)
 ATTRS = ("means", "scales", "quats", "opacity", "sh", "freqs", "weights")
 
 
@@ -38,22 +39,63 @@ def bf16_prims(prims):
     return out
 
 
-def compare_images(gpu_img, ref, amb, tol=IMG_TOL):
-    """Returns (max error at unambiguous pixels, max error at ambiguous ones, ambiguous count)."""
-    err = np.abs(gpu_img - ref).max(0)
-    amb = np.asarray(amb, bool)
-    e_clean = float(err[~amb].max()) if (~amb).any() else 0.0
-    e_amb = float(err[amb].max()) if amb.any() else 0.0
-    return e_clean, e_amb, int(amb.sum())
+def image_errors(gpu_img, out, tol=IMG_TOL, mask=None):
+    """Per-pixel check of a [C][H][W] image against the oracle: every channel within tol of the
+    oracle, or, at a pixel the oracle flags (a threshold decision float32 may take the other way),
+    within tol + the oracle's allowance for that pixel (the result with each flagged decision
+    flipped).  Returns (max error at unflagged pixels, largest excess over the allowance at flagged
+    ones (<= 0 passes), flagged count); mask restricts the check to some pixels."""
+    err = np.abs(np.asarray(gpu_img, np.float64) - out["image"].numpy())
+    amb = np.asarray(out["ambiguous"].numpy(), bool)
+    allow = out["allowance"].numpy()
+    if mask is None:
+        mask = np.ones(amb.shape, bool)
+    clean = mask & ~amb
+    flagged = mask & amb
+    e_clean = float(err.max(0)[clean].max()) if clean.any() else 0.0
+    excess = float((err - tol - allow).max(0)[flagged].max()) if flagged.any() else -tol
+    return e_clean, excess, int(flagged.sum())
 
 
-def assert_image_parity(gpu_img, out, tol=IMG_TOL, max_amb_frac=0.02):
-    e_clean, e_amb, namb = compare_images(gpu_img, out["image"].numpy(), out["ambiguous"].numpy())
-    npx = gpu_img.shape[1] * gpu_img.shape[2]
-    assert e_clean <= tol, f"max |gpu - oracle| = {e_clean:.3e} at unambiguous pixels"
-    assert e_amb <= tol + AMBIG_EXTRA, f"ambiguous pixel error {e_amb:.3e}"
-    assert namb <= max_amb_frac * npx, f"{namb} ambiguous pixels of {npx}"
+def listed_pixel_pairs(spec, shape, mask=None):
+    """Sum over the (masked) pixels of their tile's list length: the threshold decisions a pixel
+    can face, an upper bound on its evaluated pairs."""
+    L = (spec["ranges"][:, 1].astype(np.int64) - spec["ranges"][:, 0]).reshape(spec["tiles_y"], spec["tiles_x"])
+    per_px = np.repeat(np.repeat(L, 16, 0), 16, 1)[:shape[0], :shape[1]]
+    return int(per_px[mask].sum()) if mask is not None else int(per_px.sum())
+
+
+def assert_image_parity(gpu_img, out, tol=IMG_TOL, max_flagged=None, mask=None):
+    """Image bars of the parity tests.  Every pixel within tol, or, if flagged, within tol + its
+    flip allowance.  The flagged count is capped: each of a pixel's threshold decisions can fall
+    inside its float32 window, so the expected count grows with the pairs a pixel evaluates; the
+    cap is 0.1% of the pixels or 2e-5 per listed pixel-pair (tile list length summed over the
+    pixels), whichever is larger (measured: at most 1.2e-5 per listed pixel-pair at config 2,
+    4e-5 per pixel-pair and 0.06% of the pixels at config 1).  max_flagged overrides it as a
+    fraction of the pixels."""
+    e_clean, excess, namb = image_errors(gpu_img, out, tol, mask)
+    npx = int(np.asarray(mask).sum()) if mask is not None else gpu_img.shape[1] * gpu_img.shape[2]
+    assert e_clean <= tol, f"max |gpu - oracle| = {e_clean:.3e} at unflagged pixels"
+    assert excess <= 0.0, f"a flagged pixel exceeds tol + its flip allowance by {excess:.3e}"
+    if max_flagged is not None:
+        cap = max(1.0, max_flagged * npx)
+    else:
+        pairs = listed_pixel_pairs(out["spec"], gpu_img.shape[1:], mask) if "spec" in out else 0
+        cap = max(1.0, MAX_FLAGGED * npx, FLAGS_PER_PAIR * pairs)
+    assert namb <= cap, f"{namb} flagged pixels of {npx} (cap {cap:.0f})"
     return e_clean, namb
+
+
+def assert_decisions_flagged(v, out, mask=None):
+    """The flags are a valid account of float32 / float64 branch differences: at every pixel where
+    the GPU's composited-pair count or last contributor differs from the oracle's, the oracle has
+    flagged a decision."""
+    amb = out["ambiguous"].numpy()
+    diff = (v["n_comp"].cpu().numpy() != out["n_comp"].numpy()) | (v["n_contrib"].cpu().numpy() != out["n_contrib"].numpy())
+    if mask is not None:
+        diff &= mask
+    assert not (diff & ~amb).any(), f"{int((diff & ~amb).sum())} unflagged pixels take another branch on the GPU"
+    return int(diff.sum())
 
 
 def rel_l2(a, b):

@@ -1,9 +1,11 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
 Bars: tile lists / depth ranks / sorted pairs / ranges / touched counts bit-exact; images within 2e-4 max-abs per
-channel (pixels where float32 and float64 may branch differently at alpha_min or T_min get the
-extra allowance of one skipped pair and are counted); gradients within 1e-3 relative L2 per
-attribute group of the oracle's analytic gradients and of its central finite differences.
+channel (a pixel where the oracle finds that float32 may take a threshold decision at alpha_min,
+alpha_max or T_min the other way is flagged, and gets 2e-4 plus the oracle's result with that
+decision flipped; at most 0.1% of the pixels are flagged, and every pixel whose decisions differ
+on the GPU must be flagged); gradients within 1e-3 relative L2 per attribute group of the
+oracle's analytic gradients and of its central finite differences.
 """
 import numpy as np
 import pytest
@@ -12,8 +14,8 @@ import torch
 from oracle import gabsplat_oracle as O
 from paper_2508_05343_b300 import scenes
 from tests.conftest import cuda_available
-from tests.gpu_util import (AMBIG_EXTRA, ATTRS, GRAD_TOL, IMG_TOL, assert_image_parity, bf16_prims, by_prim,
-                            cfg_pair, compare_images, gpu_grads, gpu_render, rel_l2)
+from tests.gpu_util import (ATTRS, GRAD_TOL, IMG_TOL, assert_decisions_flagged, assert_image_parity, bf16_prims,
+                            by_prim, cfg_pair, gpu_grads, gpu_render, rel_l2)
 
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_available(), reason="needs a CUDA device")]
 
@@ -88,13 +90,11 @@ def test_config0_every_stage(eps2d):
     r, _, img, T = gpu_render(prims, cam, gc)
     v = check_binning(r, out["spec"])
     check_records(v, out, prims)
-    assert_image_parity(img.cpu().numpy(), out)
+    _, namb = assert_image_parity(img.cpu().numpy(), out)
+    print(f"flagged pixels: {namb} of {img.shape[1] * img.shape[2]}")
     amb = out["ambiguous"].numpy()
     np.testing.assert_allclose(T.cpu().numpy()[~amb], out["T"].numpy()[~amb], atol=IMG_TOL)
-    nc = v["n_contrib"].cpu().numpy()
-    assert (nc[~amb] == out["n_contrib"].numpy()[~amb]).mean() > 0.999
-    ncomp = v["n_comp"].cpu().numpy()
-    assert (ncomp[~amb] == out["n_comp"].numpy()[~amb]).mean() > 0.999
+    assert_decisions_flagged(v, out)   # n_contrib and n_comp equal the oracle's at every unflagged pixel
 
 
 def test_config1_forward_bitexact_bins_and_image():
@@ -106,7 +106,9 @@ def test_config1_forward_bitexact_bins_and_image():
     check_records(v, out, prims)
     flags = v["records"].cpu().numpy()[:, 11]
     assert (flags == 1.0).any() and (flags == 0.0).any()   # both bank evaluations are exercised
-    assert_image_parity(img.cpu().numpy(), out)
+    _, namb = assert_image_parity(img.cpu().numpy(), out)
+    print(f"flagged pixels: {namb} of {img.shape[1] * img.shape[2]}")
+    assert_decisions_flagged(v, out)
 
 
 @pytest.mark.parametrize("cfgi", [0, 1])
@@ -118,7 +120,8 @@ def test_frequency_map_matches_oracle(cfgi):
     r, _, _, _ = gpu_render(prims, cam, gc)
     m = r.frequency_map()
     torch.cuda.synchronize()
-    assert_image_parity(m.cpu().numpy(), {"image": ref["map"], "ambiguous": ref["ambiguous"]})
+    assert_image_parity(m.cpu().numpy(), {"image": ref["map"], "ambiguous": ref["ambiguous"],
+                                          "allowance": ref["allowance"], "spec": ref["spec"]})
     assert np.abs(ref["map"].numpy()).max() > 1e-2
 
 
@@ -347,8 +350,95 @@ def test_config1_gradients_vs_oracle_finite_differences():
     assert checked == 3
 
 
-@pytest.mark.parametrize("K,storage,w,h", [(0, 0, 100, 70), (1, 0, 100, 70), (3, 0, 53, 97), (8, 0, 100, 70),
-                                           (2, 1, 100, 70), (4, 1, 64, 48)])
+def test_config1_gradients_p8_coordinates_and_directions():
+    """Survey pin p8 at config 1: the GPU's analytic gradient against central differences of the
+    FP64 oracle, per attribute group, along 8 seeded random directions (each moving 8 primitives)
+    and at 2000 seeded random single coordinates, h = 1e-6 max(1, |theta|).  Samples where some
+    pixel of the affected tiles changes a compositing decision between the two renders (the image
+    is not differentiable there) are drawn again; per group, the relative L2 distance between the
+    analytic and the finite-difference values is within 1e-3."""
+    from tests.fd_util import directional_fds
+    prims, cam = scenes.config_scene(1), scenes.config_cameras(1)[0]
+    oc, gc = cfg_pair()
+    out = O.render(prims, cam, oc)
+    spec = out["spec"]
+    target = scenes.make_target(cam["width"], cam["height"], 1103)
+    dL = _masked_l2_grad(out["image"].numpy(), target, out["ambiguous_bwd"].numpy())
+    r, _, _, _ = gpu_render(prims, cam, gc)
+    g = gpu_grads(r, dL)
+    rng = np.random.default_rng(88)
+    act = np.nonzero(spec["touched"] > 0)[0]
+    p64 = {k: (np.asarray(v, np.float64) if k in ATTRS else v) for k, v in prims.items()}
+
+    def draw_coordinate():
+        k = ATTRS[rng.integers(len(ATTRS))]
+        i = int(rng.choice(act))
+        row = p64[k][i]
+        j = int(rng.integers(row.size))
+        u = np.zeros((1,) + row.shape)
+        u.reshape(-1)[j] = 1.0
+        h = 1e-6 * max(1.0, abs(float(row.reshape(-1)[j])))
+        return k, (np.array([i]), {k: u}, h), float(g[k][i].reshape(-1)[j])
+
+    def draw_direction(k):
+        ids = np.sort(rng.choice(act, 8, replace=False))
+        u = rng.standard_normal((8,) + p64[k].shape[1:])
+        u *= max(1.0, float(np.abs(p64[k][ids]).max())) / np.abs(u).max()
+        return k, (ids, {k: u}, 1e-6), float((g[k][ids].astype(np.float64) * u).sum())
+
+    samples = [draw_direction(k) for k in ATTRS for _ in range(8)] + [draw_coordinate() for _ in range(2000)]
+    got = []
+    while samples:
+        res = directional_fds(p64, cam, oc, dL, spec, [s[1] for s in samples])
+        redo = 0
+        for (k, job, analytic), (fd, flipped) in zip(samples, res):
+            if flipped:
+                redo += 1
+            else:
+                got.append((k, analytic, fd))
+        assert redo <= 0.05 * len(samples) + 2, f"{redo} of {len(samples)} samples straddle a decision"
+        samples = [draw_coordinate() for _ in range(redo)]
+    errs = {}
+    for k in ATTRS:
+        a = np.array([x[1] for x in got if x[0] == k])
+        f = np.array([x[2] for x in got if x[0] == k])
+        assert a.size >= 8 + 150, (k, a.size)
+        errs[k] = rel_l2(a, f)
+    assert all(e <= GRAD_TOL for e in errs.values()), errs
+
+
+def test_2dgabsplat_fixed_direction_case():
+    """Survey pin p9 (Sec. 3.2.2, relation to 2DGabSplat): every frequency of every primitive on
+    one world axis.  Eq. 7-8 are linear in f, so each primitive's K projected frequencies are
+    multiples of the projected axis; the GPU path renders and differentiates the scene at the
+    usual bars."""
+    spec = scenes.SceneSpec(n=900, K=3, sh_degree=1, layout="uniform", box=1.0, log_scale=(-2.8, 0.5))
+    prims = scenes.make_scene(spec, 909)
+    axis = np.array([0.75, 0.0, 0.5], np.float32)       # multiples m / 8 of it are exact in float32
+    mags = (np.random.default_rng(910).integers(-64, 65, (900, 3)) / 8.0).astype(np.float32)
+    mags[mags == 0] = 0.125
+    prims["freqs"] = (mags[:, :, None] * axis[None, None, :]).astype(np.float32)
+    cam = scenes.orbit_camera(112, 80, 25.0, 10.0, 3.5)
+    oc, gc = cfg_pair(bg=(0.1, 0.1, 0.1))
+    out = O.render(prims, cam, oc)
+    f2d = out["proj"]["f2d"].numpy()                       # [n, K, 2]
+    unit = f2d / mags[:, :, None]                          # the projected axis, the same for every i
+    np.testing.assert_allclose(unit, np.repeat(unit[:, :1], 3, 1), rtol=1e-9, atol=1e-12)
+    r, _, img, _ = gpu_render(prims, cam, gc)
+    v = check_binning(r, out["spec"])
+    assert_image_parity(img.cpu().numpy(), out)
+    assert_decisions_flagged(v, out)
+    dL = np.random.default_rng(911).standard_normal((3, cam["height"], cam["width"])) * 1e-3
+    dL[:, out["ambiguous_bwd"].numpy()] = 0.0
+    ref = O.render_backward(prims, cam, oc, dL)
+    g = gpu_grads(r, dL)
+    errs = {k: rel_l2(g[k], ref[k]) for k in ATTRS}
+    assert all(e <= GRAD_TOL for e in errs.values()), errs
+
+
+@pytest.mark.parametrize("K,storage,w,h", [(0, 0, 100, 70), (1, 0, 100, 70), (3, 0, 53, 97), (4, 0, 100, 70),
+                                           (5, 0, 53, 97), (8, 0, 100, 70), (2, 1, 100, 70), (4, 1, 64, 48),
+                                           (6, 1, 64, 48)])
 def test_components_storage_and_ragged_sizes(K, storage, w, h):
     spec = scenes.SceneSpec(n=600, K=K, sh_degree=2, layout="uniform", box=1.0, log_scale=(-2.8, 0.5))
     prims = scenes.make_scene(spec, 4242 + K)
@@ -391,9 +481,8 @@ def test_depth_ties_and_single_tile_images(w, h):
     v = check_binning(r, out["spec"])
     depth = np.asarray(out["spec"]["depth"], np.float32)[v["order"].cpu().numpy()]
     assert (np.diff(depth) == 0).any()                  # ties occur among the ranked primitives
-    # 240 overlapping primitives over as few as 117 pixels: a few pixels sit at a float32 / float64
-    # branch tie (each still within its error bound), more than the 2% of larger images
-    assert_image_parity(img.cpu().numpy(), out, max_amb_frac=0.05)
+    assert_image_parity(img.cpu().numpy(), out)
+    assert_decisions_flagged(v, out)
 
 
 def test_binning_near_the_image_border():
@@ -423,10 +512,13 @@ def test_binning_near_the_image_border():
     r, _, img, _ = gpu_render(prims, cam, gc)
     touched = out["spec"]["touched"]
     assert 50 < (touched > 0).sum() < n - 500          # both kept and culled primitives in the band
-    check_binning(r, out["spec"])
-    # about 130 evaluated pairs per pixel (large footprints overlapping along the edges): 4% of the
-    # pixels hold a pair inside the float32 / float64 ambiguity band, above the usual 2%
-    assert_image_parity(img.cpu().numpy(), out, max_amb_frac=0.06)
+    v = check_binning(r, out["spec"])
+    # about 130 evaluated pairs per pixel, many from footprints hundreds of pixels wide at high
+    # frequency: their float32 phases carry errors of up to ~1e-3 rad, so about 1.6% of the pixels
+    # hold a pair whose decision float32 may take the other way (each still checked against its
+    # flip allowance)
+    assert_image_parity(img.cpu().numpy(), out, max_flagged=0.02)
+    assert_decisions_flagged(v, out)
 
 
 def test_empty_scene_and_all_culled():
@@ -507,29 +599,38 @@ def test_bounded_lookback_wait_reports_timeout():
     assert r.status()[0] == B.GS_OK and torch.isfinite(img).all()
 
 
-def test_full_size_training_view_sampled():
+_BIN_CACHE = {}
+
+
+@pytest.mark.parametrize("K,storage", [(4, 0), (8, 0), (4, 1)])
+def test_full_size_training_view_sampled(K, storage):
     """1.5M primitives at 1600x1064 in the benchmark's launch configuration: bins bit-exact against
     the oracle's binning, images on a seeded sample of tiles (incl. the longest list) against the
-    oracle, and gradients of the primitives in those tiles for a loss restricted to them."""
-    prims, cam = scenes.config_scene(2), scenes.config_cameras(2)[0]
+    oracle, and gradients of the primitives in those tiles for a loss restricted to them.  K = 8
+    runs the per-pixel adjoint (above the packed two-pixel adjoint's K <= 4), storage 1 the BF16
+    SH / frequency / weight path (the oracle consumes the same rounded values).  The binning does
+    not depend on K or on the storage, so the oracle bins once."""
+    prims, cam = scenes.config_scene(2, K=K), scenes.config_cameras(2)[0]
+    if storage == 1:
+        prims = bf16_prims(prims)
     oc, gc = cfg_pair()
-    spec = O.bin_spec(prims, cam, oc)
-    r, _, img, _ = gpu_render(prims, cam, gc)
+    if "cfg2" not in _BIN_CACHE:
+        _BIN_CACHE["cfg2"] = O.bin_spec(prims, cam, oc)
+    spec = _BIN_CACHE["cfg2"]
+    r, _, img, _ = gpu_render(prims, cam, gc, storage=storage)
     check_binning(r, spec)
     L = spec["ranges"][:, 1].astype(np.int64) - spec["ranges"][:, 0]
     rng = np.random.default_rng(2)
     nonempty = np.nonzero(L > 0)[0]
     tiles = sorted(set(rng.choice(nonempty, 10, replace=False).tolist()) | {int(L.argmax())})
-    out = O.render(prims, cam, oc, tiles=tiles)
+    out = O.render(prims, cam, oc, tiles=tiles, spec=spec)
     gi = img.cpu().numpy()
     tx = spec["tiles_x"]
     mask = np.zeros((cam["height"], cam["width"]), bool)
     for t in tiles:
         mask[(t // tx) * 16:(t // tx) * 16 + 16, (t % tx) * 16:(t % tx) * 16 + 16] = True
-    amb = out["ambiguous"].numpy()
-    err = np.abs(gi - out["image"].numpy()).max(0)
-    assert err[mask & ~amb].max() <= IMG_TOL
-    assert err[mask & amb].max(initial=0.0) <= IMG_TOL + AMBIG_EXTRA
+    assert_image_parity(gi, out, mask=mask)
+    assert_decisions_flagged(r.views(), out, mask=mask)
     # gradients restricted to the sampled tiles
     dL = np.zeros((3, cam["height"], cam["width"]))
     dL[:, mask] = np.random.default_rng(3).standard_normal((3, int(mask.sum()))) * 1e-3
@@ -543,3 +644,23 @@ def test_full_size_training_view_sampled():
     for k in ATTRS:
         e = rel_l2(g[k][ids], ref[k])
         assert e <= GRAD_TOL, (k, e)
+
+
+def test_frequency_sweep_scene_centre_crop():
+    """Config 4's scene (3M primitives, 1920x1080, K = 4) against the oracle on the 256 x 256
+    centre crop [832, 1088) x [412, 668): bins bit-exact for the whole frame, the crop's pixels at
+    the image bars."""
+    prims, cam = scenes.config_scene(4, K=4), scenes.config_cameras(4)[0]
+    oc, gc = cfg_pair()
+    r, _, img, _ = gpu_render(prims, cam, gc)
+    spec = O.bin_spec(prims, cam, oc)
+    v = check_binning(r, spec)
+    x0, x1, y0, y1 = 832, 1088, 412, 668
+    tx = spec["tiles_x"]
+    tiles = [ty * tx + t for ty in range(y0 // 16, (y1 - 1) // 16 + 1) for t in range(x0 // 16, (x1 - 1) // 16 + 1)]
+    out = O.render(prims, cam, oc, tiles=tiles, spec=spec)
+    mask = np.zeros((cam["height"], cam["width"]), bool)
+    mask[y0:y1, x0:x1] = True
+    _, namb = assert_image_parity(img.cpu().numpy(), out, mask=mask)
+    print(f"crop: {namb} flagged pixels of {mask.sum()}")
+    assert_decisions_flagged(v, out, mask=mask)
