@@ -32,6 +32,7 @@ class Rasterizer:
         self.frame = B.gs_frame()
         self._alloc(pair_capacity if pair_capacity is not None else max(1 << 16, 8 * n))
         self._loss_scratch = None
+        self.generation = 0     # counts forwards: the workspace holds the state of the last one
 
     def _alloc(self, cap):
         cap = int(cap)
@@ -52,6 +53,7 @@ class Rasterizer:
         """preprocess -> bin_sort -> render_fwd.  With auto_capacity the pair count is read back once
         (a host synchronisation) and the workspace regrown if it overflowed.  forward_only renders
         without the state a backward pass needs (gabsplat_render_fwd_only)."""
+        self.generation += 1
         self._prims = B.make_prims(prims_t, storage)
         self.storage = storage
         self.frame.storage = storage        # the frame carries the storage type to every stage
@@ -137,28 +139,49 @@ class Rasterizer:
 
 
 class GabSplatRender(torch.autograd.Function):
-    """image = render(primitives, camera); backward via the hand-written adjoint kernels.
+    """image = render(primitives, camera), differentiable in every primitive attribute; the backward
+    runs the hand-written adjoint kernels (gabsplat_render_bwd), which recompute transmittance
+    instead of storing per-pair state.
 
-    Inputs are activated attributes (exp / sigmoid are applied by the caller in torch)."""
+    Inputs are activated attributes (exp / sigmoid are applied by the caller in torch).
+
+    Storage: with storage="bf16" the SH, frequency and weight tensors are rounded to BF16 (nearest
+    even) for the kernels, which evaluate and composite in FP32.  Gradients are always computed in
+    FP32 and returned in each input's own dtype: FP32 master tensors (the usual mixed-precision
+    setup) receive the FP32 gradient, the rounding being passed straight through; BF16 inputs
+    receive the FP32 gradient rounded to BF16 (autograd requires a gradient of the input's dtype).
+
+    The rasterizer's workspace holds the state of its last forward only.  If another forward ran
+    on the same Rasterizer before this one's backward, the backward first re-renders this forward's
+    inputs (same inputs, same frame), so the gradients always belong to this forward."""
 
     @staticmethod
-    def forward(ctx, rast: Rasterizer, camera: dict, cfg, means, scales, quats, opacity, sh, freqs, weights):
-        prims = dict(means=means.contiguous(), scales=scales.contiguous(), quats=quats.contiguous(),
-                     opacity=opacity.contiguous(), sh=sh.contiguous(), freqs=freqs.contiguous(),
-                     weights=weights.contiguous())
-        storage = B.GS_BF16 if sh.dtype == torch.bfloat16 else B.GS_F32
-        img = rast.forward(prims, camera, cfg, storage=storage)
-        ctx.rast = rast
+    def forward(ctx, rast: Rasterizer, camera: dict, cfg, storage, means, scales, quats, opacity, sh, freqs,
+                weights):
+        if storage not in ("f32", "bf16"):
+            raise ValueError("storage is 'f32' or 'bf16'")
+        st = B.GS_BF16 if storage == "bf16" else B.GS_F32
+        prims = dict(means=means.float().contiguous(), scales=scales.float().contiguous(),
+                     quats=quats.float().contiguous(), opacity=opacity.float().contiguous())
+        for k, t in (("sh", sh), ("freqs", freqs), ("weights", weights)):
+            prims[k] = (t.to(torch.bfloat16) if st == B.GS_BF16 else t.float()).contiguous()
+        img = rast.forward(prims, camera, cfg, storage=st)
+        ctx.rast, ctx.camera, ctx.cfg, ctx.storage = rast, camera, cfg, st
+        ctx.generation = rast.generation
+        ctx.prims = prims            # the tensors the kernels read (kept for a re-render)
         ctx.dtypes = [t.dtype for t in (means, scales, quats, opacity, sh, freqs, weights)]
         return img
 
     @staticmethod
     def backward(ctx, grad_img):
-        g = ctx.rast.backward(grad_img.contiguous())
-        outs = [g[k] for k in ATTRS]
-        outs = [o.to(dt) if o.dtype != dt else o for o, dt in zip(outs, ctx.dtypes)]
-        return (None, None, None, *outs)
+        rast = ctx.rast
+        if rast.generation != ctx.generation:
+            rast.forward(ctx.prims, ctx.camera, ctx.cfg, storage=ctx.storage)
+        g = rast.backward(grad_img.float().contiguous())
+        outs = [g[k] if g[k].dtype == dt else g[k].to(dt) for k, dt in zip(ATTRS, ctx.dtypes)]
+        return (None, None, None, None, *outs)
 
 
-def render(rast: Rasterizer, camera: dict, cfg, means, scales, quats, opacity, sh, freqs, weights):
-    return GabSplatRender.apply(rast, camera, cfg, means, scales, quats, opacity, sh, freqs, weights)
+def render(rast: Rasterizer, camera: dict, cfg, means, scales, quats, opacity, sh, freqs, weights, storage="f32"):
+    """Differentiable render of one view (see GabSplatRender): a [3][H][W] FP32 image."""
+    return GabSplatRender.apply(rast, camera, cfg, storage, means, scales, quats, opacity, sh, freqs, weights)
