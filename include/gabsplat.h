@@ -270,7 +270,9 @@ gs_status gabsplat_loss(const float* image, const float* target, long long count
  *  - count must be at most GS_LOSS_NOALLOC_MAX_COUNT (33,554,432 values, e.g. a 3 x 3840 x 2160
  *    image fits); larger counts return GS_ERR_INVALID_ARG without launching anything.
  *  - The first call on each device looks up the array's device address (with that device
- *    current); make that first call before any stream capture.
+ *    current) and keeps it for the rest of the process; make that first call before any stream
+ *    capture.  A cudaDeviceReset of a device invalidates the kept address: do not call this entry
+ *    point on a device after resetting it.
  *  - All calls share the one array and each call overwrites the slots it reads, so nothing has to
  *    be cleared between calls, but calls that overlap on the GPU (different streams, or different
  *    host threads without ordering) race on it.  Issue them in order on one stream.

@@ -5,6 +5,7 @@
 // whose allocator owns the whole device heap, or a service under a fixed memory budget that
 // forbids allocations once it is running.  gabsplat_loss_noalloc() keeps those partial sums in a
 // fixed array compiled into the library instead, so the caller passes only inputs and outputs.
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -68,8 +69,11 @@ __global__ void k_loss_noalloc_final(const double* __restrict__ partials, int n,
 
 // Device address of the partials array, looked up once per device with that device current.
 // In host code the symbol g_loss_partials is only a host-side stand-in, never a device address.
+// The cached address belongs to the device's primary context as it was at the lookup: after a
+// cudaDeviceReset of that device it is stale (the header says so).  Reads take no lock; the
+// mutex only serialises the first lookup on a device.
 constexpr int NOALLOC_MAX_DEVICES = 64;
-static double* g_partials_dev[NOALLOC_MAX_DEVICES] = {nullptr};
+static std::atomic<double*> g_partials_dev[NOALLOC_MAX_DEVICES];
 static std::mutex g_partials_mutex;
 
 static cudaError_t partials_address(double** out) {
@@ -77,14 +81,19 @@ static cudaError_t partials_address(double** out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_partials_mutex);
-  if (!g_partials_dev[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_loss_partials);
-    if (e != cudaSuccess) return e;
-    g_partials_dev[dev] = reinterpret_cast<double*>(p);
+  double* p = g_partials_dev[dev].load(std::memory_order_acquire);
+  if (!p) {
+    std::lock_guard<std::mutex> lock(g_partials_mutex);
+    p = g_partials_dev[dev].load(std::memory_order_relaxed);
+    if (!p) {
+      void* a = nullptr;
+      e = cudaGetSymbolAddress(&a, g_loss_partials);
+      if (e != cudaSuccess) return e;
+      p = reinterpret_cast<double*>(a);
+      g_partials_dev[dev].store(p, std::memory_order_release);
+    }
   }
-  *out = g_partials_dev[dev];
+  *out = p;
   return cudaSuccess;
 }
 
