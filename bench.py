@@ -439,19 +439,20 @@ class TrainStep:
 
     def timed(self, steps, warmup, barrier, dev):
         """W untimed steps, then K steps between a barrier + synchronize on each side, with CUDA
-        events on the launching stream around the whole region and every stage; clocks sampled
-        throughout.  Returns (ms per step, {stage: ms}, clocks)."""
+        events on the launching stream around the whole region; clocks sampled throughout.  Then
+        the same K steps again with an event between every two stages for the per-stage split
+        (an event between two kernels keeps the second from starting in the first one's tail, so
+        the split comes from its own pass).  Returns (ms per step, {stage: ms}, clocks)."""
         import torch
         sampler = ClockSampler(_pci_id(torch.cuda.get_device_properties(dev)))
         for s in range(warmup):
             self.step(s)
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(steps)]
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
         start.record()
         for s in range(steps):
-            self.step(s, evs[s])
+            self.step(s)
         end.record()
         torch.cuda.synchronize()
         barrier()
@@ -459,6 +460,10 @@ class TrainStep:
         st, _ = self.rast.status()
         if st != self.B.GS_OK:
             raise RuntimeError(f"device status after timed region: {self.B.status_string(st)}")
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(steps)]
+        for s in range(steps):
+            self.step(s, evs[s])
+        torch.cuda.synchronize()
         stage_ms = {nm: float(np.mean([evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(steps)]))
                     for i, nm in enumerate(self.STAGES)}
         return start.elapsed_time(end) / steps, stage_ms, clocks

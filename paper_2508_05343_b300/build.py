@@ -4,7 +4,9 @@
 
 Each translation unit under csrc/ is compiled in parallel into _build/ and linked into
 paper_2508_05343_b300/libgabsplat.so next to the Python binding.  A unit is rebuilt only when it
-or a header is newer than its object file.
+or a header is newer than its object file.  GS_NVCC_EXTRA (environment) appends nvcc flags, e.g.
+-DGS_PDL=0 for a build whose kernels launch without programmatic dependent launch; remove _build/
+before switching flags.
 """
 from __future__ import annotations
 
@@ -47,7 +49,8 @@ def _compile(src, ptxas_info=False, verbose=False):
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep and not ptxas_info:
         return obj, ""
-    cmd = [nvcc(), *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *FLAGS, *os.environ.get("GS_NVCC_EXTRA", "").split(), "-I", INCLUDE, "-I", CSRC, "-c", src,
+           "-o", obj]
     if ptxas_info:
         cmd += ["-Xptxas", "-v"]
     if verbose:

@@ -118,6 +118,7 @@ __device__ __forceinline__ void cta_rank3(const bool f[3], u32 rank[3], u32 tota
 
 // (1) per-block counts of kept originals, clones and split primitives
 __global__ void __launch_bounds__(DN_THREADS) k_densify_count(DensifyParams P, u32* block_counts) {
+  pdl_begin();
   const int i = blockIdx.x * DN_THREADS + threadIdx.x;
   bool f[3] = {false, false, false};
   if (i < P.n) {
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(DN_THREADS) k_densify_count(DensifyParams P, u
 // (2) one CTA: exclusive offsets of each block inside the three output segments (in place) and the
 //     totals: counts = {all rows, originals, clones, split children}
 __global__ void __launch_bounds__(DN_THREADS) k_densify_offsets(u32* block_counts, int nblocks, int* counts) {
+  pdl_begin();
   __shared__ u32 s_carry[3];
   if (threadIdx.x < 3) s_carry[threadIdx.x] = 0;
   __syncthreads();
@@ -221,6 +223,7 @@ __device__ __forceinline__ void write_row(const DensifyParams& P, int i, u32 o, 
 // (3) ranks inside the block + block offsets -> rows of the three segments
 __global__ void __launch_bounds__(DN_THREADS) k_densify_write(DensifyParams P, const u32* block_offsets,
                                                              const int* counts) {
+  pdl_begin();
   const int i = blockIdx.x * DN_THREADS + threadIdx.x;
   Decision d = {false, false, false};
   if (i < P.n) d = densify_decision(P, i);
@@ -242,6 +245,7 @@ __global__ void __launch_bounds__(DN_THREADS) k_densify_write(DensifyParams P, c
 // visit.  sqrt((gx gx) + (gy gy)) and the sums are single correctly rounded float32 operations.
 __global__ void k_densify_accumulate(const u32* __restrict__ touched, int n, const float* __restrict__ grad,
                                      float* __restrict__ acc, float* __restrict__ den) {
+  pdl_begin();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (touched[i] == 0) continue;
     const float gx = grad[2 * (size_t)i], gy = grad[2 * (size_t)i + 1];
@@ -255,13 +259,14 @@ cudaError_t launch_densify_accumulate(const u32* touched, int n, const float* gr
   if (n <= 0) return cudaSuccess;
   int blocks = (n + 255) / 256;
   if (blocks > 8 * sm_count) blocks = 8 * sm_count;
-  k_densify_accumulate<<<blocks, 256, 0, s>>>(touched, n, grad, acc, den);
+  launch_pdl<PDL_DENSIFY>(k_densify_accumulate, blocks, 256, 0, s, touched, n, grad, acc, den);
   return cudaGetLastError();
 }
 
 // The periodic reset: opacity capped at opacity_cap, every weight set to `weight`.
 __global__ void k_reset_opacity_weights(float* __restrict__ opacity, unsigned char* __restrict__ weights, int n,
                                         int K, int esz, float opacity_cap, float weight) {
+  pdl_begin();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     opacity[i] = fminf(opacity[i], opacity_cap);
     fill_values(weights + (size_t)i * K * esz, K, esz, weight);
@@ -332,9 +337,9 @@ extern "C" gs_status gabsplat_densify(const gs_prims* in, const float* grad_accu
   P.child_weight = cfg->child_weight;
   const int nb = densify_blocks(in->n);
   u32* block_counts = static_cast<u32*>(scratch);
-  k_densify_count<<<nb, DN_THREADS, 0, st>>>(P, block_counts);
-  k_densify_offsets<<<1, DN_THREADS, 0, st>>>(block_counts, nb, counts);
-  k_densify_write<<<nb, DN_THREADS, 0, st>>>(P, block_counts, counts);
+  launch_pdl<PDL_DENSIFY>(k_densify_count, nb, DN_THREADS, 0, st, P, block_counts);
+  launch_pdl<PDL_DENSIFY>(k_densify_offsets, 1, DN_THREADS, 0, st, block_counts, nb, counts);
+  launch_pdl<PDL_DENSIFY>(k_densify_write, nb, DN_THREADS, 0, st, P, block_counts, counts);
   return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
@@ -347,7 +352,7 @@ extern "C" gs_status gabsplat_reset_opacity_weights(const gs_prim_arrays* prims,
   if (!prims->opacity || (K > 0 && !prims->weights)) return GS_ERR_INVALID_ARG;
   int blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  k_reset_opacity_weights<<<blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+  launch_pdl<PDL_DENSIFY>(k_reset_opacity_weights, blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream), 
       prims->opacity, static_cast<unsigned char*>(prims->weights), n, K, storage == GS_BF16 ? 2 : 4, opacity_cap,
       weight);
   return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;

@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_loss_partial(const float* __re
                                                               const float* __restrict__ tgt, long long count,
                                                               int kind, float* __restrict__ dL,
                                                               double* __restrict__ partials) {
+  pdl_begin();
   __shared__ double s_warp[LOSS_THREADS / 32];
   const double invN = 1.0 / (double)count;
   const float invNf = (float)invN;                   // = (float)(+-1.0 * invN): the same dL bits
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_loss_partial(const float* __re
 }
 
 __global__ void k_loss_final(const double* __restrict__ partials, int n, long long count, double* out) {
+  pdl_begin();
   __shared__ double s[256];
   double a = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) a += partials[i];
@@ -90,8 +92,8 @@ __global__ void k_loss_final(const double* __restrict__ partials, int n, long lo
 
 cudaError_t launch_loss(const float* img, const float* tgt, long long count, int kind, double* loss_out, float* dL,
                         double* partials, int nblocks, cudaStream_t s) {
-  k_loss_partial<<<nblocks, LOSS_THREADS, 0, s>>>(img, tgt, count, kind, dL, partials);
-  k_loss_final<<<1, 256, 0, s>>>(partials, nblocks, count, loss_out);
+  launch_pdl<PDL_LOSS>(k_loss_partial, nblocks, LOSS_THREADS, 0, s, img, tgt, count, kind, dL, partials);
+  launch_pdl<PDL_LOSS>(k_loss_final, 1, 256, 0, s, partials, nblocks, count, loss_out);
   return cudaGetLastError();
 }
 
@@ -140,6 +142,7 @@ struct SsimWindow {
 __global__ void __launch_bounds__(SS_THREADS) k_l1_dssim(const float* __restrict__ img, const float* __restrict__ tgt,
                                                         int H, int W, float lambda, double invN, SsimWindow win,
                                                         float* __restrict__ dL, double* __restrict__ partials) {
+  pdl_begin();
   extern __shared__ __align__(16) float sm[];
   float* sx = sm;                                  // [IN][SX]
   float* sy = sx + SS_IN * SX;                     // [IN][SX]
@@ -354,9 +357,9 @@ cudaError_t launch_l1_dssim(const float* img, const float* tgt, int C, int H, in
   for (int k = 0; k < SS_K; ++k) win.w[k] = (float)(g[k] / sum);
   const long long count = (long long)C * H * W;
   const dim3 grid((W + SS_T - 1) / SS_T, (H + SS_T - 1) / SS_T, C);
-  k_l1_dssim<<<grid, SS_THREADS, SS_SMEM, s>>>(img, tgt, H, W, lambda, 1.0 / (double)count, win, dL, partials);
+  launch_pdl<PDL_LOSS>(k_l1_dssim, grid, SS_THREADS, SS_SMEM, s, img, tgt, H, W, lambda, 1.0 / (double)count, win, dL, partials);
   const int n = (int)l1_dssim_partials(C, H, W);
-  k_loss_final<<<1, 256, 0, s>>>(partials, n, count, loss_out);
+  launch_pdl<PDL_LOSS>(k_loss_final, 1, 256, 0, s, partials, n, count, loss_out);
   return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@ namespace gs {
 static_assert(sizeof(FrameTable) + sizeof(WsPtrs) <= 4096, "k_setup parameters must fit the classic 4 KB limit");
 
 __global__ void k_setup(FrameTable tbl, WsPtrs p) {
+  pdl_begin();
   const u32* src = reinterpret_cast<const u32*>(&tbl);
   u32* dst = reinterpret_cast<u32*>(const_cast<FrameTable*>(p.tbl));
   for (int i = threadIdx.x; i < (int)(sizeof(FrameTable) / 4); i += blockDim.x) dst[i] = src[i];
@@ -499,6 +500,7 @@ __device__ __forceinline__ u32 warp_excl_scan(u32 v, int lane, u32& total) {
 }
 
 __global__ void __launch_bounds__(BLOCK) k_bin(WsPtrs p) {
+  pdl_begin();
   __shared__ u32 s_cnt[BLOCK / 32][32];
   __shared__ Owner s_own[BLOCK / 32][32];
   const FrameTable* tbl = p.tbl;
@@ -579,6 +581,7 @@ __device__ __forceinline__ u64 chunk_scan(u32 sum, const u64* partial, u32 chunk
 
 // (2a) Active primitives per chunk of 4096 (partials of the active-list scan).
 __global__ void __launch_bounds__(BLOCK) k_count_active(WsPtrs p) {
+  pdl_begin();
   __shared__ u64 s_red[BLOCK / 32];
   if (read_status(p.hdr) != 0) return;
   const u32 total = p.tbl->total_prims;
@@ -595,6 +598,7 @@ __global__ void __launch_bounds__(BLOCK) k_count_active(WsPtrs p) {
 // (2b) Active list: the primitives with at least one kept tile and their depth keys, in primitive
 // order, and the digit counts of the depth sort.  Publishes n_active.
 __global__ void __launch_bounds__(BLOCK) k_scan_active(WsPtrs p) {
+  pdl_begin();
   __shared__ u32 s_warp[BLOCK / 32];
   __shared__ u64 s_red[BLOCK / 32];
   __shared__ u64 s_tot;
@@ -637,6 +641,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan_active(WsPtrs p) {
 
 // (4a) Kept tiles per chunk of 4096 depth ranks (partials of the rank-order scan).
 __global__ void __launch_bounds__(BLOCK) k_count_ranked(WsPtrs p) {
+  pdl_begin();
   __shared__ u64 s_red[BLOCK / 32];
   if (read_status(p.hdr) != 0) return;
   const u32 total = p.hdr->n_active;
@@ -657,6 +662,7 @@ __global__ void __launch_bounds__(BLOCK) k_count_ranked(WsPtrs p) {
 // first pair position (exclusive scan of the kept-tile counts in rank order).  Publishes the pair
 // count and checks the pair capacity.
 __global__ void __launch_bounds__(BLOCK) k_scan_ranked(WsPtrs p) {
+  pdl_begin();
   __shared__ u32 s_warp[BLOCK / 32];
   __shared__ u64 s_red[BLOCK / 32];
   __shared__ u64 s_tot;
@@ -703,6 +709,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan_ranked(WsPtrs p) {
 // and then writes tile << 32 | rank for the kept tiles of those 32 rows, 32 at a time, at
 // offsets[rank] + the tile's index among the owner's kept tiles (row-major).
 __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
+  pdl_begin();
   __shared__ u32 s_run[BLOCK / 32][32];
   __shared__ Owner s_own[BLOCK / 32][32];
   const FrameTable* tbl = p.tbl;
@@ -775,6 +782,7 @@ __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
 // 2D records of the active primitives (full warps over the active list), each at its depth rank.
 template <int K, int STORAGE>
 __global__ void __launch_bounds__(BLOCK, GS_RECORDS_MIN_CTAS) k_records(WsPtrs p) {
+  pdl_begin();
   if (read_status(p.hdr) != 0) return;
   const u32 n = p.hdr->n_active;
   for (u32 i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
@@ -796,6 +804,7 @@ __device__ __forceinline__ void zero_fill(float* a, size_t count, size_t tid, si
 }
 
 __global__ void k_zero_grads(gs_prim_grads G, int n, int K, int nsh) {
+  pdl_begin();
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
   zero_fill(G.means, 3 * (size_t)n, tid, nt);
   zero_fill(G.scales, 3 * (size_t)n, tid, nt);
@@ -831,6 +840,7 @@ ZeroJob make_zero_job(const gs_prim_grads& g, int n, int K, int nsh, u32 ntiles)
 
 template <int K, int STORAGE>
 __global__ void __launch_bounds__(BLOCK, GS_PBWD_MIN_CTAS) k_preprocess_bwd(WsPtrs p, gs_prim_grads G) {
+  pdl_begin();
   const FrameTable* tbl = p.tbl;
   if (read_status(p.hdr) != 0) return;
   const ViewDesc& V = tbl->v[0];
@@ -1126,7 +1136,7 @@ static int persistent_grid(Kern kern, int threads, size_t smem, int sms) {
 }
 
 cudaError_t launch_setup(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
-  k_setup<<<1, 256, 0, L.stream>>>(tbl, p);
+  launch_pdl<PDL_BIN>(k_setup, 1, 256, 0, L.stream, tbl, p);
   return cudaGetLastError();
 }
 
@@ -1139,16 +1149,16 @@ static cudaError_t launch_pre_t(const FrameTable& tbl, const WsPtrs& p, const La
   const int need = (int)((tbl.launch_prims + BLOCK - 1) / BLOCK);
   const int schunks = (int)((tbl.launch_prims + SCAN_CHUNK - 1) / SCAN_CHUNK);
   auto clampg = [](int g, int cap) { return g < 1 ? 1 : (g > cap ? cap : g); };
-  k_bin<<<clampg(need, bgrid), BLOCK, 0, L.stream>>>(p);
+  launch_pdl<PDL_BIN>(k_bin, clampg(need, bgrid), BLOCK, 0, L.stream, p);
   const int sg = schunks < 1 ? 1 : schunks;   // one CTA per chunk (CTAs past the data return)
-  k_count_active<<<sg, BLOCK, 0, L.stream>>>(p);
-  k_scan_active<<<sg, BLOCK, 0, L.stream>>>(p);
+  launch_pdl<PDL_BIN>(k_count_active, sg, BLOCK, 0, L.stream, p);
+  launch_pdl<PDL_BIN>(k_scan_active, sg, BLOCK, 0, L.stream, p);
   cudaError_t e = launch_depth_sort(tbl, p, L);
   if (e != cudaSuccess) return e;
-  k_count_ranked<<<sg, BLOCK, 0, L.stream>>>(p);
-  k_scan_ranked<<<sg, BLOCK, 0, L.stream>>>(p);
-  k_emit<<<clampg(need, egrid), BLOCK, 0, L.stream>>>(p);
-  k_records<K, ST><<<clampg(need, rgrid), BLOCK, 0, L.stream>>>(p);
+  launch_pdl<PDL_RANK>(k_count_ranked, sg, BLOCK, 0, L.stream, p);
+  launch_pdl<PDL_RANK>(k_scan_ranked, sg, BLOCK, 0, L.stream, p);
+  launch_pdl<PDL_EMIT>(k_emit, clampg(need, egrid), BLOCK, 0, L.stream, p);
+  launch_pdl<PDL_EMIT>(k_records<K, ST>, clampg(need, rgrid), BLOCK, 0, L.stream, p);
   return cudaGetLastError();
 }
 
@@ -1159,11 +1169,11 @@ static cudaError_t launch_pre_bwd_t(const FrameTable& tbl, const WsPtrs& p, cons
   if (!grid) grid = persistent_grid(k_preprocess_bwd<K, ST>, BLOCK, 0, L.sm_count);
   const int n = tbl.v[0].n;
   const int nsh = (tbl.sh_degree + 1) * (tbl.sh_degree + 1);
-  if (!prezeroed) k_zero_grads<<<L.sm_count * 4, 256, 0, L.stream>>>(g, n, K, nsh);
+  if (!prezeroed) launch_pdl<PDL_PBWD>(k_zero_grads, L.sm_count * 4, 256, 0, L.stream, g, n, K, nsh);
   int blocks = (n + BLOCK - 1) / BLOCK;
   if (blocks > grid) blocks = grid;
   if (blocks < 1) blocks = 1;
-  k_preprocess_bwd<K, ST><<<blocks, BLOCK, 0, L.stream>>>(p, g);
+  launch_pdl<PDL_PBWD>(k_preprocess_bwd<K, ST>, blocks, BLOCK, 0, L.stream, p, g);
   return cudaGetLastError();
 }
 

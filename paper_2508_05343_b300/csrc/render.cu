@@ -227,6 +227,7 @@ __device__ __forceinline__ int2 thread_pixel(int tx, int ty, int tid) {
 template <int K, int PPT, bool FMAP, bool MASKS>
 __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
                                                             float* out_T) {
+  pdl_begin();
   constexpr int NT = BLOCK / PPT;
   constexpr int F4 = SRec<K>::F4;
   extern __shared__ __align__(16) float4 s_rec[];   // [NT][F4]
@@ -488,6 +489,7 @@ __device__ __noinline__ void zero_chunks(const ZeroJob& z, u32 c0, u32 count) {
 template <int K, int PPT>
 __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ dL_drgb,
                                            const __grid_constant__ ZeroJob z) {
+  pdl_begin();
   constexpr int NT = BLOCK / PPT;
   constexpr int F4 = SRec<K>::F4;
   constexpr int NV = 10 + 3 * K;         // gradient values per pair
@@ -859,13 +861,14 @@ static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, float* r
   int g = grid;
   if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
   if (g < 1) g = 1;
-  k_render_fwd<K, PPT, FMAP, MASKS><<<g, NT, smem, L.stream>>>(p, rgb, T);
+  launch_pdl<PDL_RENDER>(k_render_fwd<K, PPT, FMAP, MASKS>, g, NT, smem, L.stream, p, rgb, T);
   return cudaGetLastError();
 }
 
 // Clears the 2D gradient rows of the n_active ranked primitives before the backward accumulates.
 template <int K>
 __global__ void __launch_bounds__(256) k_zero_grad2d(WsPtrs p) {
+  pdl_begin();
   if (read_status(p.hdr) != 0) return;
   static_assert(g2d_floats(K) % 4 == 0, "grad2d rows are whole float4s");
   const size_t n4 = (size_t)p.hdr->n_active * (g2d_floats(K) / 4);
@@ -896,8 +899,8 @@ static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const fl
   if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
   if (g < 1) g = 1;
   ZeroJob none{};
-  k_zero_grad2d<K><<<L.sm_count * 2, 256, 0, L.stream>>>(p);
-  k_render_bwd<K, PPT><<<g, NT, smem, L.stream>>>(p, dL, z ? *z : none);
+  launch_pdl<PDL_RENDER>(k_zero_grad2d<K>, L.sm_count * 2, 256, 0, L.stream, p);
+  launch_pdl<PDL_RENDER>(k_render_bwd<K, PPT>, g, NT, smem, L.stream, p, dL, z ? *z : none);
   return cudaGetLastError();
 }
 

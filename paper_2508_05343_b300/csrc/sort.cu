@@ -19,6 +19,7 @@ namespace gs {
 
 // Tile-digit counts of the emitted pairs (slots DPASSES .. DPASSES + tpasses_needed - 1).
 __global__ void __launch_bounds__(256) k_digit_hist(WsPtrs p) {
+  pdl_begin();
   __shared__ u32 s_h[MAX_PASSES - DPASSES][RADIX];
   if (read_status(p.hdr) != 0) return;
   for (int i = threadIdx.x; i < (MAX_PASSES - DPASSES) * RADIX; i += blockDim.x) (&s_h[0][0])[i] = 0;
@@ -75,6 +76,7 @@ __device__ __forceinline__ u32 block_excl_scan(u32 v, u32* scratch /*SORT_THREAD
 template <int ITEMS>
 __global__ void __launch_bounds__(SORT_THREADS, GS_SORT_MIN_CTAS) k_onesweep(WsPtrs p, const u64* __restrict__ kin,
                                                                            u64* __restrict__ kout, int slot) {
+  pdl_begin();
   constexpr int PART = SORT_THREADS * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem<ITEMS>& S = *reinterpret_cast<SortSmem<ITEMS>*>(smem_raw);
@@ -181,6 +183,7 @@ __global__ void __launch_bounds__(SORT_THREADS, GS_SORT_MIN_CTAS) k_onesweep(WsP
 // predecessor (successor) has another tile.  Neighbours come from the adjacent lanes; only the
 // warp's edge lanes load them.
 __global__ void __launch_bounds__(256) k_tile_ranges(WsPtrs p) {
+  pdl_begin();
   if (read_status(p.hdr) != 0) return;
   const u64* __restrict__ keys = (p.tbl->tpasses_needed & 1) ? p.keys1 : p.keys0;
   const u64 Pall = p.hdr->pairs;
@@ -211,6 +214,7 @@ __global__ void __launch_bounds__(256) k_tile_ranges(WsPtrs p) {
 // so persistent CTAs start the longest lists first and the launch ends on short ones.  One CTA.
 constexpr int ORDER_THREADS = 1024, ORDER_BUCKETS = 1024, ORDER_SHIFT = 2;
 __global__ void __launch_bounds__(ORDER_THREADS) k_tile_order(WsPtrs p) {
+  pdl_begin();
   __shared__ u32 s_off[ORDER_BUCKETS];
   __shared__ u32 s_warp[ORDER_THREADS / 32];
   if (read_status(p.hdr) != 0) return;
@@ -263,7 +267,7 @@ static int sort_grid(const Launch& L) {
 // Passes [first, first + count) of one sort, ping-ponging between b0 and b1 (input in b0); a pass
 // with no work leaves its input in place, so the result is in b1 iff the number of working passes is
 // odd.  `items` bounds the keys a pass can have.
-template <int ITEMS>
+template <int ITEMS, int GROUP>
 static cudaError_t run_passes(const WsPtrs& p, u64* b0, u64* b1, int first, int count, u64 items, const Launch& L) {
   const int sg = sort_grid<ITEMS>(L);
   if (sg < 0) return cudaErrorInvalidValue;
@@ -272,7 +276,7 @@ static cudaError_t run_passes(const WsPtrs& p, u64* b0, u64* b1, int first, int 
   int grid = (u64)sg < parts ? sg : (int)parts;
   if (grid < 1) grid = 1;
   for (int ps = 0; ps < count; ++ps) {
-    k_onesweep<ITEMS><<<grid, SORT_THREADS, sizeof(SortSmem<ITEMS>), L.stream>>>(p, b0, b1, first + ps);
+    launch_pdl<GROUP>(k_onesweep<ITEMS>, grid, SORT_THREADS, sizeof(SortSmem<ITEMS>), L.stream, p, b0, b1, first + ps);
     u64* t = b0;
     b0 = b1;
     b1 = t;
@@ -281,17 +285,17 @@ static cudaError_t run_passes(const WsPtrs& p, u64* b0, u64* b1, int first, int 
 }
 
 cudaError_t launch_depth_sort(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
-  return run_passes<DSORT_ITEMS>(p, p.dkeys0, p.dkeys1, 0, DPASSES, tbl.launch_prims, L);
+  return run_passes<DSORT_ITEMS, PDL_DSORT>(p, p.dkeys0, p.dkeys1, 0, DPASSES, tbl.launch_prims, L);
 }
 
 cudaError_t launch_bin_sort(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
   if (tbl.tpasses > 0) {
-    k_digit_hist<<<L.sm_count * 4, 256, 0, L.stream>>>(p);
-    const cudaError_t e = run_passes<SORT_ITEMS>(p, p.keys0, p.keys1, DPASSES, tbl.tpasses, p.capacity, L);
+    launch_pdl<PDL_TSORT>(k_digit_hist, L.sm_count * 4, 256, 0, L.stream, p);
+    const cudaError_t e = run_passes<SORT_ITEMS, PDL_TSORT>(p, p.keys0, p.keys1, DPASSES, tbl.tpasses, p.capacity, L);
     if (e != cudaSuccess) return e;
   }
-  k_tile_ranges<<<L.sm_count * 8, 256, 0, L.stream>>>(p);
-  k_tile_order<<<1, ORDER_THREADS, 0, L.stream>>>(p);
+  launch_pdl<PDL_TSORT>(k_tile_ranges, L.sm_count * 8, 256, 0, L.stream, p);
+  launch_pdl<PDL_TSORT>(k_tile_order, 1, ORDER_THREADS, 0, L.stream, p);
   return cudaGetLastError();
 }
 
