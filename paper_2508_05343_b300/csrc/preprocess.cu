@@ -19,6 +19,9 @@ namespace gs {
 #define FS __fsub_rn
 #define FDV __fdiv_rn
 
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_CHUNK = BLOCK * SCAN_ITEMS;   // counts per look-back partition
+
 static_assert(sizeof(FrameTable) + sizeof(WsPtrs) <= 4096, "k_setup parameters must fit the classic 4 KB limit");
 
 __global__ void k_setup(FrameTable tbl, WsPtrs p) {
@@ -27,6 +30,8 @@ __global__ void k_setup(FrameTable tbl, WsPtrs p) {
   u32* dst = reinterpret_cast<u32*>(const_cast<FrameTable*>(p.tbl));
   for (int i = threadIdx.x; i < (int)(sizeof(FrameTable) / 4); i += blockDim.x) dst[i] = src[i];
   for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) p.hist[i] = 0;
+  const u32 schunks = (tbl.total_prims + SCAN_CHUNK - 1) / SCAN_CHUNK;   // k_bin adds its active counts
+  for (u32 i = threadIdx.x; i < schunks; i += blockDim.x) p.scan_partials[i] = 0;
   if (threadIdx.x == 0) {
     WsHeader* h = p.hdr;
     h->status = 0;
@@ -499,6 +504,10 @@ __device__ __forceinline__ u32 warp_excl_scan(u32 v, int lane, u32& total) {
   return incl - v;
 }
 
+
+// (1) Binning of every primitive (warp-cooperative tile walks): kept-tile counts, the depth key of
+// each active primitive at its index, and the active primitives per chunk of SCAN_CHUNK (added
+// into scan_partials, cleared by k_setup).
 __global__ void __launch_bounds__(BLOCK) k_bin(WsPtrs p) {
   pdl_begin();
   __shared__ u32 s_cnt[BLOCK / 32][32];
@@ -531,11 +540,13 @@ __global__ void __launch_bounds__(BLOCK) k_bin(WsPtrs p) {
       // depth in (znear, zfar]: its float bits minus bits(znear) lie in [1, 2^depth_bits)
       if (cnt > 0) p.dkeys1[gi] = ((u64)(dbits - tbl->depth_base) << 32) | gi;
     }
+    // active primitives per scan chunk: a group of 32 lies in one chunk (32 divides SCAN_CHUNK)
+    const u32 nact = __popc(__ballot_sync(0xffffffffu, gi < total && cnt > 0));
+    if (lane == 0 && nact) atomicAdd(reinterpret_cast<unsigned long long*>(p.scan_partials + grp * 32 / SCAN_CHUNK),
+                                     (unsigned long long)nact);
   }
 }
 
-constexpr int SCAN_ITEMS = 16;
-constexpr int SCAN_CHUNK = BLOCK * SCAN_ITEMS;   // counts per look-back partition
 
 // The two scans below run as reduce-then-scan: one launch writes each 4096-element chunk's sum, the
 // next adds up its chunk's predecessors directly and scans the chunk.  With about as many chunks as
@@ -577,22 +588,6 @@ __device__ __forceinline__ u64 chunk_scan(u32 sum, const u64* partial, u32 chunk
   }
   __syncthreads();
   return before + s_warp[warp] + wex;
-}
-
-// (2a) Active primitives per chunk of 4096 (partials of the active-list scan).
-__global__ void __launch_bounds__(BLOCK) k_count_active(WsPtrs p) {
-  pdl_begin();
-  __shared__ u64 s_red[BLOCK / 32];
-  if (read_status(p.hdr) != 0) return;
-  const u32 total = p.tbl->total_prims;
-  const u64 base = (u64)blockIdx.x * SCAN_CHUNK;
-  if (base >= total) return;
-  const u64 my0 = base + (u64)threadIdx.x * SCAN_ITEMS;
-  u32 c = 0;
-#pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i) c += (my0 + i < total && p.touched[my0 + i] > 0) ? 1u : 0u;
-  const u64 t = block_sum(c, s_red);
-  if (threadIdx.x == 0) p.scan_partials[blockIdx.x] = t;
 }
 
 // (2b) Active list: the primitives with at least one kept tile and their depth keys, in primitive
@@ -1151,7 +1146,6 @@ static cudaError_t launch_pre_t(const FrameTable& tbl, const WsPtrs& p, const La
   auto clampg = [](int g, int cap) { return g < 1 ? 1 : (g > cap ? cap : g); };
   launch_pdl<PDL_BIN>(k_bin, clampg(need, bgrid), BLOCK, 0, L.stream, p);
   const int sg = schunks < 1 ? 1 : schunks;   // one CTA per chunk (CTAs past the data return)
-  launch_pdl<PDL_BIN>(k_count_active, sg, BLOCK, 0, L.stream, p);
   launch_pdl<PDL_BIN>(k_scan_active, sg, BLOCK, 0, L.stream, p);
   cudaError_t e = launch_depth_sort(tbl, p, L);
   if (e != cudaSuccess) return e;
