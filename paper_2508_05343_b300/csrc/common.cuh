@@ -17,6 +17,8 @@ typedef unsigned int u32;
 constexpr int TILE = GS_TILE;
 constexpr int BLOCK = 256;            // threads per CTA for every tile / chunk kernel
 constexpr int CHUNK = BLOCK;          // primitives per preprocess chunk (one per thread)
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_CHUNK = BLOCK * SCAN_ITEMS;   // elements per chunk of the active-list and rank-order scans
 #ifndef GS_SORT_THREADS
 #define GS_SORT_THREADS 256
 #endif

@@ -19,8 +19,6 @@ namespace gs {
 #define FS __fsub_rn
 #define FDV __fdiv_rn
 
-constexpr int SCAN_ITEMS = 16;
-constexpr int SCAN_CHUNK = BLOCK * SCAN_ITEMS;   // counts per look-back partition
 
 static_assert(sizeof(FrameTable) + sizeof(WsPtrs) <= 4096, "k_setup parameters must fit the classic 4 KB limit");
 
@@ -31,7 +29,10 @@ __global__ void k_setup(FrameTable tbl, WsPtrs p) {
   for (int i = threadIdx.x; i < (int)(sizeof(FrameTable) / 4); i += blockDim.x) dst[i] = src[i];
   for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) p.hist[i] = 0;
   const u32 schunks = (tbl.total_prims + SCAN_CHUNK - 1) / SCAN_CHUNK;   // k_bin adds its active counts
-  for (u32 i = threadIdx.x; i < schunks; i += blockDim.x) p.scan_partials[i] = 0;
+  for (u32 i = threadIdx.x; i < schunks; i += blockDim.x) {   // k_bin and the last depth pass add into these
+    p.scan_partials[i] = 0;
+    p.rank_partials[i] = 0;
+  }
   if (threadIdx.x == 0) {
     WsHeader* h = p.hdr;
     h->status = 0;
@@ -517,7 +518,10 @@ __global__ void __launch_bounds__(BLOCK) k_bin(WsPtrs p) {
   if (read_status(hdr) != 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 total = tbl->total_prims;
-  for (u32 i = blockIdx.x * BLOCK + threadIdx.x; i < tbl->total_tiles; i += gridDim.x * BLOCK) p.ranges[i] = make_uint2(0u, 0u);
+  // ranges start empty as (~0, 0): the last tile-sort pass lowers .x and raises .y of each tile it
+  // finds, and the tile schedule turns the ones still empty into (0, 0)
+  for (u32 i = blockIdx.x * BLOCK + threadIdx.x; i < tbl->total_tiles; i += gridDim.x * BLOCK)
+    p.ranges[i] = make_uint2(0xFFFFFFFFu, 0u);
   const u32 nwarps = gridDim.x * (BLOCK / 32);
   for (u32 grp = blockIdx.x * (BLOCK / 32) + warp; (u64)grp * 32 < total; grp += nwarps) {
     const u32 gi = grp * 32 + lane;
@@ -634,25 +638,6 @@ __global__ void __launch_bounds__(BLOCK) k_scan_active(WsPtrs p) {
   }
 }
 
-// (4a) Kept tiles per chunk of 4096 depth ranks (partials of the rank-order scan).
-__global__ void __launch_bounds__(BLOCK) k_count_ranked(WsPtrs p) {
-  pdl_begin();
-  __shared__ u64 s_red[BLOCK / 32];
-  if (read_status(p.hdr) != 0) return;
-  const u32 total = p.hdr->n_active;
-  const u64 base = (u64)blockIdx.x * SCAN_CHUNK;
-  if (base >= total) return;
-  const u64* __restrict__ sorted = (p.tbl->dpasses_needed & 1) ? p.dkeys1 : p.dkeys0;
-  const u64 my0 = base + (u64)threadIdx.x * SCAN_ITEMS;
-  u32 gi[SCAN_ITEMS], c = 0;
-#pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i) gi[i] = my0 + i < total ? (u32)sorted[my0 + i] : 0xFFFFFFFFu;
-#pragma unroll
-  for (int i = 0; i < SCAN_ITEMS; ++i) c += gi[i] != 0xFFFFFFFFu ? p.touched[gi[i]] : 0u;
-  const u64 t = block_sum(c, s_red);
-  if (threadIdx.x == 0) p.rank_partials[blockIdx.x] = t;
-}
-
 // (4b) Rank order: order[r] = the primitive of depth rank r, rank_of[order[r]] = r, offsets[r] = its
 // first pair position (exclusive scan of the kept-tile counts in rank order).  Publishes the pair
 // count and checks the pair capacity.
@@ -707,11 +692,15 @@ __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
   pdl_begin();
   __shared__ u32 s_run[BLOCK / 32][32];
   __shared__ Owner s_own[BLOCK / 32][32];
+  __shared__ u32 s_th[MAX_PASSES - DPASSES][RADIX];   // tile-sort digit counts of this CTA's pairs
   const FrameTable* tbl = p.tbl;
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 nact = hdr->n_active;
+  const int tneed = tbl->tpasses_needed;
+  for (int i = threadIdx.x; i < (MAX_PASSES - DPASSES) * RADIX; i += BLOCK) (&s_th[0][0])[i] = 0;
+  __syncthreads();
   const u32 nwarps = gridDim.x * (BLOCK / 32);
   for (u32 grp = blockIdx.x * (BLOCK / 32) + warp; (u64)grp * 32 < nact; grp += nwarps) {
     const u32 ia = grp * 32 + lane;
@@ -732,6 +721,20 @@ __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
     for (u32 base = 0; base < rows_total; base += 32) {
       FlatRow fr;
       flat_row(base + lane, rows_total, my_row_excl, s_own[warp], fr);
+      // the tile sort's digit counts above the lowest digit: a row's kept tiles are consecutive, so
+      // a higher digit changes at most a few times along them (one add per run)
+      if (fr.count > 0) {
+        const Owner& o = s_own[warp][fr.owner];
+        const u32 t0 = o.tile_base + (u32)fr.ty * o.tiles_x + (u32)fr.first, t1 = t0 + (u32)fr.count;
+        for (int ps = 1; ps < tneed; ++ps) {
+          const int sh = RADIX_BITS * ps;
+          for (u32 a = t0; a < t1;) {
+            const u32 b = min(t1, ((a >> sh) + 1u) << sh);
+            atomicAdd(&s_th[ps][(a >> sh) & (RADIX - 1)], b - a);
+            a = b;
+          }
+        }
+      }
       // this row's first pair position: the owner's kept tiles in earlier rows (earlier steps, and
       // earlier lanes of this step)
       u32 tot;
@@ -755,13 +758,22 @@ __global__ void __launch_bounds__(BLOCK) k_emit(WsPtrs p) {
         const int first = __shfl_sync(0xffffffffu, fr.first, src);
         const int owner = __shfl_sync(0xffffffffu, fr.owner, src);
         const u32 pos = __shfl_sync(0xffffffffu, pos0, src) + k;
-        if (e < tot && pos < p.capacity) {
+        u32 tile = 0;
+        if (e < tot) {
           const Owner& o = s_own[warp][owner];
-          p.keys0[pos] = ((u64)(o.tile_base + (u32)ty * o.tiles_x + (u32)(first + (int)k)) << 32) | o.rank;
+          tile = o.tile_base + (u32)ty * o.tiles_x + (u32)(first + (int)k);
+          if (pos < p.capacity) p.keys0[pos] = ((u64)tile << 32) | o.rank;
         }
+        // the lowest digit, one add per pair (the warp's pairs are mostly consecutive tiles)
+        if (e < tot && tneed > 0) atomicAdd(&s_th[0][tile & (RADIX - 1)], 1u);
       }
       __syncwarp();
     }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < tneed * RADIX; i += BLOCK) {
+    const u32 c = (&s_th[0][0])[i];
+    if (c) atomicAdd(p.hist + DPASSES * RADIX + i, c);
   }
 }
 
@@ -1149,7 +1161,6 @@ static cudaError_t launch_pre_t(const FrameTable& tbl, const WsPtrs& p, const La
   launch_pdl<PDL_BIN>(k_scan_active, sg, BLOCK, 0, L.stream, p);
   cudaError_t e = launch_depth_sort(tbl, p, L);
   if (e != cudaSuccess) return e;
-  launch_pdl<PDL_RANK>(k_count_ranked, sg, BLOCK, 0, L.stream, p);
   launch_pdl<PDL_RANK>(k_scan_ranked, sg, BLOCK, 0, L.stream, p);
   launch_pdl<PDL_EMIT>(k_emit, clampg(need, egrid), BLOCK, 0, L.stream, p);
   launch_pdl<PDL_EMIT>(k_records<K, ST>, clampg(need, rgrid), BLOCK, 0, L.stream, p);

@@ -10,33 +10,13 @@
 //   2. Tile sort of the pairs (this stage): the emission writes tile << 32 | depth rank in rank
 //      order, so a stable sort on the tile bits alone leaves every tile's pairs in depth order
 //      (ties by primitive index): the order of a sort of (tile, depth, primitive).
-// Both sorts move 8-byte keys only.  Digit counts come from the active-list scan (depth) and one
-// histogram kernel (tile); counts stay on the device; persistent CTAs take partitions in order from
-// an atomic counter.
+// Both sorts move 8-byte keys only.  Digit counts come from the active-list scan (depth) and from
+// the emission (tile); counts stay on the device; persistent CTAs take partitions in order from an
+// atomic counter.  The last depth pass also adds each rank chunk's kept-tile counts (the partials
+// of the rank-order scan), and the last tile pass writes each tile's [start, end) range.
 #include "common.cuh"
 
 namespace gs {
-
-// Tile-digit counts of the emitted pairs (slots DPASSES .. DPASSES + tpasses_needed - 1).
-__global__ void __launch_bounds__(256) k_digit_hist(WsPtrs p) {
-  pdl_begin();
-  __shared__ u32 s_h[MAX_PASSES - DPASSES][RADIX];
-  if (read_status(p.hdr) != 0) return;
-  for (int i = threadIdx.x; i < (MAX_PASSES - DPASSES) * RADIX; i += blockDim.x) (&s_h[0][0])[i] = 0;
-  __syncthreads();
-  const u64 P = p.hdr->pairs;
-  const u64 n = P < p.capacity ? P : p.capacity;
-  const int need = p.tbl->tpasses_needed;
-  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
-    const u32 t = (u32)(p.keys0[i] >> 32);
-    for (int ps = 0; ps < need; ++ps) atomicAdd(&s_h[ps][(t >> (RADIX_BITS * ps)) & (RADIX - 1)], 1u);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < need * RADIX; i += blockDim.x) {
-    const u32 c = (&s_h[0][0])[i];
-    if (c) atomicAdd(p.hist + DPASSES * RADIX + i, c);
-  }
-}
 
 static_assert(SORT_THREADS >= RADIX && SORT_THREADS % 32 == 0, "one digit per thread of the first RADIX threads");
 
@@ -84,7 +64,10 @@ __global__ void __launch_bounds__(SORT_THREADS, GS_SORT_MIN_CTAS) k_onesweep(WsP
   if (read_status(hdr) != 0) return;
   const bool tiles = slot >= DPASSES;
   const int pass = tiles ? slot - DPASSES : slot;
-  if (pass >= (tiles ? p.tbl->tpasses_needed : p.tbl->dpasses_needed)) return;   // digits zero for every key
+  const int need = tiles ? p.tbl->tpasses_needed : p.tbl->dpasses_needed;
+  if (pass >= need) return;   // digits zero for every key
+  const bool last = pass == need - 1;   // the pass that writes the final order
+  const u32 ntiles = p.tbl->total_tiles;
   const int shift = 32 + RADIX_BITS * pass;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   u64 P;
@@ -173,40 +156,31 @@ __global__ void __launch_bounds__(SORT_THREADS, GS_SORT_MIN_CTAS) k_onesweep(WsP
     for (u32 j = tid; j < nvalid; j += SORT_THREADS) {
       const u64 k = S.keys[j];
       const u32 d = (u32)(k >> shift) & (RADIX - 1);
-      kout[S.glob[d] + j] = k;
+      const u32 g = S.glob[d] + j;
+      kout[g] = k;
+      if (last && tiles) {
+        // final positions: this partition's keys of one digit land contiguously and in tile order,
+        // so a tile's first (last) key here is one whose shared-memory neighbour has another tile;
+        // the tile's range is the least first and the greatest last position over the partitions
+        const u32 t = (u32)(k >> 32);
+        if (t >= ntiles) {   // cannot happen for keys this frame emitted; guards the table write
+          set_status(hdr, GS_ERR_INVALID_ARG);
+        } else {
+          if (j == 0 || (u32)(S.keys[j - 1] >> 32) != t) atomicMin(&p.ranges[t].x, g);
+          if (j + 1 == nvalid || (u32)(S.keys[j + 1] >> 32) != t) atomicMax(&p.ranges[t].y, g + 1);
+        }
+      } else if (last) {
+        // depth ranks: the kept-tile count of the primitive at rank g joins its rank chunk's sum
+        // (one add per chunk and warp; a warp's positions are mostly consecutive)
+        const u32 chunk = g / SCAN_CHUNK;
+        const u32 v = p.touched[(u32)k];
+        const u32 peers = __match_any_sync(__activemask(), chunk);
+        const u32 sum = __reduce_add_sync(peers, v);
+        if (lane == __ffs(peers) - 1 && sum)
+          atomicAdd(reinterpret_cast<unsigned long long*>(p.rank_partials + chunk), (unsigned long long)sum);
+      }
     }
     __syncthreads();
-  }
-}
-
-// Per-tile [start, end) of the sorted pairs: a pair starts (ends) its tile's range when its
-// predecessor (successor) has another tile.  Neighbours come from the adjacent lanes; only the
-// warp's edge lanes load them.
-__global__ void __launch_bounds__(256) k_tile_ranges(WsPtrs p) {
-  pdl_begin();
-  if (read_status(p.hdr) != 0) return;
-  const u64* __restrict__ keys = (p.tbl->tpasses_needed & 1) ? p.keys1 : p.keys0;
-  const u64 Pall = p.hdr->pairs;
-  const u64 P = Pall < p.capacity ? Pall : p.capacity;
-  const u32 ntiles = p.tbl->total_tiles;
-  const int lane = threadIdx.x & 31;
-  const u64 stride = (u64)gridDim.x * blockDim.x;
-  // warp-uniform trip count: every lane takes part in the shuffles
-  for (u64 w0 = ((u64)blockIdx.x * blockDim.x + threadIdx.x) & ~31ull; w0 < P; w0 += stride) {
-    const u64 i = w0 + lane;
-    const bool in = i < P;
-    const u32 t = in ? (u32)(keys[i] >> 32) : 0xFFFFFFFFu;
-    u32 prev = __shfl_up_sync(0xffffffffu, t, 1);
-    u32 next = __shfl_down_sync(0xffffffffu, t, 1);
-    if (lane == 0) prev = i > 0 && in ? (u32)(keys[i - 1] >> 32) : 0xFFFFFFFFu;
-    if (lane == 31 || i + 1 >= P) next = i + 1 < P ? (u32)(keys[i + 1] >> 32) : 0xFFFFFFFFu;
-    if (!in) continue;
-    if (t >= ntiles) {   // cannot happen for keys this frame emitted; guards the table write
-      set_status(p.hdr, GS_ERR_INVALID_ARG);
-      continue;
-    }
-    if (i == 0 || prev != t) p.ranges[t].x = (u32)i;
-    if (i + 1 == P || next != t) p.ranges[t].y = (u32)(i + 1);
   }
 }
 
@@ -224,6 +198,17 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_tile_order(WsPtrs p) {
     const u32 b = (rg.y - rg.x) >> ORDER_SHIFT;
     return (u32)(ORDER_BUCKETS - 1) - (b < (u32)(ORDER_BUCKETS - 1) ? b : (u32)(ORDER_BUCKETS - 1));
   };
+  // the ranges the last tile pass left: a tile it never saw is still (~0, 0) and becomes (0, 0);
+  // with one tile there is no tile pass and every pair is that tile's
+  if (p.tbl->tpasses_needed == 0) {
+    if (tid == 0 && ntiles > 0) {
+      const u64 Pall = p.hdr->pairs;
+      p.ranges[0] = make_uint2(0u, (u32)(Pall < p.capacity ? Pall : p.capacity));
+    }
+  } else {
+    for (u32 t = tid; t < ntiles; t += ORDER_THREADS)
+      if (p.ranges[t].x > p.ranges[t].y) p.ranges[t] = make_uint2(0u, 0u);
+  }
   s_off[tid] = 0;   // ORDER_THREADS == ORDER_BUCKETS
   __syncthreads();
   for (u32 t = tid; t < ntiles; t += ORDER_THREADS) atomicAdd(&s_off[bucket(p.ranges[t])], 1u);
@@ -289,12 +274,11 @@ cudaError_t launch_depth_sort(const FrameTable& tbl, const WsPtrs& p, const Laun
 }
 
 cudaError_t launch_bin_sort(const FrameTable& tbl, const WsPtrs& p, const Launch& L) {
+  // the tile-digit counts come from the emission; the last tile pass writes the ranges
   if (tbl.tpasses > 0) {
-    launch_pdl<PDL_TSORT>(k_digit_hist, L.sm_count * 4, 256, 0, L.stream, p);
     const cudaError_t e = run_passes<SORT_ITEMS, PDL_TSORT>(p, p.keys0, p.keys1, DPASSES, tbl.tpasses, p.capacity, L);
     if (e != cudaSuccess) return e;
   }
-  launch_pdl<PDL_TSORT>(k_tile_ranges, L.sm_count * 8, 256, 0, L.stream, p);
   launch_pdl<PDL_TSORT>(k_tile_order, 1, ORDER_THREADS, 0, L.stream, p);
   return cudaGetLastError();
 }
