@@ -20,6 +20,13 @@ namespace gs {
 
 static_assert(SORT_THREADS >= RADIX && SORT_THREADS % 32 == 0, "one digit per thread of the first RADIX threads");
 
+// Ranking of a warp's keys by digit: 1 = the lanes sharing a digit from one vote per digit bit and
+// the warp's digit counter bumped with one shared atomic; 0 = __match_any_sync and a shared
+// read-modify-write of the counter.
+#ifndef GS_SORT_BALLOT_RANK
+#define GS_SORT_BALLOT_RANK 1
+#endif
+
 template <int ITEMS>
 struct SortSmem {
   u32 warp_cnt[SORT_THREADS / 32][RADIX];
@@ -104,6 +111,19 @@ __global__ void __launch_bounds__(SORT_THREADS, GS_SORT_MIN_CTAS) k_onesweep(WsP
       const u64 idx = wbase + (u64)i * 32 + lane;
       const bool valid = idx < P;
       const u32 d = (u32)(key[i] >> shift) & (RADIX - 1);
+#if GS_SORT_BALLOT_RANK
+      // the lanes holding the same digit, one vote per digit bit
+      u32 peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+      for (int b = 0; b < RADIX_BITS; ++b) {
+        const u32 v = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? v : ~v;
+      }
+      const int leader = __ffs(peers) - 1;
+      u32 old = 0;
+      if (valid && lane == leader) old = atomicAdd(&S.warp_cnt[warp][d], (u32)__popc(peers));
+      old = __shfl_sync(0xffffffffu, old, leader & 31);
+#else
       const u32 peers = __match_any_sync(0xffffffffu, valid ? d : (RADIX + lane));
       const int leader = __ffs(peers) - 1;
       u32 old = 0;
@@ -112,6 +132,7 @@ __global__ void __launch_bounds__(SORT_THREADS, GS_SORT_MIN_CTAS) k_onesweep(WsP
         S.warp_cnt[warp][d] = old + __popc(peers);
       }
       old = __shfl_sync(0xffffffffu, old, leader);
+#endif
       rank[i] = old + __popc(peers & lt_mask);
       __syncwarp();
     }
