@@ -243,6 +243,12 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 #ifndef GS_FWD_BULK
 #define GS_FWD_BULK 0
 #endif
+// GS_FWD_WORD_BITS=1: the forward combines the lanes' composited-pair bits once per 32 sorted
+// positions (__reduce_or_sync) and tests for an all-done warp there, instead of a vote and a
+// ballot per pair.
+#ifndef GS_FWD_WORD_BITS
+#define GS_FWD_WORD_BITS 1
+#endif
 
 // Resident CTAs per SM the compositing kernels are compiled for (0: the compiler's choice).  At
 // K = 4 the backward's two-pixel packed adjoint takes 127 registers (4 CTAs per SM) on its own;
@@ -382,7 +388,7 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
     // composited-pair bits of this warp (warp-uniform), one word per 32 sorted positions, for the
     // backward pass to skip the pairs no pixel of the warp composited
     u32* cplane = p.cmask + (size_t)(tid >> 5) * p.cmask_plane;
-    u32 cword = 0, cword_idx = 0xffffffffu;
+    u32 cword = 0, cword_idx = 0xffffffffu, lbits = 0;
     constexpr bool masks = MASKS;
 #if GS_FWD_BULK
     int kb = 0;                  // buffer of the batch at `start`
@@ -425,11 +431,15 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
 #endif
       const int cnt = (int)min((u32)NT, rg.y - start);
       for (int j = 0; j < cnt; ++j) {
+#if GS_FWD_WORD_BITS
+        if (!masks && tdone) break;   // with the bits the loop is warp-uniform up to a word's end
+#else
         if (masks) {
           if (!__any_sync(0xffffffffu, !tdone)) break;   // warp-uniform: the ballot below needs every lane
         } else if (tdone) {
           break;
         }
+#endif
         const float4* r = s_rec + j * F4;
         const float4 h0 = r[0], h1 = r[1];
         const bool fast = reinterpret_cast<const float*>(r)[11] != 0.f;   // the same for every lane
@@ -528,8 +538,25 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
 #pragma unroll
         for (int q = 0; q < PPT; ++q) tdone = tdone && done[q];
         if (masks) {
-          const u32 b = __ballot_sync(0xffffffffu, comp);
           const u32 gpos = start + (u32)j;
+#if GS_FWD_WORD_BITS
+          // each lane keeps its own bits of the current word; the warp's word is their OR, taken
+          // at the word's last position or the batch's last pair (warp-uniform), where the warp
+          // also stops once every lane is done
+          if (comp) lbits |= 1u << (gpos & 31);
+          if ((gpos & 31u) == 31u || j + 1 == cnt) {
+            cword |= __reduce_or_sync(0xffffffffu, lbits);
+            lbits = 0;
+            cword_idx = (gpos >> 5) + tile;   // each tile owns whole words
+            if ((gpos & 31u) == 31u) {
+              if ((tid & 31) == 0) cplane[cword_idx] = cword;
+              cword = 0;
+              cword_idx = 0xffffffffu;
+            }
+            if (__all_sync(0xffffffffu, tdone)) break;
+          }
+#else
+          const u32 b = __ballot_sync(0xffffffffu, comp);
           const u32 wi = (gpos >> 5) + tile;             // each tile owns whole words
           if (wi != cword_idx) {
             if (cword_idx != 0xffffffffu && (tid & 31) == 0) cplane[cword_idx] = cword;
@@ -537,6 +564,7 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
             cword = 0;
           }
           if (b) cword |= 1u << (gpos & 31);
+#endif
         }
       }
     }
