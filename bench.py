@@ -198,15 +198,19 @@ def oracle_sample_ms(scene, cam, seed, n_tiles=4, prim_slice=8, pose_key=None):
     return ms, desc, time.perf_counter() - w0
 
 
+ORACLE_DRAWS = 16   # the fixed draws (seed s at pose s) that both the baseline and the reference arm use
+
+
 def oracle_baseline(scene, cams, samples, threads, seed0=0):
-    """Mean of oracle_sample_ms over `samples` draws cycling through the poses, on `threads` host
-    threads: the same sampling as the reference arm's steps."""
+    """Mean of oracle_sample_ms over draws seed0 .. seed0 + samples - 1 (draw s at pose s mod the
+    poses), on `threads` host threads: the reference arm's step s is draw s mod ORACLE_DRAWS."""
     import torch
     prev = torch.get_num_threads()
     torch.set_num_threads(threads)
     try:
         oracle_sample_ms(scene, cams[0], 10_000 + seed0, pose_key=0)        # untimed first call
-        runs = [oracle_sample_ms(scene, cams[s % len(cams)], seed0 + s, pose_key=s % len(cams)) for s in range(samples)]
+        runs = [oracle_sample_ms(scene, cams[(seed0 + s) % len(cams)], seed0 + s, pose_key=(seed0 + s) % len(cams))
+                for s in range(samples)]
     finally:
         torch.set_num_threads(prev)
     return float(np.mean([r[0] for r in runs])), runs[0][1], float(sum(r[2] for r in runs))
@@ -327,7 +331,8 @@ def run_reference(args):
     times = []
     w0 = time.time()
     for s in range(args.steps):
-        ms, desc, _ = oracle_sample_ms(scene, cams[s % len(cams)], s, pose_key=s % len(cams))
+        d = s % ORACLE_DRAWS   # the same fixed draws as bench's cpu_baseline
+        ms, desc, _ = oracle_sample_ms(scene, cams[d % len(cams)], d, pose_key=d % len(cams))
         times.append(ms)
     v = float(np.mean(times))
     W, H = cams[0]["width"], cams[0]["height"]
@@ -721,10 +726,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        ms, desc, wall = oracle_baseline(scene, cams, 8, cores)
-        ms1, _, wall1 = oracle_baseline(scene, cams, 1, 1, seed0=8)
+        ms, desc, wall = oracle_baseline(scene, cams, ORACLE_DRAWS, cores)
+        ms1, _, wall1 = oracle_baseline(scene, cams, 1, 1)
         cpu = {"value": round(ms, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": desc + "; mean of 8 draws over poses 0-7, the reference arm's sampling",
+               "sample": desc + f"; mean of the {ORACLE_DRAWS} fixed draws (seed s at pose s) that the "
+                                "reference arm's steps cycle through",
                "wall_s": round(wall, 1), "single_thread": {"value": round(ms1, 1), "cores": 1, "wall_s": round(wall1, 1)}}
 
     serve_out = None
