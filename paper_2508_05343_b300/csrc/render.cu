@@ -249,6 +249,10 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 #ifndef GS_FWD_WORD_BITS
 #define GS_FWD_WORD_BITS 1
 #endif
+// Records a forward thread stages per batch (a batch holds GS_FWD_BATCH_RECS x threads pairs).
+#ifndef GS_FWD_BATCH_RECS
+#define GS_FWD_BATCH_RECS 1
+#endif
 
 // Resident CTAs per SM the compositing kernels are compiled for (0: the compiler's choice).  At
 // K = 4 the backward's two-pixel packed adjoint takes 127 registers (4 CTAs per SM) on its own;
@@ -308,13 +312,15 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
                                                             float* out_T) {
   pdl_begin();
   constexpr int NT = BLOCK / PPT;
+  constexpr int NB = NT * GS_FWD_BATCH_RECS;   // pairs per staged batch
   constexpr int F4 = SRec<K>::F4;
+  static_assert(!GS_FWD_BULK || GS_FWD_BATCH_RECS == 1, "the bulk-copy staging moves one record per thread");
 #if GS_FWD_BULK
   extern __shared__ __align__(16) float4 s_buf[];   // [2][NT][F4]: batch k in buffer k & 1
   __shared__ __align__(8) u64 s_full[2];             // completion of each buffer's bulk copies
   __shared__ int s_abort;
 #else
-  extern __shared__ __align__(16) float4 s_rec[];   // [NT][F4]
+  extern __shared__ __align__(16) float4 s_rec[];   // [NB][F4]
 #endif
   __shared__ u32 s_tile;
   WsHeader* hdr = p.hdr;
@@ -395,7 +401,7 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
     bool pending = rg.y > rg.x;  // a batch has been issued and not yet waited for
     if (pending) issue(rg.x, rg.y, 0);
 #endif
-    for (u32 start = rg.x; start < rg.y; start += NT) {
+    for (u32 start = rg.x; start < rg.y; start += NB) {
       if (__syncthreads_count(tdone) == NT) break;
 #if GS_FWD_BULK
       // batch k arrived: each thread finishes staging its own row in place; then batch k + 1 goes
@@ -421,15 +427,19 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
       }
       kb ^= 1;
 #else
-      const u32 idx = start + tid;
-      if (idx < rg.y) {
-        const float* rec = p.records + (size_t)(u32)pairs[idx] * rec_floats(K);
-        stage_record<K>(rec, s_rec + tid * F4, amin);
-        if (FMAP) s_rec[tid * F4 + 2] = frequency_features<K>(rec);
+#pragma unroll
+      for (int rr = 0; rr < GS_FWD_BATCH_RECS; ++rr) {
+        const int slot = tid + rr * NT;
+        const u32 idx = start + (u32)slot;
+        if (idx < rg.y) {
+          const float* rec = p.records + (size_t)(u32)pairs[idx] * rec_floats(K);
+          stage_record<K>(rec, s_rec + slot * F4, amin);
+          if (FMAP) s_rec[slot * F4 + 2] = frequency_features<K>(rec);
+        }
       }
       __syncthreads();
 #endif
-      const int cnt = (int)min((u32)NT, rg.y - start);
+      const int cnt = (int)min((u32)NB, rg.y - start);
       for (int j = 0; j < cnt; ++j) {
 #if GS_FWD_WORD_BITS
         if (!masks && tdone) break;   // with the bits the loop is warp-uniform up to a word's end
@@ -1023,7 +1033,7 @@ static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, float* r
                                 const Launch& L) {
   constexpr int PPT = GS_PPT_FWD, NT = BLOCK / PPT;
   static int grid = 0;
-  const size_t smem = (GS_FWD_BULK ? 2 : 1) * (size_t)NT * SRec<K>::F * sizeof(float);
+  const size_t smem = (GS_FWD_BULK ? 2 : GS_FWD_BATCH_RECS) * (size_t)NT * SRec<K>::F * sizeof(float);
   if (!grid) {
     cudaError_t e =
         cudaFuncSetAttribute(k_render_fwd<K, PPT, FMAP, MASKS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
