@@ -395,8 +395,8 @@ class TrainStep:
         self.rast = raster.Rasterizer(n, K, deg, W, H, device=dev)
         # size the pair capacity for every pose once (host reads; outside the timed region)
         self.pose_stats = []
-        for c in cams:
-            self.rast.forward(self.pt, c, self.cfg, storage=storage)
+        for c in cams:   # the work counters come from the forward that writes them
+            self.rast.forward(self.pt, c, self.cfg, storage=storage, stats=True)
             v = self.rast.views()
             self.pose_stats.append(dict(pairs=v["pairs"], n_eval=int(v["n_eval"].sum().item()),
                                         active=int((v["touched"] > 0).sum().item()),

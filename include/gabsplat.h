@@ -148,7 +148,8 @@ typedef struct {
  * rank, so each tile's pairs are in depth order; unsorted: emission order); ranges [tiles][2] uint32
  * [start, end);
  * T_final [H][W] float32; n_contrib [H][W] uint32 (1-based position in the tile's list of
- * the last composited pair); n_eval [H][W] uint32 pairs the forward pass evaluated at the pixel
+ * the last composited pair); the per-pixel work counters, written only by
+ * gabsplat_render_fwd_stats: n_eval [H][W] uint32 pairs the forward pass evaluated at the pixel
  * (its tile's list length, or up to the pair that ended compositing); n_reach [H][W] uint32 of those,
  * pairs whose envelope passed o G >= alpha_min; n_comp [H][W] uint32 pairs composited; grad2d
  * [n_active][grad2d_floats] float32 by depth rank
@@ -208,6 +209,13 @@ gs_status gabsplat_bin_sort(const gs_frame* frame, gs_stream stream);
  * out_rgb [3][H][W] (device, required) and out_T [H][W] (device, may be NULL).  Keeps the final
  * transmittance and the last contributor per pixel in the workspace for the backward pass. */
 gs_status gabsplat_render_fwd(const gs_frame* frame, float* out_rgb, float* out_T, gs_stream stream);
+
+/* gabsplat_render_fwd that also writes the per-pixel work counters (n_eval, n_reach, n_comp of
+ * gabsplat_workspace_views: pairs evaluated, reached by the envelope, composited), for work
+ * accounting and tests.  The image, the transmittance, the last contributor and the state the
+ * backward pass reads are the same; the counters cost the forward about 7% of its time, so
+ * gabsplat_render_fwd leaves them as they were.  The paper has no counterpart. */
+gs_status gabsplat_render_fwd_stats(const gs_frame* frame, float* out_rgb, float* out_T, gs_stream stream);
 
 /* Stage 3 for frames that will not be differentiated (rendering only): the same images and
  * per-pixel state as gabsplat_render_fwd, without recording, per warp of 64 pixels, which pairs

@@ -83,6 +83,7 @@ SIGNATURES = {
     "gabsplat_render_fwd": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p, C.c_void_p]),
     "gabsplat_render_freq_map": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p]),
     "gabsplat_render_fwd_only": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gabsplat_render_fwd_stats": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p, C.c_void_p]),
     "gabsplat_densify_accumulate": (C.c_int, [P_(gs_frame), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gabsplat_densify_scratch_bytes": (C.c_size_t, [C.c_int]),
     "gabsplat_densify": (C.c_int, [P_(gs_prims), C.c_void_p, C.c_void_p, C.c_void_p, P_(gs_densify_config),
@@ -172,6 +173,11 @@ def gabsplat_bin_sort(frame, stream=None):
 
 def gabsplat_render_fwd(frame, out_rgb, out_T=None, stream=None):
     _check("gabsplat_render_fwd", lib.gabsplat_render_fwd(C.byref(frame), _ptr(out_rgb), _ptr(out_T), _stream(stream)))
+
+
+def gabsplat_render_fwd_stats(frame, out_rgb, out_T=None, stream=None):
+    _check("gabsplat_render_fwd_stats", lib.gabsplat_render_fwd_stats(C.byref(frame), _ptr(out_rgb), _ptr(out_T),
+                                                                       _stream(stream)))
 
 
 def gabsplat_render_fwd_only(frame, out_rgb, out_T=None, stream=None):

@@ -244,6 +244,15 @@ gs_status gabsplat_render_fwd(const gs_frame* frame, float* out_rgb, float* out_
   return from_cuda(launch_render_fwd(t, make_ptrs(L, frame->ws), out_rgb, out_T, make_launch(stream), true));
 }
 
+gs_status gabsplat_render_fwd_stats(const gs_frame* frame, float* out_rgb, float* out_T, gs_stream stream) {
+  FrameTable t;
+  WsLayout L;
+  const gs_status s = frame_meta(frame, t, L);
+  if (s != GS_OK) return s;
+  if (!out_rgb) return GS_ERR_INVALID_ARG;
+  return from_cuda(launch_render_fwd(t, make_ptrs(L, frame->ws), out_rgb, out_T, make_launch(stream), true, true));
+}
+
 gs_status gabsplat_render_fwd_only(const gs_frame* frame, float* out_rgb, float* out_T, gs_stream stream) {
   FrameTable t;
   WsLayout L;

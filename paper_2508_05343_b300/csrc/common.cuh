@@ -418,8 +418,9 @@ cudaError_t launch_preprocess(const FrameTable& tbl, const WsPtrs& p, const Laun
 cudaError_t launch_depth_sort(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
 cudaError_t launch_bin_sort(const FrameTable& tbl, const WsPtrs& p, const Launch& L);
 // masks: record the composited-pair bits the backward pass reads (off for forward-only rendering)
+// stats: also write the per-pixel work counters n_eval, n_reach, n_comp (only with masks)
 cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L,
-                              bool masks);
+                              bool masks, bool stats = false);
 cudaError_t launch_render_freq_map(const FrameTable& tbl, const WsPtrs& p, float* out_map, const Launch& L);
 // Zero-fill of the attribute gradients carried out by the compositing backward: that kernel is
 // bound by instruction issue and the fill by HBM writes, so the fill runs in its shadow.  The

@@ -307,7 +307,9 @@ __device__ __forceinline__ int2 thread_pixel(int tx, int ty, int tid) {
 // sum_i w_i |f2D_i,y|, cycles per pixel) in place of its colour, with no background.
 // MASKS: record per warp which pairs its pixels composited (for the backward pass); forward-only
 // uses (serving, frequency maps) skip it and keep the per-thread early exit.
-template <int K, int PPT, bool FMAP, bool MASKS>
+// STATS: also write the per-pixel work counters (pairs evaluated, reached and composited), which
+// only the work accounting and the tests read.
+template <int K, int PPT, bool FMAP, bool MASKS, bool STATS>
 __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
                                                             float* out_T) {
   pdl_begin();
@@ -489,12 +491,18 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
             const bool stop0 = pass0 && test.x < Tmin, stop1 = pass1 && test.y < Tmin;
             const bool comp0 = pass0 && !stop0, comp1 = pass1 && !stop1;
             const u32 here = start + (u32)j + 1u - rg.x;
-            reached[0] += reach[0] ? 1u : 0u;
-            reached[1] += reach[1] ? 1u : 0u;
-            if (stop0) { done[0] = true; evaluated[0] = here; }
-            if (stop1) { done[1] = true; evaluated[1] = here; }
-            if (comp0) { T[0] = test.x; last[0] = here; ++composited[0]; } else { wgt.x = 0.f; }
-            if (comp1) { T[1] = test.y; last[1] = here; ++composited[1]; } else { wgt.y = 0.f; }
+            if (STATS) {
+              reached[0] += reach[0] ? 1u : 0u;
+              reached[1] += reach[1] ? 1u : 0u;
+              if (stop0) evaluated[0] = here;
+              if (stop1) evaluated[1] = here;
+              composited[0] += comp0 ? 1u : 0u;
+              composited[1] += comp1 ? 1u : 0u;
+            }
+            if (stop0) done[0] = true;
+            if (stop1) done[1] = true;
+            if (comp0) { T[0] = test.x; last[0] = here; } else { wgt.x = 0.f; }
+            if (comp1) { T[1] = test.y; last[1] = here; } else { wgt.y = 0.f; }
             const float4 c = r[2];   // a zero weight leaves the (non-negative) sums unchanged
             const float2 s0 = __ffma2_rn(f2(c.x), wgt, make_float2(C0[0], C0[1]));
             const float2 s1 = __ffma2_rn(f2(c.y), wgt, make_float2(C1[0], C1[1]));
@@ -513,7 +521,7 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
 #pragma unroll
                 for (int i = 0; i < K; ++i) th[i] = __fadd_rn(th[i], fr[2 * i + 1]);
               if (reach[q]) {
-                ++reached[q];
+                if (STATS) ++reached[q];
                 const float G = ex2_approx(pwq[q]);
                 const float bank = filter_bank<K, decltype(fast_tag)::value>(th, fr + 2 * K, h1.w);
                 const float alpha = fminf(amax, __fmul_rn(__fmul_rn(h1.z, G), bank));
@@ -521,7 +529,7 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
                   const float test = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
                   if (test < Tmin) {
                     done[q] = true;
-                    evaluated[q] = start + (u32)j + 1u - rg.x;
+                    if (STATS) evaluated[q] = start + (u32)j + 1u - rg.x;
                   } else {
                     const float4 c = r[2];
                     const float wgt = alpha * T[q];
@@ -530,7 +538,7 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
                     C2[q] = __fmaf_rn(c.z, wgt, C2[q]);
                     T[q] = test;
                     last[q] = start + (u32)j + 1u - rg.x;
-                    ++composited[q];
+                    if (STATS) ++composited[q];
                     comp = true;
                   }
                 }
@@ -602,9 +610,11 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
         if (oT) oT[pix] = T[q];
         p.T_final[V.pix_base + pix] = T[q];
         p.n_contrib[V.pix_base + pix] = last[q];
-        p.n_eval[V.pix_base + pix] = evaluated[q];
-        p.n_reach[V.pix_base + pix] = reached[q];
-        p.n_comp[V.pix_base + pix] = composited[q];
+        if (STATS) {
+          p.n_eval[V.pix_base + pix] = evaluated[q];
+          p.n_reach[V.pix_base + pix] = reached[q];
+          p.n_comp[V.pix_base + pix] = composited[q];
+        }
       }
     }
     __syncthreads();
@@ -1028,7 +1038,7 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ d
   if (tid == 0) release_tile_counter(&hdr->tile_counter_bwd, &hdr->bwd_exits, &hdr->zero_counter);
 }
 
-template <int K, bool FMAP, bool MASKS>
+template <int K, bool FMAP, bool MASKS, bool STATS>
 static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, float* rgb, float* T,
                                 const Launch& L) {
   constexpr int PPT = GS_PPT_FWD, NT = BLOCK / PPT;
@@ -1036,10 +1046,10 @@ static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, float* r
   const size_t smem = (GS_FWD_BULK ? 2 : GS_FWD_BATCH_RECS) * (size_t)NT * SRec<K>::F * sizeof(float);
   if (!grid) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_render_fwd<K, PPT, FMAP, MASKS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_render_fwd<K, PPT, FMAP, MASKS, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<K, PPT, FMAP, MASKS>, NT, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<K, PPT, FMAP, MASKS, STATS>, NT, smem) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     grid = per_sm * L.sm_count;
@@ -1047,7 +1057,7 @@ static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, float* r
   int g = grid;
   if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
   if (g < 1) g = 1;
-  launch_pdl<PDL_RENDER>(k_render_fwd<K, PPT, FMAP, MASKS>, g, NT, smem, L.stream, p, rgb, T);
+  launch_pdl<PDL_RENDER>(k_render_fwd<K, PPT, FMAP, MASKS, STATS>, g, NT, smem, L.stream, p, rgb, T);
   return cudaGetLastError();
 }
 
@@ -1091,30 +1101,31 @@ static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const fl
 }
 
 
-template <bool FMAP, bool MASKS>
+template <bool FMAP, bool MASKS, bool STATS>
 static cudaError_t launch_fwd_k(const FrameTable& tbl, const WsPtrs& p, float* out, float* out_T, const Launch& L) {
   switch (tbl.K) {
-    case 0: return launch_fwd_t<0, FMAP, MASKS>(tbl, p, out, out_T, L);
-    case 1: return launch_fwd_t<1, FMAP, MASKS>(tbl, p, out, out_T, L);
-    case 2: return launch_fwd_t<2, FMAP, MASKS>(tbl, p, out, out_T, L);
-    case 3: return launch_fwd_t<3, FMAP, MASKS>(tbl, p, out, out_T, L);
-    case 4: return launch_fwd_t<4, FMAP, MASKS>(tbl, p, out, out_T, L);
-    case 5: return launch_fwd_t<5, FMAP, MASKS>(tbl, p, out, out_T, L);
-    case 6: return launch_fwd_t<6, FMAP, MASKS>(tbl, p, out, out_T, L);
-    case 7: return launch_fwd_t<7, FMAP, MASKS>(tbl, p, out, out_T, L);
-    case 8: return launch_fwd_t<8, FMAP, MASKS>(tbl, p, out, out_T, L);
+    case 0: return launch_fwd_t<0, FMAP, MASKS, STATS>(tbl, p, out, out_T, L);
+    case 1: return launch_fwd_t<1, FMAP, MASKS, STATS>(tbl, p, out, out_T, L);
+    case 2: return launch_fwd_t<2, FMAP, MASKS, STATS>(tbl, p, out, out_T, L);
+    case 3: return launch_fwd_t<3, FMAP, MASKS, STATS>(tbl, p, out, out_T, L);
+    case 4: return launch_fwd_t<4, FMAP, MASKS, STATS>(tbl, p, out, out_T, L);
+    case 5: return launch_fwd_t<5, FMAP, MASKS, STATS>(tbl, p, out, out_T, L);
+    case 6: return launch_fwd_t<6, FMAP, MASKS, STATS>(tbl, p, out, out_T, L);
+    case 7: return launch_fwd_t<7, FMAP, MASKS, STATS>(tbl, p, out, out_T, L);
+    case 8: return launch_fwd_t<8, FMAP, MASKS, STATS>(tbl, p, out, out_T, L);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_render_fwd(const FrameTable& tbl, const WsPtrs& p, float* out_rgb, float* out_T, const Launch& L,
-                              bool masks) {
-  return masks ? launch_fwd_k<false, true>(tbl, p, out_rgb, out_T, L)
-               : launch_fwd_k<false, false>(tbl, p, out_rgb, out_T, L);
+                              bool masks, bool stats) {
+  if (!masks) return launch_fwd_k<false, false, false>(tbl, p, out_rgb, out_T, L);
+  return stats ? launch_fwd_k<false, true, true>(tbl, p, out_rgb, out_T, L)
+               : launch_fwd_k<false, true, false>(tbl, p, out_rgb, out_T, L);
 }
 
 cudaError_t launch_render_freq_map(const FrameTable& tbl, const WsPtrs& p, float* out_map, const Launch& L) {
-  return launch_fwd_k<true, false>(tbl, p, out_map, nullptr, L);
+  return launch_fwd_k<true, false, false>(tbl, p, out_map, nullptr, L);
 }
 
 cudaError_t launch_render_bwd(const FrameTable& tbl, const WsPtrs& p, const float* dL, const ZeroJob* z,

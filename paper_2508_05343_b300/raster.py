@@ -49,10 +49,11 @@ class Rasterizer:
 
     # ---- stages -------------------------------------------------------------------------
     def forward(self, prims_t: dict, camera: dict, cfg: B.gs_config, storage=B.GS_F32, out_rgb=None, out_T=None,
-                auto_capacity=True, forward_only=False):
+                auto_capacity=True, forward_only=False, stats=False):
         """preprocess -> bin_sort -> render_fwd.  With auto_capacity the pair count is read back once
         (a host synchronisation) and the workspace regrown if it overflowed.  forward_only renders
-        without the state a backward pass needs (gabsplat_render_fwd_only)."""
+        without the state a backward pass needs (gabsplat_render_fwd_only); stats also writes the
+        per-pixel work counters n_eval / n_reach / n_comp (gabsplat_render_fwd_stats)."""
         self.generation += 1
         self._prims = B.make_prims(prims_t, storage)
         self.storage = storage
@@ -65,7 +66,9 @@ class Rasterizer:
         for _ in range(2):
             B.gabsplat_preprocess(self.frame, self._prims, self._cam, cfg)
             B.gabsplat_bin_sort(self.frame)
-            (B.gabsplat_render_fwd_only if forward_only else B.gabsplat_render_fwd)(self.frame, out_rgb, out_T)
+            fwd = B.gabsplat_render_fwd_only if forward_only else (
+                B.gabsplat_render_fwd_stats if stats else B.gabsplat_render_fwd)
+            fwd(self.frame, out_rgb, out_T)
             if not auto_capacity:
                 break
             st, pairs = B.gabsplat_device_status(self.frame)

@@ -26,7 +26,7 @@ def gpu_render(prims, cam, gcfg, storage=0, capacity=None):
     r = raster.Rasterizer(n, K, deg, cam["width"], cam["height"], pair_capacity=capacity)
     pt = raster.to_device(prims, storage=storage)
     T = torch.empty(cam["height"], cam["width"], device="cuda")
-    img = r.forward(pt, cam, gcfg, storage=storage, out_T=T)
+    img = r.forward(pt, cam, gcfg, storage=storage, out_T=T, stats=True)
     torch.cuda.synchronize()
     return r, pt, img, T
 
