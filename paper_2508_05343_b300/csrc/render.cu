@@ -249,6 +249,11 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 #ifndef GS_FWD_WORD_BITS
 #define GS_FWD_WORD_BITS 1
 #endif
+// The backward adds each pair's gradients into its grad2d row with vector reductions that return
+// nothing (red.global.add.v4.f32) instead of value-returning atomics.
+#ifndef GS_BWD_VECTOR_RED
+#define GS_BWD_VECTOR_RED 1
+#endif
 // Records a forward thread stages per batch (a batch holds GS_FWD_BATCH_RECS x threads pairs).
 #ifndef GS_FWD_BATCH_RECS
 #define GS_FWD_BATCH_RECS 1
@@ -656,7 +661,16 @@ __device__ __forceinline__ void flush_pair_grads(const float* a, float* dst) {
 #pragma unroll
   for (int i = 0; i < NG / 4; ++i) {
     const float4 qv = make_float4(row[4 * i], row[4 * i + 1], row[4 * i + 2], row[4 * i + 3]);
-    if (qv.x != 0.f || qv.y != 0.f || qv.z != 0.f || qv.w != 0.f) atomicAdd(reinterpret_cast<float4*>(dst) + i, qv);
+    if (qv.x != 0.f || qv.y != 0.f || qv.z != 0.f || qv.w != 0.f) {
+#if GS_BWD_VECTOR_RED
+      // a reduction without a returned value: nothing waits on the memory system's reply
+      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(reinterpret_cast<float4*>(dst) + i),
+                   "f"(qv.x), "f"(qv.y), "f"(qv.z), "f"(qv.w)
+                   : "memory");
+#else
+      atomicAdd(reinterpret_cast<float4*>(dst) + i, qv);
+#endif
+    }
   }
 }
 
