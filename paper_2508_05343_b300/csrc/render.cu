@@ -1,8 +1,10 @@
 // Per-tile compositing of the 2D Gabor primitives (Sec. 3.3.2 Eq. 9, Sec. 3.3.3 Eq. 10) and its
-// reverse-order adjoint.  One CTA owns a 16x16 tile and pulls tiles from an atomic counter, longest
-// pair lists first.  The tile's depth-sorted pairs are staged into shared memory in
-// batches of 256 records; the evaluation of alpha is a single inlined function with explicit
-// fused-multiply-add intrinsics so the backward kernel reproduces the forward's decisions exactly.
+// reverse-order adjoint.  Forward: one CTA owns a 16x16 tile and pulls tiles from an atomic
+// counter, longest pair lists first, staging the tile's depth-sorted pairs into shared memory one
+// batch per CTA pass.  Backward: each warp pulls one 8x8 footprint of a tile at a time and walks,
+// back to front, only the pairs the forward recorded as composited there.  Envelope, bank and
+// alpha are evaluated with explicit rounding intrinsics in both, so the backward reproduces the
+// forward's decisions exactly.
 #include <type_traits>
 
 #include "common.cuh"
@@ -223,10 +225,6 @@ __device__ __forceinline__ float filter_bank(const float* th, const float* w, fl
 #define GS_PPT_BWD 2
 #endif
 static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-warp composited-pair bits: same warp footprints");
-// Backward per-pair reduction: 1 = transpose through shared memory, 0 = warp reduce-scatter.
-#ifndef GS_BWD_SMEM_REDUCE
-#define GS_BWD_SMEM_REDUCE 1
-#endif
 
 // Warp footprint inside the 16x16 tile: 1 = 8 pixels wide and 4 PPT rows high (two warp columns),
 // 0 = the full tile width and 2 PPT rows high.  A compact footprint means fewer warps overlap a
@@ -249,27 +247,22 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 #ifndef GS_FWD_WORD_BITS
 #define GS_FWD_WORD_BITS 1
 #endif
-// The backward adds each pair's gradients into its grad2d row with vector reductions that return
-// nothing (red.global.add.v4.f32) instead of value-returning atomics.
-#ifndef GS_BWD_VECTOR_RED
-#define GS_BWD_VECTOR_RED 1
-#endif
 // Records a forward thread stages per batch (a batch holds GS_FWD_BATCH_RECS x threads pairs).
 #ifndef GS_FWD_BATCH_RECS
 #define GS_FWD_BATCH_RECS 1
 #endif
 
 // Resident CTAs per SM the compositing kernels are compiled for (0: the compiler's choice).  At
-// K = 4 the backward's two-pixel packed adjoint takes 127 registers (4 CTAs per SM) on its own;
-// held to 96 for 5 CTAs per SM it spills 16 bytes and runs 5% faster.  The packed adjoint holds
-// both pixels' cosines and sines, so above GS_BWD_PACKED_MAX_K components it would spill heavily
-// under that cap (404 bytes at K = 8, 1.8x slower): those K keep the per-pixel adjoint at 4 CTAs
-// per SM (left to itself the compiler takes 159 registers at K = 8, 3 CTAs per SM).
+// K = 4 the backward's warp walk with the two-pixel packed adjoint takes 95 registers (5 CTAs of
+// 128 threads per SM) on its own; held to 72 for 7 CTAs per SM it spills 24 bytes and runs 2%
+// faster (0.750 against 0.767 ms at 1.5M primitives, 1600x1064; 6 CTAs: 0.760).  The packed
+// adjoint holds both pixels' cosines and sines, so above GS_BWD_PACKED_MAX_K components it would
+// spill heavily under such a cap: those K keep the per-pixel adjoint at 4 CTAs per SM.
 #ifndef GS_FWD_MIN_CTAS
 #define GS_FWD_MIN_CTAS 0
 #endif
 #ifndef GS_BWD_MIN_CTAS
-#define GS_BWD_MIN_CTAS 5
+#define GS_BWD_MIN_CTAS 7
 #endif
 #ifndef GS_BWD_PACKED_MAX_K
 #define GS_BWD_PACKED_MAX_K 4
@@ -627,56 +620,207 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
   if (tid == 0) release_tile_counter(&hdr->tile_counter_fwd, &hdr->fwd_exits);
 }
 
-// Reduce-scatter of 32 per-lane values across a warp: afterwards lane i holds the warp sum of
-// value i (31 shuffles instead of 32 x 5 for independent butterflies).
-__device__ __forceinline__ float warp_reduce_scatter(float (&v)[32], int lane) {
-#pragma unroll
-  for (int level = 16; level >= 1; level >>= 1) {
-    const bool upper = (lane & level) != 0;
-#pragma unroll
-    for (int k = 0; k < level; ++k) {
-      const float send = upper ? v[k] : v[k + level];
-      const float keep = upper ? v[k + level] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, level);
-    }
-  }
-  return v[0];
-}
+// Per-thread pixel state of the reverse walk (PPT vertically adjacent pixels).
+template <int PPT>
+struct BwdPix {
+  // tbg: T_final (bg . dL/dC), the background's share of dL/dalpha (scaled by 1 / (1 - alpha))
+  float T[PPT], g0[PPT], g1[PPT], g2[PPT], tbg[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
+  u32 last[PPT];
+};
 
-// One pair's accumulated 2D gradients, converted from the log2-domain conic (A' = -a/2 log2 e,
-// B' = -b log2 e, C' = -c/2 log2 e) to (a, b, c) and from the staged 2 pi f2D to f2D, added to its
-// grad2d row with one vector atomic per 4 values (zero groups skipped).
-template <int K>
-__device__ __forceinline__ void flush_pair_grads(const float* a, float* dst) {
-  constexpr int NV = 10 + 3 * K, NG = g2d_floats(K);
-  const float cA = -0.5f * LOG2E, cB = -LOG2E;
-  float row[NG];
-#pragma unroll
-  for (int i = 0; i < NG; ++i) row[i] = i < NV ? a[i] : 0.f;
-  row[2] *= cA;
-  row[3] *= cB;
-  row[4] *= cA;
-#pragma unroll
-  for (int i = 9; i < 9 + 2 * K; ++i) row[i] *= TWO_PI;
-#pragma unroll
-  for (int i = 0; i < NG / 4; ++i) {
-    const float4 qv = make_float4(row[4 * i], row[4 * i + 1], row[4 * i + 2], row[4 * i + 3]);
-    if (qv.x != 0.f || qv.y != 0.f || qv.z != 0.f || qv.w != 0.f) {
-#if GS_BWD_VECTOR_RED
-      // a reduction without a returned value: nothing waits on the memory system's reply
-      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(reinterpret_cast<float4*>(dst) + i),
-                   "f"(qv.x), "f"(qv.y), "f"(qv.z), "f"(qv.w)
-                   : "memory");
-#else
-      atomicAdd(reinterpret_cast<float4*>(dst) + i, qv);
-#endif
-    }
-  }
-}
+// One pair's adjoint at a thread's PPT pixels (Eq. 9-10 differentiated, back to front): restores
+// the transmittance before the pair, updates the colour sums behind it and adds the pair's
+// gradient contributions into col, its column of the warp's transpose buffer.  pos: 0-based position of the pair in the
+// tile list.  Returns whether a pixel of the thread composited the pair.  The envelope, bank and
+// alpha are evaluated exactly as the forward evaluates them, so both take the same decisions.
+// Row stride (floats) of a warp's transpose buffer: value v of lane l at [v * BWD_RS + l]; 36 keeps
+// the reading lanes' 16-byte loads free of bank conflicts.
+constexpr int BWD_RS = 36;
 
-// Chunks [c0, c0 + count) of a zero-fill, by the whole CTA: 16-byte streaming stores where the
-// array is 16-byte aligned (chunks are multiples of 4 floats), scalar stores otherwise.
-__device__ __noinline__ void zero_chunks(const ZeroJob& z, u32 c0, u32 count) {
+template <int K, int PPT, bool FAST>
+__device__ __forceinline__ bool pair_adjoint(BwdPix<PPT>& S, const float4* r, u32 pos, float fpx, float fpy0,
+                                             float amin, float amax, float* col) {
+  constexpr int NV = 10 + 3 * K;
+  const float4 h0 = r[0], h1 = r[1];
+  const float* fw = reinterpret_cast<const float*>(r + 3);   // 2 pi f2D, then the weights
+  const float dx = __fsub_rn(fpx, h0.x);
+  const float oln2 = h1.z * 0.6931471805599453f;   // opacity ln 2
+  bool contrib = false;
+  float dyq[PPT], pwq[PPT];
+  pixel_powers<PPT>(h0, h1, dx, __fsub_rn(fpy0, h0.y), dyq, pwq);
+  if constexpr (PPT == 2 && K <= GS_BWD_PACKED_MAX_K) {
+    // Both pixels at once.  Envelope, bank and alpha in packed FP32, bit-identical to the
+    // forward's decisions.  A pixel that does not take part gets alpha 0 (its transmittance
+    // and colour sums stay as they are) and dL/dalpha 0 (it adds exact zeros), and the two
+    // pixels' adjoints are summed before they meet the shared factors: dx is common, and
+    // sums against dy use each pixel's own offset.  The code is straight-line: a pair is
+    // walked only where a pixel of the warp composited it, so a lane leaving early would
+    // only wait, and its column stores would no longer coincide with the other lanes'.
+    const bool live0 = pos < S.last[0] && pwq[0] >= h1.y;
+    const bool live1 = pos < S.last[1] && pwq[1] >= h1.y;
+    float2 thp[K > 0 ? K : 1];
+#pragma unroll
+    for (int i = 0; i < K; ++i) thp[i] = row_phases2(fw[2 * i], fw[2 * i + 1], dx, dyq);
+    const float2 G = make_float2(ex2_approx(pwq[0]), ex2_approx(pwq[1]));
+    float2 cs[K > 0 ? K : 1], sn[K > 0 ? K : 1];
+    float2 bank = f2(h1.w);
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const float2 a = reduced_angle2<FAST>(thp[i]);
+      cs[i] = make_float2(__cosf(a.x), __cosf(a.y));
+      sn[i] = make_float2(__sinf(a.x), __sinf(a.y));
+      bank = __ffma2_rn(f2(fw[2 * K + i]), cs[i], bank);
+    }
+    const float2 araw = __fmul2_rn(__fmul2_rn(f2(h1.z), G), bank);
+    const float ax = fminf(amax, araw.x), ay = fminf(amax, araw.y);
+    const bool pass0 = live0 && ax >= amin, pass1 = live1 && ay >= amin;
+    contrib = pass0 || pass1;
+    const float2 alpha = make_float2(pass0 ? ax : 0.f, pass1 ? ay : 0.f);
+    const float2 oma = __ffma2_rn(alpha, f2(-1.f), f2(1.f));
+    const float2 ioma = make_float2(rcp_approx(oma.x), rcp_approx(oma.y));
+    const float2 Tn = __fmul2_rn(make_float2(S.T[0], S.T[1]), ioma);   // transmittance before this pair
+    if (pass0) S.T[0] = Tn.x;
+    if (pass1) S.T[1] = Tn.y;
+    const float4 c = r[2];
+    const float2 wgt = __fmul2_rn(alpha, Tn);
+    const float2 G0 = make_float2(S.g0[0], S.g0[1]), G1 = make_float2(S.g1[0], S.g1[1]), G2 = make_float2(S.g2[0], S.g2[1]);
+    float2 A0 = make_float2(S.acc0[0], S.acc0[1]), A1 = make_float2(S.acc1[0], S.acc1[1]),
+           A2 = make_float2(S.acc2[0], S.acc2[1]);
+    // (c - acc) . dL/dC, then dL/dalpha = T (c - acc) . dL/dC - tbg / (1 - alpha)
+    float2 dcg = __fmul2_rn(__ffma2_rn(A2, f2(-1.f), f2(c.z)), G2);
+    dcg = __ffma2_rn(__ffma2_rn(A1, f2(-1.f), f2(c.y)), G1, dcg);
+    dcg = __ffma2_rn(__ffma2_rn(A0, f2(-1.f), f2(c.x)), G0, dcg);
+    float2 dLda = __ffma2_rn(__fmul2_rn(make_float2(S.tbg[0], S.tbg[1]), ioma), f2(-1.f), __fmul2_rn(Tn, dcg));
+    A0 = __ffma2_rn(oma, A0, __fmul2_rn(alpha, f2(c.x)));
+    A1 = __ffma2_rn(oma, A1, __fmul2_rn(alpha, f2(c.y)));
+    A2 = __ffma2_rn(oma, A2, __fmul2_rn(alpha, f2(c.z)));
+    S.acc0[0] = A0.x; S.acc0[1] = A0.y;
+    S.acc1[0] = A1.x; S.acc1[1] = A1.y;
+    S.acc2[0] = A2.x; S.acc2[1] = A2.y;
+    // no gradient through a clamped alpha, none from a pixel that does not take part
+    if (!pass0 || araw.x > amax) dLda.x = 0.f;
+    if (!pass1 || araw.y > amax) dLda.y = 0.f;
+    col[(6) * BWD_RS] = fmaf(wgt.y, S.g0[1], wgt.x * S.g0[0]);
+    col[(7) * BWD_RS] = fmaf(wgt.y, S.g1[1], wgt.x * S.g1[0]);
+    col[(8) * BWD_RS] = fmaf(wgt.y, S.g2[1], wgt.x * S.g2[0]);
+    const float2 dLdG = __fmul2_rn(dLda, G);
+    const float2 dLdbank = __fmul2_rn(dLdG, f2(h1.z));
+    const float2 dLdo = __fmul2_rn(dLdG, bank);
+    // log2-domain power p2: G = 2^p2, dG/dp2 = G ln 2, so dL/dp2 = dLda o bank G ln 2
+    const float2 dLdp2 = __fmul2_rn(dLdo, f2(oln2));
+    const float2 edy = __fmul2_rn(dLdp2, make_float2(dyq[0], dyq[1]));
+    const float P = dLdp2.x + dLdp2.y;               // sum of dL/dp2
+    const float Y = edy.x + edy.y;                   // sum of dL/dp2 dy
+    const float Ex = P * dx;                         // sum of dL/dp2 dx
+    col[(5) * BWD_RS] = dLdo.x + dLdo.y;                         // d opacity
+    col[(2) * BWD_RS] = Ex * dx;                                 // w.r.t. A' (converted at flush)
+    col[(3) * BWD_RS] = Y * dx;                                  // w.r.t. B'
+    col[(4) * BWD_RS] = fmaf(edy.y, dyq[1], edy.x * dyq[0]);     // w.r.t. C'
+    float gdx = 2.f * h0.z * Ex + h0.w * Y;
+    float gdy = h0.w * Ex + 2.f * h1.x * Y;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const float wi = fw[2 * K + i];
+      const float2 kc = __fmul2_rn(dLdbank, cs[i]);
+      const float2 ks = __fmul2_rn(dLdbank, sn[i]);
+      col[(9 + 2 * K + i) * BWD_RS] = kc.x + kc.y;                         // d (cosine weight i)
+      const float gth = -wi * (ks.x + ks.y);                   // d phase (radians), both pixels
+      const float gthdy = -wi * fmaf(ks.y, dyq[1], ks.x * dyq[0]);
+      col[(9 + 2 * i) * BWD_RS] = gth * dx;                                // w.r.t. 2 pi f2D (scaled at flush)
+      col[(9 + 2 * i + 1) * BWD_RS] = gthdy;
+      gdx += gth * fw[2 * i];
+      gdy += gth * fw[2 * i + 1];
+    }
+    col[(9 + 3 * K) * BWD_RS] = dLdbank.x + dLdbank.y;           // d (1 - sum w)
+    col[(0) * BWD_RS] = -gdx;                                    // d mu = - d (pixel - mu)
+    col[(1) * BWD_RS] = -gdy;
+  } else {
+    float gv[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) gv[i] = 0.f;
+    // raw phases of the current row, taken as the forward takes them (two rows: row_phases2)
+    float th[K > 0 ? K : 1], th1[K > 0 ? K : 1];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      if constexpr (PPT == 2) {
+        const float2 t = row_phases2(fw[2 * i], fw[2 * i + 1], dx, dyq);
+        th[i] = t.x;
+        th1[i] = t.y;
+      } else {
+        th[i] = raw_phase(fw[2 * i], fw[2 * i + 1], dx, dyq[0]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      if (q > 0)
+#pragma unroll
+        for (int i = 0; i < K; ++i) th[i] = PPT == 2 ? th1[i] : __fadd_rn(th[i], fw[2 * i + 1]);
+      if (pos >= S.last[q]) continue;
+      const float dy = dyq[q];
+      const float pw = pwq[q];
+      if (pw < h1.y) continue;
+      const float G = ex2_approx(pw);
+      float cs[K > 0 ? K : 1], sn[K > 0 ? K : 1];
+      float bank = h1.w;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const float ang = reduced_angle<FAST>(th[i]);
+        cs[i] = __cosf(ang);
+        sn[i] = __sinf(ang);
+      }
+#pragma unroll
+      for (int i = 0; i < K; ++i) bank = __fmaf_rn(fw[2 * K + i], cs[i], bank);
+      const float araw = __fmul_rn(__fmul_rn(h1.z, G), bank);
+      const float alpha = fminf(amax, araw);
+      if (alpha < amin) continue;
+      contrib = true;
+      const float oma = 1.f - alpha;
+      const float ioma = rcp_approx(oma);
+      S.T[q] = S.T[q] * ioma;                              // transmittance before this pair
+      const float4 c = r[2];
+      const float wgt = alpha * S.T[q];
+      gv[6] += wgt * S.g0[q];
+      gv[7] += wgt * S.g1[q];
+      gv[8] += wgt * S.g2[q];
+      float dLda = S.T[q] * ((c.x - S.acc0[q]) * S.g0[q] + (c.y - S.acc1[q]) * S.g1[q] + (c.z - S.acc2[q]) * S.g2[q]) -
+                   S.tbg[q] * ioma;
+      S.acc0[q] = alpha * c.x + oma * S.acc0[q];
+      S.acc1[q] = alpha * c.y + oma * S.acc1[q];
+      S.acc2[q] = alpha * c.z + oma * S.acc2[q];
+      if (araw > amax) dLda = 0.f;                     // clamped: no gradient through alpha
+      const float dLdG = dLda * G;
+      const float dLdbank = dLdG * h1.z;
+      const float dLdo = dLdG * bank;
+      gv[5] += dLdo;                                   // d opacity
+      // log2-domain power p2: G = 2^p2, dG/dp2 = G ln 2, so dL/dp2 = dLda o bank G ln 2
+      const float dLdp2 = dLdo * oln2;
+      const float ex = dLdp2 * dx, ey = dLdp2 * dy;
+      gv[2] += ex * dx;                                // w.r.t. A' (converted at flush)
+      gv[3] += ex * dy;                                // w.r.t. B'
+      gv[4] += ey * dy;                                // w.r.t. C'
+      float gdx = 2.f * h0.z * ex + h0.w * ey;
+      float gdy = h0.w * ex + 2.f * h1.x * ey;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const float wi = fw[2 * K + i];
+        gv[9 + 2 * K + i] += dLdbank * cs[i];                  // d (cosine weight i)
+        const float gth = -dLdbank * wi * sn[i];                // d phase (radians)
+        gv[9 + 2 * i] += gth * dx;                              // w.r.t. 2 pi f2D (scaled at flush)
+        gv[9 + 2 * i + 1] += gth * dy;
+        gdx += gth * fw[2 * i];
+        gdy += gth * fw[2 * i + 1];
+      }
+      gv[9 + 3 * K] += dLdbank;                        // d (1 - sum w)
+      gv[0] -= gdx;                                    // d mu = - d (pixel - mu)
+      gv[1] -= gdy;
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) col[i * BWD_RS] = gv[i];
+  }
+  return contrib;
+}
+// Chunks [c0, c0 + count) of a zero-fill, by one warp (zero_chunks with lane strides).
+__device__ __noinline__ void zero_chunks_warp(const ZeroJob& z, u32 c0, u32 count, int lane) {
   const u32 total = z.base[ZERO_ARRAYS];
   const u32 c1 = c0 < total - min(total, count) ? c0 + count : total;
   for (u32 c = c0; c < c1; ++c) {
@@ -688,35 +832,50 @@ __device__ __noinline__ void zero_chunks(const ZeroJob& z, u32 c0, u32 count) {
     u32 done = 0;
     if ((reinterpret_cast<uintptr_t>(z.a[i]) & 15u) == 0) {
       const u32 n4 = len >> 2;
-      for (u32 j = threadIdx.x; j < n4; j += blockDim.x)
-        __stcs(reinterpret_cast<float4*>(a) + j, make_float4(0.f, 0.f, 0.f, 0.f));
+      for (u32 j = (u32)lane; j < n4; j += 32u) __stcs(reinterpret_cast<float4*>(a) + j, make_float4(0.f, 0.f, 0.f, 0.f));
       done = 4 * n4;
     }
-    for (u32 j = done + threadIdx.x; j < len; j += blockDim.x) a[j] = 0.f;
+    for (u32 j = done + (u32)lane; j < len; j += 32u) a[j] = 0.f;
   }
 }
 
+// Position of the (r + 1)-th highest set bit of m (m has more than r set bits): the largest b with
+// popc(m >> b) > r.
+__device__ __forceinline__ int nth_high_bit(u32 m, int r) {
+  int b = 0;
+#pragma unroll
+  for (int s = 16; s; s >>= 1)
+    if (__popc(m >> (b + s)) > r) b += s;
+  return b;
+}
+
+// Warps of one tile: one per 8x8 (PPT = 2) footprint, the units the forward records
+// composited-pair bits for.
+constexpr int BWD_WARPS_PER_TILE = BLOCK / GS_PPT_BWD / 32;
+
+// The reverse walk with independent warps.  A task is one warp footprint of one tile (tiles in the
+// order of tile_order, longest pair lists first); a warp takes tasks from the device counter, walks
+// the pairs that the forward recorded as composited by its pixels, back to front, staging them 32
+// at a time into its own shared-memory rows, and adds each pair's warp-reduced gradients straight
+// into the pair's grad2d row with vector reductions.  No CTA barrier sits on the walk, so a warp
+// with little work moves on instead of waiting for the others of its CTA.  After each task the
+// warp zero-fills its share of the attribute gradients.
 template <int K, int PPT>
-__global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ dL_drgb,
-                                           const __grid_constant__ ZeroJob z) {
+__global__ void GS_BWD_BOUNDS k_render_bwd_w(WsPtrs p, const float* __restrict__ dL_drgb,
+                                             const __grid_constant__ ZeroJob z) {
   pdl_begin();
-  constexpr int NT = BLOCK / PPT;
+  constexpr int NW = BLOCK / PPT / 32;   // warps per CTA
+  constexpr int WPT = BWD_WARPS_PER_TILE;
   constexpr int F4 = SRec<K>::F4;
   constexpr int NV = 10 + 3 * K;         // gradient values per pair
   constexpr int NG = g2d_floats(K);      // padded row in global memory
-  constexpr int NS = NV | 1;             // shared accumulator row (odd stride: conflict-free)
   constexpr int NVP = (NV + 31) / 32 * 32;
   extern __shared__ __align__(16) float4 smem4[];
-  float4* s_rec = smem4;                                        // [NT][F4]
-  float* s_acc = reinterpret_cast<float*>(smem4 + NT * F4);     // [NT][NS]
-  u32* s_id = reinterpret_cast<u32*>(s_acc + NT * NS);           // [NT]
-#if GS_BWD_SMEM_REDUCE
-  constexpr int RS = 36;                                         // row stride of the transpose buffer
-  float* s_red = reinterpret_cast<float*>(smem4 + NT * F4) + NT * NS + NT + (threadIdx.x >> 5) * (NV * RS + 4);
-#endif
-  __shared__ u32 s_tile;
-  __shared__ u32 s_max;
-  __shared__ u32 s_zc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4* s_rec = smem4 + warp * 32 * F4;                                              // [32][F4]
+  u32* s_id = reinterpret_cast<u32*>(smem4 + NW * 32 * F4) + warp * 64;                // [32] rows
+  u32* s_pos = s_id + 32;                                                              // [32] positions
+  float* s_red = reinterpret_cast<float*>(smem4 + NW * 32 * F4 + NW * 16) + warp * (NV * BWD_RS + 4);
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
   if (hdr->masks_epoch != hdr->epoch) {   // no forward of this frame recorded the composited-pair bits
@@ -726,330 +885,160 @@ __global__ void GS_BWD_BOUNDS k_render_bwd(WsPtrs p, const float* __restrict__ d
   const FrameTable* tbl = p.tbl;
   // sorted pairs tile << 32 | depth rank; the rank is the record (and grad2d) row
   const u64* __restrict__ pairs = (tbl->tpasses_needed & 1) ? p.keys1 : p.keys0;
-  const int tid = threadIdx.x, lane = tid & 31;
   const u32 ntiles = tbl->total_tiles;
   const float amax = tbl->alpha_max, amin = tbl->alpha_min;
+  // lane v's share of the record-gradient conversion: log2-domain conic (A' = -a/2 log2 e,
+  // B' = -b log2 e, C' = -c/2 log2 e) to (a, b, c), and the staged 2 pi f2D to f2D
+  float conv[NVP / 32];
+#pragma unroll
+  for (int g = 0; g < NVP / 32; ++g) {
+    const int v = 32 * g + lane;
+    conv[g] = (v == 2 || v == 4) ? -0.5f * LOG2E : v == 3 ? -LOG2E : (v >= 9 && v < 9 + 2 * K) ? TWO_PI : 1.f;
+  }
   for (;;) {
-    if (tid == 0) {   // tiles in the order of tile_order: longest pair lists first
-      const u32 slot = atomicAdd(&hdr->tile_counter_bwd, 1u);
-      s_tile = slot < ntiles ? p.tile_order[slot] : 0xFFFFFFFFu;
-      s_max = 0;
-    }
-    __syncthreads();
-    const u32 tile = s_tile;
-    if (tile >= ntiles) break;
+    u32 slot = 0;
+    if (lane == 0) slot = atomicAdd(&hdr->tile_counter_bwd, 1u);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot >= ntiles * (u32)WPT) break;   // warp-uniform
+    const u32 tile = p.tile_order[slot / WPT];
+    const int quad = (int)(slot % WPT);
     const int v = view_of_tile(tbl, tile);
     const ViewDesc& V = tbl->v[v];
     const u32 local = tile - V.tile_base;
     const int tx = (int)(local % (u32)V.tiles_x), ty = (int)(local / (u32)V.tiles_x);
-    const int2 pxy = thread_pixel<PPT>(tx, ty, tid);
+    const int2 pxy = thread_pixel<PPT>(tx, ty, quad * 32 + lane);
     const int px = pxy.x, py0 = pxy.y;
     const uint2 rg = p.ranges[tile];
     const float fpx = (float)px + 0.5f, fpy0 = (float)py0 + 0.5f;
     const float* gsrc = dL_drgb ? dL_drgb : V.dL_drgb;
     const size_t hw = (size_t)V.width * V.height;
-    // tbg: T_final (bg . dL/dC), the background's share of dL/dalpha (scaled by 1 / (1 - alpha))
-    float T[PPT], g0[PPT], g1[PPT], g2[PPT], tbg[PPT], acc0[PPT], acc1[PPT], acc2[PPT];
-    u32 last[PPT];
+    BwdPix<PPT> S;
     u32 wlast = 0;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-      T[q] = 1.f;
-      g0[q] = g1[q] = g2[q] = 0.f;
-      acc0[q] = acc1[q] = acc2[q] = 0.f;
-      last[q] = 0;
+      S.T[q] = 1.f;
+      S.g0[q] = S.g1[q] = S.g2[q] = 0.f;
+      S.acc0[q] = S.acc1[q] = S.acc2[q] = 0.f;
+      S.last[q] = 0;
       const int py = py0 + q;
       if (px < V.width && py < V.height) {
         const size_t pix = (size_t)py * V.width + px;
-        T[q] = p.T_final[V.pix_base + pix];
-        last[q] = p.n_contrib[V.pix_base + pix];
-        g0[q] = gsrc[pix];
-        g1[q] = gsrc[hw + pix];
-        g2[q] = gsrc[2 * hw + pix];
+        S.T[q] = p.T_final[V.pix_base + pix];
+        S.last[q] = p.n_contrib[V.pix_base + pix];
+        S.g0[q] = gsrc[pix];
+        S.g1[q] = gsrc[hw + pix];
+        S.g2[q] = gsrc[2 * hw + pix];
       }
-      tbg[q] = T[q] * (tbl->bg[0] * g0[q] + tbl->bg[1] * g1[q] + tbl->bg[2] * g2[q]);
-      wlast = max(wlast, last[q]);
+      S.tbg[q] = S.T[q] * (tbl->bg[0] * S.g0[q] + tbl->bg[1] * S.g1[q] + tbl->bg[2] * S.g2[q]);
+      wlast = max(wlast, S.last[q]);
     }
-    // the last composited pair over the warp / CTA bounds the reverse walk
+    // the last composited pair over the warp bounds the reverse walk: sorted positions [rg.x, hi)
 #pragma unroll
     for (int o = 16; o; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
-    if (lane == 0) atomicMax(&s_max, wlast);
-    __syncthreads();
-    const u32 end = rg.x + s_max;
-    u32 flush_cnt = 0;   // pairs of the previous batch whose accumulators are still to be flushed
-    for (u32 bend = end;;) {
-      // Thread tid owns row tid of the batch buffers: it flushes the previous batch's pair tid,
-      // clears its accumulator row and stages this batch's pair tid, so one barrier separates
-      // this phase from the processing that reads every row.
-      if ((u32)tid < flush_cnt) flush_pair_grads<K>(s_acc + tid * NS, p.grad2d + (size_t)s_id[tid] * NG);
-      if (bend <= rg.x) break;                  // CTA-uniform
-      const u32 bstart = bend - rg.x > (u32)NT ? bend - NT : rg.x;
-      const u32 cnt = bend - bstart;
-      if ((u32)tid < cnt) {
-        const u32 id = (u32)pairs[bstart + tid];
-        s_id[tid] = id;
-        stage_record<K>(p.records + (size_t)id * rec_floats(K), s_rec + tid * F4, amin);
-      }
-#pragma unroll
-      for (int i = 0; i < NS; ++i) s_acc[tid * NS + i] = 0.f;
-      __syncthreads();
-      // back to front over the pairs the forward recorded as composited by a pixel of this warp,
-      // below the warp's last contributor (the words are read uniformly by the warp)
-      const u32* cplane = p.cmask + (size_t)(tid >> 5) * p.cmask_plane;
-      const u32 hi = min(bend, rg.x + wlast);    // sorted positions [bstart, hi)
-      for (int wk = hi > bstart ? (int)((hi - 1) >> 5) : -1; wk >= (int)(bstart >> 5); --wk) {
+    const u32 lo = rg.x, hi = rg.x + wlast;
+    const u32* cplane = p.cmask + (size_t)quad * p.cmask_plane;
+    const int wk_bot = (int)(lo >> 5);
+    int wk_top = hi > lo ? (int)((hi - 1) >> 5) : wk_bot - 1;   // highest word still to walk
+    while (wk_top >= wk_bot) {   // warp-uniform
+      // collect: lane l reads word wk_top - l; the leading words whose bits add up to at most 32
+      // are taken, and lane s finds the s-th highest of their set bits
+      const int wk = wk_top - lane;
+      u32 m = 0;
+      if (wk >= wk_bot) {
         const u32 w0 = (u32)wk << 5;
-        u32 m = cplane[(u32)wk + tile];
-        if (w0 < bstart) m &= ~0u << (bstart - w0);
+        m = cplane[(u32)wk + tile];
+        if (w0 < lo) m &= ~0u << (lo - w0);
         if (hi - w0 < 32u) m &= (1u << (hi - w0)) - 1u;
-        while (m) {
-        const int bit = 31 - __clz(m);
-        m &= ~(1u << bit);
-        const int j = (int)(w0 + (u32)bit - bstart);
-        const u32 pos = w0 + (u32)bit - rg.x;     // 0-based position in the tile list
-        const float4* r = s_rec + j * F4;
-        const float4 h0 = r[0], h1 = r[1];
+      }
+      const int c = __popc(m);
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int excl = incl - c;
+      const int nw = __popc(__ballot_sync(0xffffffffu, incl <= 32 && wk >= wk_bot));   // >= 1
+      const int total = __shfl_sync(0xffffffffu, incl, nw - 1);
+      int j = 0;   // the word holding slot `lane`: the largest j < nw with excl_j <= lane
+#pragma unroll
+      for (int s = 16; s; s >>= 1) {
+        const int e = __shfl_sync(0xffffffffu, excl, (j + s) & 31);
+        if (j + s < nw && e <= lane) j += s;
+      }
+      const u32 mj = __shfl_sync(0xffffffffu, m, j);
+      const int ej = __shfl_sync(0xffffffffu, excl, j);
+      if (lane < total) {
+        const u32 pos = ((u32)(wk_top - j) << 5) + (u32)nth_high_bit(mj, lane - ej);
+        const u32 id = (u32)pairs[pos];
+        s_id[lane] = id;
+        s_pos[lane] = pos - lo;   // 0-based position in the tile list
+        stage_record<K>(p.records + (size_t)id * rec_floats(K), s_rec + lane * F4, amin);
+      }
+      wk_top -= nw;
+      __syncwarp();
+      for (int sl = 0; sl < total; ++sl) {   // descending positions
+        const float4* r = s_rec + sl * F4;
         const bool fast = reinterpret_cast<const float*>(r)[11] != 0.f;   // the same for every lane
-        const float* fw = reinterpret_cast<const float*>(r + 3);   // 2 pi f2D, then the weights
-        float gv[NVP];
-#pragma unroll
-        for (int i = 0; i < NVP; ++i) gv[i] = 0.f;
-        bool contrib = false;
-        const float dx = __fsub_rn(fpx, h0.x);
-        const float oln2 = h1.z * 0.6931471805599453f;   // opacity ln 2
-        // the per-pixel work, instantiated for records with and without phase reduction
-        auto pixels = [&](auto fast_tag) {
-        float dyq[PPT], pwq[PPT];
-        pixel_powers<PPT>(h0, h1, dx, __fsub_rn(fpy0, h0.y), dyq, pwq);
-        if constexpr (PPT == 2 && K <= GS_BWD_PACKED_MAX_K) {
-          // Both pixels at once.  Envelope, bank and alpha in packed FP32, bit-identical to the
-          // forward's decisions.  A pixel that does not take part gets alpha 0 (its transmittance
-          // and colour sums stay as they are) and dL/dalpha 0 (it adds nothing), and the two
-          // pixels' adjoints are summed before they meet the shared factors: dx is common, and
-          // sums against dy use each pixel's own offset.
-          const bool live0 = pos < last[0] && pwq[0] >= h1.y;
-          const bool live1 = pos < last[1] && pwq[1] >= h1.y;
-          if (!(live0 || live1)) return;
-          float2 thp[K > 0 ? K : 1];
-#pragma unroll
-          for (int i = 0; i < K; ++i) thp[i] = row_phases2(fw[2 * i], fw[2 * i + 1], dx, dyq);
-          const float2 G = make_float2(ex2_approx(pwq[0]), ex2_approx(pwq[1]));
-          float2 cs[K > 0 ? K : 1], sn[K > 0 ? K : 1];
-          float2 bank = f2(h1.w);
-#pragma unroll
-          for (int i = 0; i < K; ++i) {
-            const float2 a = reduced_angle2<decltype(fast_tag)::value>(thp[i]);
-            cs[i] = make_float2(__cosf(a.x), __cosf(a.y));
-            sn[i] = make_float2(__sinf(a.x), __sinf(a.y));
-            bank = __ffma2_rn(f2(fw[2 * K + i]), cs[i], bank);
-          }
-          const float2 araw = __fmul2_rn(__fmul2_rn(f2(h1.z), G), bank);
-          const float ax = fminf(amax, araw.x), ay = fminf(amax, araw.y);
-          const bool pass0 = live0 && ax >= amin, pass1 = live1 && ay >= amin;
-          if (!(pass0 || pass1)) return;
-          contrib = true;
-          const float2 alpha = make_float2(pass0 ? ax : 0.f, pass1 ? ay : 0.f);
-          const float2 oma = __ffma2_rn(alpha, f2(-1.f), f2(1.f));
-          const float2 ioma = make_float2(rcp_approx(oma.x), rcp_approx(oma.y));
-          const float2 Tn = __fmul2_rn(make_float2(T[0], T[1]), ioma);   // transmittance before this pair
-          if (pass0) T[0] = Tn.x;
-          if (pass1) T[1] = Tn.y;
-          const float4 c = r[2];
-          const float2 wgt = __fmul2_rn(alpha, Tn);
-          const float2 G0 = make_float2(g0[0], g0[1]), G1 = make_float2(g1[0], g1[1]), G2 = make_float2(g2[0], g2[1]);
-          float2 A0 = make_float2(acc0[0], acc0[1]), A1 = make_float2(acc1[0], acc1[1]),
-                 A2 = make_float2(acc2[0], acc2[1]);
-          // (c - acc) . dL/dC, then dL/dalpha = T (c - acc) . dL/dC - tbg / (1 - alpha)
-          float2 dcg = __fmul2_rn(__ffma2_rn(A2, f2(-1.f), f2(c.z)), G2);
-          dcg = __ffma2_rn(__ffma2_rn(A1, f2(-1.f), f2(c.y)), G1, dcg);
-          dcg = __ffma2_rn(__ffma2_rn(A0, f2(-1.f), f2(c.x)), G0, dcg);
-          float2 dLda = __ffma2_rn(__fmul2_rn(make_float2(tbg[0], tbg[1]), ioma), f2(-1.f), __fmul2_rn(Tn, dcg));
-          A0 = __ffma2_rn(oma, A0, __fmul2_rn(alpha, f2(c.x)));
-          A1 = __ffma2_rn(oma, A1, __fmul2_rn(alpha, f2(c.y)));
-          A2 = __ffma2_rn(oma, A2, __fmul2_rn(alpha, f2(c.z)));
-          acc0[0] = A0.x; acc0[1] = A0.y;
-          acc1[0] = A1.x; acc1[1] = A1.y;
-          acc2[0] = A2.x; acc2[1] = A2.y;
-          // no gradient through a clamped alpha, none from a pixel that does not take part
-          if (!pass0 || araw.x > amax) dLda.x = 0.f;
-          if (!pass1 || araw.y > amax) dLda.y = 0.f;
-          gv[6] = fmaf(wgt.y, g0[1], wgt.x * g0[0]);
-          gv[7] = fmaf(wgt.y, g1[1], wgt.x * g1[0]);
-          gv[8] = fmaf(wgt.y, g2[1], wgt.x * g2[0]);
-          const float2 dLdG = __fmul2_rn(dLda, G);
-          const float2 dLdbank = __fmul2_rn(dLdG, f2(h1.z));
-          const float2 dLdo = __fmul2_rn(dLdG, bank);
-          // log2-domain power p2: G = 2^p2, dG/dp2 = G ln 2, so dL/dp2 = dLda o bank G ln 2
-          const float2 dLdp2 = __fmul2_rn(dLdo, f2(oln2));
-          const float2 edy = __fmul2_rn(dLdp2, make_float2(dyq[0], dyq[1]));
-          const float P = dLdp2.x + dLdp2.y;               // sum of dL/dp2
-          const float Y = edy.x + edy.y;                   // sum of dL/dp2 dy
-          const float Ex = P * dx;                         // sum of dL/dp2 dx
-          gv[5] = dLdo.x + dLdo.y;                         // d opacity
-          gv[2] = Ex * dx;                                 // w.r.t. A' (converted at flush)
-          gv[3] = Y * dx;                                  // w.r.t. B'
-          gv[4] = fmaf(edy.y, dyq[1], edy.x * dyq[0]);     // w.r.t. C'
-          float gdx = 2.f * h0.z * Ex + h0.w * Y;
-          float gdy = h0.w * Ex + 2.f * h1.x * Y;
-#pragma unroll
-          for (int i = 0; i < K; ++i) {
-            const float wi = fw[2 * K + i];
-            const float2 kc = __fmul2_rn(dLdbank, cs[i]);
-            const float2 ks = __fmul2_rn(dLdbank, sn[i]);
-            gv[9 + 2 * K + i] = kc.x + kc.y;                         // d (cosine weight i)
-            const float gth = -wi * (ks.x + ks.y);                   // d phase (radians), both pixels
-            const float gthdy = -wi * fmaf(ks.y, dyq[1], ks.x * dyq[0]);
-            gv[9 + 2 * i] = gth * dx;                                // w.r.t. 2 pi f2D (scaled at flush)
-            gv[9 + 2 * i + 1] = gthdy;
-            gdx += gth * fw[2 * i];
-            gdy += gth * fw[2 * i + 1];
-          }
-          gv[9 + 3 * K] = dLdbank.x + dLdbank.y;           // d (1 - sum w)
-          gv[0] = -gdx;                                    // d mu = - d (pixel - mu)
-          gv[1] = -gdy;
-        } else {
-          // raw phases of the current row, taken as the forward takes them (two rows: row_phases2)
-          float th[K > 0 ? K : 1], th1[K > 0 ? K : 1];
-#pragma unroll
-          for (int i = 0; i < K; ++i) {
-            if constexpr (PPT == 2) {
-              const float2 t = row_phases2(fw[2 * i], fw[2 * i + 1], dx, dyq);
-              th[i] = t.x;
-              th1[i] = t.y;
-            } else {
-              th[i] = raw_phase(fw[2 * i], fw[2 * i + 1], dx, dyq[0]);
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < PPT; ++q) {
-            if (q > 0)
-#pragma unroll
-              for (int i = 0; i < K; ++i) th[i] = PPT == 2 ? th1[i] : __fadd_rn(th[i], fw[2 * i + 1]);
-            if (pos >= last[q]) continue;
-            const float dy = dyq[q];
-            const float pw = pwq[q];
-            if (pw < h1.y) continue;
-            const float G = ex2_approx(pw);
-            float cs[K > 0 ? K : 1], sn[K > 0 ? K : 1];
-            float bank = h1.w;
-#pragma unroll
-            for (int i = 0; i < K; ++i) {
-              const float ang = reduced_angle<decltype(fast_tag)::value>(th[i]);
-              cs[i] = __cosf(ang);
-              sn[i] = __sinf(ang);
-            }
-#pragma unroll
-            for (int i = 0; i < K; ++i) bank = __fmaf_rn(fw[2 * K + i], cs[i], bank);
-            const float araw = __fmul_rn(__fmul_rn(h1.z, G), bank);
-            const float alpha = fminf(amax, araw);
-            if (alpha < amin) continue;
-            contrib = true;
-            const float oma = 1.f - alpha;
-            const float ioma = rcp_approx(oma);
-            T[q] = T[q] * ioma;                              // transmittance before this pair
-            const float4 c = r[2];
-            const float wgt = alpha * T[q];
-            gv[6] += wgt * g0[q];
-            gv[7] += wgt * g1[q];
-            gv[8] += wgt * g2[q];
-            float dLda = T[q] * ((c.x - acc0[q]) * g0[q] + (c.y - acc1[q]) * g1[q] + (c.z - acc2[q]) * g2[q]) -
-                         tbg[q] * ioma;
-            acc0[q] = alpha * c.x + oma * acc0[q];
-            acc1[q] = alpha * c.y + oma * acc1[q];
-            acc2[q] = alpha * c.z + oma * acc2[q];
-            if (araw > amax) dLda = 0.f;                     // clamped: no gradient through alpha
-            const float dLdG = dLda * G;
-            const float dLdbank = dLdG * h1.z;
-            const float dLdo = dLdG * bank;
-            gv[5] += dLdo;                                   // d opacity
-            // log2-domain power p2: G = 2^p2, dG/dp2 = G ln 2, so dL/dp2 = dLda o bank G ln 2
-            const float dLdp2 = dLdo * oln2;
-            const float ex = dLdp2 * dx, ey = dLdp2 * dy;
-            gv[2] += ex * dx;                                // w.r.t. A' (converted at flush)
-            gv[3] += ex * dy;                                // w.r.t. B'
-            gv[4] += ey * dy;                                // w.r.t. C'
-            float gdx = 2.f * h0.z * ex + h0.w * ey;
-            float gdy = h0.w * ex + 2.f * h1.x * ey;
-#pragma unroll
-            for (int i = 0; i < K; ++i) {
-              const float wi = fw[2 * K + i];
-              gv[9 + 2 * K + i] += dLdbank * cs[i];                  // d (cosine weight i)
-              const float gth = -dLdbank * wi * sn[i];                // d phase (radians)
-              gv[9 + 2 * i] += gth * dx;                              // w.r.t. 2 pi f2D (scaled at flush)
-              gv[9 + 2 * i + 1] += gth * dy;
-              gdx += gth * fw[2 * i];
-              gdy += gth * fw[2 * i + 1];
-            }
-            gv[9 + 3 * K] += dLdbank;                        // d (1 - sum w)
-            gv[0] -= gdx;                                    // d mu = - d (pixel - mu)
-            gv[1] -= gdy;
-          }
-        }
-        };
+        const u32 pos = s_pos[sl];
+        // every walked pair was composited by a pixel of the warp: each lane stores its gradient
+        // values in its column of the transpose buffer (value v in row v), lane v adds up row v
+        // with eight 16-byte loads, and lanes 4i add values 4i .. 4i + 3 to the pair's grad2d row
+        // with one vector reduction
         if (fast)
-          pixels(std::true_type{});
+          pair_adjoint<K, PPT, true>(S, r, pos, fpx, fpy0, amin, amax, s_red + lane);
         else
-          pixels(std::false_type{});
-        if (__ballot_sync(0xffffffffu, contrib)) {
-#if GS_BWD_SMEM_REDUCE
-          // transpose through shared memory: lane l stores value v at row v, column l; lane v
-          // then adds up its row with eight 16-byte loads
-#pragma unroll
-          for (int v = 0; v < NV; ++v) s_red[v * RS + lane] = gv[v];
+          pair_adjoint<K, PPT, false>(S, r, pos, fpx, fpy0, amin, amax, s_red + lane);
+        {
           __syncwarp();
+          float* dst = p.grad2d + (size_t)s_id[sl] * NG;
 #pragma unroll
           for (int g = 0; g < NVP / 32; ++g) {
-            const int v = 32 * g + lane;
-            if (v < NV) {
-              const float4* row = reinterpret_cast<const float4*>(s_red + v * RS);
+            const int vv = 32 * g + lane;
+            float sum = 0.f;
+            if (vv < NV) {
+              const float4* row = reinterpret_cast<const float4*>(s_red + vv * BWD_RS);
               const float4 a = row[0];
-              float2 lo = make_float2(a.x, a.y), hi = make_float2(a.z, a.w);   // packed column sums
+              float2 l2 = make_float2(a.x, a.y), h2 = make_float2(a.z, a.w);   // packed column sums
 #pragma unroll
-              for (int c = 1; c < 8; ++c) {
-                const float4 t = row[c];
-                lo = __fadd2_rn(lo, make_float2(t.x, t.y));
-                hi = __fadd2_rn(hi, make_float2(t.z, t.w));
+              for (int cc = 1; cc < 8; ++cc) {
+                const float4 t = row[cc];
+                l2 = __fadd2_rn(l2, make_float2(t.x, t.y));
+                h2 = __fadd2_rn(h2, make_float2(t.z, t.w));
               }
-              atomicAdd(&s_acc[j * NS + v], (lo.x + lo.y) + (hi.x + hi.y));
+              sum = ((l2.x + l2.y) + (h2.x + h2.y)) * conv[g];
             }
+            const float s1 = __shfl_down_sync(0xffffffffu, sum, 1);
+            const float s2 = __shfl_down_sync(0xffffffffu, sum, 2);
+            const float s3 = __shfl_down_sync(0xffffffffu, sum, 3);
+            if ((lane & 3) == 0 && vv < NG && (sum != 0.f || s1 != 0.f || s2 != 0.f || s3 != 0.f))
+              asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + vv), "f"(sum), "f"(s1),
+                           "f"(s2), "f"(s3)
+                           : "memory");
           }
           __syncwarp();
-#else
-#pragma unroll
-          for (int g = 0; g < NVP / 32; ++g) {
-            float part[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) part[i] = gv[32 * g + i];
-            const float red = warp_reduce_scatter(part, lane);
-            if (32 * g + lane < NV) atomicAdd(&s_acc[j * NS + 32 * g + lane], red);
-          }
-#endif
-        }
         }
       }
-      __syncthreads();
-      flush_cnt = cnt;
-      bend = bstart;
+      __syncwarp();   // every lane is done with the staged rows before the next collection
     }
-    __syncthreads();
-    if (z.quota) {   // this tile's share of the zero-fill, issued behind its walk
-      if (tid == 0) s_zc = atomicAdd(&hdr->zero_counter, z.quota);
-      __syncthreads();
-      zero_chunks(z, s_zc, z.quota);
+    if (z.quota) {   // this task's share of the zero-fill, issued behind its walk
+      u32 c0 = 0;
+      if (lane == 0) c0 = atomicAdd(&hdr->zero_counter, z.quota);
+      zero_chunks_warp(z, __shfl_sync(0xffffffffu, c0, 0), z.quota, lane);
     }
   }
-  // the tile queue is empty: the chunks still unclaimed
+  // the task queue is empty: the chunks still unclaimed
   if (z.quota) {
     for (;;) {
-      __syncthreads();   // every thread has read s_tile / s_zc of the previous round
-      if (tid == 0) s_zc = atomicAdd(&hdr->zero_counter, z.quota);
-      __syncthreads();
-      const u32 c0 = s_zc;
-      if (c0 >= z.base[ZERO_ARRAYS]) break;   // CTA-uniform
-      zero_chunks(z, c0, z.quota);
+      u32 c0 = 0;
+      if (lane == 0) c0 = atomicAdd(&hdr->zero_counter, z.quota);
+      c0 = __shfl_sync(0xffffffffu, c0, 0);
+      if (c0 >= z.base[ZERO_ARRAYS]) break;   // warp-uniform
+      zero_chunks_warp(z, c0, z.quota, lane);
     }
   }
-  if (tid == 0) release_tile_counter(&hdr->tile_counter_bwd, &hdr->bwd_exits, &hdr->zero_counter);
+  __syncthreads();   // every warp of the CTA has left its task loop
+  if (threadIdx.x == 0) release_tile_counter(&hdr->tile_counter_bwd, &hdr->bwd_exits, &hdr->zero_counter);
 }
 
 template <int K, bool FMAP, bool MASKS, bool STATS>
@@ -1092,25 +1081,29 @@ static cudaError_t launch_bwd_t(const FrameTable& tbl, const WsPtrs& p, const fl
                                 const Launch& L) {
   constexpr int PPT = GS_PPT_BWD, NT = BLOCK / PPT;
   static int grid = 0;
-  const size_t smem = (size_t)NT * SRec<K>::F * sizeof(float) + (size_t)NT * ((10 + 3 * K) | 1) * sizeof(float) +
-                      (size_t)NT * sizeof(u32) +
-                      (GS_BWD_SMEM_REDUCE ? (size_t)(NT / 32) * ((10 + 3 * K) * 36 + 4) * sizeof(float) : 0);
+  constexpr int NW = NT / 32;
+  const size_t smem = (size_t)NW * (32 * SRec<K>::F * sizeof(float) + 64 * sizeof(u32) +
+                                    ((10 + 3 * K) * 36 + 4) * sizeof(float));
   if (!grid) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_render_bwd<K, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_render_bwd_w<K, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<K, PPT>, NT, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd_w<K, PPT>, NT, smem) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     grid = per_sm * L.sm_count;
   }
   int g = grid;
-  if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
+  if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;   // one task per warp footprint: NW per tile
   if (g < 1) g = 1;
-  ZeroJob none{};
+  ZeroJob zw{};
+  if (z) {   // the fill's chunks per tile spread over the tile's warp tasks
+    zw = *z;
+    if (zw.quota) zw.quota = (zw.quota + BWD_WARPS_PER_TILE - 1) / BWD_WARPS_PER_TILE;
+  }
   launch_pdl<PDL_RENDER>(k_zero_grad2d<K>, L.sm_count * 2, 256, 0, L.stream, p);
-  launch_pdl<PDL_RENDER>(k_render_bwd<K, PPT>, g, NT, smem, L.stream, p, dL, z ? *z : none);
+  launch_pdl<PDL_RENDER>(k_render_bwd_w<K, PPT>, g, NT, smem, L.stream, p, dL, zw);
   return cudaGetLastError();
 }
 
