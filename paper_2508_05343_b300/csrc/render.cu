@@ -1,10 +1,10 @@
 // Per-tile compositing of the 2D Gabor primitives (Sec. 3.3.2 Eq. 9, Sec. 3.3.3 Eq. 10) and its
-// reverse-order adjoint.  Forward: one CTA owns a 16x16 tile and pulls tiles from an atomic
-// counter, longest pair lists first, staging the tile's depth-sorted pairs into shared memory one
-// batch per CTA pass.  Backward: each warp pulls one 8x8 footprint of a tile at a time and walks,
-// back to front, only the pairs the forward recorded as composited there.  Envelope, bank and
-// alpha are evaluated with explicit rounding intrinsics in both, so the backward reproduces the
-// forward's decisions exactly.
+// reverse-order adjoint.  Both kernels run independent warps: a warp pulls one 8x8 footprint of a
+// 16x16 tile at a time from an atomic counter (tiles with the longest pair lists first) and stages
+// pair records into its own shared-memory rows.  The forward walks the tile's depth-sorted pairs
+// front to back until its pixels saturate; the backward walks, back to front, only the pairs the
+// forward recorded as composited in that footprint.  Envelope, bank and alpha are evaluated with
+// explicit rounding intrinsics in both, so the backward reproduces the forward's decisions exactly.
 #include <type_traits>
 
 #include "common.cuh"
@@ -50,57 +50,6 @@ __device__ __forceinline__ void stage_record(const float* __restrict__ rec, floa
   }
 }
 
-// The same transform applied in place to a record that a bulk copy left in shared memory.
-template <int K>
-__device__ __forceinline__ void stage_in_place(float4* r, float alpha_min) {
-  const float4 h0 = r[0], h1 = r[1];
-  const float o = h1.y;
-  r[0] = make_float4(h0.x, h0.y, -0.5f * LOG2E * h0.z, -LOG2E * h0.w);
-  r[1] = make_float4(-0.5f * LOG2E * h1.x, o > 0.f ? log2f(alpha_min / o) : 3.0e38f, o, h1.z);
-#pragma unroll
-  for (int i = 0; i < SRec<K>::F4 - 3; ++i) {
-    float4 t = r[3 + i];
-    if (4 * i + 0 < 2 * K) t.x = __fmul_rn(TWO_PI, t.x);
-    if (4 * i + 1 < 2 * K) t.y = __fmul_rn(TWO_PI, t.y);
-    if (4 * i + 2 < 2 * K) t.z = __fmul_rn(TWO_PI, t.z);
-    if (4 * i + 3 < 2 * K) t.w = __fmul_rn(TWO_PI, t.w);
-    r[3 + i] = t;
-  }
-}
-
-// Bulk (TMA engine) copies of record rows into shared memory, completion counted on an mbarrier.
-__device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(u64* m, u32 count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(u64* m) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(m)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(u64* m, u32 bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, u32 bytes, u64* m) {
-  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(m))
-               : "memory");
-}
-// Wait for the phase of parity `parity` of m to complete; false after SPIN_LIMIT_NS (or the poll limit).
-__device__ __forceinline__ bool mbar_wait(u64* m, u32 parity) {
-  const u32 a = smem_u32(m);
-  u32 polls = 0;
-  const u64 t0 = global_timer_ns();
-  for (;;) {
-    u32 ok;
-    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                 : "=r"(ok)
-                 : "r"(a), "r"(parity)
-                 : "memory");
-    if (ok) return true;
-    if (++polls > SPIN_LIMIT_POLLS || ((polls & 1023u) == 0 && global_timer_ns() - t0 > SPIN_LIMIT_NS)) return false;
-  }
-}
-
 // Frequency features of one record: sum_i w_i |f2D_i|, sum_i w_i |f2D_i,x|, sum_i w_i |f2D_i,y|.
 template <int K>
 __device__ __forceinline__ float4 frequency_features(const float* __restrict__ rec) {
@@ -108,20 +57,6 @@ __device__ __forceinline__ float4 frequency_features(const float* __restrict__ r
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     const float fx = __ldg(rec + 12 + 2 * i), fy = __ldg(rec + 13 + 2 * i), w = __ldg(rec + 12 + 2 * K + i);
-    m = fmaf(w, sqrtf(fx * fx + fy * fy), m);
-    mx = fmaf(w, fabsf(fx), mx);
-    my = fmaf(w, fabsf(fy), my);
-  }
-  return make_float4(m, mx, my, 0.f);
-}
-
-// frequency_features of a raw record already in shared memory
-template <int K>
-__device__ __forceinline__ float4 frequency_features_smem(const float* rec) {
-  float m = 0.f, mx = 0.f, my = 0.f;
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    const float fx = rec[12 + 2 * i], fy = rec[13 + 2 * i], w = rec[12 + 2 * K + i];
     m = fmaf(w, sqrtf(fx * fx + fy * fy), m);
     mx = fmaf(w, fabsf(fx), mx);
     my = fmaf(w, fabsf(fy), my);
@@ -233,33 +168,17 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 #ifndef GS_WARP_SQUARE
 #define GS_WARP_SQUARE 1
 #endif
-// GS_FWD_BULK=1: the forward stages each batch of records with bulk copies (cp.async.bulk of each
-// 96-byte row on an mbarrier) into one of two buffers, issued one batch ahead, instead of loading
-// them through registers.  Measured at 1.5M primitives, 1600x1064: 0.617 against 0.572 ms for the
-// register gather (128 small copies per batch, the in-place transform and the barrier traffic cost
-// more than the latency they hide at 8 resident CTAs per SM), so it is off by default.
-#ifndef GS_FWD_BULK
-#define GS_FWD_BULK 0
-#endif
-// GS_FWD_WORD_BITS=1: the forward combines the lanes' composited-pair bits once per 32 sorted
-// positions (__reduce_or_sync) and tests for an all-done warp there, instead of a vote and a
-// ballot per pair.
-#ifndef GS_FWD_WORD_BITS
-#define GS_FWD_WORD_BITS 1
-#endif
-// Records a forward thread stages per batch (a batch holds GS_FWD_BATCH_RECS x threads pairs).
-#ifndef GS_FWD_BATCH_RECS
-#define GS_FWD_BATCH_RECS 1
-#endif
 
 // Resident CTAs per SM the compositing kernels are compiled for (0: the compiler's choice).  At
 // K = 4 the backward's warp walk with the two-pixel packed adjoint takes 95 registers (5 CTAs of
 // 128 threads per SM) on its own; held to 72 for 7 CTAs per SM it spills 24 bytes and runs 2%
 // faster (0.750 against 0.767 ms at 1.5M primitives, 1600x1064; 6 CTAs: 0.760).  The packed
 // adjoint holds both pixels' cosines and sines, so above GS_BWD_PACKED_MAX_K components it would
-// spill heavily under such a cap: those K keep the per-pixel adjoint at 4 CTAs per SM.
+// spill heavily under such a cap: those K keep the per-pixel adjoint at 4 CTAs per SM.  The
+// forward's training variant, left to itself, takes 48 registers with a 16-byte spill; at 9 CTAs
+// per SM (56 registers, no spill) it is 0.7% faster.
 #ifndef GS_FWD_MIN_CTAS
-#define GS_FWD_MIN_CTAS 0
+#define GS_FWD_MIN_CTAS 9
 #endif
 #ifndef GS_BWD_MIN_CTAS
 #define GS_BWD_MIN_CTAS 7
@@ -301,6 +220,12 @@ __device__ __forceinline__ int2 thread_pixel(int tx, int ty, int tid) {
 #endif
 }
 
+// The forward with independent warps.  A task is one warp footprint (8x8 pixels at PPT = 2) of one
+// tile, tiles in the order of tile_order (longest pair lists first).  A warp stages the tile's
+// pairs into its own shared-memory rows one 32-position word of the sorted list at a time (the
+// unit of the composited-pair bits), composites them, and stops once every pixel of its footprint
+// is saturated; no CTA barrier sits on the walk, so a warp that is done moves on to its next task
+// instead of waiting for the others of its CTA.
 // FMAP: composite the frequency features of each primitive (sum_i w_i |f2D_i|, sum_i w_i |f2D_i,x|,
 // sum_i w_i |f2D_i,y|, cycles per pixel) in place of its colour, with no background.
 // MASKS: record per warp which pairs its pixels composited (for the backward pass); forward-only
@@ -308,75 +233,33 @@ __device__ __forceinline__ int2 thread_pixel(int tx, int ty, int tid) {
 // STATS: also write the per-pixel work counters (pairs evaluated, reached and composited), which
 // only the work accounting and the tests read.
 template <int K, int PPT, bool FMAP, bool MASKS, bool STATS>
-__global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
-                                                            float* out_T) {
+__global__ void GS_FWD_BOUNDS k_render_fwd_w(WsPtrs p, float* out_rgb, float* out_T) {
   pdl_begin();
-  constexpr int NT = BLOCK / PPT;
-  constexpr int NB = NT * GS_FWD_BATCH_RECS;   // pairs per staged batch
+  constexpr int NW = BLOCK / PPT / 32;   // warps per CTA, and warp footprints per tile
   constexpr int F4 = SRec<K>::F4;
-  static_assert(!GS_FWD_BULK || GS_FWD_BATCH_RECS == 1, "the bulk-copy staging moves one record per thread");
-#if GS_FWD_BULK
-  extern __shared__ __align__(16) float4 s_buf[];   // [2][NT][F4]: batch k in buffer k & 1
-  __shared__ __align__(8) u64 s_full[2];             // completion of each buffer's bulk copies
-  __shared__ int s_abort;
-#else
-  extern __shared__ __align__(16) float4 s_rec[];   // [NB][F4]
-#endif
-  __shared__ u32 s_tile;
+  extern __shared__ __align__(16) float4 smem4[];
+  const int lane = threadIdx.x & 31;
+  float4* s_rec = smem4 + (threadIdx.x >> 5) * 32 * F4;   // [32][F4] this warp's staged records
   WsHeader* hdr = p.hdr;
   if (read_status(hdr) != 0) return;
   if (MASKS && blockIdx.x == 0 && threadIdx.x == 0) hdr->masks_epoch = hdr->epoch;   // bits of this frame
   const FrameTable* tbl = p.tbl;
   // sorted pairs tile << 32 | depth rank; the rank is the record (and grad2d) row
   const u64* __restrict__ pairs = (tbl->tpasses_needed & 1) ? p.keys1 : p.keys0;
-  const int tid = threadIdx.x;
   const u32 ntiles = tbl->total_tiles;
   const float amax = tbl->alpha_max, amin = tbl->alpha_min, Tmin = tbl->T_min;
-#if GS_FWD_BULK
-  constexpr u32 REC_BYTES = (u32)rec_floats(K) * 4u;   // a multiple of 16, rows 16-byte aligned
-  static_assert(REC_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
-  if (tid == 0) {
-    mbar_init(&s_full[0], NT);
-    mbar_init(&s_full[1], NT);
-    s_abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  u32 parity = 0;   // bit b: parity of buffer b's next phase (the same in every thread)
-  // every thread arrives on the buffer's barrier; a thread with a pair copies its record row
-  auto issue = [&](u32 first, u32 end, int b) {
-    const u32 idx = first + tid;
-    u64* m = &s_full[b];
-    if (idx < end) {
-      mbar_arrive_tx(m, REC_BYTES);
-      bulk_g2s(s_buf + ((size_t)b * NT + tid) * F4, p.records + (size_t)(u32)pairs[idx] * rec_floats(K), REC_BYTES, m);
-    } else {
-      mbar_arrive(m);
-    }
-  };
-  auto wait_buf = [&](int b) {
-    const u32 ph = (parity >> b) & 1u;
-    if (!mbar_wait(&s_full[b], ph)) {
-      set_status(hdr, GS_ERR_TIMEOUT);
-      s_abort = 1;
-      mbar_wait(&s_full[b], ph);   // once more (bounded) for the copies still in flight
-    }
-    parity ^= 1u << b;
-  };
-#endif
   for (;;) {
-    if (tid == 0) {   // tiles in the order of tile_order: longest pair lists first
-      const u32 slot = atomicAdd(&hdr->tile_counter_fwd, 1u);
-      s_tile = slot < ntiles ? p.tile_order[slot] : 0xFFFFFFFFu;
-    }
-    __syncthreads();
-    const u32 tile = s_tile;
-    if (tile >= ntiles) break;
+    u32 slot = 0;
+    if (lane == 0) slot = atomicAdd(&hdr->tile_counter_fwd, 1u);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot >= ntiles * (u32)NW) break;   // warp-uniform
+    const u32 tile = p.tile_order[slot / NW];
+    const int quad = (int)(slot % NW);
     const int v = view_of_tile(tbl, tile);
     const ViewDesc& V = tbl->v[v];
     const u32 local = tile - V.tile_base;
     const int tx = (int)(local % (u32)V.tiles_x), ty = (int)(local / (u32)V.tiles_x);
-    const int2 pxy = thread_pixel<PPT>(tx, ty, tid);
+    const int2 pxy = thread_pixel<PPT>(tx, ty, quad * 32 + lane);
     const int px = pxy.x, py0 = pxy.y;
     const uint2 rg = p.ranges[tile];
     const float fpx = (float)px + 0.5f, fpy0 = (float)py0 + 0.5f;
@@ -391,65 +274,21 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
       done[q] = !(px < V.width && py0 + q < V.height);
       tdone = tdone && done[q];
     }
-    // composited-pair bits of this warp (warp-uniform), one word per 32 sorted positions, for the
-    // backward pass to skip the pairs no pixel of the warp composited
-    u32* cplane = p.cmask + (size_t)(tid >> 5) * p.cmask_plane;
-    u32 cword = 0, cword_idx = 0xffffffffu, lbits = 0;
-    constexpr bool masks = MASKS;
-#if GS_FWD_BULK
-    int kb = 0;                  // buffer of the batch at `start`
-    bool pending = rg.y > rg.x;  // a batch has been issued and not yet waited for
-    if (pending) issue(rg.x, rg.y, 0);
-#endif
-    for (u32 start = rg.x; start < rg.y; start += NB) {
-      if (__syncthreads_count(tdone) == NT) break;
-#if GS_FWD_BULK
-      // batch k arrived: each thread finishes staging its own row in place; then batch k + 1 goes
-      // into the other buffer (which held batch k - 1, finished by every warp before the barrier
-      // above) while batch k is composited
-      wait_buf(kb);
-      pending = false;
-      float4* s_rec = s_buf + (size_t)kb * NT * F4;
-      if (start + tid < rg.y) {
-        if (FMAP) {
-          const float4 ff = frequency_features_smem<K>(reinterpret_cast<const float*>(s_rec + tid * F4));
-          stage_in_place<K>(s_rec + tid * F4, amin);
-          s_rec[tid * F4 + 2] = ff;
-        } else {
-          stage_in_place<K>(s_rec + tid * F4, amin);
-        }
+    // composited-pair bits of this footprint, one word per 32 sorted positions (each tile owns
+    // whole words), for the backward pass to skip the pairs no pixel of the warp composited
+    u32* cplane = p.cmask + (size_t)quad * p.cmask_plane;
+    for (u32 start = rg.x; start < rg.y && !__all_sync(0xffffffffu, tdone);) {
+      const u32 end = min(rg.y, (start | 31u) + 1u);   // the rest of start's word
+      const int cnt = (int)(end - start);
+      if (lane < cnt) {
+        const float* rec = p.records + (size_t)(u32)pairs[start + (u32)lane] * rec_floats(K);
+        stage_record<K>(rec, s_rec + lane * F4, amin);
+        if (FMAP) s_rec[lane * F4 + 2] = frequency_features<K>(rec);
       }
-      __syncthreads();
-      if (s_abort) return;       // a copy did not complete in time (status set); the other buffer is idle
-      if (start + NT < rg.y) {
-        issue(start + NT, rg.y, kb ^ 1);
-        pending = true;
-      }
-      kb ^= 1;
-#else
-#pragma unroll
-      for (int rr = 0; rr < GS_FWD_BATCH_RECS; ++rr) {
-        const int slot = tid + rr * NT;
-        const u32 idx = start + (u32)slot;
-        if (idx < rg.y) {
-          const float* rec = p.records + (size_t)(u32)pairs[idx] * rec_floats(K);
-          stage_record<K>(rec, s_rec + slot * F4, amin);
-          if (FMAP) s_rec[slot * F4 + 2] = frequency_features<K>(rec);
-        }
-      }
-      __syncthreads();
-#endif
-      const int cnt = (int)min((u32)NB, rg.y - start);
+      __syncwarp();
+      u32 lbits = 0;
       for (int j = 0; j < cnt; ++j) {
-#if GS_FWD_WORD_BITS
-        if (!masks && tdone) break;   // with the bits the loop is warp-uniform up to a word's end
-#else
-        if (masks) {
-          if (!__any_sync(0xffffffffu, !tdone)) break;   // warp-uniform: the ballot below needs every lane
-        } else if (tdone) {
-          break;
-        }
-#endif
+        if (!MASKS && tdone) break;   // with the bits every lane walks the word to its end
         const float4* r = s_rec + j * F4;
         const float4 h0 = r[0], h1 = r[1];
         const bool fast = reinterpret_cast<const float*>(r)[11] != 0.f;   // the same for every lane
@@ -553,45 +392,15 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
         tdone = true;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) tdone = tdone && done[q];
-        if (masks) {
-          const u32 gpos = start + (u32)j;
-#if GS_FWD_WORD_BITS
-          // each lane keeps its own bits of the current word; the warp's word is their OR, taken
-          // at the word's last position or the batch's last pair (warp-uniform), where the warp
-          // also stops once every lane is done
-          if (comp) lbits |= 1u << (gpos & 31);
-          if ((gpos & 31u) == 31u || j + 1 == cnt) {
-            cword |= __reduce_or_sync(0xffffffffu, lbits);
-            lbits = 0;
-            cword_idx = (gpos >> 5) + tile;   // each tile owns whole words
-            if ((gpos & 31u) == 31u) {
-              if ((tid & 31) == 0) cplane[cword_idx] = cword;
-              cword = 0;
-              cword_idx = 0xffffffffu;
-            }
-            if (__all_sync(0xffffffffu, tdone)) break;
-          }
-#else
-          const u32 b = __ballot_sync(0xffffffffu, comp);
-          const u32 wi = (gpos >> 5) + tile;             // each tile owns whole words
-          if (wi != cword_idx) {
-            if (cword_idx != 0xffffffffu && (tid & 31) == 0) cplane[cword_idx] = cword;
-            cword_idx = wi;
-            cword = 0;
-          }
-          if (b) cword |= 1u << (gpos & 31);
-#endif
-        }
+        if (MASKS && comp) lbits |= 1u << ((start + (u32)j) & 31u);
       }
+      if (MASKS) {
+        const u32 cw = __reduce_or_sync(0xffffffffu, lbits);
+        if (lane == 0) cplane[(start >> 5) + tile] = cw;
+      }
+      __syncwarp();   // every lane is done with the staged rows before the next word is staged
+      start = end;
     }
-#if GS_FWD_BULK
-    if (pending) {   // the batch issued before the loop stopped early: its copies land before reuse
-      wait_buf(kb);
-      __syncthreads();
-      if (s_abort) return;
-    }
-#endif
-    if (masks && cword_idx != 0xffffffffu && (tid & 31) == 0) cplane[cword_idx] = cword;
     float* orgb = out_rgb ? out_rgb : V.out_rgb;
     float* oT = out_rgb ? out_T : V.out_T;
     const size_t hw = (size_t)V.width * V.height;
@@ -615,9 +424,9 @@ __global__ void GS_FWD_BOUNDS k_render_fwd(WsPtrs p, float* out_rgb,
         }
       }
     }
-    __syncthreads();
   }
-  if (tid == 0) release_tile_counter(&hdr->tile_counter_fwd, &hdr->fwd_exits);
+  __syncthreads();   // every warp of the CTA has left its task loop
+  if (threadIdx.x == 0) release_tile_counter(&hdr->tile_counter_fwd, &hdr->fwd_exits);
 }
 
 // Per-thread pixel state of the reverse walk (PPT vertically adjacent pixels).
@@ -1046,21 +855,19 @@ static cudaError_t launch_fwd_t(const FrameTable& tbl, const WsPtrs& p, float* r
                                 const Launch& L) {
   constexpr int PPT = GS_PPT_FWD, NT = BLOCK / PPT;
   static int grid = 0;
-  const size_t smem = (GS_FWD_BULK ? 2 : GS_FWD_BATCH_RECS) * (size_t)NT * SRec<K>::F * sizeof(float);
+  const size_t smem = (size_t)NT * SRec<K>::F * sizeof(float);   // 32 rows per warp
+  auto kern = k_render_fwd_w<K, PPT, FMAP, MASKS, STATS>;
   if (!grid) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_render_fwd<K, PPT, FMAP, MASKS, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd<K, PPT, FMAP, MASKS, STATS>, NT, smem) != cudaSuccess ||
-        per_sm < 1)
-      per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     grid = per_sm * L.sm_count;
   }
   int g = grid;
-  if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;
+  if ((u32)g > tbl.launch_tiles) g = (int)tbl.launch_tiles;   // one task per warp footprint: NT / 32 per tile
   if (g < 1) g = 1;
-  launch_pdl<PDL_RENDER>(k_render_fwd<K, PPT, FMAP, MASKS, STATS>, g, NT, smem, L.stream, p, rgb, T);
+  launch_pdl<PDL_RENDER>(kern, g, NT, smem, L.stream, p, rgb, T);
   return cudaGetLastError();
 }
 
