@@ -138,11 +138,9 @@ typedef struct {
  * rank r = 0 .. n_active - 1 (camera depth ascending, ties by primitive index), and order[r] is the
  * primitive of rank r.  records: [n_active][record_floats], row r for the primitive of rank r, the
  * projected 2D primitive laid out as
- *   {mu_x, mu_y, conic_a, conic_b, conic_c, opacity, 1 - sum w, depth, r, g, b, fast,
+ *   {mu_x, mu_y, conic_a, conic_b, conic_c, opacity, 1 - sum w, depth, r, g, b, 0,
  *    f2D_0x, f2D_0y, ..., f2D_(K-1)y, w_0 .. w_(K-1), 0 padding to a multiple of 4}
- * where the 2D Gaussian is exp(-(a dx^2 + c dy^2)/2 - b dx dy) and fast is 1.0 when every
- * |f2D_i . d| over the pixels of the primitive's tile rectangle is at most 2 cycles (the compositing
- * kernels then take the cosine of the phase without range reduction), else 0.0.
+ * where the 2D Gaussian is exp(-(a dx^2 + c dy^2)/2 - b dx dy) and f2D is in cycles per pixel.
  * touched [n] uint32 kept tiles per primitive (by primitive index); offsets [n_active] uint32 first
  * pair position of each rank; keys [pairs] uint64 = tile << 32 | depth rank (sorted: by tile, then
  * rank, so each tile's pairs are in depth order; unsorted: emission order); ranges [tiles][2] uint32

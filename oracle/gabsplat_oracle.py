@@ -485,6 +485,8 @@ def binning_differences(prims_np: dict, cam, cfg, spec=None) -> dict:
 # computed by flipping that decision (flip_allowance).
 U32 = 2.0 ** -24          # float32 unit roundoff
 COS_ERR = 2e-6            # absolute error of the single-precision cosine at |angle| <= 4 pi
+PHASE_BLOCK = 8           # pixels per side of the blocks that share a range-reduction decision
+FAST_PHASE_CYCLES = 2.0   # a block whose |f2D . (x - mu)| stays within this takes no range reduction
 F2D_ROUNDINGS = 8         # roundings charged to each float32 entry behind f2D (see f2d_rounding_bound)
 EVAL_SAFETY = 2.0         # factor over the first-order bounds below
 
@@ -545,6 +547,31 @@ def gabor_alpha(px, py, rec, cfg):
     return rec["opacity"][None, :] * G * bank
 
 
+def phase_rounding_bound(px, py, mu2d, f2d):
+    """[P, L, K] bound on the float32 rounding error (radians) of the Gabor phase 2 pi f2D . (x - mu)
+    at pixels (px, py) for pairs with projected means mu2d [L, 2] and frequencies f2d [L, K, 2].
+
+    The float32 evaluation takes d = x - mu (one rounding per axis), F = 2 pi f2D (one rounding of a
+    product with a float32 2 pi) and F_x d_x + F_y d_y by a product and a fused sum.  With
+    |phase| = 2 pi (|f2D_x d_x| + |f2D_y d_y|) that is at most u |phase| for d, 1.5 u |phase| for F,
+    u |phase| for the product and u |phase| for the sum: 5 u |phase| charged.  A pixel of a block
+    (PHASE_BLOCK x PHASE_BLOCK pixels, aligned to the tiles) where some component's |f2D . (x - mu)|
+    can exceed FAST_PHASE_CYCLES reduces the phase by whole cycles before the cosine: the product
+    with a float32 1 / (2 pi) and the final scaling by 2 pi charge another 2 u |phase| + 2 pi u.  It
+    is charged wherever the float64 test is within 1e-4 cycles of the threshold or above."""
+    fx, fy = f2d[None, :, :, 0].abs(), f2d[None, :, :, 1].abs()
+    dx, dy = (px[:, None] - mu2d[None, :, 0]).abs(), (py[:, None] - mu2d[None, :, 1]).abs()   # [P, L]
+    ph = 2.0 * math.pi * (dx[..., None] * fx + dy[..., None] * fy)
+    x0 = PHASE_BLOCK * torch.floor(px / PHASE_BLOCK) + 0.5      # the block's first and last pixel centres
+    y0 = PHASE_BLOCK * torch.floor(py / PHASE_BLOCK) + 0.5
+    x1, y1 = x0 + (PHASE_BLOCK - 1), y0 + (PHASE_BLOCK - 1)
+    ax = torch.maximum((x0[:, None] - mu2d[None, :, 0]).abs(), (x1[:, None] - mu2d[None, :, 0]).abs())
+    ay = torch.maximum((y0[:, None] - mu2d[None, :, 1]).abs(), (y1[:, None] - mu2d[None, :, 1]).abs())
+    reach = (ax[..., None] * fx + ay[..., None] * fy).amax(-1, keepdim=True)   # cycles, [P, L, 1]
+    slow = reach > FAST_PHASE_CYCLES - 1e-4
+    return 5 * U32 * ph + torch.where(slow, 2 * U32 * ph + 2 * math.pi * U32, torch.zeros_like(ph))
+
+
 def alpha_window(px, py, rec, cfg, alpha_raw, rounded=None):
     """[lo, hi] holding both this float64 alpha_raw and every float32 evaluation of it.
 
@@ -553,8 +580,9 @@ def alpha_window(px, py, rec, cfg, alpha_raw, rounded=None):
     rounded projection, with e the first-order rounding bound of: the envelope exponent
     (8 u per term of 1/2 d^T Q d, and 2^-19 for the exponential); each bank component
     (COS_ERR + the phase error of a float32 f2D, 2 pi (|df2D_x| |dx| + |df2D_y| |dy|) with df2D from
-    f2d_rounding_bound, + 4 u |phase| for rounding the phase; the cosine weight's own error in the
-    z-attenuation variant); and the products (4 u)."""
+    f2d_rounding_bound, + the roundings of the phase itself; the cosine weight's own error in the
+    z-attenuation variant); and the products (4 u).  The phase's own roundings are
+    phase_rounding_bound's."""
     with torch.no_grad():
         src = rec if rounded is None else dict(rec, mu2d=rounded["mu2d"], conic=rounded["conic"])
         alt = alpha_raw if rounded is None else gabor_alpha(px, py, src, cfg)
@@ -567,8 +595,7 @@ def alpha_window(px, py, rec, cfg, alpha_raw, rounded=None):
         w = rec["cos_weights"]
         if w.shape[1] > 0:
             f = rec["f2d"]
-            ph = 2.0 * math.pi * ((dx[..., None] * f[None, :, :, 0]).abs() + (dy[..., None] * f[None, :, :, 1]).abs())
-            err = COS_ERR + 4 * U32 * ph
+            err = COS_ERR + phase_rounding_bound(px, py, src["mu2d"], f)
             if rounded is not None and "f2d_err" in rounded:
                 fe = rounded["f2d_err"]
                 err = err + 2.0 * math.pi * (dx.abs()[..., None] * fe[None, :, :, 0] + dy.abs()[..., None] * fe[None, :, :, 1])

@@ -40,11 +40,6 @@ constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int DPASSES = 4;     // depth-sort passes launched (depth keys have at most 32 bits)
 constexpr int MAX_PASSES = 8;  // digit-pass slots: 0..3 depth sort, 4..7 tile sort
 constexpr int CMASK_PLANES = 8;
-// A primitive whose Gabor phases f2D_i . d stay within this many cycles over its tile rectangle is
-// marked in its record (slot 11); the compositing kernels then take cos / sin of the phase without
-// range reduction (the hardware approximation's error grows with the argument: measured on the
-// B300, about 4e-7 within half a cycle and 1.3e-6 within 2 cycles).
-constexpr float FAST_PHASE_CYCLES = 2.0f;   // warps of a compositing CTA (one pixel per thread at most 8 warps)
 
 // Number of floats of a projected 2D record and of a per-primitive 2D gradient row.
 __host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }

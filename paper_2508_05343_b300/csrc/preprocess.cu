@@ -378,7 +378,7 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, u32 ro
   float rec[rec_floats(K)];
   rec[0] = b.mux; rec[1] = b.muy; rec[2] = ca; rec[3] = cb;
   rec[4] = cc; rec[5] = op; rec[7] = b.tz;
-  rec[8] = fmaxf(rgb[0], 0.f); rec[9] = fmaxf(rgb[1], 0.f); rec[10] = fmaxf(rgb[2], 0.f); rec[11] = 0.f;
+  rec[8] = fmaxf(rgb[0], 0.f); rec[9] = fmaxf(rgb[1], 0.f); rec[10] = fmaxf(rgb[2], 0.f); rec[11] = 0.f;   // slot 11 unused
   float wsum = 0.f;
   if (K > 0) {
     // A^-1 b with A the undilated 2D block and b the xz / yz column of the ray-space covariance
@@ -418,14 +418,6 @@ __device__ __forceinline__ void record_one(const FrameTable* tbl, u32 gi, u32 ro
     }
 #pragma unroll
     for (int i = 12 + 3 * K; i < rec_floats(K); ++i) rec[i] = 0.f;
-    // rec[11]: 1 if |f2D_i . d| <= FAST_PHASE_CYCLES for every component at every pixel centre of
-    // the primitive's tile rectangle (the compositing kernels then skip the phase reduction)
-    const float ax = fmaxf(fabsf(FA((float)(TILE * b.x0), 0.5f) - b.mux), fabsf(FA((float)(TILE * b.x1), TILE - 0.5f) - b.mux));
-    const float ay = fmaxf(fabsf(FA((float)(TILE * b.y0), 0.5f) - b.muy), fabsf(FA((float)(TILE * b.y1), TILE - 0.5f) - b.muy));
-    float bound = 0.f;
-#pragma unroll
-    for (int i = 0; i < K; ++i) bound = fmaxf(bound, fabsf(rec[12 + 2 * i]) * ax + fabsf(rec[12 + 2 * i + 1]) * ay);
-    rec[11] = bound <= FAST_PHASE_CYCLES ? 1.f : 0.f;
   }
   rec[6] = 1.f - wsum;
   float4* dst = reinterpret_cast<float4*>(p.records + (size_t)row * rec_floats(K));

@@ -15,39 +15,50 @@ constexpr float LOG2E = 1.4426950408889634f;
 constexpr float TWO_PI = 6.283185307179586f;
 constexpr float INV_TWO_PI = 0.15915494309189535f;
 
-// Shared-memory record (floats): {mu_x, mu_y, A', B'}, {C', thr, o, 1 - sum w}, {r, g, b, fast},
-// {2 pi f2D_0x, 2 pi f2D_0y, ...}, {w_0 ...}; A' = -a/2 log2 e, B' = -b log2 e, C' = -c/2 log2 e so
-// that G = 2^(A' dx^2 + B' dx dy + C' dy^2); thr = log2(alpha_min / o): o G < alpha_min <=>
-// power < thr, and since the filter bank is <= 1 (weights >= 0) such pairs have alpha < alpha_min:
-// skipped early.  fast (set by the record kernel) = 1 when every |f2D_i . d| over the primitive's
-// tile rectangle is within FAST_PHASE_CYCLES, so the phase needs no range reduction; the forward
-// and the backward read the same flag, so both evaluate the bank the same way.
+// Shared-memory record (floats), staged by a warp for its footprint: {mu_x, mu_y, A', B'},
+// {C', thr, o, 1 - sum w}, {r, g, b, fast}, {2 pi f2D_0x, 2 pi f2D_0y, ...}, {w_0 ...};
+// A' = -a/2 log2 e, B' = -b log2 e, C' = -c/2 log2 e so that G = 2^(A' dx^2 + B' dx dy + C' dy^2);
+// thr = log2(alpha_min / o): o G < alpha_min <=> power < thr, and since the filter bank is <= 1
+// (weights >= 0) such pairs have alpha < alpha_min: skipped early.  fast = 1 when every
+// |f2D_i . (x - mu)| over the pixel centres x of the footprint is within FAST_PHASE_CYCLES, so the
+// phase needs no range reduction; the forward and the backward stage the same footprints, so both
+// evaluate the bank the same way.
 template <int K>
 struct SRec {
   static constexpr int F = rec_floats(K);
   static constexpr int F4 = F / 4;
 };
+// Largest |phase| (cycles) taken by cos / sin without range reduction: the hardware approximation's
+// error grows with the argument (measured on the B300: about 4e-7 within half a cycle, 1.3e-6
+// within two cycles).
+constexpr float FAST_PHASE_CYCLES = 2.0f;
 
-// The f2D values are scaled by 2 pi one float4 at a time, so little is live while the pixel state is.
+// Stages one global record for a footprint whose pixel centres span [lo.x, hi.x] x [lo.y, hi.y]:
+// the f2D values are scaled by 2 pi, and the footprint's fast flag replaces slot 11.
 template <int K>
-__device__ __forceinline__ void stage_record(const float* __restrict__ rec, float4* dst, float alpha_min) {
+__device__ __forceinline__ void stage_record(const float* __restrict__ rec, float4* dst, float alpha_min, float2 lo,
+                                             float2 hi) {
   const float4* src = reinterpret_cast<const float4*>(rec);
   const float4 h0 = __ldg(src), h1 = __ldg(src + 1), h2 = __ldg(src + 2);
   const float o = h1.y;
   dst[0] = make_float4(h0.x, h0.y, -0.5f * LOG2E * h0.z, -LOG2E * h0.w);
   dst[1] = make_float4(-0.5f * LOG2E * h1.x, o > 0.f ? log2f(alpha_min / o) : 3.0e38f, o, h1.z);
-  dst[2] = h2;
+  const float ax = fmaxf(fabsf(lo.x - h0.x), fabsf(hi.x - h0.x)), ay = fmaxf(fabsf(lo.y - h0.y), fabsf(hi.y - h0.y));
+  float bound = 0.f;   // the largest |f2D_i . (x - mu)| over the footprint, in cycles
 #pragma unroll
   for (int i = 0; i < SRec<K>::F4 - 3; ++i) {
     float4 t = __ldg(src + 3 + i);
     // floats 0 .. 2K - 1 after the colour are f2D (scaled); the weights follow (for odd K in the
     // same float4 as the last component)
+    if (4 * i + 1 < 2 * K) bound = fmaxf(bound, fabsf(t.x) * ax + fabsf(t.y) * ay);
+    if (4 * i + 3 < 2 * K) bound = fmaxf(bound, fabsf(t.z) * ax + fabsf(t.w) * ay);
     if (4 * i + 0 < 2 * K) t.x = __fmul_rn(TWO_PI, t.x);
     if (4 * i + 1 < 2 * K) t.y = __fmul_rn(TWO_PI, t.y);
     if (4 * i + 2 < 2 * K) t.z = __fmul_rn(TWO_PI, t.z);
     if (4 * i + 3 < 2 * K) t.w = __fmul_rn(TWO_PI, t.w);
     dst[3 + i] = t;
   }
+  dst[2] = make_float4(h2.x, h2.y, h2.z, bound <= FAST_PHASE_CYCLES ? 1.f : 0.f);
 }
 
 // Frequency features of one record: sum_i w_i |f2D_i|, sum_i w_i |f2D_i,x|, sum_i w_i |f2D_i,y|.
@@ -220,6 +231,20 @@ __device__ __forceinline__ int2 thread_pixel(int tx, int ty, int tid) {
 #endif
 }
 
+// Pixel-centre bounds (lo and hi corners) of the warp footprint holding lane `lane`, whose first
+// pixel centre is (fpx, fpy0) (thread_pixel's layout).
+template <int PPT>
+__device__ __forceinline__ void footprint_bounds(float fpx, float fpy0, int lane, float2& lo, float2& hi) {
+#if GS_WARP_SQUARE
+  constexpr int FW = 8, FH = 4 * PPT;
+  lo = make_float2(fpx - (float)(lane & 7), fpy0 - (float)((lane >> 3) * PPT));
+#else
+  constexpr int FW = TILE, FH = 2 * PPT;
+  lo = make_float2(fpx - (float)(lane & 15), fpy0 - (float)((lane >> 4) * PPT));
+#endif
+  hi = make_float2(lo.x + (float)(FW - 1), lo.y + (float)(FH - 1));
+}
+
 // The forward with independent warps.  A task is one warp footprint (8x8 pixels at PPT = 2) of one
 // tile, tiles in the order of tile_order (longest pair lists first).  A warp stages the tile's
 // pairs into its own shared-memory rows one 32-position word of the sorted list at a time (the
@@ -282,8 +307,14 @@ __global__ void GS_FWD_BOUNDS k_render_fwd_w(WsPtrs p, float* out_rgb, float* ou
       const int cnt = (int)(end - start);
       if (lane < cnt) {
         const float* rec = p.records + (size_t)(u32)pairs[start + (u32)lane] * rec_floats(K);
-        stage_record<K>(rec, s_rec + lane * F4, amin);
-        if (FMAP) s_rec[lane * F4 + 2] = frequency_features<K>(rec);
+        float2 flo, fhi;
+        footprint_bounds<PPT>(fpx, fpy0, lane, flo, fhi);
+        stage_record<K>(rec, s_rec + lane * F4, amin, flo, fhi);
+        if (FMAP) {   // the frequency features take the colour's place; the fast flag stays
+          float4 ff = frequency_features<K>(rec);
+          ff.w = s_rec[lane * F4 + 2].w;
+          s_rec[lane * F4 + 2] = ff;
+        }
       }
       __syncwarp();
       u32 lbits = 0;
@@ -782,7 +813,9 @@ __global__ void GS_BWD_BOUNDS k_render_bwd_w(WsPtrs p, const float* __restrict__
         const u32 id = (u32)pairs[pos];
         s_id[lane] = id;
         s_pos[lane] = pos - lo;   // 0-based position in the tile list
-        stage_record<K>(p.records + (size_t)id * rec_floats(K), s_rec + lane * F4, amin);
+        float2 flo, fhi;
+        footprint_bounds<PPT>(fpx, fpy0, lane, flo, fhi);
+        stage_record<K>(p.records + (size_t)id * rec_floats(K), s_rec + lane * F4, amin, flo, fhi);
       }
       wk_top -= nw;
       __syncwarp();

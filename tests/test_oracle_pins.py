@@ -896,3 +896,53 @@ def test_z_attenuation_variant_render_brute_force():
     proj = O.project(O._to_f64(prims), cam, cfg)
     c2 = (proj["cos_weights"] / proj["weights"]).detach().numpy()
     assert np.all(c2 <= 1.0) and c2.min() < 0.9
+
+
+def _fma32(a, b, c):
+    """float32 fused multiply-add: the float32 product is exact in float64, so one float64 sum then
+    one rounding to float32 (a double rounding differs from a single one only at float64 ties)."""
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(np.float32)
+
+
+def test_phase_rounding_bound_covers_a_float32_evaluation():
+    """phase_rounding_bound against a float32 emulation of the compositing kernels' phase:
+    d = x - mu, F = 2 pi f, theta = F_x d_x + F_y d_y (a product and a fused sum), and in a block
+    (8 x 8 pixels) where some |f . (x - mu)| can exceed 2 cycles, theta reduced by whole cycles
+    (t = theta / (2 pi), 2 pi (t - rint t)).  The float32 angle stays within the bound of the exact
+    phase 2 pi f . (x - mu) of the same float32 inputs (modulo 2 pi), over means up to 600 pixels
+    away and frequencies up to about 1 cycle per pixel (both paths taken)."""
+    f32 = np.float32
+    rng = np.random.default_rng(11)
+    two_pi, inv_two_pi = f32(2 * np.pi), f32(1 / (2 * np.pi))
+    n_slow = n_fast = 0
+    ratio = 0.0
+    for trial in range(40):
+        L = 64
+        mu = (rng.uniform(-600, 600, (L, 2)) * rng.choice([0.01, 0.1, 1.0], (L, 1)) + 40).astype(f32)
+        f = (rng.standard_normal((L, 1, 2)) * rng.choice([0.01, 0.1, 0.3], (L, 1, 1))).astype(f32)
+        tx, ty = rng.integers(0, 6, 2)
+        xs, ys = np.meshgrid(np.arange(16 * tx, 16 * tx + 16), np.arange(16 * ty, 16 * ty + 16))
+        px, py = xs.reshape(-1) + 0.5, ys.reshape(-1) + 0.5
+        bound = O.phase_rounding_bound(torch.tensor(px), torch.tensor(py), torch.tensor(mu, dtype=torch.float64),
+                                       torch.tensor(f, dtype=torch.float64)).numpy()[:, :, 0]
+        fx, fy = f[None, :, 0, 0], f[None, :, 0, 1]
+        dx = (px.astype(f32)[:, None] - mu[None, :, 0]).astype(f32)
+        dy = (py.astype(f32)[:, None] - mu[None, :, 1]).astype(f32)
+        Fx, Fy = (two_pi * fx).astype(f32), (two_pi * fy).astype(f32)
+        theta = _fma32(np.broadcast_to(Fx, dx.shape), dx, (Fy * dy).astype(f32))
+        # the block's range-reduction decision, from float32 bounds of |f . (x - mu)| over its pixels
+        x0, y0 = (8 * np.floor(px / 8) + 0.5).astype(f32), (8 * np.floor(py / 8) + 0.5).astype(f32)
+        ax = np.maximum(np.abs(x0[:, None] - mu[None, :, 0]), np.abs(x0[:, None] + f32(7) - mu[None, :, 0]))
+        ay = np.maximum(np.abs(y0[:, None] - mu[None, :, 1]), np.abs(y0[:, None] + f32(7) - mu[None, :, 1]))
+        slow = (np.abs(fx) * ax + np.abs(fy) * ay).astype(f32) > f32(2.0)
+        t = (theta * inv_two_pi).astype(f32)
+        theta = np.where(slow, (two_pi * (t - np.rint(t)).astype(f32)).astype(f32), theta)
+        n_slow += int(slow.sum())
+        n_fast += int((~slow).sum())
+        exact = 2 * np.pi * (fx.astype(np.float64) * (px[:, None] - mu[None, :, 0]) +
+                             fy.astype(np.float64) * (py[:, None] - mu[None, :, 1]))
+        d = np.abs(np.angle(np.exp(1j * (theta.astype(np.float64) - exact))))
+        assert (d <= bound).all(), float((d / bound).max())
+        ratio = max(ratio, float((d / bound).max()))
+    assert n_slow > 1000 and n_fast > 1000
+    assert ratio > 0.2   # the bound is not vacuous
