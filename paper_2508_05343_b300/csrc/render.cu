@@ -414,7 +414,9 @@ __global__ void GS_FWD_BOUNDS k_render_fwd_w(WsPtrs p, float* out_rgb, float* ou
             }
           }
         };
-        if (any) {
+        // with the composited-pair bits every lane walks the whole word, so the branch can be a
+        // warp vote: the lanes without a reached pixel run the same instructions and keep nothing
+        if (MASKS ? __any_sync(0xffffffffu, any) : any) {
           if (fast)
             pixels(std::true_type{});
           else
