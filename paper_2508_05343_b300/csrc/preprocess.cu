@@ -850,30 +850,18 @@ __global__ void __launch_bounds__(BLOCK, GS_PBWD_MIN_CTAS) k_preprocess_bwd(WsPt
     const u32 gi = p.active[ia];
     const u32 row = p.rank_of[gi];   // grad2d rows are depth ranks
     const int k = (int)(gi - V.prim_base);
-    const bool active = true;
     float g2[g2d_floats(K)];
-    if (active) {
+    {
       const float4* src = reinterpret_cast<const float4*>(p.grad2d + (size_t)row * g2d_floats(K));
 #pragma unroll
       for (int i = 0; i < g2d_floats(K) / 4; ++i) {
         const float4 t = src[i];
         g2[4 * i] = t.x; g2[4 * i + 1] = t.y; g2[4 * i + 2] = t.z; g2[4 * i + 3] = t.w;
       }
-    } else {
-#pragma unroll
-      for (int i = 0; i < g2d_floats(K); ++i) g2[i] = 0.f;
     }
     float gmean[3] = {0.f, 0.f, 0.f}, gscale[3] = {0.f, 0.f, 0.f}, gquat[4] = {0.f, 0.f, 0.f, 0.f};
     if (G.opacity) G.opacity[k] = g2[5];
     if (G.means2d) store_row<2>(G.means2d, k, g2);
-    if (!active) {
-      if (G.means) for (int i = 0; i < 3; ++i) G.means[3 * (size_t)k + i] = 0.f;
-      if (G.scales) for (int i = 0; i < 3; ++i) G.scales[3 * (size_t)k + i] = 0.f;
-      if (G.quats) for (int i = 0; i < 4; ++i) G.quats[4 * (size_t)k + i] = 0.f;
-      if (G.sh) for (int i = 0; i < nsh * 3; ++i) G.sh[(size_t)k * nsh * 3 + i] = 0.f;
-      if (K > 0 && G.freqs) for (int i = 0; i < 3 * K; ++i) G.freqs[(size_t)k * 3 * K + i] = 0.f;
-      continue;
-    }
     const float mx = __ldg(V.means + 3 * (size_t)k), my = __ldg(V.means + 3 * (size_t)k + 1),
                 mz = __ldg(V.means + 3 * (size_t)k + 2);
     const float s[3] = {__ldg(V.scales + 3 * (size_t)k), __ldg(V.scales + 3 * (size_t)k + 1),
