@@ -11,6 +11,21 @@
 
 namespace gs {
 
+// Unroll factors of the pair loops: consecutive pairs' independent arithmetic (phases, cosines,
+// exponentials) can then overlap the previous pair's blend.  Measured at 1.5M primitives,
+// 1600x1064: forward 4 at 8 CTAs per SM 0.459 ms (1: 0.493 at 9 CTAs, 8: 0.468, 32: 0.989, the
+// instruction cache overflowing); backward 2 at 6 CTAs per SM 0.732 ms (1: 0.742 at 7 CTAs; 2 at 7
+// CTAs: 0.748; 4: 0.796).
+#ifndef GS_FWD_UNROLL
+#define GS_FWD_UNROLL 4
+#endif
+constexpr int FWD_UNROLL = GS_FWD_UNROLL;
+// Unroll factor of the backward's pair loop.
+#ifndef GS_BWD_UNROLL
+#define GS_BWD_UNROLL 2
+#endif
+constexpr int BWD_UNROLL = GS_BWD_UNROLL;
+
 constexpr float LOG2E = 1.4426950408889634f;
 constexpr float TWO_PI = 6.283185307179586f;
 constexpr float INV_TWO_PI = 0.15915494309189535f;
@@ -180,19 +195,19 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 #define GS_WARP_SQUARE 1
 #endif
 
-// Resident CTAs per SM the compositing kernels are compiled for (0: the compiler's choice).  At
-// K = 4 the backward's warp walk with the two-pixel packed adjoint takes 95 registers (5 CTAs of
-// 128 threads per SM) on its own; held to 72 for 7 CTAs per SM it spills 24 bytes and runs 2%
-// faster (0.750 against 0.767 ms at 1.5M primitives, 1600x1064; 6 CTAs: 0.760).  The packed
-// adjoint holds both pixels' cosines and sines, so above GS_BWD_PACKED_MAX_K components it would
-// spill heavily under such a cap: those K keep the per-pixel adjoint at 4 CTAs per SM.  The
-// forward's training variant, left to itself, takes 48 registers with a 16-byte spill; at 9 CTAs
-// per SM (56 registers, no spill) it is 0.7% faster.
+// Resident CTAs per SM the compositing kernels are compiled for (0: the compiler's choice).  With
+// the pair loops unrolled (above), the backward's warp walk with the two-pixel packed adjoint runs
+// at 6 CTAs of 128 threads per SM (80 registers, a 4-byte spill) and the forward at 8 (64
+// registers, no spill).  Without the unroll the backward measured 0.750 ms at 7 CTAs (72
+// registers), 0.760 at 6 and 0.767 at 5; the forward 0.503 at 9 (56 registers) and 0.507 at the
+// compiler's own 48 registers.  The packed adjoint holds both pixels' cosines and sines, so above
+// GS_BWD_PACKED_MAX_K components it would spill heavily under such a cap: those K keep the
+// per-pixel adjoint at 4 CTAs per SM.
 #ifndef GS_FWD_MIN_CTAS
-#define GS_FWD_MIN_CTAS 9
+#define GS_FWD_MIN_CTAS 8
 #endif
 #ifndef GS_BWD_MIN_CTAS
-#define GS_BWD_MIN_CTAS 7
+#define GS_BWD_MIN_CTAS 6
 #endif
 #ifndef GS_BWD_PACKED_MAX_K
 #define GS_BWD_PACKED_MAX_K 4
@@ -318,6 +333,7 @@ __global__ void GS_FWD_BOUNDS k_render_fwd_w(WsPtrs p, float* out_rgb, float* ou
       }
       __syncwarp();
       u32 lbits = 0;
+#pragma unroll FWD_UNROLL
       for (int j = 0; j < cnt; ++j) {
         if (!MASKS && tdone) break;   // with the bits every lane walks the word to its end
         const float4* r = s_rec + j * F4;
@@ -712,6 +728,7 @@ __global__ void GS_BWD_BOUNDS k_render_bwd_w(WsPtrs p, const float* __restrict__
   constexpr int NV = 10 + 3 * K;         // gradient values per pair
   constexpr int NG = g2d_floats(K);      // padded row in global memory
   constexpr int NVP = (NV + 31) / 32 * 32;
+  constexpr int BWD_UNR = K <= GS_BWD_PACKED_MAX_K ? BWD_UNROLL : 1;   // the per-pixel adjoint: no unroll
   extern __shared__ __align__(16) float4 smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float4* s_rec = smem4 + warp * 32 * F4;                                              // [32][F4]
@@ -821,6 +838,7 @@ __global__ void GS_BWD_BOUNDS k_render_bwd_w(WsPtrs p, const float* __restrict__
       }
       wk_top -= nw;
       __syncwarp();
+#pragma unroll BWD_UNR
       for (int sl = 0; sl < total; ++sl) {   // descending positions
         const float4* r = s_rec + sl * F4;
         const bool fast = reinterpret_cast<const float*>(r)[11] != 0.f;   // the same for every lane
