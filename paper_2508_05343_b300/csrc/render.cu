@@ -201,16 +201,23 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 // registers, no spill).  Without the unroll the backward measured 0.750 ms at 7 CTAs (72
 // registers), 0.760 at 6 and 0.767 at 5; the forward 0.503 at 9 (56 registers) and 0.507 at the
 // compiler's own 48 registers.  The packed adjoint holds both pixels' cosines and sines, so above
-// GS_BWD_PACKED_MAX_K components it would spill heavily under such a cap: those K keep the
-// per-pixel adjoint at 4 CTAs per SM.
+// K = 4 it runs at GS_BWD_MIN_CTAS_HIGHK (K = 8: 96 registers, a 16-byte spill at 5 CTAs per SM;
+// render_bwd 1.280 ms at 3M primitives, 1920x1080, against 1.338 at 4 CTAs and 1.487 for the
+// per-pixel adjoint, which K above GS_BWD_PACKED_MAX_K and PPT other than 2 use, at 4 CTAs).
 #ifndef GS_FWD_MIN_CTAS
 #define GS_FWD_MIN_CTAS 8
 #endif
 #ifndef GS_BWD_MIN_CTAS
 #define GS_BWD_MIN_CTAS 6
 #endif
+#ifndef GS_BWD_MIN_CTAS_HIGHK
+#define GS_BWD_MIN_CTAS_HIGHK 5   // the packed adjoint above K = 4
+#endif
+#ifndef GS_BWD_UNROLL_HIGHK
+#define GS_BWD_UNROLL_HIGHK 2
+#endif
 #ifndef GS_BWD_PACKED_MAX_K
-#define GS_BWD_PACKED_MAX_K 4
+#define GS_BWD_PACKED_MAX_K 8
 #endif
 #if GS_FWD_MIN_CTAS
 #define GS_FWD_BOUNDS __launch_bounds__(BLOCK / PPT, GS_FWD_MIN_CTAS)
@@ -218,7 +225,8 @@ static_assert(GS_PPT_FWD == GS_PPT_BWD, "the backward reads the forward's per-wa
 #define GS_FWD_BOUNDS __launch_bounds__(BLOCK / PPT)
 #endif
 #if GS_BWD_MIN_CTAS
-#define GS_BWD_BOUNDS __launch_bounds__(BLOCK / PPT, K <= GS_BWD_PACKED_MAX_K ? GS_BWD_MIN_CTAS : 4)
+#define GS_BWD_BOUNDS \
+  __launch_bounds__(BLOCK / PPT, K <= 4 ? GS_BWD_MIN_CTAS : K <= GS_BWD_PACKED_MAX_K ? GS_BWD_MIN_CTAS_HIGHK : 4)
 #else
 #define GS_BWD_BOUNDS __launch_bounds__(BLOCK / PPT)
 #endif
@@ -728,7 +736,8 @@ __global__ void GS_BWD_BOUNDS k_render_bwd_w(WsPtrs p, const float* __restrict__
   constexpr int NV = 10 + 3 * K;         // gradient values per pair
   constexpr int NG = g2d_floats(K);      // padded row in global memory
   constexpr int NVP = (NV + 31) / 32 * 32;
-  constexpr int BWD_UNR = K <= GS_BWD_PACKED_MAX_K ? BWD_UNROLL : 1;   // the per-pixel adjoint: no unroll
+  // the packed adjoint's unroll (K > 4: its own factor); the per-pixel adjoint: no unroll
+  constexpr int BWD_UNR = K <= 4 ? BWD_UNROLL : K <= GS_BWD_PACKED_MAX_K ? GS_BWD_UNROLL_HIGHK : 1;
   extern __shared__ __align__(16) float4 smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float4* s_rec = smem4 + warp * 32 * F4;                                              // [32][F4]

@@ -641,8 +641,8 @@ def test_full_size_training_view_sampled(K, storage):
     """1.5M primitives at 1600x1064 in the benchmark's launch configuration: bins bit-exact against
     the oracle's binning, images on a seeded sample of tiles (incl. the longest list) against the
     oracle, and gradients of the primitives in those tiles for a loss restricted to them.  K = 8
-    runs the per-pixel adjoint (above the packed two-pixel adjoint's K <= 4), storage 1 the BF16
-    SH / frequency / weight path (the oracle consumes the same rounded values).  The binning does
+    runs the packed adjoint at its own occupancy (5 CTAs per SM against 6 up to K = 4), storage 1
+    the BF16 SH / frequency / weight path (the oracle consumes the same rounded values).  The binning does
     not depend on K or on the storage, so the oracle bins once."""
     prims, cam = scenes.config_scene(2, K=K), scenes.config_cameras(2)[0]
     if storage == 1:
